@@ -1,0 +1,198 @@
+"""Seeded synthetic graphs shaped like the paper's workloads (Section 5 uses
+undirected SNAP/KONECT graphs; those are not available, so Erdos-Renyi, R-MAT
+and Chung-Lu graphs stand in for them).
+
+This package produces inputs only and holds none of the Katz arithmetic: the
+CPU oracle and the CUDA path both consume its CSR graphs.  Every graph is
+undirected, stored as a symmetric CSR (int64 ``rowptr``, int32 ``col``) with
+sorted rows, no self-loops and no duplicate arcs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen.c")
+_LIB = os.path.join(_HERE, "libgraphgen.so")
+_lock = threading.Lock()
+_lib = None
+
+# Seeds: one per workload, derived from the paper's arXiv id.
+SEED_BASE = 180703847
+
+
+def build(force: bool = False) -> str:
+    """Compile ``libgraphgen.so`` next to its source (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            i64, u64, dbl = ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+            lib.gg_er.restype = P
+            lib.gg_er.argtypes = [i64, i64, u64]
+            lib.gg_rmat.restype = P
+            lib.gg_rmat.argtypes = [ctypes.c_int, i64, dbl, dbl, dbl, u64]
+            lib.gg_chung_lu.restype = P
+            lib.gg_chung_lu.argtypes = [i64, i64, dbl, dbl, u64]
+            lib.gg_from_pairs.restype = P
+            lib.gg_from_pairs.argtypes = [i64, i64, P, P]
+            lib.gg_n.restype = i64
+            lib.gg_n.argtypes = [P]
+            lib.gg_nnz.restype = i64
+            lib.gg_nnz.argtypes = [P]
+            lib.gg_copy.restype = None
+            lib.gg_copy.argtypes = [P, P, P]
+            lib.gg_free.restype = None
+            lib.gg_free.argtypes = [P]
+            lib.gg_max_threads.restype = ctypes.c_int
+            lib.gg_update_batch.restype = i64
+            lib.gg_update_batch.argtypes = [i64, P, P, i64, dbl, u64, P, P, P]
+            _lib = lib
+    return _lib
+
+
+class Graph:
+    """Undirected graph as a symmetric CSR on the host."""
+
+    def __init__(self, rowptr: np.ndarray, col: np.ndarray, name: str = ""):
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.name = name
+
+    @property
+    def n(self) -> int:
+        return int(self.rowptr.shape[0] - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.rowptr)
+
+    def deg_max(self) -> int:
+        return int(self.degrees().max()) if self.n else 0
+
+    def __repr__(self) -> str:
+        return f"Graph({self.name!r}, n={self.n}, nnz={self.nnz})"
+
+
+def _take(ptr, name: str) -> Graph:
+    lib = _load()
+    if not ptr:
+        raise MemoryError(f"graph generator failed for {name}")
+    try:
+        n, nnz = lib.gg_n(ptr), lib.gg_nnz(ptr)
+        rowptr = np.empty(n + 1, dtype=np.int64)
+        col = np.empty(max(nnz, 1), dtype=np.int32)
+        lib.gg_copy(ptr, rowptr.ctypes.data, col.ctypes.data)
+    finally:
+        lib.gg_free(ptr)
+    return Graph(rowptr, col[:nnz], name)
+
+
+def erdos_renyi(n: int, m: int, seed: int) -> Graph:
+    """G(n, m): m distinct uniform undirected edges, no self-loops."""
+    return _take(_load().gg_er(n, m, seed), f"er_n{n}_m{m}_s{seed}")
+
+
+def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+         seed: int = SEED_BASE) -> Graph:
+    """R-MAT with 2^scale vertices and edge_factor*2^scale generated pairs,
+    symmetrised and deduplicated (no noise, no vertex permutation)."""
+    return _take(_load().gg_rmat(scale, edge_factor, a, b, c, seed), f"rmat{scale}_ef{edge_factor}_s{seed}")
+
+
+def chung_lu(n: int, mean_degree: float = 16.0, exponent: float = 2.1, seed: int = SEED_BASE,
+             pairs: int | None = None) -> Graph:
+    """Chung-Lu graph with Pareto expected degrees (pdf exponent ``exponent``,
+    scale chosen for the requested mean before capping at sqrt(sum w))."""
+    tail = exponent - 1.0
+    x_m = mean_degree * (tail - 1.0) / tail
+    if pairs is None:
+        pairs = int(n * mean_degree // 2)
+    return _take(_load().gg_chung_lu(n, pairs, tail, x_m, seed), f"chunglu_n{n}_s{seed}")
+
+
+def from_edges(n: int, u, v, name: str = "pairs") -> Graph:
+    """Symmetric CSR of the undirected pairs (u[i], v[i]) (self-loops dropped,
+    repeats merged)."""
+    u = np.ascontiguousarray(u, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.int32)
+    assert u.shape == v.shape
+    return _take(_load().gg_from_pairs(n, u.shape[0], u.ctypes.data, v.ctypes.data), name)
+
+
+def complete(n: int) -> Graph:
+    iu, ju = np.triu_indices(n, 1)
+    return from_edges(n, iu, ju, f"K{n}")
+
+
+def star(leaves: int) -> Graph:
+    return from_edges(leaves + 1, np.zeros(leaves, np.int32), np.arange(1, leaves + 1), f"star{leaves}")
+
+
+def path(n: int) -> Graph:
+    return from_edges(n, np.arange(n - 1), np.arange(1, n), f"path{n}")
+
+
+def cycle(n: int) -> Graph:
+    return from_edges(n, np.arange(n), (np.arange(n) + 1) % n, f"cycle{n}")
+
+
+def update_batch(g: Graph, m: int, seed: int, p_insert: float = 0.5):
+    """Draw m undirected updates against g: inserts are uniform non-edges,
+    deletes are uniform existing edges; no pair repeats within the batch.
+    Returns (src, dst, is_insert) as int32/int32/uint8 arrays."""
+    lib = _load()
+    src = np.empty(max(m, 1), np.int32)
+    dst = np.empty(max(m, 1), np.int32)
+    ins = np.empty(max(m, 1), np.uint8)
+    got = lib.gg_update_batch(g.n, g.rowptr.ctypes.data, g.col.ctypes.data, m, p_insert, seed,
+                              src.ctypes.data, dst.ctypes.data, ins.ctypes.data)
+    return src[:got], dst[:got], ins[:got]
+
+
+def apply_batch(g: Graph, src, dst, is_insert) -> Graph:
+    """The graph after an update batch (host-side, for building test inputs)."""
+    n = g.n
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.rowptr))
+    keys = rows * n + g.col.astype(np.int64)
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    ins = np.asarray(is_insert).astype(bool)
+    dele = np.concatenate([src[~ins] * n + dst[~ins], dst[~ins] * n + src[~ins]])
+    keep = keys[~np.isin(keys, dele)]
+    add = np.concatenate([src[ins] * n + dst[ins], dst[ins] * n + src[ins]])
+    allk = np.concatenate([keep, add])
+    u = (allk // n).astype(np.int32)
+    v = (allk % n).astype(np.int32)
+    sel = u < v
+    return from_edges(n, u[sel], v[sel], g.name + "+batch")
+
+
+def workload(name: str) -> Graph:
+    """The named synthetic workloads (sizes as in the measurement plan)."""
+    if name == "er16k":
+        return erdos_renyi(16384, 131072, SEED_BASE + 0)
+    if name.startswith("rmat"):
+        scale = int(name[4:])
+        return rmat(scale, 16, seed=SEED_BASE + scale)
+    if name == "chunglu27":
+        return chung_lu(1 << 27, 16.0, 2.1, SEED_BASE + 27)
+    raise KeyError(name)

@@ -1,0 +1,370 @@
+/*
+ * Seeded synthetic graph generators (Erdos-Renyi, R-MAT, Chung-Lu) and the
+ * CSR assembly they share: symmetrise, drop self-loops, sort each row and
+ * remove duplicate arcs.
+ *
+ * This module produces INPUTS only.  It holds none of the Katz arithmetic, so
+ * both the CPU oracle and the CUDA path may consume its graphs.
+ *
+ * Randomness is counter based: draw number t of stream s is
+ * splitmix64(seed ^ stream_key(s) + t * golden), the SplitMix64 output
+ * function of Steele, Lea and Flood (OOPSLA 2014).  Every edge is a pure
+ * function of (seed, edge index), so the generated multiset of arcs does not
+ * depend on the number of threads; CSR assembly sorts every row, so the final
+ * CSR is bit-identical for any thread count.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define GOLDEN 0x9E3779B97F4A7C15ULL
+
+static inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* draw t of stream `key` under `seed` */
+static inline uint64_t draw(uint64_t seed, uint64_t key, uint64_t t) {
+    return mix64(seed ^ (mix64(key) + (t + 1) * GOLDEN));
+}
+
+/* uniform double in [0,1) from the top 53 bits */
+static inline double unit(uint64_t x) { return (double)(x >> 11) * (1.0 / 9007199254740992.0); }
+
+/* uniform integer in [0, n) by 128-bit multiply-shift (Lemire) */
+static inline uint64_t below(uint64_t x, uint64_t n) {
+    return (uint64_t)(((unsigned __int128)x * n) >> 64);
+}
+
+/* ------------------------------------------------------------------------- */
+/* CSR assembly                                                               */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    int64_t *rowptr;  /* n+1 */
+    int32_t *col;     /* nnz */
+} gg_csr;
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+static void sort_row(int32_t *p, int64_t len) {
+    if (len < 24) {
+        for (int64_t i = 1; i < len; ++i) {
+            int32_t v = p[i];
+            int64_t j = i - 1;
+            while (j >= 0 && p[j] > v) { p[j + 1] = p[j]; --j; }
+            p[j + 1] = v;
+        }
+    } else {
+        qsort(p, (size_t)len, sizeof(int32_t), cmp_i32);
+    }
+}
+
+/*
+ * Build a symmetric, sorted, duplicate-free CSR from m undirected pairs
+ * (u[e], v[e]).  Pairs with u == v are skipped.  Returns NULL on allocation
+ * failure.
+ */
+static gg_csr *assemble(int64_t n, int64_t m, const int32_t *u, const int32_t *v) {
+    int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!cnt) return NULL;
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < m; ++e) {
+        if (u[e] == v[e]) continue;
+        __atomic_fetch_add(&cnt[u[e]], 1, __ATOMIC_RELAXED);
+        __atomic_fetch_add(&cnt[v[e]], 1, __ATOMIC_RELAXED);
+    }
+    int64_t *start = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    if (!start) { free(cnt); return NULL; }
+    start[0] = 0;
+    for (int64_t i = 0; i < n; ++i) start[i + 1] = start[i] + cnt[i];
+    int64_t arcs = start[n];
+    int32_t *tmp = (int32_t *)malloc((size_t)(arcs > 0 ? arcs : 1) * sizeof(int32_t));
+    if (!tmp) { free(cnt); free(start); return NULL; }
+    memcpy(cnt, start, (size_t)n * sizeof(int64_t)); /* cursors */
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < m; ++e) {
+        if (u[e] == v[e]) continue;
+        int64_t p = __atomic_fetch_add(&cnt[u[e]], 1, __ATOMIC_RELAXED);
+        tmp[p] = v[e];
+        p = __atomic_fetch_add(&cnt[v[e]], 1, __ATOMIC_RELAXED);
+        tmp[p] = u[e];
+    }
+    /* sort + dedup every row in place; cnt[i] becomes the unique length */
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t *p = tmp + start[i];
+        int64_t len = start[i + 1] - start[i];
+        sort_row(p, len);
+        int64_t w = 0;
+        for (int64_t j = 0; j < len; ++j)
+            if (w == 0 || p[j] != p[w - 1]) p[w++] = p[j];
+        cnt[i] = w;
+    }
+    gg_csr *g = (gg_csr *)malloc(sizeof(gg_csr));
+    g->n = n;
+    g->rowptr = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    g->rowptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) g->rowptr[i + 1] = g->rowptr[i] + cnt[i];
+    g->nnz = g->rowptr[n];
+    g->col = (int32_t *)malloc((size_t)(g->nnz > 0 ? g->nnz : 1) * sizeof(int32_t));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        memcpy(g->col + g->rowptr[i], tmp + start[i], (size_t)cnt[i] * sizeof(int32_t));
+    free(tmp);
+    free(start);
+    free(cnt);
+    return g;
+}
+
+/* ------------------------------------------------------------------------- */
+/* public API                                                                 */
+/* ------------------------------------------------------------------------- */
+
+int64_t gg_n(const gg_csr *g) { return g->n; }
+int64_t gg_nnz(const gg_csr *g) { return g->nnz; }
+void gg_copy(const gg_csr *g, int64_t *rowptr, int32_t *col) {
+    memcpy(rowptr, g->rowptr, ((size_t)g->n + 1) * sizeof(int64_t));
+    if (g->nnz) memcpy(col, g->col, (size_t)g->nnz * sizeof(int32_t));
+}
+void gg_free(gg_csr *g) {
+    if (!g) return;
+    free(g->rowptr);
+    free(g->col);
+    free(g);
+}
+
+int gg_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* CSR of an arbitrary pair list (used for hand-made graphs and update tests) */
+gg_csr *gg_from_pairs(int64_t n, int64_t m, const int32_t *u, const int32_t *v) {
+    return assemble(n, m, u, v);
+}
+
+/*
+ * Erdos-Renyi G(n, m): exactly m distinct undirected edges, drawn as uniform
+ * ordered pairs; self-loops and repeats are rejected and redrawn.  Sequential
+ * (the graph is small), with an open-addressing set of canonical pairs.
+ */
+gg_csr *gg_er(int64_t n, int64_t m, uint64_t seed) {
+    if (n < 2 || m < 0 || (double)m > 0.5 * (double)n * (double)(n - 1)) return NULL;
+    uint64_t cap = 1;
+    while (cap < (uint64_t)(2 * m + 16)) cap <<= 1;
+    uint64_t *set = (uint64_t *)malloc(cap * sizeof(uint64_t));
+    int32_t *u = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    int32_t *v = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    memset(set, 0xff, cap * sizeof(uint64_t));
+    uint64_t t = 0;
+    for (int64_t e = 0; e < m;) {
+        uint64_t a = below(draw(seed, 1, t), (uint64_t)n);
+        uint64_t b = below(draw(seed, 2, t), (uint64_t)n);
+        ++t;
+        if (a == b) continue;
+        uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+        uint64_t key = (lo << 32) | hi;
+        uint64_t h = mix64(key) & (cap - 1);
+        int dup = 0;
+        while (set[h] != ~0ULL) {
+            if (set[h] == key) { dup = 1; break; }
+            h = (h + 1) & (cap - 1);
+        }
+        if (dup) continue;
+        set[h] = key;
+        u[e] = (int32_t)lo;
+        v[e] = (int32_t)hi;
+        ++e;
+    }
+    gg_csr *g = assemble(n, m, u, v);
+    free(set);
+    free(u);
+    free(v);
+    return g;
+}
+
+/*
+ * R-MAT (Chakrabarti, Zhan, Faloutsos 2004): 2^scale vertices, edge_factor *
+ * 2^scale generated pairs.  Each pair descends `scale` levels of the
+ * recursive quadrant split with probabilities (a, b, c, 1-a-b-c); no noise,
+ * no vertex permutation.  The result is symmetrised and deduplicated.
+ */
+gg_csr *gg_rmat(int scale, int64_t edge_factor, double a, double b, double c, uint64_t seed) {
+    if (scale < 1 || scale > 30) return NULL;
+    int64_t n = (int64_t)1 << scale;
+    int64_t m = edge_factor * n;
+    int32_t *u = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+    int32_t *v = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+    if (!u || !v) { free(u); free(v); return NULL; }
+    const double ab = a + b, abc = a + b + c;
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < m; ++e) {
+        uint32_t s = 0, d = 0;
+        for (int l = 0; l < scale; ++l) {
+            double x = unit(draw(seed, 3, (uint64_t)e * (uint64_t)scale + (uint64_t)l));
+            uint32_t sb, db;
+            if (x < a) { sb = 0; db = 0; }
+            else if (x < ab) { sb = 0; db = 1; }
+            else if (x < abc) { sb = 1; db = 0; }
+            else { sb = 1; db = 1; }
+            s = (s << 1) | sb;
+            d = (d << 1) | db;
+        }
+        u[e] = (int32_t)s;
+        v[e] = (int32_t)d;
+    }
+    gg_csr *g = assemble(n, m, u, v);
+    free(u);
+    free(v);
+    return g;
+}
+
+/*
+ * Chung-Lu graph with Pareto expected degrees.  Weights w_i = x_m * U^(-1/tail)
+ * (pdf exponent tail+1), capped at sqrt(sum w).  `pairs` endpoint pairs are
+ * drawn, each endpoint independently proportional to w (Walker/Vose alias
+ * table), then symmetrised and deduplicated.
+ */
+gg_csr *gg_chung_lu(int64_t n, int64_t pairs, double tail, double x_m, uint64_t seed) {
+    if (n < 2 || n > 2147483647LL) return NULL;
+    double *w = (double *)malloc((size_t)n * sizeof(double));
+    double *prob = (double *)malloc((size_t)n * sizeof(double));
+    int32_t *alias = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *small = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *large = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!w || !prob || !alias || !small || !large) return NULL;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double x = unit(draw(seed, 4, (uint64_t)i));
+        w[i] = x_m * pow(1.0 - x, -1.0 / tail);
+    }
+    double sum = 0.0; /* sequential: the cap must not depend on the thread count */
+    for (int64_t i = 0; i < n; ++i) sum += w[i];
+    const double cap = sqrt(sum);
+    double csum = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (w[i] > cap) w[i] = cap;
+        csum += w[i];
+    }
+    /* Vose's alias method */
+    int64_t ns = 0, nl = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        prob[i] = w[i] * (double)n / csum;
+        if (prob[i] < 1.0) small[ns++] = (int32_t)i; else large[nl++] = (int32_t)i;
+    }
+    while (ns > 0 && nl > 0) {
+        int32_t s = small[--ns], l = large[--nl];
+        alias[s] = l;
+        prob[l] = (prob[l] + prob[s]) - 1.0;
+        if (prob[l] < 1.0) small[ns++] = l; else large[nl++] = l;
+    }
+    while (nl > 0) { int32_t l = large[--nl]; prob[l] = 1.0; alias[l] = l; }
+    while (ns > 0) { int32_t s = small[--ns]; prob[s] = 1.0; alias[s] = s; }
+    free(small);
+    free(large);
+    free(w);
+    int32_t *u = (int32_t *)malloc((size_t)pairs * sizeof(int32_t));
+    int32_t *v = (int32_t *)malloc((size_t)pairs * sizeof(int32_t));
+    if (!u || !v) return NULL;
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < pairs; ++e) {
+        int32_t ends[2];
+        for (int k = 0; k < 2; ++k) {
+            uint64_t t = (uint64_t)e * 4u + 2u * (uint64_t)k;
+            uint64_t i = below(draw(seed, 5, t), (uint64_t)n);
+            double y = unit(draw(seed, 5, t + 1));
+            ends[k] = (y < prob[i]) ? (int32_t)i : alias[i];
+        }
+        u[e] = ends[0];
+        v[e] = ends[1];
+    }
+    free(prob);
+    free(alias);
+    gg_csr *g = assemble(n, pairs, u, v);
+    free(u);
+    free(v);
+    return g;
+}
+
+/*
+ * A stream of update batches for the dynamic experiments.  Given the current
+ * graph (sorted CSR), draw `m` undirected updates: with probability
+ * p_insert a uniform non-edge {a,b} (a != b) not already used in this batch,
+ * otherwise a uniform existing edge (an arc chosen uniformly, so an edge with
+ * probability 2/nnz) not already used in this batch.  Writes src, dst,
+ * is_insert (1/0).  Returns the number written (== m unless the graph has no
+ * edges to delete).
+ */
+static int has_arc(const int64_t *rowptr, const int32_t *col, int32_t a, int32_t b) {
+    int64_t lo = rowptr[a], hi = rowptr[a + 1];
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < b) lo = mid + 1; else hi = mid;
+    }
+    return lo < rowptr[a + 1] && col[lo] == b;
+}
+
+int64_t gg_update_batch(int64_t n, const int64_t *rowptr, const int32_t *col, int64_t m,
+                        double p_insert, uint64_t seed, int32_t *src, int32_t *dst, uint8_t *is_insert) {
+    int64_t nnz = rowptr[n];
+    uint64_t cap = 1;
+    while (cap < (uint64_t)(4 * m + 16)) cap <<= 1;
+    uint64_t *set = (uint64_t *)malloc(cap * sizeof(uint64_t));
+    memset(set, 0xff, cap * sizeof(uint64_t));
+    uint64_t t = 0;
+    int64_t e = 0;
+    int64_t guard = 0;
+    while (e < m && guard < 1000 * (m + 10)) {
+        ++guard;
+        int ins = unit(draw(seed, 6, t)) < p_insert;
+        uint64_t a, b;
+        if (ins) {
+            a = below(draw(seed, 7, t), (uint64_t)n);
+            b = below(draw(seed, 8, t), (uint64_t)n);
+            ++t;
+            if (a == b || has_arc(rowptr, col, (int32_t)a, (int32_t)b)) continue;
+        } else {
+            ++t;
+            if (nnz == 0) continue;
+            uint64_t arc = below(draw(seed, 9, t), (uint64_t)nnz);
+            int64_t lo = 0, hi = n; /* row containing arc: last i with rowptr[i] <= arc */
+            while (hi - lo > 1) {
+                int64_t mid = (lo + hi) >> 1;
+                if ((uint64_t)rowptr[mid] <= arc) lo = mid; else hi = mid;
+            }
+            a = (uint64_t)lo;
+            b = (uint64_t)col[arc];
+        }
+        uint64_t lo_ = a < b ? a : b, hi_ = a < b ? b : a;
+        uint64_t key = (lo_ << 32) | hi_;
+        uint64_t h = mix64(key) & (cap - 1);
+        int dup = 0;
+        while (set[h] != ~0ULL) {
+            if (set[h] == key) { dup = 1; break; }
+            h = (h + 1) & (cap - 1);
+        }
+        if (dup) continue;
+        set[h] = key;
+        src[e] = (int32_t)a;
+        dst[e] = (int32_t)b;
+        is_insert[e] = (uint8_t)ins;
+        ++e;
+    }
+    free(set);
+    return e;
+}
