@@ -1,0 +1,188 @@
+/*
+ * katz.h - C ABI of the GB300 (sm_103a) certified Katz ranking library.
+ *
+ * Method: van der Grinten, Bergamini, Green, Bader, Meyerhenke, "Scalable
+ * Katz Ranking Computation in Large Static and Dynamic Graphs" (ESA 2018).
+ *
+ *   Katz centrality (Eq. 1): c(v) = sum_{i>=1} alpha^i omega_i(v), omega_i(v)
+ *   the number of walks of length i that start at v.  The library never
+ *   forms c exactly; it iterates the walk recurrence of Eq. (4),
+ *   omega_i(v) = sum_{v->x} omega_{i-1}(x), and keeps per-node bounds
+ *   l_r(v) <= c(v) <= u_r(v) (Sec. 3.1, Theorem 1) until the top-k
+ *   criterion holds: the k nodes with the highest lower bounds are
+ *   eps-separated (Eq. 3) from each other and from every other node
+ *   (Algorithm 1 with its converged() procedure).
+ *
+ * Internally the walk vectors are stored scaled, s_i = alpha^i omega_i, so
+ * that they stay in [0, 1] when alpha * deg_max < 1.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a katz_status; KATZ_OK is 0.  No function
+ *     throws or aborts.  On failure the handle is left as it was before the
+ *     call (an update batch is applied completely or not at all) and
+ *     katz_last_error() describes the failure.
+ *   - Pointers are plain host or device addresses; the library tells them
+ *     apart with CUDA unified addressing unless a flag says otherwise.
+ *     Output buffers are owned by the caller and must hold the stated
+ *     number of elements.  Input arrays are read during the call only; the
+ *     library keeps its own device copies.
+ *   - Node ids are int32 in [0, n).  Graph arrays are CSR: rowptr (int64,
+ *     n+1 entries, rowptr[0] = 0, non-decreasing) and col (int32, nnz =
+ *     rowptr[n] entries).  An undirected graph is passed as its symmetric
+ *     CSR (each edge as two arcs; Sec. 2.1).
+ *   - A handle is used by one host thread at a time.  All device work is
+ *     ordered on the handle's CUDA stream (katz_opts.cuda_stream, or a
+ *     stream the library creates).
+ */
+#ifndef KATZ_H_
+#define KATZ_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct katz_handle* katz_h;
+
+typedef enum {
+    KATZ_OK = 0,
+    KATZ_EINVAL = 1,      /* bad argument, malformed graph or batch */
+    KATZ_EALPHA = 2,      /* alpha * deg_bound >= 1 (Theorem 1 needs alpha < 1/deg_max) */
+    KATZ_ENOMEM = 3,      /* device or pinned host allocation failed */
+    KATZ_ECUDA = 4,       /* a CUDA runtime call failed */
+    KATZ_ENOTCONV = 5,    /* r_max iterations ran without meeting the criterion */
+    KATZ_EPRECISION = 6,  /* FP32-certified mode cannot separate the remaining pairs */
+    KATZ_ETIMEOUT = 7,    /* a bounded wait expired */
+    KATZ_EBUSY = 8,       /* no free slot / request still running */
+    KATZ_ESTATE = 9       /* call not valid in the handle's state (e.g. no ranking yet) */
+} katz_status;
+
+/* Arithmetic of the walk vectors. */
+enum {
+    KATZ_FP64 = 0,        /* s_i in FP64, as the paper (which implies FP64) */
+    KATZ_FP32_CERT = 1    /* s_i in FP32, bounds widened by a rigorous rounding term */
+};
+
+typedef struct {
+    int32_t precision;     /* KATZ_FP64 (default) or KATZ_FP32_CERT */
+    int32_t undirected;    /* 1 (default): the CSR is symmetric; use the undirected lower
+                              bound l_r = c_r + alpha^{r+1} omega_r (Sec. 3.1) */
+    int32_t keep_history;  /* 1: keep s_1..s_r (needed by katz_apply_update_batch and
+                              katz_get_walk for i < r-1); 0 (default): two live levels */
+    int32_t r_max;         /* iteration cap, default 128 */
+    int64_t deg_bound;     /* D >= deg_max used in gamma = D/(1 - alpha D); 0 (default):
+                              deg_max of the input graph */
+    double frontier_abort_frac; /* dynamic update: fall back to a full level when the
+                              affected set exceeds this fraction of n (Sec. 4; default 0.05) */
+    void* cuda_stream;     /* cudaStream_t to run on; NULL: the library creates one */
+    int32_t use_graph;     /* 1 (default): run the iteration as a CUDA graph with a
+                              device-side while loop; 0: host-driven loop */
+    int32_t slack;         /* dynamic handles: spare arcs reserved per row (default 0) */
+    int32_t profile;       /* 1: time every walk-count SpMV launch with CUDA events on the
+                              handle's stream (katz_info.spmv_ms); forces the host-driven loop */
+    int32_t reserved;
+} katz_opts;
+
+typedef struct {
+    int32_t r;             /* iterations performed (walk length reached) */
+    int32_t converged;     /* 1 if the top-k criterion holds at r */
+    int64_t active;        /* |M| after the last convergence check */
+    int64_t k;             /* effective k = min(k, n) */
+    double alpha;          /* attenuation used */
+    double gamma;          /* D / (1 - alpha D) */
+    double time_ms;        /* device time of the call (CUDA events) */
+    int64_t nnz;           /* arcs the walk recurrence visited per iteration */
+    int32_t fp32_levels;   /* FP32-certified mode: levels carried in FP32 */
+    int32_t full_levels;   /* dynamic update: levels recomputed for every node */
+    int64_t affected;      /* dynamic update: nodes whose walk counts were recomputed */
+    double spmv_ms;        /* profile = 1: summed device time of the SpMV launches */
+    int64_t launches;      /* kernels this call launched */
+    int32_t spmv_launches; /* SpMV launches this call made */
+    int32_t reserved;
+} katz_info;
+
+/* Fill *opts with the defaults listed above. */
+void katz_default_opts(katz_opts* opts);
+
+/* Human-readable name of a status code (static string). */
+const char* katz_status_string(katz_status s);
+
+/*
+ * Create a handle for the graph (n, rowptr, col) and copy it to device
+ * memory the library owns.  rowptr/col may be host or device pointers.
+ * Validates rowptr (monotone, rowptr[0] = 0, rowptr[n] = nnz) and every
+ * col entry in [0, n); self-loops are accepted (a self-loop is a walk of
+ * length 1).  opts may be NULL for the defaults.
+ * Errors: KATZ_EINVAL (n < 1, nnz < 0, malformed CSR), KATZ_ENOMEM, KATZ_ECUDA.
+ */
+katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* rowptr,
+                            const int32_t* col, const katz_opts* opts);
+
+/* Release the handle and all device memory it owns (NULL is ignored). */
+void katz_destroy(katz_h h);
+
+/* Description of the last failure on this handle ("" if none). */
+const char* katz_last_error(katz_h h);
+
+/*
+ * Algorithm 1 (Sec. 3.2) with the top-k criterion (Sec. 3.1).
+ * alpha: attenuation; alpha <= 0 selects alpha = 1/(1 + D) (Sec. 3.1).
+ * k: 1 <= k; clamped to n; at most KATZ_MAX_K.
+ * eps > 0: absolute separation slack of Eq. (3).
+ * Runs iterations r = 1, 2, ... (s_r = alpha A s_{r-1}, c_r = c_{r-1} + s_r,
+ * l_r, u_r, then converged()) until the criterion holds or r_max is hit.
+ * The ranking and bounds stay in the handle (katz_get_ranking/_bounds).
+ * info may be NULL.
+ * Errors: KATZ_EINVAL, KATZ_EALPHA, KATZ_ENOTCONV (the state at r_max is
+ * still readable), KATZ_EPRECISION (FP32-certified mode), KATZ_ECUDA.
+ */
+#define KATZ_MAX_K 8192
+katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz_info* info);
+
+/*
+ * The certified top-k after the last rank/update call: ids[0..k) in
+ * decreasing order of lower bound (ties by smaller id).  k must equal the
+ * effective k of that call or be smaller (a prefix).
+ * Errors: KATZ_ESTATE (no ranking yet), KATZ_EINVAL.
+ */
+katz_status katz_get_ranking(katz_h h, int32_t* ids, int64_t k);
+
+/*
+ * Per-node bounds at the current r: lower[v] = l_r(v), upper[v] = u_r(v)
+ * (Alg. 1), each n doubles, host or device.  err (nullable): in
+ * KATZ_FP32_CERT mode the width added for rounding, per node; zeros in
+ * FP64 mode.  Any pointer may be NULL to skip it.
+ */
+katz_status katz_get_bounds(katz_h h, double* lower, double* upper, double* err);
+
+/*
+ * The scaled walk vector s_i = alpha^i omega_i (n doubles, host or device)
+ * for 1 <= i <= r; i < r-1 requires keep_history.
+ */
+katz_status katz_get_walk(katz_h h, int32_t i, double* s_out);
+
+/* Number of active nodes |M| after each iteration 1..r (cap entries). */
+katz_status katz_get_trace(katz_h h, int64_t* active_per_iter, int32_t cap);
+
+/*
+ * Algorithm 2 (Sec. 4): apply a batch of m undirected edge updates
+ * {src[e], dst[e]} (insert if is_insert[e] != 0, else delete) to the graph
+ * of a handle that has ranked with keep_history = 1, repair the stored
+ * walk vectors s_1..s_r, recompute the bounds, re-derive the active set
+ * and continue iterating until the top-k criterion holds again.
+ * Preconditions (checked, Sec. 4): inserted edges are absent, deleted
+ * edges are present, no pair appears twice in the batch, no self-loops,
+ * and no row exceeds the degree bound D afterwards.  Arrays may be host or
+ * device pointers.
+ * Errors: KATZ_EINVAL (precondition), KATZ_EALPHA (a row would exceed D),
+ * KATZ_ESTATE (no ranking / no history), KATZ_ENOMEM, KATZ_ECUDA.
+ */
+katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t* dst,
+                                    const uint8_t* is_insert, int64_t m, katz_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KATZ_H_ */

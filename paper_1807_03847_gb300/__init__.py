@@ -1,0 +1,235 @@
+"""Thin Python binding of libkatz.so (include/katz.h).
+
+Argument marshalling only: every step of the ranking runs in the CUDA
+kernels behind the C ABI.  Arrays may be numpy arrays (host) or torch
+tensors (host or CUDA); the binding passes their raw pointers.  The library
+must have been built (``build.build()``); importing fails loudly otherwise,
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "KatzError", "katz_opts", "katz_info", "katz_default_opts", "katz_create_csr", "katz_destroy",
+    "katz_rank_static", "katz_get_ranking", "katz_get_bounds", "katz_get_walk", "katz_get_trace",
+    "katz_apply_update_batch", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT",
+    "KATZ_MAX_K", "library_path",
+]
+
+KATZ_FP64, KATZ_FP32_CERT = 0, 1
+KATZ_MAX_K = 8192
+STATUS = ["KATZ_OK", "KATZ_EINVAL", "KATZ_EALPHA", "KATZ_ENOMEM", "KATZ_ECUDA", "KATZ_ENOTCONV",
+          "KATZ_EPRECISION", "KATZ_ETIMEOUT", "KATZ_EBUSY", "KATZ_ESTATE"]
+
+
+class katz_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("undirected", ctypes.c_int32), ("keep_history", ctypes.c_int32),
+                ("r_max", ctypes.c_int32), ("deg_bound", ctypes.c_int64), ("frontier_abort_frac", ctypes.c_double),
+                ("cuda_stream", ctypes.c_void_p), ("use_graph", ctypes.c_int32), ("slack", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class katz_info(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int32), ("converged", ctypes.c_int32), ("active", ctypes.c_int64),
+                ("k", ctypes.c_int64), ("alpha", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("time_ms", ctypes.c_double), ("nnz", ctypes.c_int64), ("fp32_levels", ctypes.c_int32),
+                ("full_levels", ctypes.c_int32), ("affected", ctypes.c_int64), ("spmv_ms", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("spmv_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class KatzError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{what}: {name}" + (f" ({detail})" if detail else ""))
+        self.status = status
+        self.name = name
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"{_build.LIB} is missing: build it with paper_1807_03847_gb300.build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "katz_default_opts": (None, [ctypes.POINTER(katz_opts)]),
+        "katz_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "katz_create_csr": (ctypes.c_int, [ctypes.POINTER(P), i64, i64, P, P, ctypes.POINTER(katz_opts)]),
+        "katz_destroy": (None, [P]),
+        "katz_last_error": (ctypes.c_char_p, [P]),
+        "katz_rank_static": (ctypes.c_int, [P, dbl, i64, dbl, ctypes.POINTER(katz_info)]),
+        "katz_get_ranking": (ctypes.c_int, [P, P, i64]),
+        "katz_get_bounds": (ctypes.c_int, [P, P, P, P]),
+        "katz_get_walk": (ctypes.c_int, [P, i32, P]),
+        "katz_get_trace": (ctypes.c_int, [P, P, i32]),
+        "katz_apply_update_batch": (ctypes.c_int, [P, P, P, P, i64, ctypes.POINTER(katz_info)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"expected numpy array or torch tensor, got {type(a)}")
+
+
+def _check(h, status, what):
+    if status != 0:
+        detail = _load().katz_last_error(h).decode() if h else ""
+        raise KatzError(status, what, detail)
+
+
+def katz_status_string(status: int) -> str:
+    return _load().katz_status_string(status).decode()
+
+
+def katz_default_opts(**kw) -> katz_opts:
+    o = katz_opts()
+    _load().katz_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def katz_create_csr(n: int, nnz: int, rowptr, col, opts: katz_opts | None = None) -> int:
+    """Create a handle (copies the CSR to library-owned device memory)."""
+    lib = _load()
+    h = ctypes.c_void_p()
+    st = lib.katz_create_csr(ctypes.byref(h), int(n), int(nnz), _ptr(rowptr), _ptr(col),
+                             ctypes.byref(opts) if opts is not None else None)
+    if st != 0:
+        raise KatzError(st, "katz_create_csr")
+    return h.value
+
+
+def katz_destroy(h) -> None:
+    if h:
+        _load().katz_destroy(h)
+
+
+def katz_last_error(h) -> str:
+    return _load().katz_last_error(h).decode()
+
+
+def katz_rank_static(h, alpha: float, k: int, eps: float, check: bool = True) -> katz_info:
+    info = katz_info()
+    st = _load().katz_rank_static(h, float(alpha), int(k), float(eps), ctypes.byref(info))
+    if check:
+        _check(h, st, "katz_rank_static")
+    info.status = st
+    return info
+
+
+def katz_get_ranking(h, k: int, out=None):
+    if out is None:
+        out = np.empty(int(k), np.int32)
+    _check(h, _load().katz_get_ranking(h, _ptr(out), int(k)), "katz_get_ranking")
+    return out
+
+
+def katz_get_bounds(h, n: int | None = None, lower=None, upper=None, err=None):
+    if lower is None and upper is None and err is None:
+        lower, upper, err = (np.empty(int(n), np.float64) for _ in range(3))
+    _check(h, _load().katz_get_bounds(h, _ptr(lower), _ptr(upper), _ptr(err)), "katz_get_bounds")
+    return lower, upper, err
+
+
+def katz_get_walk(h, i: int, n: int | None = None, out=None):
+    if out is None:
+        out = np.empty(int(n), np.float64)
+    _check(h, _load().katz_get_walk(h, int(i), _ptr(out)), "katz_get_walk")
+    return out
+
+
+def katz_get_trace(h, cap: int = 1024) -> np.ndarray:
+    out = np.zeros(cap, np.int64)
+    _check(h, _load().katz_get_trace(h, _ptr(out), int(cap)), "katz_get_trace")
+    return out
+
+
+def katz_apply_update_batch(h, src, dst, is_insert, m: int | None = None, check: bool = True) -> katz_info:
+    info = katz_info()
+    if m is None:
+        m = len(src)
+    st = _load().katz_apply_update_batch(h, _ptr(src), _ptr(dst), _ptr(is_insert), int(m), ctypes.byref(info))
+    if check:
+        _check(h, st, "katz_apply_update_batch")
+    info.status = st
+    return info
+
+
+class Katz:
+    """Owning wrapper around a handle (destroyed with the object)."""
+
+    def __init__(self, rowptr, col, opts: katz_opts | None = None):
+        rowptr_np = rowptr
+        n = (rowptr.shape[0] if hasattr(rowptr, "shape") else len(rowptr)) - 1
+        nnz = col.shape[0] if hasattr(col, "shape") else len(col)
+        self.n = int(n)
+        self.h = katz_create_csr(self.n, int(nnz), rowptr_np, col, opts)
+
+    def close(self):
+        if self.h:
+            katz_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rank(self, alpha=0.0, k=100, eps=1e-9, check=True) -> katz_info:
+        return katz_rank_static(self.h, alpha, k, eps, check)
+
+    def ranking(self, k):
+        return katz_get_ranking(self.h, k)
+
+    def bounds(self):
+        return katz_get_bounds(self.h, self.n)
+
+    def walk(self, i):
+        return katz_get_walk(self.h, i, self.n)
+
+    def trace(self, cap=1024):
+        return katz_get_trace(self.h, cap)
+
+    def update(self, src, dst, is_insert, check=True) -> katz_info:
+        return katz_apply_update_batch(self.h, src, dst, is_insert, check=check)
+
+
+_load()

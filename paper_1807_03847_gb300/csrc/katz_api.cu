@@ -1,0 +1,610 @@
+// C-ABI entry points (include/katz.h): handle lifecycle, the driver of
+// Algorithm 1's loop and the getters.  All arithmetic of the method runs in
+// the kernels of katz_kernels.cu; this file only allocates, launches and
+// copies.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "katz_common.cuh"
+#include "katz_handle.h"
+
+using namespace katz;
+
+namespace {
+
+const char* kStatusNames[] = {"KATZ_OK",     "KATZ_EINVAL",     "KATZ_EALPHA",   "KATZ_ENOMEM",
+                              "KATZ_ECUDA",  "KATZ_ENOTCONV",   "KATZ_EPRECISION", "KATZ_ETIMEOUT",
+                              "KATZ_EBUSY",  "KATZ_ESTATE"};
+
+}  // namespace
+
+namespace katz {
+
+katz_status fail(katz_handle* h, katz_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+katz_status cuda_fail(katz_handle* h, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (h) h->err = m;
+    return e == cudaErrorMemoryAllocation ? KATZ_ENOMEM : KATZ_ECUDA;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename X>
+cudaError_t dmalloc(X** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(X));
+}
+
+void free_iter(katz_handle* h) {
+    IterBuffers& b = h->b;
+    cudaFree(b.walk);
+    cudaFree(b.c);
+    cudaFree(b.active);
+    cudaFree(b.partA);
+    cudaFree(b.partB);
+    cudaFree(b.ticket);
+    cudaFree(b.cand_l);
+    cudaFree(b.cand_u);
+    cudaFree(b.cand_id);
+    cudaFree(b.topk_id);
+    cudaFree(b.topk_l);
+    cudaFree(b.topk_u);
+    cudaFree(b.trace);
+    cudaFree(b.ctrl);
+    b = IterBuffers();
+    h->walk_slots = 0;
+}
+
+// (Re)allocate the per-iteration buffers for the handle's precision,
+// history setting and r_max.
+katz_status ensure_iter_buffers(katz_handle* h) {
+    const int slots = h->opts.keep_history ? h->opts.r_max + 1 : 2;
+    const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+    if (h->b.walk && h->walk_slots == slots && h->walk_esz == esz) return KATZ_OK;
+    free_iter(h);
+    IterBuffers& b = h->b;
+    const int64_t n = h->g.n;
+    const int64_t stride = ((n + 1) + 31) / 32 * 32;
+    cudaError_t e;
+#define KALLOC(ptr, cnt)                                          \
+    if ((e = dmalloc(&(ptr), (size_t)(cnt))) != cudaSuccess) {    \
+        free_iter(h);                                             \
+        return cuda_fail(h, e, "cudaMalloc " #ptr);               \
+    }
+    char* walk = nullptr;
+    KALLOC(walk, (size_t)slots * stride * esz);
+    b.walk = walk;
+    KALLOC(b.c, n);
+    KALLOC(b.active, n);
+    char* pa = nullptr;
+    char* pb = nullptr;
+    KALLOC(pa, (size_t)h->g.ntiles * esz);
+    KALLOC(pb, (size_t)h->g.ntiles * esz);
+    b.partA = pa;
+    b.partB = pb;
+    KALLOC(b.ticket, n);
+    KALLOC(b.cand_l, n);
+    KALLOC(b.cand_u, n);
+    KALLOC(b.cand_id, n);
+    KALLOC(b.topk_id, KATZ_MAX_K);
+    KALLOC(b.topk_l, KATZ_MAX_K);
+    KALLOC(b.topk_u, KATZ_MAX_K);
+    KALLOC(b.trace, h->opts.r_max + 2);
+    KALLOC(b.ctrl, 1);
+#undef KALLOC
+    b.cand_cap = n;
+    if ((e = cudaMemsetAsync(b.ticket, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "memset ticket");
+    h->walk_slots = slots;
+    h->walk_esz = esz;
+    h->stride = stride;
+    return KATZ_OK;
+}
+
+// One iteration of Algorithm 1 (four kernels, no host synchronisation).
+// ev_pair: optional events recorded around the SpMV launch.
+cudaError_t launch_iteration(katz_handle* h, cudaEvent_t* ev_pair = nullptr) {
+    cudaError_t e;
+    if (ev_pair && (e = cudaEventRecord(ev_pair[0], h->stream)) != cudaSuccess) return e;
+    if ((e = launch_spmv(h->g, h->b, h->p, h->fp32, h->stream)) != cudaSuccess) return e;
+    if (ev_pair && (e = cudaEventRecord(ev_pair[1], h->stream)) != cudaSuccess) return e;
+    if ((e = launch_select(h->b, h->p, h->b.cand_l, h->b.cand_u, h->b.cand_id, h->fp32, h->stream)) != cudaSuccess)
+        return e;
+    if ((e = launch_count(h->b, h->p, h->fp32, h->stream)) != cudaSuccess) return e;
+    return launch_finalize(h->b, h->p, h->stream);
+}
+
+bool same_params(const IterParams& a, const IterParams& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+
+void drop_graph(katz_handle* h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+}
+
+// Capture one iteration as the body of a conditional while node; the
+// finalize kernel clears the condition once converged() holds or r_max is hit.
+katz_status ensure_graph(katz_handle* h) {
+    if (h->graph_exec && same_params(h->graph_params, h->p) && h->graph_fp32 == h->fp32) return KATZ_OK;
+    drop_graph(h);
+    cudaError_t e;
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphCreate");
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "cudaGraphConditionalHandleCreate");
+    }
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "cudaGraphAddNode(conditional)");
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    h->b.cond_handle = (unsigned long long)cond;
+    h->b.use_cond = 1;
+    e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = launch_iteration(h);
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(h->stream, &out);
+        if (e2 != cudaSuccess) e = e2;
+    }
+    h->b.use_cond = 0;
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "capture iteration");
+    }
+    if ((e = cudaGraphInstantiate(&h->graph_exec, graph, 0)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    h->graph = graph;
+    h->graph_params = h->p;
+    h->graph_fp32 = h->fp32;
+    return KATZ_OK;
+}
+
+// theta_r for a candidate set too large for the one-CTA select: radix select
+// of the k-th composite key (8-bit digits, most significant first), then the
+// k winners go through the one-CTA select for their order.
+katz_status big_select(katz_handle* h) {
+    cudaError_t e;
+    Ctrl& hc = *h->h_ctrl;
+    const unsigned long long nc = hc.n_cand;
+    unsigned long long krem = (unsigned long long)std::min<int64_t>(h->p.k, (int64_t)nc);
+    unsigned __int128 prefix = 0;
+    std::vector<unsigned long long> hist(256);
+    for (int pass = 0; pass < 12; ++pass) {
+        if ((e = cudaMemsetAsync(h->d_hist256, 0, 256 * sizeof(unsigned long long), h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "memset hist");
+        if ((e = launch_radix_hist(h->b, pass, (unsigned long long)(prefix >> 32), (unsigned int)prefix,
+                                   h->d_hist256, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "radix_hist");
+        if ((e = cudaMemcpyAsync(hist.data(), h->d_hist256, 256 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "copy hist");
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "sync");
+        unsigned long long cum = 0;
+        int bsel = -1;
+        for (int bkt = 255; bkt >= 0; --bkt) {
+            if (cum + hist[bkt] >= krem) {
+                bsel = bkt;
+                break;
+            }
+            cum += hist[bkt];
+        }
+        if (bsel < 0) return fail(h, KATZ_ECUDA, "radix select lost the k-th candidate");
+        prefix |= (unsigned __int128)bsel << (88 - 8 * pass);
+        krem -= cum;
+    }
+    if ((e = cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "memset count");
+    if ((e = launch_radix_filter(h->b, (unsigned long long)(prefix >> 32), (unsigned int)prefix, h->d_big_l,
+                                 h->d_big_u, h->d_big_id, h->d_count, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "radix_filter");
+    Ctrl* dc = h->b.ctrl;
+    if ((e = cudaMemcpyAsync(&dc->n_cand, h->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                             h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "copy count");
+    const int32_t zero = 0;
+    (void)zero;
+    if ((e = cudaMemsetAsync(&dc->flags, 0, sizeof(int32_t), h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(&dc->stop, 0, sizeof(int32_t), h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "reset flags");
+    if ((e = launch_select(h->b, h->p, h->d_big_l, h->d_big_u, h->d_big_id, h->fp32, h->stream)) != cudaSuccess ||
+        (e = launch_count(h->b, h->p, h->fp32, h->stream)) != cudaSuccess ||
+        (e = launch_finalize(h->b, h->p, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "iteration tail");
+    return KATZ_OK;
+}
+
+// Run iterations until the device sets ctrl.stop (converged or r_max).
+// Graph mode: one graph launch runs the whole loop on the device; the host
+// only steps in when the candidate set outgrows the one-CTA select.
+// Host mode: iterations are launched in batches and ctrl is read between
+// batches (launches after a stop return at once).
+katz_status run_loop(katz_handle* h) {
+    cudaError_t e;
+    const bool graph_mode = h->opts.use_graph && !h->opts.profile;
+    const bool prof = h->opts.profile != 0;
+    const int batch = 4;
+    if (prof && h->sp_ev.size() < 2 * (size_t)(h->opts.r_max + 8)) {
+        for (cudaEvent_t ev : h->sp_ev) cudaEventDestroy(ev);
+        h->sp_ev.assign(2 * (size_t)(h->opts.r_max + 8), nullptr);
+        for (auto& ev : h->sp_ev)
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+    }
+    if (graph_mode) {
+        katz_status s = ensure_graph(h);
+        if (s != KATZ_OK) return s;
+    }
+    int launched_iters = 0;
+    for (;;) {
+        if (graph_mode) {
+            if ((e = cudaGraphLaunch(h->graph_exec, h->stream)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+        } else {
+            for (int q = 0; q < batch; ++q) {
+                cudaEvent_t* ev = nullptr;
+                if (prof && 2 * launched_iters + 1 < (int)h->sp_ev.size()) ev = &h->sp_ev[2 * launched_iters];
+                if ((e = launch_iteration(h, ev)) != cudaSuccess) return cuda_fail(h, e, "launch iteration");
+                h->launches += 4;
+                ++launched_iters;
+            }
+        }
+        if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "copy ctrl");
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "iteration");
+        const Ctrl& hc = *h->h_ctrl;
+        if (hc.flags & F_NEED_BIG) {
+            katz_status s = big_select(h);
+            if (s != KATZ_OK) return s;
+            h->launches += 16;  // 12 histogram passes, filter, select, count, finalize
+            h->big_paths += 1;
+            if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+                return cuda_fail(h, e, "copy ctrl");
+            if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "big select");
+            if (h->h_ctrl->stop) return KATZ_OK;
+            continue;
+        }
+        if (hc.stop) return KATZ_OK;
+    }
+}
+
+}  // namespace katz
+
+extern "C" {
+
+void katz_default_opts(katz_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = KATZ_FP64;
+    o->undirected = 1;
+    o->keep_history = 0;
+    o->r_max = 128;
+    o->deg_bound = 0;
+    o->frontier_abort_frac = 0.05;
+    o->cuda_stream = nullptr;
+    o->use_graph = 1;
+    o->slack = 0;
+}
+
+const char* katz_status_string(katz_status s) {
+    const int i = (int)s;
+    return (i >= 0 && i < (int)(sizeof(kStatusNames) / sizeof(kStatusNames[0]))) ? kStatusNames[i] : "KATZ_UNKNOWN";
+}
+
+const char* katz_last_error(katz_h h) { return h ? h->err.c_str() : "null handle"; }
+
+void katz_destroy(katz_h h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_iter(h);
+    cudaFree(h->g.rowptr);
+    cudaFree(h->g.col);
+    cudaFree(h->g.tile_row);
+    cudaFree(h->d_deghist);
+    cudaFree(h->d_big_l);
+    cudaFree(h->d_big_u);
+    cudaFree(h->d_big_id);
+    cudaFree(h->d_hist256);
+    cudaFree(h->d_count);
+    cudaFree(h->d_scratch);
+    cudaFreeHost(h->h_ctrl);
+    drop_graph(h);
+    for (cudaEvent_t ev : h->sp_ev) cudaEventDestroy(ev);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                            const katz_opts* opts) {
+    if (!out) return KATZ_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > 0x7ffffffeLL || nnz < 0 || !rowptr || (nnz > 0 && !col)) return KATZ_EINVAL;
+    katz_handle* h = new katz_handle();
+    katz_default_opts(&h->opts);
+    if (opts) h->opts = *opts;
+    if (h->opts.r_max < 1) h->opts.r_max = 1;
+    if (h->opts.precision != KATZ_FP64 && h->opts.precision != KATZ_FP32_CERT) {
+        delete h;
+        return KATZ_EINVAL;
+    }
+    h->fp32 = h->opts.precision == KATZ_FP32_CERT;
+    cudaError_t e;
+    katz_status st = KATZ_OK;
+#define KCHK(call, what)                       \
+    if ((e = (call)) != cudaSuccess) {         \
+        st = cuda_fail(h, e, what);            \
+        katz_destroy(h);                       \
+        return st;                             \
+    }
+    KCHK(cudaGetDevice(&h->dev), "cudaGetDevice");
+    KCHK(prepare_kernels(), "prepare kernels");
+    if (h->opts.cuda_stream) {
+        h->stream = (cudaStream_t)h->opts.cuda_stream;
+        h->own_stream = false;
+    } else {
+        KCHK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        h->own_stream = true;
+    }
+    KCHK(cudaEventCreate(&h->ev0), "cudaEventCreate");
+    KCHK(cudaEventCreate(&h->ev1), "cudaEventCreate");
+    KCHK(cudaMallocHost((void**)&h->h_ctrl, sizeof(Ctrl)), "cudaMallocHost");
+    DeviceGraph& g = h->g;
+    g.n = n;
+    g.nnz = nnz;
+    g.off64 = (n + nnz) >= 0x7fffffffLL;
+    // copy the CSR (int64 rowptr staged, narrowed to int32 when it fits)
+    int64_t* rp64 = nullptr;
+    KCHK(dmalloc(&rp64, (size_t)n + 1), "cudaMalloc rowptr");
+    e = cudaMemcpyAsync(rp64, rowptr, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) {
+        cudaFree(rp64);
+        st = cuda_fail(h, e, "copy rowptr");
+        katz_destroy(h);
+        return st;
+    }
+    KCHK(dmalloc(&g.col, (size_t)nnz), "cudaMalloc col");
+    if (nnz > 0) KCHK(cudaMemcpyAsync(g.col, col, (size_t)nnz * sizeof(int32_t), cudaMemcpyDefault, h->stream), "copy col");
+    // validate on the int64 copy
+    unsigned long long* d_bad = nullptr;
+    int64_t* d_degmax = nullptr;
+    KCHK(dmalloc(&d_bad, 1), "cudaMalloc");
+    KCHK(dmalloc(&d_degmax, 1), "cudaMalloc");
+    KCHK(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), h->stream), "memset");
+    KCHK(cudaMemsetAsync(d_degmax, 0, sizeof(int64_t), h->stream), "memset");
+    {
+        DeviceGraph g64 = g;
+        g64.off64 = true;
+        g64.rowptr = rp64;
+        KCHK(launch_validate_csr(g64, d_bad, d_degmax, h->stream), "validate");
+    }
+    unsigned long long bad = 0;
+    int64_t degmax = 0;
+    KCHK(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "copy");
+    KCHK(cudaMemcpyAsync(&degmax, d_degmax, sizeof(degmax), cudaMemcpyDeviceToHost, h->stream), "copy");
+    KCHK(cudaStreamSynchronize(h->stream), "validate sync");
+    cudaFree(d_bad);
+    cudaFree(d_degmax);
+    if (bad) {
+        cudaFree(rp64);
+        katz_destroy(h);
+        return KATZ_EINVAL;
+    }
+    h->deg_max = degmax;
+    h->D = std::max<int64_t>(h->opts.deg_bound, degmax);
+    if (g.off64) {
+        g.rowptr = rp64;
+    } else {
+        int32_t* rp32 = nullptr;
+        KCHK(dmalloc(&rp32, (size_t)n + 1), "cudaMalloc rowptr32");
+        KCHK(launch_narrow_rowptr(rp64, rp32, n + 1, h->stream), "narrow rowptr");
+        KCHK(cudaStreamSynchronize(h->stream), "narrow sync");
+        cudaFree(rp64);
+        g.rowptr = rp32;
+    }
+    g.ntiles = std::max<int64_t>(1, (n + nnz + TILE_ITEMS - 1) / TILE_ITEMS);
+    KCHK(dmalloc(&g.tile_row, (size_t)g.ntiles + 1), "cudaMalloc tiles");
+    KCHK(launch_partition(g, h->stream), "partition");
+    KCHK(dmalloc(&h->d_deghist, (size_t)h->D + 1), "cudaMalloc deghist");
+    KCHK(dmalloc(&h->d_big_l, SELECT_CAP), "cudaMalloc");
+    KCHK(dmalloc(&h->d_big_u, SELECT_CAP), "cudaMalloc");
+    KCHK(dmalloc(&h->d_big_id, SELECT_CAP), "cudaMalloc");
+    KCHK(dmalloc(&h->d_hist256, 256), "cudaMalloc");
+    KCHK(dmalloc(&h->d_count, 1), "cudaMalloc");
+    KCHK(cudaStreamSynchronize(h->stream), "create sync");
+#undef KCHK
+    *out = h;
+    return KATZ_OK;
+}
+
+katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz_info* info) {
+    if (!h) return KATZ_EINVAL;
+    h->err.clear();
+    if (!(eps > 0.0) || !std::isfinite(eps) || k < 1 || !std::isfinite(alpha))
+        return fail(h, KATZ_EINVAL, "need eps > 0, k >= 1, finite alpha");
+    const int64_t k_eff = std::min<int64_t>(k, h->g.n);
+    if (k_eff > KATZ_MAX_K) return fail(h, KATZ_EINVAL, "k exceeds KATZ_MAX_K");
+    const double D = (double)h->D;
+    const double a = alpha > 0.0 ? alpha : 1.0 / (D + 1.0);
+    if (!(a * D < 1.0)) return fail(h, KATZ_EALPHA, "alpha * deg_bound >= 1");
+    katz_status st = ensure_iter_buffers(h);
+    if (st != KATZ_OK) return st;
+    const double gamma = D / (1.0 - a * D);
+    IterParams& p = h->p;
+    p.alpha = a;
+    p.ag = a * gamma;
+    p.eps = eps;
+    p.n = h->g.n;
+    p.k = k_eff;
+    p.stride = h->stride;
+    p.slots = h->walk_slots;
+    p.undirected = h->opts.undirected ? 1 : 0;
+    p.r_max = h->opts.r_max;
+    h->b.use_cond = 0;
+    h->ranked = false;
+    h->launches = 3;  // init_walk, deg_hist, kth_degree
+    h->big_paths = 0;
+    cudaError_t e;
+    if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+    if ((e = cudaMemsetAsync(h->b.ctrl, 0, sizeof(Ctrl), h->stream)) != cudaSuccess) return cuda_fail(h, e, "memset ctrl");
+    if ((e = launch_init_walk(h->g, h->b, p, h->fp32, h->stream)) != cudaSuccess) return cuda_fail(h, e, "init");
+    if ((e = launch_theta0(h->g, h->b, p, h->d_deghist, h->D, h->stream)) != cudaSuccess) return cuda_fail(h, e, "theta0");
+    st = run_loop(h);
+    if (st != KATZ_OK) return st;
+    if ((e = cudaEventRecord(h->ev1, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+    if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "copy ctrl");
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "sync");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    const Ctrl& hc = *h->h_ctrl;
+    h->r = hc.r;
+    h->converged = hc.converged;
+    h->k_eff = hc.k_eff;
+    h->alpha = a;
+    h->gamma = gamma;
+    h->eps = eps;
+    h->ranked = true;
+    h->last_ms = ms;
+    std::vector<int64_t> tr((size_t)h->opts.r_max + 2, 0);
+    if ((e = cudaMemcpy(tr.data(), h->b.trace, tr.size() * sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "copy trace");
+    h->trace.assign(tr.begin() + 1, tr.begin() + 1 + std::max(0, h->r));
+    if (h->opts.use_graph && !h->opts.profile)
+        h->launches += 4 * ((int64_t)hc.body_runs - h->big_paths);
+    double spmv_ms = 0.0;
+    if (h->opts.profile) {
+        for (int q = 0; q < h->r && 2 * q + 1 < (int)h->sp_ev.size(); ++q) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, h->sp_ev[2 * q], h->sp_ev[2 * q + 1]) == cudaSuccess) spmv_ms += t;
+        }
+    }
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->spmv_ms = spmv_ms;
+        info->spmv_launches = h->r;
+        info->launches = h->launches;
+        info->r = h->r;
+        info->converged = h->converged;
+        info->active = h->trace.empty() ? h->g.n : h->trace.back();
+        info->k = h->k_eff;
+        info->alpha = a;
+        info->gamma = gamma;
+        info->time_ms = ms;
+        info->nnz = h->g.nnz;
+    }
+    if (!h->converged) return fail(h, KATZ_ENOTCONV, "r_max reached before the top-k criterion held");
+    return KATZ_OK;
+}
+
+katz_status katz_get_ranking(katz_h h, int32_t* ids, int64_t k) {
+    if (!h || !ids) return KATZ_EINVAL;
+    if (!h->ranked) return fail(h, KATZ_ESTATE, "no ranking yet");
+    if (k < 0 || k > h->k_eff) return fail(h, KATZ_EINVAL, "k larger than the ranked k");
+    if (k == 0) return KATZ_OK;
+    cudaError_t e = cudaMemcpyAsync(ids, h->b.topk_id, (size_t)k * sizeof(int32_t), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? KATZ_OK : cuda_fail(h, e, "copy ranking");
+}
+
+katz_status katz_get_bounds(katz_h h, double* lower, double* upper, double* err) {
+    if (!h) return KATZ_EINVAL;
+    if (!h->ranked) return fail(h, KATZ_ESTATE, "no ranking yet");
+    const int64_t n = h->g.n;
+    cudaError_t e;
+    const bool dev = (!lower || is_device_ptr(lower)) && (!upper || is_device_ptr(upper));
+    double* dl = lower;
+    double* du = upper;
+    if (!dev) {
+        if (!h->d_scratch) {
+            if ((e = dmalloc(&h->d_scratch, 2 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+        }
+        dl = lower ? h->d_scratch : nullptr;
+        du = upper ? h->d_scratch + n : nullptr;
+    }
+    if ((e = launch_bounds_out(h->b, h->p, h->r, h->fp32, dl, du, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "bounds");
+    if (!dev) {
+        if (lower && (e = cudaMemcpyAsync(lower, dl, (size_t)n * sizeof(double), cudaMemcpyDefault, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "copy lower");
+        if (upper && (e = cudaMemcpyAsync(upper, du, (size_t)n * sizeof(double), cudaMemcpyDefault, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "copy upper");
+    }
+    if (err) {
+        if (is_device_ptr(err)) e = cudaMemsetAsync(err, 0, (size_t)n * sizeof(double), h->stream);
+        else std::memset(err, 0, (size_t)n * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(h, e, "err");
+    }
+    e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? KATZ_OK : cuda_fail(h, e, "sync");
+}
+
+katz_status katz_get_walk(katz_h h, int32_t i, double* s_out) {
+    if (!h || !s_out) return KATZ_EINVAL;
+    if (!h->ranked) return fail(h, KATZ_ESTATE, "no ranking yet");
+    if (i < 0 || i > h->r || i <= h->r - h->walk_slots)
+        return fail(h, KATZ_EINVAL, "walk level not retained (keep_history = 0 keeps the last two)");
+    const int64_t n = h->g.n;
+    cudaError_t e;
+    double* dst = s_out;
+    const bool dev = is_device_ptr(s_out);
+    if (!dev) {
+        if (!h->d_scratch && (e = dmalloc(&h->d_scratch, 2 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+        dst = h->d_scratch;
+    }
+    if ((e = launch_walk_out(h->b, h->p, i, h->fp32, dst, h->stream)) != cudaSuccess) return cuda_fail(h, e, "walk");
+    if (!dev && (e = cudaMemcpyAsync(s_out, dst, (size_t)n * sizeof(double), cudaMemcpyDefault, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "copy walk");
+    e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? KATZ_OK : cuda_fail(h, e, "sync");
+}
+
+katz_status katz_get_trace(katz_h h, int64_t* active_per_iter, int32_t cap) {
+    if (!h || !active_per_iter || cap < 0) return KATZ_EINVAL;
+    if (!h->ranked) return fail(h, KATZ_ESTATE, "no ranking yet");
+    const int32_t m = std::min<int32_t>(cap, (int32_t)h->trace.size());
+    for (int32_t q = 0; q < m; ++q) active_per_iter[q] = h->trace[q];
+    return KATZ_OK;
+}
+
+katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t* dst, const uint8_t* is_insert,
+                                    int64_t m, katz_info* info) {
+    (void)src;
+    (void)dst;
+    (void)is_insert;
+    (void)m;
+    (void)info;
+    if (!h) return KATZ_EINVAL;
+    return fail(h, KATZ_ESTATE, "dynamic updates are not available in this build");
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Internal declarations shared by the kernels and the C-ABI driver.
+//
+// Data layout in device memory (one handle):
+//   rowptr   Off[n+1]     CSR row offsets (Off = int32 when n+nnz < 2^31, else int64)
+//   col      int32[nnz]   CSR column ids (out-neighbours)
+//   tile_row int32[T+1]   merge-path partition: first row of each tile of
+//                         TILE_ITEMS (row-end + nonzero) merge items
+//   walk     T[slots][stride]  scaled walk vectors s_i = alpha^i omega_i,
+//                         slot i % slots; entry n of every slot is 0
+//   c        f64[n]       Katz partial sum c_r (Eq. 1 truncated at r)
+//   active   u8[n]        membership in the active set M (Alg. 1)
+//   cand     {f64 l, f64 u, i32 id}[n]  nodes of M with l_r >= theta_{r-1}
+//   topk     {i32 id, f64 l, f64 u}[KATZ_MAX_K]  current top-k, sorted
+//   ctrl     Ctrl         iteration counters read and written by the kernels
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/katz.h"
+
+namespace katz {
+
+constexpr int SPMV_THREADS = 256;
+constexpr int SPMV_IPT = 8;
+constexpr int TILE_ITEMS = SPMV_THREADS * SPMV_IPT;
+constexpr int SELECT_CAP = KATZ_MAX_K;
+constexpr int SELECT_THREADS = 1024;
+
+enum : int32_t { F_NEED_BIG = 1 };
+
+// Iteration state kept on the device so that a captured graph can loop
+// without host round trips.
+struct Ctrl {
+    int32_t r;           // iterations completed
+    int32_t converged;   // result of the last converged() evaluation
+    int32_t stop;        // 1: leave the loop
+    int32_t flags;       // F_NEED_BIG: candidate set too large for the one-CTA select
+    unsigned long long n_cand;     // |{v in M : l_r(v) >= theta_{r-1}}|
+    unsigned long long cnt_cross;  // active nodes outside the top-k with u_r - eps >= theta_r
+    unsigned long long n_active;   // |M| after deactivation
+    double theta_prev;   // theta_{r-1}: k-th largest lower bound of the previous iteration
+    double theta;        // theta_r
+    int32_t theta_id;    // id of the k-th node (ties of l broken by smaller id)
+    int32_t k_eff;       // entries in the top-k list
+    double tau;          // candidate filter used by the select (diagnostic)
+    unsigned long long body_runs;  // loop bodies executed (finalize calls that did work)
+};
+
+// Per-call constants.
+struct IterParams {
+    double alpha;      // attenuation
+    double ag;         // alpha * gamma, gamma = D / (1 - alpha D) (Theorem 1)
+    double eps;        // separation slack of Eq. (3)
+    int64_t n;
+    int64_t k;         // effective k
+    int64_t stride;    // elements per walk slot
+    int32_t slots;     // walk slots (ring of `slots` levels)
+    int32_t undirected;
+    int32_t r_max;
+    int32_t pad;
+};
+
+// Lower and upper bound of Alg. 1 from c_r and s_r = alpha^r omega_r:
+//   l_r = c_r + alpha * s_r   (undirected; Sec. 3.1)      l_r = c_r (directed)
+//   u_r = c_r + alpha*gamma * s_r                          (Theorem 1)
+// Explicit round-to-nearest intrinsics: every kernel that re-derives the
+// bounds gets bit-identical values (no contraction into FMA).
+__device__ __forceinline__ void node_bounds(double c_r, double s_r, const IterParams& p, double& l,
+                                            double& u) {
+    l = p.undirected ? __dadd_rn(c_r, __dmul_rn(p.alpha, s_r)) : c_r;
+    u = __dadd_rn(c_r, __dmul_rn(p.ag, s_r));
+}
+
+// Position order of converged()'s partial sort: larger l first, ties by smaller id.
+__device__ __forceinline__ bool ranks_before(double la, int32_t ia, double lb, int32_t ib) {
+    return la > lb || (la == lb && ia < ib);
+}
+
+template <typename T>
+__device__ __forceinline__ T* walk_slot(T* base, const IterParams& p, int level) {
+    return base + (size_t)(level % p.slots) * (size_t)p.stride;
+}
+
+// ---- launchers (katz_kernels.cu) -------------------------------------------
+
+struct DeviceGraph {
+    int64_t n = 0, nnz = 0;
+    bool off64 = false;
+    void* rowptr = nullptr;   // int32_t* or int64_t*
+    int32_t* col = nullptr;
+    int32_t* tile_row = nullptr;
+    int64_t ntiles = 0;
+};
+
+struct IterBuffers {
+    void* walk = nullptr;     // double* or float*
+    double* c = nullptr;
+    uint8_t* active = nullptr;
+    void* partA = nullptr;    // per-tile partial sums (T)
+    void* partB = nullptr;
+    int32_t* ticket = nullptr;
+    double* cand_l = nullptr;
+    double* cand_u = nullptr;
+    int32_t* cand_id = nullptr;
+    int64_t cand_cap = 0;
+    int32_t* topk_id = nullptr;
+    double* topk_l = nullptr;
+    double* topk_u = nullptr;
+    int64_t* trace = nullptr; // |M| per iteration
+    Ctrl* ctrl = nullptr;
+    unsigned long long cond_handle = 0;  // cudaGraphConditionalHandle (0: none)
+    int32_t use_cond = 0;
+};
+
+cudaError_t prepare_kernels();  // one-time function attributes (outside any capture)
+cudaError_t launch_partition(const DeviceGraph& g, cudaStream_t st);
+cudaError_t launch_validate_csr(const DeviceGraph& g, unsigned long long* d_bad, int64_t* d_degmax,
+                                cudaStream_t st);
+cudaError_t launch_init_walk(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
+                             cudaStream_t st);
+cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const IterParams& p,
+                          uint32_t* d_deghist, int64_t D, cudaStream_t st);
+cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
+                        cudaStream_t st);
+cudaError_t launch_select(const IterBuffers& b, const IterParams& p, const double* cl, const double* cu,
+                          const int32_t* cid, bool fp32, cudaStream_t st);
+cudaError_t launch_count(const IterBuffers& b, const IterParams& p, bool fp32, cudaStream_t st);
+cudaError_t launch_finalize(const IterBuffers& b, const IterParams& p, cudaStream_t st);
+cudaError_t launch_bounds_out(const IterBuffers& b, const IterParams& p, int level, bool fp32, double* lower,
+                              double* upper, cudaStream_t st);
+cudaError_t launch_walk_out(const IterBuffers& b, const IterParams& p, int level, bool fp32, double* out,
+                            cudaStream_t st);
+// radix select over candidates (large candidate sets): one pass of 8-bit digits
+cudaError_t launch_radix_hist(const IterBuffers& b, int pass, unsigned long long key_hi, unsigned int key_lo,
+                              unsigned long long* d_hist, cudaStream_t st);
+cudaError_t launch_radix_filter(const IterBuffers& b, unsigned long long key_hi, unsigned int key_lo,
+                                double* out_l, double* out_u, int32_t* out_id, unsigned long long* d_count,
+                                cudaStream_t st);
+
+}  // namespace katz

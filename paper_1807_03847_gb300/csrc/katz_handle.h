@@ -1,0 +1,62 @@
+// The opaque katz_handle behind include/katz.h (host-side state).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "katz_common.cuh"
+
+struct katz_handle {
+    katz_opts opts;
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool fp32 = false;
+    katz::DeviceGraph g;
+    int64_t deg_max = 0;
+    int64_t D = 0;  // degree bound used for gamma
+    katz::IterBuffers b;
+    katz::IterParams p{};
+    int walk_slots = 0;
+    size_t walk_esz = 0;
+    int64_t stride = 0;
+    // scratch
+    uint32_t* d_deghist = nullptr;
+    double* d_big_l = nullptr;
+    double* d_big_u = nullptr;
+    int32_t* d_big_id = nullptr;
+    unsigned long long* d_hist256 = nullptr;
+    unsigned long long* d_count = nullptr;
+    double* d_scratch = nullptr;
+    katz::Ctrl* h_ctrl = nullptr;  // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // profiling: one event pair per SpMV launch
+    std::vector<cudaEvent_t> sp_ev;
+    int64_t launches = 0;   // kernels launched by the current call (host-counted part)
+    int64_t big_paths = 0;  // iterations whose select fell back to the radix path
+    // CUDA graph of one iteration inside a device-side while loop
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    katz::IterParams graph_params{};
+    bool graph_fp32 = false;
+    // result of the last rank/update call
+    bool ranked = false;
+    int r = 0;
+    int converged = 0;
+    int64_t k_eff = 0;
+    double alpha = 0, gamma = 0, eps = 0;
+    float last_ms = 0.f;
+    std::vector<int64_t> trace;
+    std::string err;
+};
+
+namespace katz {
+katz_status fail(katz_handle* h, katz_status s, const std::string& msg);
+katz_status cuda_fail(katz_handle* h, cudaError_t e, const char* what);
+bool is_device_ptr(const void* p);
+void drop_graph(katz_handle* h);
+cudaError_t launch_narrow_rowptr(const int64_t* in, int32_t* out, int64_t count, cudaStream_t st);
+}  // namespace katz

@@ -1,0 +1,724 @@
+// Device kernels of the static bound iteration (Algorithm 1).
+//
+// One iteration r (all on one stream, no host round trip):
+//   spmv_fused   s_r = alpha * A s_{r-1}  (Eq. 4, scaled), c_r = c_{r-1} + s_r,
+//                and for active nodes l_r, u_r; nodes with l_r >= theta_{r-1}
+//                are appended to the candidate list.  Merge-path tiles of
+//                TILE_ITEMS (row-end + nonzero) items balance power-law rows;
+//                rows that cross tiles are finished by the last tile to touch
+//                them (ticket counter, fixed summation order).
+//   select_topk  theta_r = k-th largest l_r over M (ties by id): one CTA sorts
+//                the candidates in shared memory; replaces partialSort.
+//   count        deactivates nodes of M outside the top-k with
+//                u_r - eps < theta_r and counts those that stay.
+//   finalize     converged(): |M| > k -> false, else adjacent-pair check of
+//                the sorted top-k; sets the loop condition.
+#include <cooperative_groups.h>
+#include <stdint.h>
+
+#include "katz_common.cuh"
+
+namespace katz {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T ld_nc(const T* p) { return __ldg(p); }
+
+template <typename T>
+__device__ __forceinline__ T scale(double alpha, T sum);
+template <>
+__device__ __forceinline__ double scale<double>(double alpha, double sum) { return __dmul_rn(alpha, sum); }
+
+template <typename T>
+__device__ __forceinline__ T add(T a, T b);
+template <>
+__device__ __forceinline__ double add<double>(double a, double b) { return __dadd_rn(a, b); }
+
+// ---------------------------------------------------------------------------
+// merge-path partition: tile t starts at merge diagonal t*TILE_ITEMS; its first
+// row is the number of row ends that precede that diagonal.
+// ---------------------------------------------------------------------------
+template <typename Off>
+__global__ void partition_kernel(const Off* __restrict__ rowptr, int64_t n, int64_t nnz, int64_t ntiles,
+                                 int32_t* __restrict__ tile_row) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    const int64_t total = n + nnz;
+    const int64_t d = min(t * (int64_t)TILE_ITEMS, total);
+    int64_t lo = max((int64_t)0, d - nnz), hi = min(d, n);
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)rowptr[mid] <= d - mid) lo = mid; else hi = mid - 1;
+    }
+    tile_row[t] = (int32_t)lo;
+}
+
+template <typename Off>
+__global__ void validate_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t n,
+                                int64_t nnz, unsigned long long* bad, int64_t* degmax) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long nb = 0;
+    long long dm = 0;
+    for (int64_t v = tid; v < n; v += stride) {
+        const int64_t a = rowptr[v], b = rowptr[v + 1];
+        if (b < a) ++nb;
+        dm = max(dm, (long long)(b - a));
+    }
+    if (tid == 0 && ((int64_t)rowptr[0] != 0 || (int64_t)rowptr[n] != nnz)) ++nb;
+    for (int64_t j = tid; j < nnz; j += stride) {
+        const int32_t x = col[j];
+        if (x < 0 || (int64_t)x >= n) ++nb;
+    }
+    if (nb) atomicAdd(bad, nb);
+    atomicMax((unsigned long long*)degmax, (unsigned long long)dm);
+}
+
+template <typename T>
+__global__ void init_walk_kernel(T* walk, double* c, uint8_t* active, IterParams p) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = tid; v < p.n; v += stride) {
+        walk[v] = (T)1;  // s_0 = omega_0 = 1 (Alg. 1)
+        c[v] = 0.0;      // c_0 = 0
+        active[v] = 1;   // M = V
+    }
+    for (int64_t s = tid; s < p.slots; s += stride) walk[(size_t)s * p.stride + p.n] = (T)0;  // sentinel
+}
+
+// ---------------------------------------------------------------------------
+// theta_0: the k-th largest l_1.  l_1 is an increasing function of the degree
+// (s_1 = alpha deg), so it is l_1 evaluated at the k-th largest degree.
+// ---------------------------------------------------------------------------
+template <typename Off>
+__global__ void deg_hist_kernel(const Off* __restrict__ rowptr, int64_t n, uint32_t* hist) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        const long long d = v < n ? (long long)(rowptr[v + 1] - rowptr[v]) : -1;
+        const unsigned mask = __match_any_sync(FULL, d);
+        if (d >= 0 && lane == __ffs(mask) - 1) atomicAdd(&hist[d], (uint32_t)__popc(mask));
+    }
+}
+
+template <typename T>
+__global__ void kth_degree_kernel(const uint32_t* __restrict__ hist, int64_t D, IterParams p, Ctrl* ctrl) {
+    __shared__ unsigned long long part[SELECT_THREADS];
+    __shared__ long long found;
+    const int tid = threadIdx.x;
+    const int64_t bins = D + 1;
+    const int64_t chunk = (bins + SELECT_THREADS - 1) / SELECT_THREADS;
+    // thread tid owns bins [D - (tid+1)*chunk + 1, D - tid*chunk], scanned from the top
+    const int64_t top = D - (int64_t)tid * chunk;
+    unsigned long long s = 0;
+    for (int64_t b = top; b > top - chunk && b >= 0; --b) s += hist[b];
+    part[tid] = s;
+    if (tid == 0) found = 0;
+    __syncthreads();
+    for (int off = 1; off < SELECT_THREADS; off <<= 1) {
+        unsigned long long add_v = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += add_v;
+        __syncthreads();
+    }
+    const unsigned long long before = tid ? part[tid - 1] : 0;
+    if (before < (unsigned long long)p.k && part[tid] >= (unsigned long long)p.k) {
+        unsigned long long cum = before;
+        for (int64_t b = top; b > top - chunk && b >= 0; --b) {
+            cum += hist[b];
+            if (cum >= (unsigned long long)p.k) { found = b; break; }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const T s1 = scale<T>(p.alpha, (T)found);
+        const double sd = (double)s1;
+        double l, u;
+        node_bounds(add<double>(0.0, sd), sd, p, l, u);
+        ctrl->theta_prev = l;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The fused walk-count SpMV.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct EpilogueArgs {
+    T* y;
+    double* c;
+    uint8_t* active;
+    double* cand_l;
+    double* cand_u;
+    int32_t* cand_id;
+    int64_t cand_cap;
+    Ctrl* ctrl;
+    double theta_prev;
+};
+
+// Finish row v: s_r(v) = alpha * sum, c_r = c_{r-1} + s_r, bounds, candidate.
+template <typename T>
+__device__ __forceinline__ void finish_row(int64_t v, T sum, const EpilogueArgs<T>& e, const IterParams& p) {
+    const T s = scale<T>(p.alpha, sum);
+    e.y[v] = s;
+    const double sd = (double)s;
+    const double cn = add<double>(e.c[v], sd);
+    e.c[v] = cn;
+    if (e.active[v]) {
+        double l, u;
+        node_bounds(cn, sd, p, l, u);
+        if (l >= e.theta_prev) {
+            const unsigned long long pos = atomicAdd(&e.ctrl->n_cand, 1ULL);
+            if (pos < (unsigned long long)e.cand_cap) {
+                e.cand_l[pos] = l;
+                e.cand_u[pos] = u;
+                e.cand_id[pos] = (int32_t)v;
+            }
+        }
+    }
+}
+
+// A row shared with other tiles: publish this tile's partial; the last tile
+// to arrive adds the partials in tile order and finishes the row.
+template <typename Off, typename T>
+__device__ void share_row(int64_t R, int64_t t, bool slotA, T part, T* partA, T* partB, int32_t* ticket,
+                          const Off* rowptr, const int32_t* tile_row, const EpilogueArgs<T>& e,
+                          const IterParams& p) {
+    (slotA ? partA : partB)[t] = part;
+    __threadfence();
+    const int64_t ts = (R + (int64_t)rowptr[R]) / TILE_ITEMS;
+    const int64_t te = (R + (int64_t)rowptr[R + 1]) / TILE_ITEMS;
+    const int old = atomicAdd(&ticket[R], 1);
+    if ((int64_t)old == te - ts) {
+        __threadfence();
+        T acc = (tile_row[ts] == (int32_t)R) ? __ldcg(partA + ts) : __ldcg(partB + ts);
+        for (int64_t tt = ts + 1; tt <= te; ++tt) acc = add<T>(acc, __ldcg(partA + tt));
+        ticket[R] = 0;
+        finish_row<T>(R, acc, e, p);
+    }
+}
+
+template <typename Off, typename T>
+__global__ void __launch_bounds__(SPMV_THREADS, 4)
+spmv_fused_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                  const int32_t* __restrict__ tile_row, int64_t n, int64_t nnz, T* walk, double* c,
+                  uint8_t* active, T* partA, T* partB, int32_t* ticket, double* cand_l, double* cand_u,
+                  int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
+    __shared__ T vals[TILE_ITEMS];            // gathered s_{r-1}(col[j]); reused for row sums
+    __shared__ int32_t rend[TILE_ITEMS + 1];  // local row-end offsets
+    __shared__ T scan_v[SPMV_THREADS];
+    __shared__ int32_t warp_k[SPMV_THREADS / 32];
+    __shared__ T warp_v[SPMV_THREADS / 32];
+    __shared__ int32_t pre_k[SPMV_THREADS / 32];
+    __shared__ T pre_v[SPMV_THREADS / 32];
+
+    if (ctrl->stop) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int r_cur = ctrl->r + 1;
+    const T* __restrict__ x = walk_slot(walk, p, r_cur - 1);
+    T* y = walk_slot(walk, p, r_cur);
+    EpilogueArgs<T> e{y, c, active, cand_l, cand_u, cand_id, cand_cap, ctrl, ctrl->theta_prev};
+
+    const int64_t t = blockIdx.x;
+    const int64_t total = n + nnz;
+    const int64_t d0 = t * (int64_t)TILE_ITEMS;
+    const int64_t d1 = min(d0 + (int64_t)TILE_ITEMS, total);
+    const int64_t row0 = tile_row[t], row1 = tile_row[t + 1];
+    const int64_t nz0 = d0 - row0, nz1 = d1 - row1;
+    const int nrows = (int)(row1 - row0);
+    const int nnzl = (int)(nz1 - nz0);
+    const int items = (int)(d1 - d0);
+
+    for (int i = tid; i < nrows; i += SPMV_THREADS) rend[i] = (int32_t)((int64_t)rowptr[row0 + i + 1] - nz0);
+    if (tid == 0) rend[nrows] = 0x7fffffff;
+#pragma unroll
+    for (int q = 0; q < SPMV_IPT; ++q) {
+        const int j = tid + q * SPMV_THREADS;
+        if (j < nnzl) vals[j] = ld_nc(x + col[nz0 + j]);
+    }
+    __syncthreads();
+
+    // this thread's merge-path start (i rows ended, j nonzeros consumed)
+    const int d = min(tid * SPMV_IPT, items);
+    int lo = max(0, d - nnzl), hi = min(d, nrows);
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rend[mid - 1] <= d - mid) lo = mid; else hi = mid - 1;
+    }
+    int i = lo, j = d - lo;
+    T sum = (T)0;
+    T rs[SPMV_IPT];
+    int ri[SPMV_IPT];
+#pragma unroll
+    for (int q = 0; q < SPMV_IPT; ++q) {
+        ri[q] = -1;
+        if (d + q < items) {
+            if (rend[i] <= j) {
+                rs[q] = sum;
+                ri[q] = i;
+                sum = (T)0;
+                ++i;
+            } else {
+                sum = add<T>(sum, vals[j]);
+                ++j;
+            }
+        }
+    }
+
+    // segmented inclusive scan of (row, partial) across the block; keys are
+    // non-decreasing in tid, so equal keys bound one contiguous segment
+    int key = i;
+    T val = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int k2 = __shfl_up_sync(FULL, key, off);
+        const T v2 = __shfl_up_sync(FULL, val, off);
+        if (lane >= off && k2 == key) val = add<T>(v2, val);
+    }
+    if (lane == 31) {
+        warp_k[wid] = key;
+        warp_v[wid] = val;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int pk = -1;
+        T pv = (T)0;
+        for (int w = 0; w < SPMV_THREADS / 32; ++w) {
+            pre_k[w] = pk;
+            pre_v[w] = pv;
+            pv = (warp_k[w] == pk) ? add<T>(pv, warp_v[w]) : warp_v[w];
+            pk = warp_k[w];
+        }
+    }
+    __syncthreads();
+    if (key == pre_k[wid]) val = add<T>(pre_v[wid], val);
+    scan_v[tid] = val;
+    __syncthreads();  // all reads of vals[] are done; reuse it for row sums
+    const T carry_in = tid ? scan_v[tid - 1] : (T)0;
+    T* rowsum = vals;
+    bool first = true;
+#pragma unroll
+    for (int q = 0; q < SPMV_IPT; ++q) {
+        if (ri[q] >= 0) {
+            T v = rs[q];
+            if (first) {
+                v = add<T>(v, carry_in);
+                first = false;
+            }
+            rowsum[ri[q]] = v;
+        }
+    }
+    __syncthreads();
+
+    // rows that start and end in this tile: coalesced epilogue
+    const bool head_before = nrows > 0 && (int64_t)rowptr[row0] < nz0;
+    for (int q = tid; q < nrows; q += SPMV_THREADS) {
+        if (q == 0 && head_before) continue;
+        finish_row<T>(row0 + q, rowsum[q], e, p);
+    }
+    if (tid == 0) {
+        const T tail = scan_v[SPMV_THREADS - 1];
+        if (nrows == 0) {
+            share_row<Off, T>(row0, t, true, tail, partA, partB, ticket, rowptr, tile_row, e, p);
+        } else {
+            if (head_before) share_row<Off, T>(row0, t, true, rowsum[0], partA, partB, ticket, rowptr, tile_row, e, p);
+            if (row1 < n && (int64_t)rowptr[row1] < nz1)
+                share_row<Off, T>(row1, t, false, tail, partA, partB, ticket, rowptr, tile_row, e, p);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// select: sort the candidates by (l desc, id asc) in shared memory; the k-th
+// entry is theta_r and the first k entries are the current top-k.
+// ---------------------------------------------------------------------------
+struct SelEntry {
+    unsigned long long key;  // bit pattern of l (monotone for l >= 0)
+    int32_t id;
+    int32_t src;             // index into the candidate arrays
+};
+
+__device__ __forceinline__ bool sel_before(const SelEntry& a, const SelEntry& b) {
+    return a.key > b.key || (a.key == b.key && a.id < b.id);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SELECT_THREADS)
+select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, const int32_t* __restrict__ cid,
+              const T* walk, const double* c, int32_t* topk_id, double* topk_l, double* topk_u, Ctrl* ctrl,
+              IterParams p) {
+    extern __shared__ SelEntry sel[];
+    __shared__ unsigned int s_cnt;
+    __shared__ double s_tau;
+    __shared__ int s_big;
+    if (ctrl->stop) return;
+    const int tid = threadIdx.x;
+    const unsigned long long nc = ctrl->n_cand;
+    const int r_cur = ctrl->r + 1;
+    if (tid == 0) {
+        s_cnt = 0;
+        s_tau = -1.0;
+        s_big = 0;
+    }
+    __syncthreads();
+    if (nc > (unsigned long long)SELECT_CAP) {
+        // Narrow the candidates: the previous top-k nodes are still active and
+        // each has l_r >= tau := min of their l_r, so the top-k of M lies in
+        // {l_r >= tau}.
+        const int kprev = ctrl->k_eff;
+        if (r_cur <= 1 || kprev < (int)p.k) {
+            if (tid == 0) s_big = 1;
+        } else {
+            const T* s = walk_slot(walk, p, r_cur);
+            double m = 1.0 / 0.0;
+            for (int q = tid; q < kprev; q += SELECT_THREADS) {
+                const int32_t v = topk_id[q];
+                double l, u;
+                node_bounds(c[v], (double)s[v], p, l, u);
+                m = fmin(m, l);
+            }
+            for (int off = 16; off; off >>= 1) m = fmin(m, __shfl_xor_sync(FULL, m, off));
+            __shared__ double wmin[SELECT_THREADS / 32];
+            if ((tid & 31) == 0) wmin[tid >> 5] = m;
+            __syncthreads();
+            if (tid == 0) {
+                double mm = wmin[0];
+                for (int w = 1; w < SELECT_THREADS / 32; ++w) mm = fmin(mm, wmin[w]);
+                s_tau = mm;
+            }
+        }
+        __syncthreads();
+    }
+    if (s_big) {
+        if (tid == 0) atomicOr(&ctrl->flags, F_NEED_BIG);
+        return;
+    }
+    const double tau = s_tau;
+    for (unsigned long long q = tid; q < nc; q += SELECT_THREADS) {
+        const double l = cl[q];
+        if (l >= tau) {
+            const unsigned int pos = atomicAdd(&s_cnt, 1u);
+            if (pos < (unsigned int)SELECT_CAP) sel[pos] = SelEntry{(unsigned long long)__double_as_longlong(l), cid[q], (int32_t)q};
+        }
+    }
+    __syncthreads();
+    const unsigned int cnt = s_cnt;
+    if (cnt > (unsigned int)SELECT_CAP) {
+        if (tid == 0) atomicOr(&ctrl->flags, F_NEED_BIG);
+        return;
+    }
+    int P = 1;
+    while (P < (int)cnt) P <<= 1;
+    for (int q = (int)cnt + tid; q < P; q += SELECT_THREADS) sel[q] = SelEntry{0ULL, 0x7fffffff, -1};
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int q = tid; q < (P >> 1); q += SELECT_THREADS) {
+                const int pos = 2 * q - (q & (stride - 1));
+                const int partner = pos + stride;
+                const SelEntry a = sel[pos], b = sel[partner];
+                const bool up = (pos & size) == 0;
+                const bool sw = up ? sel_before(b, a) : sel_before(a, b);
+                if (sw) {
+                    sel[pos] = b;
+                    sel[partner] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int kk = (int)min((long long)p.k, (long long)cnt);
+    for (int q = tid; q < kk; q += SELECT_THREADS) {
+        const SelEntry a = sel[q];
+        topk_id[q] = a.id;
+        topk_l[q] = __longlong_as_double((long long)a.key);
+        topk_u[q] = cu[a.src];
+    }
+    if (tid == 0) {
+        ctrl->k_eff = kk;
+        ctrl->tau = tau;
+        if (kk > 0) {
+            ctrl->theta = __longlong_as_double((long long)sel[kk - 1].key);
+            ctrl->theta_id = sel[kk - 1].id;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// count: deactivate nodes of M outside the top-k with u_r - eps < theta_r and
+// count the ones that remain (converged() returns false if any remain).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void count_kernel(const T* walk, const double* __restrict__ c, uint8_t* active, Ctrl* ctrl,
+                             IterParams p) {
+    if (ctrl->stop || (ctrl->flags & F_NEED_BIG)) return;
+    const int r_cur = ctrl->r + 1;
+    const T* __restrict__ s = walk_slot(walk, p, r_cur);
+    const double th = ctrl->theta;
+    const int32_t thid = ctrl->theta_id;
+    unsigned long long cross = 0, act = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
+        if (!active[v]) continue;
+        double l, u;
+        node_bounds(c[v], (double)s[v], p, l, u);
+        if (!ranks_before(l, (int32_t)v, th, thid) && !(l == th && (int32_t)v == thid)) {
+            if (__dsub_rn(u, p.eps) < th) {
+                active[v] = 0;
+                continue;
+            }
+            ++cross;
+        }
+        ++act;
+    }
+    for (int off = 16; off; off >>= 1) {
+        cross += __shfl_xor_sync(FULL, cross, off);
+        act += __shfl_xor_sync(FULL, act, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cross) atomicAdd(&ctrl->cnt_cross, cross);
+        if (act) atomicAdd(&ctrl->n_active, act);
+    }
+}
+
+__global__ void finalize_kernel(const double* __restrict__ topk_l, const double* __restrict__ topk_u,
+                                int64_t* trace, Ctrl* ctrl, IterParams p, unsigned long long cond, int use_cond) {
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    if (ctrl->stop) return;
+    if (tid == 0) ctrl->body_runs += 1;
+    if (ctrl->flags & F_NEED_BIG) {
+        if (tid == 0) {
+            ctrl->stop = 1;
+            if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0);
+        }
+        return;
+    }
+    const int kk = ctrl->k_eff;
+    const bool none_cross = ctrl->cnt_cross == 0;
+    if (none_cross) {
+        for (int q = tid + 1; q < kk; q += blockDim.x)
+            if (__dsub_rn(topk_u[q], p.eps) >= topk_l[q - 1]) bad = 1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int conv = none_cross && !bad;
+        const int r_cur = ctrl->r + 1;
+        if (r_cur <= p.r_max) trace[r_cur] = (int64_t)ctrl->n_active;
+        ctrl->r = r_cur;
+        ctrl->converged = conv;
+        ctrl->theta_prev = ctrl->theta;
+        ctrl->n_cand = 0;
+        ctrl->cnt_cross = 0;
+        ctrl->n_active = 0;
+        const int stop = conv || r_cur >= p.r_max;
+        ctrl->stop = stop;
+        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, stop ? 0u : 1u);
+    }
+}
+
+template <typename T>
+__global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, IterParams p, int level,
+                                  double* lower, double* upper) {
+    const T* s = walk_slot(walk, p, level);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
+        double l, u;
+        node_bounds(c[v], (double)s[v], p, l, u);
+        if (lower) lower[v] = l;
+        if (upper) upper[v] = u;
+    }
+}
+
+template <typename T>
+__global__ void walk_out_kernel(const T* walk, IterParams p, int level, double* out) {
+    const T* s = walk_slot(walk, p, level);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) out[v] = (double)s[v];
+}
+
+// ---------------------------------------------------------------------------
+// radix select over a large candidate set (composite key: l bits, then
+// bitwise-complemented id, 96 bits, most significant digit first)
+// ---------------------------------------------------------------------------
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 cand_key(double l, int32_t id) {
+    return ((u128)(unsigned long long)__double_as_longlong(l) << 32) | (u128)(0xffffffffu ^ (uint32_t)id);
+}
+
+__global__ void radix_hist_kernel(const double* __restrict__ cl, const int32_t* __restrict__ cid,
+                                  const Ctrl* ctrl, int pass, unsigned long long phi, unsigned int plo,
+                                  unsigned long long* hist) {
+    __shared__ unsigned int h[256];
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) h[q] = 0;
+    __syncthreads();
+    const unsigned long long nc = ctrl->n_cand;
+    const int shift = 88 - 8 * pass;
+    const u128 prefix = ((u128)phi << 32) | plo;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)nc; q += stride) {
+        const u128 key = cand_key(cl[q], cid[q]);
+        if (pass == 0 || (key >> (shift + 8)) == (prefix >> (shift + 8)))
+            atomicAdd(&h[(unsigned)(key >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 256; q += blockDim.x)
+        if (h[q]) atomicAdd(&hist[q], (unsigned long long)h[q]);
+}
+
+__global__ void radix_filter_kernel(const double* __restrict__ cl, const double* __restrict__ cu,
+                                    const int32_t* __restrict__ cid, Ctrl* ctrl, unsigned long long phi,
+                                    unsigned int plo, double* out_l, double* out_u, int32_t* out_id,
+                                    unsigned long long* count) {
+    const unsigned long long nc = ctrl->n_cand;
+    const u128 th = ((u128)phi << 32) | plo;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)nc; q += stride) {
+        if (cand_key(cl[q], cid[q]) >= th) {
+            const unsigned long long pos = atomicAdd(count, 1ULL);
+            if (pos < (unsigned long long)SELECT_CAP) {
+                out_l[pos] = cl[q];
+                out_u[pos] = cu[q];
+                out_id[pos] = cid[q];
+            }
+        }
+    }
+}
+
+__global__ void narrow_kernel(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) out[q] = (int32_t)in[q];
+}
+
+inline int grid_for(int64_t n, int threads, int max_blocks = 152 * 8) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+}  // namespace
+
+// ---- launchers --------------------------------------------------------------
+
+cudaError_t launch_narrow_rowptr(const int64_t* in, int32_t* out, int64_t count, cudaStream_t st) {
+    narrow_kernel<<<grid_for(count, 256), 256, 0, st>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_partition(const DeviceGraph& g, cudaStream_t st) {
+    const int64_t cnt = g.ntiles + 1;
+    const int blocks = (int)((cnt + 255) / 256);
+    if (g.off64)
+        partition_kernel<int64_t><<<blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.n, g.nnz, g.ntiles, g.tile_row);
+    else
+        partition_kernel<int32_t><<<blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.n, g.nnz, g.ntiles, g.tile_row);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_csr(const DeviceGraph& g, unsigned long long* d_bad, int64_t* d_degmax,
+                                cudaStream_t st) {
+    const int blocks = grid_for(g.n > g.nnz ? g.n : g.nnz, 256);
+    if (g.off64)
+        validate_kernel<int64_t><<<blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, g.n, g.nnz, d_bad, d_degmax);
+    else
+        validate_kernel<int32_t><<<blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, g.n, g.nnz, d_bad, d_degmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_walk(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
+                             cudaStream_t st) {
+    (void)g;
+    if (fp32) return cudaErrorNotSupported;
+    init_walk_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((double*)b.walk, b.c, b.active, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, uint32_t* d_deghist,
+                          int64_t D, cudaStream_t st) {
+    cudaError_t err = cudaMemsetAsync(d_deghist, 0, (size_t)(D + 1) * sizeof(uint32_t), st);
+    if (err != cudaSuccess) return err;
+    const int blocks = grid_for(g.n, 256);
+    if (g.off64)
+        deg_hist_kernel<int64_t><<<blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.n, d_deghist);
+    else
+        deg_hist_kernel<int32_t><<<blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.n, d_deghist);
+    kth_degree_kernel<double><<<1, SELECT_THREADS, 0, st>>>(d_deghist, D, p, b.ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
+                        cudaStream_t st) {
+    if (fp32) return cudaErrorNotSupported;
+    const dim3 grid((unsigned)g.ntiles);
+    if (g.off64)
+        spmv_fused_kernel<int64_t, double><<<grid, SPMV_THREADS, 0, st>>>(
+            (const int64_t*)g.rowptr, g.col, g.tile_row, g.n, g.nnz, (double*)b.walk, b.c, b.active,
+            (double*)b.partA, (double*)b.partB, b.ticket, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
+    else
+        spmv_fused_kernel<int32_t, double><<<grid, SPMV_THREADS, 0, st>>>(
+            (const int32_t*)g.rowptr, g.col, g.tile_row, g.n, g.nnz, (double*)b.walk, b.c, b.active,
+            (double*)b.partA, (double*)b.partB, b.ticket, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_kernels() {
+    const int smem = SELECT_CAP * (int)sizeof(SelEntry);
+    return cudaFuncSetAttribute(select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_select(const IterBuffers& b, const IterParams& p, const double* cl, const double* cu,
+                          const int32_t* cid, bool fp32, cudaStream_t st) {
+    if (fp32) return cudaErrorNotSupported;
+    const int smem = SELECT_CAP * (int)sizeof(SelEntry);
+    select_kernel<double><<<1, SELECT_THREADS, smem, st>>>(cl, cu, cid, (const double*)b.walk, b.c, b.topk_id,
+                                                           b.topk_l, b.topk_u, b.ctrl, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const IterBuffers& b, const IterParams& p, bool fp32, cudaStream_t st) {
+    if (fp32) return cudaErrorNotSupported;
+    count_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.active, b.ctrl, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const IterBuffers& b, const IterParams& p, cudaStream_t st) {
+    finalize_kernel<<<1, 256, 0, st>>>(b.topk_l, b.topk_u, b.trace, b.ctrl, p, b.cond_handle, b.use_cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds_out(const IterBuffers& b, const IterParams& p, int level, bool fp32, double* lower,
+                              double* upper, cudaStream_t st) {
+    if (fp32) return cudaErrorNotSupported;
+    bounds_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, p, level, lower, upper);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walk_out(const IterBuffers& b, const IterParams& p, int level, bool fp32, double* out,
+                            cudaStream_t st) {
+    if (fp32) return cudaErrorNotSupported;
+    walk_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, p, level, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_radix_hist(const IterBuffers& b, int pass, unsigned long long key_hi, unsigned int key_lo,
+                              unsigned long long* d_hist, cudaStream_t st) {
+    radix_hist_kernel<<<152 * 4, 256, 0, st>>>(b.cand_l, b.cand_id, b.ctrl, pass, key_hi, key_lo, d_hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_radix_filter(const IterBuffers& b, unsigned long long key_hi, unsigned int key_lo,
+                                double* out_l, double* out_u, int32_t* out_id, unsigned long long* d_count,
+                                cudaStream_t st) {
+    radix_filter_kernel<<<152 * 4, 256, 0, st>>>(b.cand_l, b.cand_u, b.cand_id, b.ctrl, key_hi, key_lo, out_l,
+                                                 out_u, out_id, d_count);
+    return cudaGetLastError();
+}
+
+}  // namespace katz

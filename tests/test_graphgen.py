@@ -1,0 +1,68 @@
+"""The seeded generators produce valid symmetric CSR graphs (CPU only)."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _check(g):
+    n = g.n
+    assert g.rowptr[0] == 0 and np.all(np.diff(g.rowptr) >= 0) and g.rowptr[-1] == g.nnz
+    rows = np.repeat(np.arange(n), np.diff(g.rowptr))
+    assert np.all(g.col >= 0) and np.all(g.col < n)
+    assert not np.any(rows == g.col), "self-loop"
+    key = rows.astype(np.int64) * n + g.col
+    assert np.all(np.diff(key) > 0), "rows sorted, no duplicates"
+    rkey = g.col.astype(np.int64) * n + rows
+    assert np.array_equal(np.sort(rkey), key), "symmetric"
+
+
+def test_er_exact_edge_count():
+    g = gg.erdos_renyi(16384, 131072, seed=gg.SEED_BASE)
+    _check(g)
+    assert g.nnz == 2 * 131072
+
+
+@pytest.mark.parametrize("scale", [8, 12])
+def test_rmat_valid(scale):
+    g = gg.rmat(scale, 16, seed=3)
+    _check(g)
+    assert g.nnz <= 2 * 16 * (1 << scale)
+    d = g.degrees()
+    assert d.max() > 5 * max(1.0, d.mean())  # skewed
+
+
+def test_chung_lu_valid():
+    g = gg.chung_lu(1 << 14, 16.0, 2.1, seed=5)
+    _check(g)
+    assert 4.0 < g.nnz / g.n < 40.0
+
+
+def test_generators_independent_of_thread_count():
+    code = ("import graphgen as gg, hashlib; g = gg.rmat(12, 16, seed=9); c = gg.chung_lu(4096, seed=9);"
+            "print(hashlib.sha1(g.col.tobytes() + c.col.tobytes()).hexdigest())")
+    outs = []
+    for t in ("1", "3"):
+        env = dict(os.environ, OMP_NUM_THREADS=t, PYTHONPATH=ROOT)
+        outs.append(subprocess.check_output([sys.executable, "-c", code], env=env, cwd=ROOT).strip())
+    assert outs[0] == outs[1]
+
+
+def test_update_batch_preconditions():
+    g = gg.rmat(10, 8, seed=1)
+    src, dst, ins = gg.update_batch(g, 200, seed=2)
+    assert len(src) == 200
+    for a, b, i in zip(src, dst, ins):
+        present = b in g.col[g.rowptr[a]:g.rowptr[a + 1]]
+        assert present != bool(i) and a != b
+    pairs = {(min(a, b), max(a, b)) for a, b in zip(src, dst)}
+    assert len(pairs) == 200
+    g2 = gg.apply_batch(g, src, dst, ins)
+    _check(g2)
+    assert g2.nnz == g.nnz + 2 * int(ins.sum()) - 2 * int((1 - ins).sum())
