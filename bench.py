@@ -35,6 +35,10 @@ WORKLOADS = {
     "rmat22": dict(graph="rmat22", k=1000, eps=1e-9, alpha=0.0, precision=0,
                    desc="undirected R-MAT scale 22 (4,194,304 vertices), edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), "
                         "symmetrised and deduplicated, int32 CSR; alpha=1/(deg_max+1); certified top-1000; eps=1e-9"),
+    "rmat21": dict(graph="rmat21", k=1000, eps=1e-9, alpha=0.0, precision=0,
+                   desc="undirected R-MAT scale 21 (2,097,152 vertices), edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), "
+                        "symmetrised and deduplicated, int32 CSR; alpha=1/(deg_max+1); certified top-1000; eps=1e-9 "
+                        "(profiling case: col array larger than L2, a few GB on the device)"),
     "er16k": dict(graph="er16k", k=100, eps=1e-9, alpha=0.0, precision=0,
                   desc="undirected Erdos-Renyi n=16384, m=131072, int32 CSR; alpha=1/(deg_max+1); certified top-100; "
                        "eps=1e-9"),
