@@ -60,9 +60,6 @@ void free_iter(katz_handle* h) {
     cudaFree(b.walk);
     cudaFree(b.c);
     cudaFree(b.active);
-    cudaFree(b.partA);
-    cudaFree(b.partB);
-    cudaFree(b.ticket);
     cudaFree(b.cand_l);
     cudaFree(b.cand_u);
     cudaFree(b.cand_id);
@@ -96,13 +93,6 @@ katz_status ensure_iter_buffers(katz_handle* h) {
     b.walk = walk;
     KALLOC(b.c, n);
     KALLOC(b.active, n);
-    char* pa = nullptr;
-    char* pb = nullptr;
-    KALLOC(pa, (size_t)h->g.ntiles * esz);
-    KALLOC(pb, (size_t)h->g.ntiles * esz);
-    b.partA = pa;
-    b.partB = pb;
-    KALLOC(b.ticket, n);
     KALLOC(b.cand_l, n);
     KALLOC(b.cand_u, n);
     KALLOC(b.cand_id, n);
@@ -113,24 +103,22 @@ katz_status ensure_iter_buffers(katz_handle* h) {
     KALLOC(b.ctrl, 1);
 #undef KALLOC
     b.cand_cap = n;
-    if ((e = cudaMemsetAsync(b.ticket, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess)
-        return cuda_fail(h, e, "memset ticket");
     h->walk_slots = slots;
     h->walk_esz = esz;
     h->stride = stride;
     return KATZ_OK;
 }
 
-// One iteration of Algorithm 1 (four kernels, no host synchronisation).
+// One iteration of Algorithm 1 (five kernels, no host synchronisation).
 // ev_pair: optional events recorded around the SpMV launch.
 cudaError_t launch_iteration(katz_handle* h, cudaEvent_t* ev_pair = nullptr) {
     cudaError_t e;
     if (ev_pair && (e = cudaEventRecord(ev_pair[0], h->stream)) != cudaSuccess) return e;
     if ((e = launch_spmv(h->g, h->b, h->p, h->fp32, h->stream)) != cudaSuccess) return e;
     if (ev_pair && (e = cudaEventRecord(ev_pair[1], h->stream)) != cudaSuccess) return e;
-    if ((e = launch_select(h->b, h->p, h->b.cand_l, h->b.cand_u, h->b.cand_id, h->fp32, h->stream)) != cudaSuccess)
+    if ((e = launch_select(h->g, h->b, h->p, h->b.cand_l, h->b.cand_u, h->b.cand_id, h->fp32, h->stream)) != cudaSuccess)
         return e;
-    if ((e = launch_count(h->b, h->p, h->fp32, h->stream)) != cudaSuccess) return e;
+    if ((e = launch_count(h->g, h->b, h->p, h->fp32, h->stream)) != cudaSuccess) return e;
     return launch_finalize(h->b, h->p, h->stream);
 }
 
@@ -237,8 +225,8 @@ katz_status big_select(katz_handle* h) {
     if ((e = cudaMemsetAsync(&dc->flags, 0, sizeof(int32_t), h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(&dc->stop, 0, sizeof(int32_t), h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "reset flags");
-    if ((e = launch_select(h->b, h->p, h->d_big_l, h->d_big_u, h->d_big_id, h->fp32, h->stream)) != cudaSuccess ||
-        (e = launch_count(h->b, h->p, h->fp32, h->stream)) != cudaSuccess ||
+    if ((e = launch_select(h->g, h->b, h->p, h->d_big_l, h->d_big_u, h->d_big_id, h->fp32, h->stream)) != cudaSuccess ||
+        (e = launch_count(h->g, h->b, h->p, h->fp32, h->stream)) != cudaSuccess ||
         (e = launch_finalize(h->b, h->p, h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "iteration tail");
     return KATZ_OK;
@@ -273,7 +261,7 @@ katz_status run_loop(katz_handle* h) {
                 cudaEvent_t* ev = nullptr;
                 if (prof && 2 * launched_iters + 1 < (int)h->sp_ev.size()) ev = &h->sp_ev[2 * launched_iters];
                 if ((e = launch_iteration(h, ev)) != cudaSuccess) return cuda_fail(h, e, "launch iteration");
-                h->launches += 4;
+                h->launches += (h->g.layout.row_warp > 0 ? 5 : 4);
                 ++launched_iters;
             }
         }
@@ -327,7 +315,11 @@ void katz_destroy(katz_h h) {
     free_iter(h);
     cudaFree(h->g.rowptr);
     cudaFree(h->g.col);
-    cudaFree(h->g.tile_row);
+    cudaFree(h->g.perm);
+    cudaFree(h->g.inv);
+    cudaFree(h->g.chunk_row);
+    cudaFree(h->g.chunk_first);
+    cudaFree(h->g.chunk_part);
     cudaFree(h->d_deghist);
     cudaFree(h->d_big_l);
     cudaFree(h->d_big_u);
@@ -382,58 +374,126 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     g.n = n;
     g.nnz = nnz;
     g.off64 = (n + nnz) >= 0x7fffffffLL;
-    // copy the CSR (int64 rowptr staged, narrowed to int32 when it fits)
+    // copy the CSR as given (int64 rowptr), validate it, then store it in
+    // internal order (degree classes, largest first)
     int64_t* rp64 = nullptr;
-    KCHK(dmalloc(&rp64, (size_t)n + 1), "cudaMalloc rowptr");
-    e = cudaMemcpyAsync(rp64, rowptr, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDefault, h->stream);
-    if (e != cudaSuccess) {
+    int32_t* col0 = nullptr;
+    e = dmalloc(&rp64, (size_t)n + 1);
+    if (e == cudaSuccess) e = dmalloc(&col0, (size_t)nnz);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rp64, rowptr, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(col0, col, (size_t)nnz * sizeof(int32_t), cudaMemcpyDefault, h->stream);
+    auto drop_staging = [&]() {
         cudaFree(rp64);
-        st = cuda_fail(h, e, "copy rowptr");
+        cudaFree(col0);
+        rp64 = nullptr;
+        col0 = nullptr;
+    };
+    if (e != cudaSuccess) {
+        drop_staging();
+        st = cuda_fail(h, e, "copy CSR");
         katz_destroy(h);
         return st;
     }
-    KCHK(dmalloc(&g.col, (size_t)nnz), "cudaMalloc col");
-    if (nnz > 0) KCHK(cudaMemcpyAsync(g.col, col, (size_t)nnz * sizeof(int32_t), cudaMemcpyDefault, h->stream), "copy col");
-    // validate on the int64 copy
+#define KCHK2(call, what)                      \
+    if ((e = (call)) != cudaSuccess) {         \
+        drop_staging();                        \
+        st = cuda_fail(h, e, what);            \
+        katz_destroy(h);                       \
+        return st;                             \
+    }
     unsigned long long* d_bad = nullptr;
     int64_t* d_degmax = nullptr;
-    KCHK(dmalloc(&d_bad, 1), "cudaMalloc");
-    KCHK(dmalloc(&d_degmax, 1), "cudaMalloc");
-    KCHK(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), h->stream), "memset");
-    KCHK(cudaMemsetAsync(d_degmax, 0, sizeof(int64_t), h->stream), "memset");
+    KCHK2(dmalloc(&d_bad, 1), "cudaMalloc");
+    KCHK2(dmalloc(&d_degmax, 1), "cudaMalloc");
+    KCHK2(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), h->stream), "memset");
+    KCHK2(cudaMemsetAsync(d_degmax, 0, sizeof(int64_t), h->stream), "memset");
     {
-        DeviceGraph g64 = g;
+        DeviceGraph g64;
+        g64.n = n;
+        g64.nnz = nnz;
         g64.off64 = true;
         g64.rowptr = rp64;
-        KCHK(launch_validate_csr(g64, d_bad, d_degmax, h->stream), "validate");
+        g64.col = col0;
+        KCHK2(launch_validate_csr(g64, d_bad, d_degmax, h->stream), "validate");
     }
     unsigned long long bad = 0;
     int64_t degmax = 0;
-    KCHK(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "copy");
-    KCHK(cudaMemcpyAsync(&degmax, d_degmax, sizeof(degmax), cudaMemcpyDeviceToHost, h->stream), "copy");
-    KCHK(cudaStreamSynchronize(h->stream), "validate sync");
+    KCHK2(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "copy");
+    KCHK2(cudaMemcpyAsync(&degmax, d_degmax, sizeof(degmax), cudaMemcpyDeviceToHost, h->stream), "copy");
+    KCHK2(cudaStreamSynchronize(h->stream), "validate sync");
     cudaFree(d_bad);
     cudaFree(d_degmax);
     if (bad) {
-        cudaFree(rp64);
+        drop_staging();
         katz_destroy(h);
         return KATZ_EINVAL;
     }
     h->deg_max = degmax;
     h->D = std::max<int64_t>(h->opts.deg_bound, degmax);
-    if (g.off64) {
-        g.rowptr = rp64;
-    } else {
-        int32_t* rp32 = nullptr;
-        KCHK(dmalloc(&rp32, (size_t)n + 1), "cudaMalloc rowptr32");
-        KCHK(launch_narrow_rowptr(rp64, rp32, n + 1, h->stream), "narrow rowptr");
-        KCHK(cudaStreamSynchronize(h->stream), "narrow sync");
-        cudaFree(rp64);
-        g.rowptr = rp32;
+    // relabel: stable counting sort by degree class
+    {
+        const int nb = relabel_blocks(n);
+        uint32_t* counts = nullptr;
+        uint64_t* class_start = nullptr;
+        KCHK2(dmalloc(&counts, (size_t)NUM_CLASSES * nb), "cudaMalloc counts");
+        KCHK2(dmalloc(&class_start, NUM_CLASSES), "cudaMalloc");
+        KCHK2(dmalloc(&g.perm, (size_t)n), "cudaMalloc perm");
+        KCHK2(dmalloc(&g.inv, (size_t)n), "cudaMalloc inv");
+        KCHK2(relabel_by_degree_class(rp64, n, counts, nb, g.perm, g.inv, class_start, h->stream), "relabel");
+        uint64_t cs[NUM_CLASSES];
+        KCHK2(cudaMemcpyAsync(cs, class_start, sizeof(cs), cudaMemcpyDeviceToHost, h->stream), "copy classes");
+        KCHK2(cudaStreamSynchronize(h->stream), "relabel sync");
+        cudaFree(counts);
+        cudaFree(class_start);
+        // rows of degree > 2048 / > 128 / > 16 come first: classes >= 13 / >= 9 / >= 6
+        const int64_t row_warp = (int64_t)cs[12], row_octet = (int64_t)cs[8], row_thread = (int64_t)cs[5];
+        int64_t* deg_new = nullptr;
+        int64_t* rp_new = nullptr;
+        int64_t* sums = nullptr;
+        KCHK2(dmalloc(&deg_new, (size_t)n + 1), "cudaMalloc");
+        KCHK2(dmalloc(&rp_new, (size_t)n + 1), "cudaMalloc");
+        KCHK2(dmalloc(&sums, (size_t)scan_blocks(n + 1)), "cudaMalloc");
+        KCHK2(dmalloc(&g.col, (size_t)nnz), "cudaMalloc col");
+        KCHK2(cudaMemsetAsync(deg_new + n, 0, sizeof(int64_t), h->stream), "memset");
+        KCHK2(relabel_rows(rp64, col0, g.perm, g.inv, n, deg_new, rp_new, sums, g.col, h->stream), "relabel rows");
+        // chunk table of the CHUNK rows (host side; there are few of them)
+        std::vector<int64_t> hrp((size_t)row_warp + 1);
+        KCHK2(cudaMemcpyAsync(hrp.data(), rp_new, hrp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream),
+              "copy rowptr head");
+        KCHK2(cudaStreamSynchronize(h->stream), "relabel rows sync");
+        std::vector<int64_t> first((size_t)row_warp + 1, 0);
+        for (int64_t u = 0; u < row_warp; ++u)
+            first[u + 1] = first[u] + (hrp[u + 1] - hrp[u] + CHUNK_ARCS - 1) / CHUNK_ARCS;
+        const int64_t chunks = first[row_warp];
+        std::vector<int32_t> crow((size_t)std::max<int64_t>(chunks, 1));
+        for (int64_t u = 0; u < row_warp; ++u)
+            for (int64_t q = first[u]; q < first[u + 1]; ++q) crow[q] = (int32_t)u;
+        KCHK2(dmalloc(&g.chunk_first, first.size()), "cudaMalloc");
+        KCHK2(dmalloc(&g.chunk_row, crow.size()), "cudaMalloc");
+        KCHK2(dmalloc(&g.chunk_part, crow.size()), "cudaMalloc");
+        KCHK2(cudaMemcpyAsync(g.chunk_first, first.data(), first.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              h->stream), "copy chunks");
+        KCHK2(cudaMemcpyAsync(g.chunk_row, crow.data(), crow.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                              h->stream), "copy chunks");
+        g.layout = make_layout(n, row_warp, row_octet, row_thread, chunks);
+        if (g.off64) {
+            g.rowptr = rp_new;
+            rp_new = nullptr;
+        } else {
+            int32_t* rp32 = nullptr;
+            KCHK2(dmalloc(&rp32, (size_t)n + 1), "cudaMalloc rowptr32");
+            KCHK2(launch_narrow_rowptr(rp_new, rp32, n + 1, h->stream), "narrow rowptr");
+            g.rowptr = rp32;
+        }
+        KCHK2(cudaStreamSynchronize(h->stream), "relabel sync");
+        cudaFree(deg_new);
+        cudaFree(rp_new);
+        cudaFree(sums);
     }
-    g.ntiles = std::max<int64_t>(1, (n + nnz + TILE_ITEMS - 1) / TILE_ITEMS);
-    KCHK(dmalloc(&g.tile_row, (size_t)g.ntiles + 1), "cudaMalloc tiles");
-    KCHK(launch_partition(g, h->stream), "partition");
+    drop_staging();
+#undef KCHK2
     KCHK(dmalloc(&h->d_deghist, (size_t)h->D + 1), "cudaMalloc deghist");
     KCHK(dmalloc(&h->d_big_l, SELECT_CAP), "cudaMalloc");
     KCHK(dmalloc(&h->d_big_u, SELECT_CAP), "cudaMalloc");
@@ -500,7 +560,7 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
         return cuda_fail(h, e, "copy trace");
     h->trace.assign(tr.begin() + 1, tr.begin() + 1 + std::max(0, h->r));
     if (h->opts.use_graph && !h->opts.profile)
-        h->launches += 4 * ((int64_t)hc.body_runs - h->big_paths);
+        h->launches += (h->g.layout.row_warp > 0 ? 5 : 4) * ((int64_t)hc.body_runs - h->big_paths);
     double spmv_ms = 0.0;
     if (h->opts.profile) {
         for (int q = 0; q < h->r && 2 * q + 1 < (int)h->sp_ev.size(); ++q) {
@@ -551,7 +611,7 @@ katz_status katz_get_bounds(katz_h h, double* lower, double* upper, double* err)
         dl = lower ? h->d_scratch : nullptr;
         du = upper ? h->d_scratch + n : nullptr;
     }
-    if ((e = launch_bounds_out(h->b, h->p, h->r, h->fp32, dl, du, h->stream)) != cudaSuccess)
+    if ((e = launch_bounds_out(h->g, h->b, h->p, h->r, h->fp32, dl, du, h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "bounds");
     if (!dev) {
         if (lower && (e = cudaMemcpyAsync(lower, dl, (size_t)n * sizeof(double), cudaMemcpyDefault, h->stream)) != cudaSuccess)
@@ -581,7 +641,7 @@ katz_status katz_get_walk(katz_h h, int32_t i, double* s_out) {
         if (!h->d_scratch && (e = dmalloc(&h->d_scratch, 2 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
         dst = h->d_scratch;
     }
-    if ((e = launch_walk_out(h->b, h->p, i, h->fp32, dst, h->stream)) != cudaSuccess) return cuda_fail(h, e, "walk");
+    if ((e = launch_walk_out(h->g, h->b, h->p, i, h->fp32, dst, h->stream)) != cudaSuccess) return cuda_fail(h, e, "walk");
     if (!dev && (e = cudaMemcpyAsync(s_out, dst, (size_t)n * sizeof(double), cudaMemcpyDefault, h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "copy walk");
     e = cudaStreamSynchronize(h->stream);

@@ -1,10 +1,11 @@
 // Internal declarations shared by the kernels and the C-ABI driver.
 //
-// Data layout in device memory (one handle):
+// Data layout in device memory (one handle), vertices in internal order
+// (degree classes, largest first; see katz_relabel.cu):
 //   rowptr   Off[n+1]     CSR row offsets (Off = int32 when n+nnz < 2^31, else int64)
-//   col      int32[nnz]   CSR column ids (out-neighbours)
-//   tile_row int32[T+1]   merge-path partition: first row of each tile of
-//                         TILE_ITEMS (row-end + nonzero) merge items
+//   col      int32[nnz]   CSR column ids (out-neighbours, internal ids)
+//   perm/inv int32[n]     internal -> original id and back
+//   chunk_*               the 2048-arc chunks of rows of degree > 2048
 //   walk     T[slots][stride]  scaled walk vectors s_i = alpha^i omega_i,
 //                         slot i % slots; entry n of every slot is 0
 //   c        f64[n]       Katz partial sum c_r (Eq. 1 truncated at r)
@@ -21,9 +22,8 @@
 
 namespace katz {
 
-constexpr int SPMV_THREADS = 256;
-constexpr int SPMV_IPT = 8;
-constexpr int TILE_ITEMS = SPMV_THREADS * SPMV_IPT;
+constexpr int NUM_CLASSES = 34;   // degree classes: 0, then ceil(log2 deg) + 1
+constexpr int CHUNK_ARCS = 2048;  // arcs per warp for rows of degree > 2048
 constexpr int SELECT_CAP = KATZ_MAX_K;
 constexpr int SELECT_THREADS = 1024;
 
@@ -84,22 +84,33 @@ __device__ __forceinline__ T* walk_slot(T* base, const IterParams& p, int level)
 
 // ---- launchers (katz_kernels.cu) -------------------------------------------
 
+// Internal row ranges of the SpMV row modes and their block ranges.
+struct SpmvLayout {
+    int64_t n;
+    int64_t row_warp;    // rows [0, row_warp): CHUNK mode (degree > 2048)
+    int64_t row_octet;   // rows [row_warp, row_octet): WARP mode
+    int64_t row_thread;  // rows [row_octet, row_thread): OCTET mode; [row_thread, n): THREAD
+    int64_t chunks;      // CHUNK_ARCS-arc chunks of the CHUNK rows
+    int64_t blk_warp, blk_octet, blk_thread, blocks_total;  // first block of each mode
+};
+
 struct DeviceGraph {
     int64_t n = 0, nnz = 0;
     bool off64 = false;
     void* rowptr = nullptr;   // int32_t* or int64_t*
     int32_t* col = nullptr;
-    int32_t* tile_row = nullptr;
-    int64_t ntiles = 0;
+    int32_t* perm = nullptr;  // internal -> original id
+    int32_t* inv = nullptr;   // original -> internal id
+    int32_t* chunk_row = nullptr;     // [chunks] row of each chunk
+    int64_t* chunk_first = nullptr;   // [row_warp + 1] first chunk of each CHUNK row
+    double* chunk_part = nullptr;     // [chunks] chunk sums
+    SpmvLayout layout{};
 };
 
 struct IterBuffers {
     void* walk = nullptr;     // double* or float*
     double* c = nullptr;
     uint8_t* active = nullptr;
-    void* partA = nullptr;    // per-tile partial sums (T)
-    void* partB = nullptr;
-    int32_t* ticket = nullptr;
     double* cand_l = nullptr;
     double* cand_u = nullptr;
     int32_t* cand_id = nullptr;
@@ -114,7 +125,17 @@ struct IterBuffers {
 };
 
 cudaError_t prepare_kernels();  // one-time function attributes (outside any capture)
-cudaError_t launch_partition(const DeviceGraph& g, cudaStream_t st);
+SpmvLayout make_layout(int64_t n, int64_t row_warp, int64_t row_octet, int64_t row_thread, int64_t chunks);
+// create-time relabelling (katz_relabel.cu)
+int relabel_blocks(int64_t n);
+int64_t scan_blocks(int64_t n);
+int degree_class_host(int64_t d);
+cudaError_t relabel_by_degree_class(const int64_t* rowptr64, int64_t n, uint32_t* counts_scratch, int nb,
+                                    int32_t* perm, int32_t* inv, uint64_t* class_start_dev, cudaStream_t st);
+cudaError_t relabel_rows(const int64_t* rowptr64, const int32_t* col, const int32_t* perm, const int32_t* inv,
+                         int64_t n, int64_t* deg_new_scratch, int64_t* rowptr_new, int64_t* sums_scratch,
+                         int32_t* col_new, cudaStream_t st);
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* sums_scratch, cudaStream_t st);
 cudaError_t launch_validate_csr(const DeviceGraph& g, unsigned long long* d_bad, int64_t* d_degmax,
                                 cudaStream_t st);
 cudaError_t launch_init_walk(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
@@ -123,14 +144,16 @@ cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const Iter
                           uint32_t* d_deghist, int64_t D, cudaStream_t st);
 cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                         cudaStream_t st);
-cudaError_t launch_select(const IterBuffers& b, const IterParams& p, const double* cl, const double* cu,
-                          const int32_t* cid, bool fp32, cudaStream_t st);
-cudaError_t launch_count(const IterBuffers& b, const IterParams& p, bool fp32, cudaStream_t st);
+cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const double* cl,
+                          const double* cu, const int32_t* cid, bool fp32, cudaStream_t st);
+cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
+                         cudaStream_t st);
 cudaError_t launch_finalize(const IterBuffers& b, const IterParams& p, cudaStream_t st);
-cudaError_t launch_bounds_out(const IterBuffers& b, const IterParams& p, int level, bool fp32, double* lower,
-                              double* upper, cudaStream_t st);
-cudaError_t launch_walk_out(const IterBuffers& b, const IterParams& p, int level, bool fp32, double* out,
-                            cudaStream_t st);
+// outputs in original vertex order
+cudaError_t launch_bounds_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
+                              double* lower, double* upper, cudaStream_t st);
+cudaError_t launch_walk_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
+                            double* out, cudaStream_t st);
 // radix select over candidates (large candidate sets): one pass of 8-bit digits
 cudaError_t launch_radix_hist(const IterBuffers& b, int pass, unsigned long long key_hi, unsigned int key_lo,
                               unsigned long long* d_hist, cudaStream_t st);

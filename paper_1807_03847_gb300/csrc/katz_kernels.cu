@@ -1,12 +1,7 @@
 // Device kernels of the static bound iteration (Algorithm 1).
 //
 // One iteration r (all on one stream, no host round trip):
-//   spmv_fused   s_r = alpha * A s_{r-1}  (Eq. 4, scaled), c_r = c_{r-1} + s_r,
-//                and for active nodes l_r, u_r; nodes with l_r >= theta_{r-1}
-//                are appended to the candidate list.  Merge-path tiles of
-//                TILE_ITEMS (row-end + nonzero) items balance power-law rows;
-//                rows that cross tiles are finished by the last tile to touch
-//                them (ticket counter, fixed summation order).
+//   spmv         (katz_spmv.cu) s_r, c_r, bounds, candidates
 //   select_topk  theta_r = k-th largest l_r over M (ties by id): one CTA sorts
 //                the candidates in shared memory; replaces partialSort.
 //   count        deactivates nodes of M outside the top-k with
@@ -36,25 +31,6 @@ template <typename T>
 __device__ __forceinline__ T add(T a, T b);
 template <>
 __device__ __forceinline__ double add<double>(double a, double b) { return __dadd_rn(a, b); }
-
-// ---------------------------------------------------------------------------
-// merge-path partition: tile t starts at merge diagonal t*TILE_ITEMS; its first
-// row is the number of row ends that precede that diagonal.
-// ---------------------------------------------------------------------------
-template <typename Off>
-__global__ void partition_kernel(const Off* __restrict__ rowptr, int64_t n, int64_t nnz, int64_t ntiles,
-                                 int32_t* __restrict__ tile_row) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t > ntiles) return;
-    const int64_t total = n + nnz;
-    const int64_t d = min(t * (int64_t)TILE_ITEMS, total);
-    int64_t lo = max((int64_t)0, d - nnz), hi = min(d, n);
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if ((int64_t)rowptr[mid] <= d - mid) lo = mid; else hi = mid - 1;
-    }
-    tile_row[t] = (int32_t)lo;
-}
 
 template <typename Off>
 __global__ void validate_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t n,
@@ -144,194 +120,6 @@ __global__ void kth_degree_kernel(const uint32_t* __restrict__ hist, int64_t D, 
 }
 
 // ---------------------------------------------------------------------------
-// The fused walk-count SpMV.
-// ---------------------------------------------------------------------------
-template <typename T>
-struct EpilogueArgs {
-    T* y;
-    double* c;
-    uint8_t* active;
-    double* cand_l;
-    double* cand_u;
-    int32_t* cand_id;
-    int64_t cand_cap;
-    Ctrl* ctrl;
-    double theta_prev;
-};
-
-// Finish row v: s_r(v) = alpha * sum, c_r = c_{r-1} + s_r, bounds, candidate.
-template <typename T>
-__device__ __forceinline__ void finish_row(int64_t v, T sum, const EpilogueArgs<T>& e, const IterParams& p) {
-    const T s = scale<T>(p.alpha, sum);
-    e.y[v] = s;
-    const double sd = (double)s;
-    const double cn = add<double>(e.c[v], sd);
-    e.c[v] = cn;
-    if (e.active[v]) {
-        double l, u;
-        node_bounds(cn, sd, p, l, u);
-        if (l >= e.theta_prev) {
-            const unsigned long long pos = atomicAdd(&e.ctrl->n_cand, 1ULL);
-            if (pos < (unsigned long long)e.cand_cap) {
-                e.cand_l[pos] = l;
-                e.cand_u[pos] = u;
-                e.cand_id[pos] = (int32_t)v;
-            }
-        }
-    }
-}
-
-// A row shared with other tiles: publish this tile's partial; the last tile
-// to arrive adds the partials in tile order and finishes the row.
-template <typename Off, typename T>
-__device__ void share_row(int64_t R, int64_t t, bool slotA, T part, T* partA, T* partB, int32_t* ticket,
-                          const Off* rowptr, const int32_t* tile_row, const EpilogueArgs<T>& e,
-                          const IterParams& p) {
-    (slotA ? partA : partB)[t] = part;
-    __threadfence();
-    const int64_t ts = (R + (int64_t)rowptr[R]) / TILE_ITEMS;
-    const int64_t te = (R + (int64_t)rowptr[R + 1]) / TILE_ITEMS;
-    const int old = atomicAdd(&ticket[R], 1);
-    if ((int64_t)old == te - ts) {
-        __threadfence();
-        T acc = (tile_row[ts] == (int32_t)R) ? __ldcg(partA + ts) : __ldcg(partB + ts);
-        for (int64_t tt = ts + 1; tt <= te; ++tt) acc = add<T>(acc, __ldcg(partA + tt));
-        ticket[R] = 0;
-        finish_row<T>(R, acc, e, p);
-    }
-}
-
-template <typename Off, typename T>
-__global__ void __launch_bounds__(SPMV_THREADS, 4)
-spmv_fused_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
-                  const int32_t* __restrict__ tile_row, int64_t n, int64_t nnz, T* walk, double* c,
-                  uint8_t* active, T* partA, T* partB, int32_t* ticket, double* cand_l, double* cand_u,
-                  int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
-    __shared__ T vals[TILE_ITEMS];            // gathered s_{r-1}(col[j]); reused for row sums
-    __shared__ int32_t rend[TILE_ITEMS + 1];  // local row-end offsets
-    __shared__ T scan_v[SPMV_THREADS];
-    __shared__ int32_t warp_k[SPMV_THREADS / 32];
-    __shared__ T warp_v[SPMV_THREADS / 32];
-    __shared__ int32_t pre_k[SPMV_THREADS / 32];
-    __shared__ T pre_v[SPMV_THREADS / 32];
-
-    if (ctrl->stop) return;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int r_cur = ctrl->r + 1;
-    const T* __restrict__ x = walk_slot(walk, p, r_cur - 1);
-    T* y = walk_slot(walk, p, r_cur);
-    EpilogueArgs<T> e{y, c, active, cand_l, cand_u, cand_id, cand_cap, ctrl, ctrl->theta_prev};
-
-    const int64_t t = blockIdx.x;
-    const int64_t total = n + nnz;
-    const int64_t d0 = t * (int64_t)TILE_ITEMS;
-    const int64_t d1 = min(d0 + (int64_t)TILE_ITEMS, total);
-    const int64_t row0 = tile_row[t], row1 = tile_row[t + 1];
-    const int64_t nz0 = d0 - row0, nz1 = d1 - row1;
-    const int nrows = (int)(row1 - row0);
-    const int nnzl = (int)(nz1 - nz0);
-    const int items = (int)(d1 - d0);
-
-    for (int i = tid; i < nrows; i += SPMV_THREADS) rend[i] = (int32_t)((int64_t)rowptr[row0 + i + 1] - nz0);
-    if (tid == 0) rend[nrows] = 0x7fffffff;
-#pragma unroll
-    for (int q = 0; q < SPMV_IPT; ++q) {
-        const int j = tid + q * SPMV_THREADS;
-        if (j < nnzl) vals[j] = ld_nc(x + col[nz0 + j]);
-    }
-    __syncthreads();
-
-    // this thread's merge-path start (i rows ended, j nonzeros consumed)
-    const int d = min(tid * SPMV_IPT, items);
-    int lo = max(0, d - nnzl), hi = min(d, nrows);
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (rend[mid - 1] <= d - mid) lo = mid; else hi = mid - 1;
-    }
-    int i = lo, j = d - lo;
-    T sum = (T)0;
-    T rs[SPMV_IPT];
-    int ri[SPMV_IPT];
-#pragma unroll
-    for (int q = 0; q < SPMV_IPT; ++q) {
-        ri[q] = -1;
-        if (d + q < items) {
-            if (rend[i] <= j) {
-                rs[q] = sum;
-                ri[q] = i;
-                sum = (T)0;
-                ++i;
-            } else {
-                sum = add<T>(sum, vals[j]);
-                ++j;
-            }
-        }
-    }
-
-    // segmented inclusive scan of (row, partial) across the block; keys are
-    // non-decreasing in tid, so equal keys bound one contiguous segment
-    int key = i;
-    T val = sum;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int k2 = __shfl_up_sync(FULL, key, off);
-        const T v2 = __shfl_up_sync(FULL, val, off);
-        if (lane >= off && k2 == key) val = add<T>(v2, val);
-    }
-    if (lane == 31) {
-        warp_k[wid] = key;
-        warp_v[wid] = val;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int pk = -1;
-        T pv = (T)0;
-        for (int w = 0; w < SPMV_THREADS / 32; ++w) {
-            pre_k[w] = pk;
-            pre_v[w] = pv;
-            pv = (warp_k[w] == pk) ? add<T>(pv, warp_v[w]) : warp_v[w];
-            pk = warp_k[w];
-        }
-    }
-    __syncthreads();
-    if (key == pre_k[wid]) val = add<T>(pre_v[wid], val);
-    scan_v[tid] = val;
-    __syncthreads();  // all reads of vals[] are done; reuse it for row sums
-    const T carry_in = tid ? scan_v[tid - 1] : (T)0;
-    T* rowsum = vals;
-    bool first = true;
-#pragma unroll
-    for (int q = 0; q < SPMV_IPT; ++q) {
-        if (ri[q] >= 0) {
-            T v = rs[q];
-            if (first) {
-                v = add<T>(v, carry_in);
-                first = false;
-            }
-            rowsum[ri[q]] = v;
-        }
-    }
-    __syncthreads();
-
-    // rows that start and end in this tile: coalesced epilogue
-    const bool head_before = nrows > 0 && (int64_t)rowptr[row0] < nz0;
-    for (int q = tid; q < nrows; q += SPMV_THREADS) {
-        if (q == 0 && head_before) continue;
-        finish_row<T>(row0 + q, rowsum[q], e, p);
-    }
-    if (tid == 0) {
-        const T tail = scan_v[SPMV_THREADS - 1];
-        if (nrows == 0) {
-            share_row<Off, T>(row0, t, true, tail, partA, partB, ticket, rowptr, tile_row, e, p);
-        } else {
-            if (head_before) share_row<Off, T>(row0, t, true, rowsum[0], partA, partB, ticket, rowptr, tile_row, e, p);
-            if (row1 < n && (int64_t)rowptr[row1] < nz1)
-                share_row<Off, T>(row1, t, false, tail, partA, partB, ticket, rowptr, tile_row, e, p);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // select: sort the candidates by (l desc, id asc) in shared memory; the k-th
 // entry is theta_r and the first k entries are the current top-k.
 // ---------------------------------------------------------------------------
@@ -348,8 +136,8 @@ __device__ __forceinline__ bool sel_before(const SelEntry& a, const SelEntry& b)
 template <typename T>
 __global__ void __launch_bounds__(SELECT_THREADS)
 select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, const int32_t* __restrict__ cid,
-              const T* walk, const double* c, int32_t* topk_id, double* topk_l, double* topk_u, Ctrl* ctrl,
-              IterParams p) {
+              const T* walk, const double* c, const int32_t* __restrict__ inv, int32_t* topk_id, double* topk_l,
+              double* topk_u, Ctrl* ctrl, IterParams p) {
     extern __shared__ SelEntry sel[];
     __shared__ unsigned int s_cnt;
     __shared__ double s_tau;
@@ -375,7 +163,7 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
             const T* s = walk_slot(walk, p, r_cur);
             double m = 1.0 / 0.0;
             for (int q = tid; q < kprev; q += SELECT_THREADS) {
-                const int32_t v = topk_id[q];
+                const int32_t v = inv[topk_id[q]];
                 double l, u;
                 node_bounds(c[v], (double)s[v], p, l, u);
                 m = fmin(m, l);
@@ -452,8 +240,8 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
 // count the ones that remain (converged() returns false if any remain).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void count_kernel(const T* walk, const double* __restrict__ c, uint8_t* active, Ctrl* ctrl,
-                             IterParams p) {
+__global__ void count_kernel(const T* walk, const double* __restrict__ c, const int32_t* __restrict__ perm,
+                             uint8_t* active, Ctrl* ctrl, IterParams p) {
     if (ctrl->stop || (ctrl->flags & F_NEED_BIG)) return;
     const int r_cur = ctrl->r + 1;
     const T* __restrict__ s = walk_slot(walk, p, r_cur);
@@ -465,7 +253,8 @@ __global__ void count_kernel(const T* walk, const double* __restrict__ c, uint8_
         if (!active[v]) continue;
         double l, u;
         node_bounds(c[v], (double)s[v], p, l, u);
-        if (!ranks_before(l, (int32_t)v, th, thid) && !(l == th && (int32_t)v == thid)) {
+        const int32_t ov = perm[v];  // ties are broken by the original id
+        if (!ranks_before(l, ov, th, thid) && !(l == th && ov == thid)) {
             if (__dsub_rn(u, p.eps) < th) {
                 active[v] = 0;
                 continue;
@@ -523,23 +312,24 @@ __global__ void finalize_kernel(const double* __restrict__ topk_l, const double*
 }
 
 template <typename T>
-__global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, IterParams p, int level,
-                                  double* lower, double* upper) {
+__global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, const int32_t* __restrict__ inv,
+                                  IterParams p, int level, double* lower, double* upper) {
     const T* s = walk_slot(walk, p, level);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
+        const int32_t w = inv[v];
         double l, u;
-        node_bounds(c[v], (double)s[v], p, l, u);
+        node_bounds(c[w], (double)s[w], p, l, u);
         if (lower) lower[v] = l;
         if (upper) upper[v] = u;
     }
 }
 
 template <typename T>
-__global__ void walk_out_kernel(const T* walk, IterParams p, int level, double* out) {
+__global__ void walk_out_kernel(const T* walk, const int32_t* __restrict__ inv, IterParams p, int level, double* out) {
     const T* s = walk_slot(walk, p, level);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) out[v] = (double)s[v];
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) out[v] = (double)s[inv[v]];
 }
 
 // ---------------------------------------------------------------------------
@@ -612,16 +402,6 @@ cudaError_t launch_narrow_rowptr(const int64_t* in, int32_t* out, int64_t count,
     return cudaGetLastError();
 }
 
-cudaError_t launch_partition(const DeviceGraph& g, cudaStream_t st) {
-    const int64_t cnt = g.ntiles + 1;
-    const int blocks = (int)((cnt + 255) / 256);
-    if (g.off64)
-        partition_kernel<int64_t><<<blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.n, g.nnz, g.ntiles, g.tile_row);
-    else
-        partition_kernel<int32_t><<<blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.n, g.nnz, g.ntiles, g.tile_row);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_validate_csr(const DeviceGraph& g, unsigned long long* d_bad, int64_t* d_degmax,
                                 cudaStream_t st) {
     const int blocks = grid_for(g.n > g.nnz ? g.n : g.nnz, 256);
@@ -653,38 +433,24 @@ cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const Iter
     return cudaGetLastError();
 }
 
-cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
-                        cudaStream_t st) {
-    if (fp32) return cudaErrorNotSupported;
-    const dim3 grid((unsigned)g.ntiles);
-    if (g.off64)
-        spmv_fused_kernel<int64_t, double><<<grid, SPMV_THREADS, 0, st>>>(
-            (const int64_t*)g.rowptr, g.col, g.tile_row, g.n, g.nnz, (double*)b.walk, b.c, b.active,
-            (double*)b.partA, (double*)b.partB, b.ticket, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
-    else
-        spmv_fused_kernel<int32_t, double><<<grid, SPMV_THREADS, 0, st>>>(
-            (const int32_t*)g.rowptr, g.col, g.tile_row, g.n, g.nnz, (double*)b.walk, b.c, b.active,
-            (double*)b.partA, (double*)b.partB, b.ticket, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
-    return cudaGetLastError();
-}
-
 cudaError_t prepare_kernels() {
     const int smem = SELECT_CAP * (int)sizeof(SelEntry);
     return cudaFuncSetAttribute(select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-cudaError_t launch_select(const IterBuffers& b, const IterParams& p, const double* cl, const double* cu,
-                          const int32_t* cid, bool fp32, cudaStream_t st) {
+cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const double* cl,
+                          const double* cu, const int32_t* cid, bool fp32, cudaStream_t st) {
     if (fp32) return cudaErrorNotSupported;
     const int smem = SELECT_CAP * (int)sizeof(SelEntry);
-    select_kernel<double><<<1, SELECT_THREADS, smem, st>>>(cl, cu, cid, (const double*)b.walk, b.c, b.topk_id,
-                                                           b.topk_l, b.topk_u, b.ctrl, p);
+    select_kernel<double><<<1, SELECT_THREADS, smem, st>>>(cl, cu, cid, (const double*)b.walk, b.c, g.inv,
+                                                           b.topk_id, b.topk_l, b.topk_u, b.ctrl, p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_count(const IterBuffers& b, const IterParams& p, bool fp32, cudaStream_t st) {
+cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
+                         cudaStream_t st) {
     if (fp32) return cudaErrorNotSupported;
-    count_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.active, b.ctrl, p);
+    count_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, g.perm, b.active, b.ctrl, p);
     return cudaGetLastError();
 }
 
@@ -693,17 +459,18 @@ cudaError_t launch_finalize(const IterBuffers& b, const IterParams& p, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_bounds_out(const IterBuffers& b, const IterParams& p, int level, bool fp32, double* lower,
-                              double* upper, cudaStream_t st) {
+cudaError_t launch_bounds_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
+                              double* lower, double* upper, cudaStream_t st) {
     if (fp32) return cudaErrorNotSupported;
-    bounds_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, p, level, lower, upper);
+    bounds_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, g.inv, p, level, lower,
+                                                                 upper);
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk_out(const IterBuffers& b, const IterParams& p, int level, bool fp32, double* out,
-                            cudaStream_t st) {
+cudaError_t launch_walk_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
+                            double* out, cudaStream_t st) {
     if (fp32) return cudaErrorNotSupported;
-    walk_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, p, level, out);
+    walk_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, g.inv, p, level, out);
     return cudaGetLastError();
 }
 

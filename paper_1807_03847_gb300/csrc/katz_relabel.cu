@@ -1,0 +1,235 @@
+// Degree-class relabelling of the graph at create time.
+//
+// Internal vertex order: vertices grouped by degree class (class 0 = degree
+// 0, class k >= 1 = degree in (2^(k-2), 2^(k-1)], i.e. ceil(log2 deg) + 1),
+// classes in decreasing order, original id order inside a class (a stable
+// counting sort).  perm[u] = original id of internal vertex u; inv = perm^-1.
+// In this order the rows a thread, a lane group or a warp processes together
+// have degrees within a factor of two, the hub rows come first, and the
+// walk-vector entries gathered most often sit together at the front.
+//
+// Only the walk-count SpMV sees internal ids; every result (ranking, bounds,
+// walk vectors) leaves the library in original ids, and every tie between
+// equal lower bounds is broken by the original id.
+#include <stdint.h>
+
+#include "katz_common.cuh"
+
+namespace katz {
+
+namespace {
+
+constexpr int RL_THREADS = 1024;   // ids per block of the counting sort
+constexpr int SCAN_THREADS = 1024;
+
+__device__ __forceinline__ int degree_class(int64_t d) {
+    if (d <= 0) return 0;
+    return (d == 1) ? 1 : 65 - __clzll((unsigned long long)(d - 1)) + 0;  // ceil(log2 d) + 1
+}
+
+// counts[c * nb + b] = vertices of class c in block b
+template <typename Off>
+__global__ void class_hist_kernel(const Off* __restrict__ rowptr, int64_t n, int nb, uint32_t* counts) {
+    __shared__ uint32_t h[NUM_CLASSES];
+    const int tid = threadIdx.x;
+    if (tid < NUM_CLASSES) h[tid] = 0;
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * RL_THREADS + tid;
+    if (v < n) atomicAdd(&h[degree_class((int64_t)rowptr[v + 1] - (int64_t)rowptr[v])], 1u);
+    __syncthreads();
+    if (tid < NUM_CLASSES) counts[(size_t)tid * nb + blockIdx.x] = h[tid];
+}
+
+// exclusive scan, in place, of counts laid out class-major but visited from
+// the highest class down: offset(c, b) = sum over classes > c + blocks < b of class c
+__global__ void class_scan_kernel(uint32_t* counts, int nb, uint64_t* class_start) {
+    __shared__ unsigned long long part[SCAN_THREADS];
+    const int tid = threadIdx.x;
+    const int64_t total = (int64_t)NUM_CLASSES * nb;
+    const int64_t chunk = (total + SCAN_THREADS - 1) / SCAN_THREADS;
+    // element e in visit order maps to class NUM_CLASSES-1 - e / nb, block e % nb
+    auto at = [&](int64_t e) -> uint32_t& {
+        const int64_t c = NUM_CLASSES - 1 - e / nb;
+        return counts[c * nb + e % nb];
+    };
+    unsigned long long s = 0;
+    for (int64_t e = tid * chunk; e < min(total, (int64_t)(tid + 1) * chunk); ++e) s += at(e);
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+        const unsigned long long a = tid >= off ? part[tid - off] : 0ull;
+        __syncthreads();
+        part[tid] += a;
+        __syncthreads();
+    }
+    unsigned long long run = tid ? part[tid - 1] : 0ull;
+    for (int64_t e = tid * chunk; e < min(total, (int64_t)(tid + 1) * chunk); ++e) {
+        const uint32_t x = at(e);
+        if (e % nb == 0) class_start[NUM_CLASSES - 1 - e / nb] = run;
+        at(e) = (uint32_t)run;
+        run += x;
+    }
+}
+
+// stable scatter: within a block, vertices of the same class keep id order
+template <typename Off>
+__global__ void class_scatter_kernel(const Off* __restrict__ rowptr, int64_t n, int nb, const uint32_t* counts,
+                                     int32_t* perm, int32_t* inv) {
+    __shared__ uint32_t base[NUM_CLASSES];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid < NUM_CLASSES) base[tid] = counts[(size_t)tid * nb + blockIdx.x];
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * RL_THREADS + tid;
+    const int cls = v < n ? degree_class((int64_t)rowptr[v + 1] - (int64_t)rowptr[v]) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, cls);
+    const int rank_in_warp = __popc(peers & ((1u << lane) - 1u));
+    // warps take their turn in id order so that ranks are stable across warps
+    for (int w = 0; w < RL_THREADS / 32; ++w) {
+        if (wid == w && v < n) {
+            const uint32_t u = base[cls] + rank_in_warp;
+            perm[u] = (int32_t)v;
+            inv[v] = (int32_t)u;
+        }
+        __syncthreads();
+        if (wid == w && v < n && lane == 31 - __clz(peers)) base[cls] += __popc(peers);
+        __syncthreads();
+    }
+}
+
+// exclusive scan of int64 values in three passes (block sums, scan of the
+// sums in one block, block scans with offsets); out may alias nothing
+__global__ void scan_block_sums(const int64_t* __restrict__ in, int64_t n, int64_t* sums) {
+    __shared__ long long red[SCAN_THREADS / 32];
+    const int64_t i = (int64_t)blockIdx.x * SCAN_THREADS + threadIdx.x;
+    long long x = i < n ? in[i] : 0;
+    for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) t += red[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void scan_sums_inplace(int64_t* sums, int64_t nb) {
+    __shared__ long long part[SCAN_THREADS];
+    const int tid = threadIdx.x;
+    const int64_t chunk = (nb + SCAN_THREADS - 1) / SCAN_THREADS;
+    long long s = 0;
+    for (int64_t e = tid * chunk; e < min(nb, (int64_t)(tid + 1) * chunk); ++e) s += sums[e];
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+        const long long a = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += a;
+        __syncthreads();
+    }
+    long long run = tid ? part[tid - 1] : 0;
+    for (int64_t e = tid * chunk; e < min(nb, (int64_t)(tid + 1) * chunk); ++e) {
+        const long long x = sums[e];
+        sums[e] = run;
+        run += x;
+    }
+}
+
+__global__ void scan_finish(const int64_t* __restrict__ in, int64_t n, const int64_t* __restrict__ offs,
+                            int64_t* out) {
+    __shared__ long long ws[SCAN_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * SCAN_THREADS + tid;
+    const long long x = i < n ? in[i] : 0;
+    long long v = x;
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += y;
+    }
+    if (lane == 31) ws[wid] = v;
+    __syncthreads();
+    if (tid == 0) {
+        long long t = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+            const long long y = ws[w];
+            ws[w] = t;
+            t += y;
+        }
+    }
+    __syncthreads();
+    if (i < n) out[i] = offs[blockIdx.x] + ws[wid] + v - x;
+}
+
+template <typename Off>
+__global__ void new_degree_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ perm, int64_t n,
+                                  int64_t* deg_new) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const int64_t v = perm[u];
+        deg_new[u] = (int64_t)rowptr[v + 1] - (int64_t)rowptr[v];
+    }
+}
+
+// one warp per new row: copy the original row, renaming its entries
+template <typename Off>
+__global__ void remap_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  const int32_t* __restrict__ perm, const int32_t* __restrict__ inv,
+                                  const int64_t* __restrict__ rowptr_new, int64_t n, int32_t* col_new) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; u < n; u += warps) {
+        const int64_t v = perm[u];
+        const int64_t a = rowptr[v], b = rowptr[v + 1];
+        const int64_t o = rowptr_new[u];
+        for (int64_t j = a + lane; j < b; j += 32) col_new[o + (j - a)] = inv[col[j]];
+    }
+}
+
+int grid_for(int64_t n, int threads, int max_blocks = 152 * 16) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+}  // namespace
+
+int degree_class_host(int64_t d) {
+    if (d <= 0) return 0;
+    int k = 0;
+    while (((int64_t)1 << k) < d) ++k;  // ceil(log2 d)
+    return k + 1;
+}
+
+cudaError_t relabel_by_degree_class(const int64_t* rowptr64, int64_t n, uint32_t* counts_scratch, int nb,
+                                    int32_t* perm, int32_t* inv, uint64_t* class_start_dev, cudaStream_t st) {
+    class_hist_kernel<int64_t><<<nb, RL_THREADS, 0, st>>>(rowptr64, n, nb, counts_scratch);
+    class_scan_kernel<<<1, SCAN_THREADS, 0, st>>>(counts_scratch, nb, class_start_dev);
+    class_scatter_kernel<int64_t><<<nb, RL_THREADS, 0, st>>>(rowptr64, n, nb, counts_scratch, perm, inv);
+    return cudaGetLastError();
+}
+
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* sums_scratch,
+                               cudaStream_t st) {
+    const int64_t nb = (n + SCAN_THREADS - 1) / SCAN_THREADS;
+    scan_block_sums<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, sums_scratch);
+    scan_sums_inplace<<<1, SCAN_THREADS, 0, st>>>(sums_scratch, nb);
+    scan_finish<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, sums_scratch, out);
+    return cudaGetLastError();
+}
+
+cudaError_t relabel_rows(const int64_t* rowptr64, const int32_t* col, const int32_t* perm, const int32_t* inv,
+                         int64_t n, int64_t* deg_new_scratch, int64_t* rowptr_new, int64_t* sums_scratch,
+                         int32_t* col_new, cudaStream_t st) {
+    new_degree_kernel<int64_t><<<grid_for(n, 256), 256, 0, st>>>(rowptr64, perm, n, deg_new_scratch);
+    // rowptr_new[0..n] = exclusive scan of the n degrees followed by the total
+    cudaError_t e = exclusive_scan_i64(deg_new_scratch, n + 1, rowptr_new, sums_scratch, st);
+    if (e != cudaSuccess) return e;
+    remap_rows_kernel<int64_t><<<grid_for(n * 32, 256), 256, 0, st>>>(rowptr64, col, perm, inv, rowptr_new, n,
+                                                                      col_new);
+    return cudaGetLastError();
+}
+
+int64_t scan_blocks(int64_t n) { return (n + SCAN_THREADS - 1) / SCAN_THREADS; }
+int relabel_blocks(int64_t n) { return (int)((n + RL_THREADS - 1) / RL_THREADS); }
+
+}  // namespace katz

@@ -180,3 +180,4 @@ def test_rmat22_top1000_full_size():
     g = gg.workload("rmat22")
     oracle.set_threads(0)
     check_parity(g, 0.0, 1000, 1e-9, walks=False)
+
