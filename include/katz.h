@@ -81,7 +81,9 @@ typedef struct {
     int32_t slack;         /* dynamic handles: spare arcs reserved per row (default 0) */
     int32_t profile;       /* 1: time every walk-count SpMV launch with CUDA events on the
                               handle's stream (katz_info.spmv_ms); forces the host-driven loop */
-    int32_t reserved;
+    int32_t fp32_from;     /* KATZ_FP32_CERT: first walk level computed in FP32 (>= 2);
+                              0 (default): chosen on the device once the FP32 rounding
+                              widening is predicted to stay below eps/16 */
 } katz_opts;
 
 typedef struct {

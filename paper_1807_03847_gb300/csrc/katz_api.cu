@@ -59,6 +59,7 @@ void free_iter(katz_handle* h) {
     IterBuffers& b = h->b;
     cudaFree(b.walk);
     cudaFree(b.c);
+    cudaFree(b.c32);
     cudaFree(b.active);
     cudaFree(b.cand_l);
     cudaFree(b.cand_u);
@@ -76,7 +77,7 @@ void free_iter(katz_handle* h) {
 // history setting and r_max.
 katz_status ensure_iter_buffers(katz_handle* h) {
     const int slots = h->opts.keep_history ? h->opts.r_max + 1 : 2;
-    const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+    const size_t esz = sizeof(double);  // slots hold FP64 levels (an FP32 level uses half a slot)
     if (h->b.walk && h->walk_slots == slots && h->walk_esz == esz) return KATZ_OK;
     free_iter(h);
     IterBuffers& b = h->b;
@@ -92,6 +93,7 @@ katz_status ensure_iter_buffers(katz_handle* h) {
     KALLOC(walk, (size_t)slots * stride * esz);
     b.walk = walk;
     KALLOC(b.c, n);
+    if (h->fp32) KALLOC(b.c32, n);
     KALLOC(b.active, n);
     KALLOC(b.cand_l, n);
     KALLOC(b.cand_u, n);
@@ -300,6 +302,8 @@ void katz_default_opts(katz_opts* o) {
     o->cuda_stream = nullptr;
     o->use_graph = 1;
     o->slack = 0;
+    o->profile = 0;
+    o->fp32_from = 0;
 }
 
 const char* katz_status_string(katz_status s) {
@@ -478,6 +482,9 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
         KCHK2(cudaMemcpyAsync(g.chunk_row, crow.data(), crow.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                               h->stream), "copy chunks");
         g.layout = make_layout(n, row_warp, row_octet, row_thread, chunks);
+        int64_t max_chunks = 0;
+        for (int64_t u = 0; u < row_warp; ++u) max_chunks = std::max<int64_t>(max_chunks, first[u + 1] - first[u]);
+        h->sum_depth = max_sum_depth(g.layout, max_chunks);
         if (g.off64) {
             g.rowptr = rp_new;
             rp_new = nullptr;
@@ -529,6 +536,15 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
     p.slots = h->walk_slots;
     p.undirected = h->opts.undirected ? 1 : 0;
     p.r_max = h->opts.r_max;
+    p.cert = h->fp32 ? 1 : 0;
+    {  // an upper bound of alpha * gamma: four ulps above the rounded product
+        double ag_hi = p.ag;
+        for (int q = 0; q < 4; ++q) ag_hi = std::nextafter(ag_hi, INFINITY);
+        p.ag_hi = ag_hi;
+    }
+    p.alpha_f = (float)a;
+    p.depth = h->sum_depth;
+    p.fp32_from = h->fp32 ? std::max(0, h->opts.fp32_from) : 0;
     h->b.use_cond = 0;
     h->ranked = false;
     h->launches = 3;  // init_walk, deg_hist, kth_degree
@@ -537,6 +553,7 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
     if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
     if ((e = cudaMemsetAsync(h->b.ctrl, 0, sizeof(Ctrl), h->stream)) != cudaSuccess) return cuda_fail(h, e, "memset ctrl");
     if ((e = launch_init_walk(h->g, h->b, p, h->fp32, h->stream)) != cudaSuccess) return cuda_fail(h, e, "init");
+    if ((e = launch_cert_init(h->b, p, h->stream)) != cudaSuccess) return cuda_fail(h, e, "init levels");
     if ((e = launch_theta0(h->g, h->b, p, h->d_deghist, h->D, h->stream)) != cudaSuccess) return cuda_fail(h, e, "theta0");
     st = run_loop(h);
     if (st != KATZ_OK) return st;
@@ -568,8 +585,11 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
             if (cudaEventElapsedTime(&t, h->sp_ev[2 * q], h->sp_ev[2 * q + 1]) == cudaSuccess) spmv_ms += t;
         }
     }
+    const int fp32_levels = (h->fp32 && hc.f32_from <= h->r) ? h->r - hc.f32_from + 1 : 0;
+    h->f32_from = hc.f32_from;
     if (info) {
         std::memset(info, 0, sizeof(*info));
+        info->fp32_levels = fp32_levels;
         info->spmv_ms = spmv_ms;
         info->spmv_launches = h->r;
         info->launches = h->launches;
@@ -582,6 +602,8 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
         info->time_ms = ms;
         info->nnz = h->g.nnz;
     }
+    if (!h->converged && hc.stall)
+        return fail(h, KATZ_EPRECISION, "FP32 rounding widening exceeds the remaining tail; rank in FP64");
     if (!h->converged) return fail(h, KATZ_ENOTCONV, "r_max reached before the top-k criterion held");
     return KATZ_OK;
 }
@@ -601,28 +623,28 @@ katz_status katz_get_bounds(katz_h h, double* lower, double* upper, double* err)
     if (!h->ranked) return fail(h, KATZ_ESTATE, "no ranking yet");
     const int64_t n = h->g.n;
     cudaError_t e;
-    const bool dev = (!lower || is_device_ptr(lower)) && (!upper || is_device_ptr(upper));
+    const bool dev = (!lower || is_device_ptr(lower)) && (!upper || is_device_ptr(upper)) &&
+                     (!err || is_device_ptr(err));
     double* dl = lower;
     double* du = upper;
+    double* de = err;
     if (!dev) {
         if (!h->d_scratch) {
-            if ((e = dmalloc(&h->d_scratch, 2 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+            if ((e = dmalloc(&h->d_scratch, 3 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
         }
         dl = lower ? h->d_scratch : nullptr;
         du = upper ? h->d_scratch + n : nullptr;
+        de = err ? h->d_scratch + 2 * n : nullptr;
     }
-    if ((e = launch_bounds_out(h->g, h->b, h->p, h->r, h->fp32, dl, du, h->stream)) != cudaSuccess)
+    if ((e = launch_bounds_out(h->g, h->b, h->p, h->r, h->fp32, dl, du, de, h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "bounds");
     if (!dev) {
         if (lower && (e = cudaMemcpyAsync(lower, dl, (size_t)n * sizeof(double), cudaMemcpyDefault, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "copy lower");
         if (upper && (e = cudaMemcpyAsync(upper, du, (size_t)n * sizeof(double), cudaMemcpyDefault, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "copy upper");
-    }
-    if (err) {
-        if (is_device_ptr(err)) e = cudaMemsetAsync(err, 0, (size_t)n * sizeof(double), h->stream);
-        else std::memset(err, 0, (size_t)n * sizeof(double));
-        if (e != cudaSuccess) return cuda_fail(h, e, "err");
+        if (err && (e = cudaMemcpyAsync(err, de, (size_t)n * sizeof(double), cudaMemcpyDefault, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "copy err");
     }
     e = cudaStreamSynchronize(h->stream);
     return e == cudaSuccess ? KATZ_OK : cuda_fail(h, e, "sync");
@@ -638,7 +660,7 @@ katz_status katz_get_walk(katz_h h, int32_t i, double* s_out) {
     double* dst = s_out;
     const bool dev = is_device_ptr(s_out);
     if (!dev) {
-        if (!h->d_scratch && (e = dmalloc(&h->d_scratch, 2 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+        if (!h->d_scratch && (e = dmalloc(&h->d_scratch, 3 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
         dst = h->d_scratch;
     }
     if ((e = launch_walk_out(h->g, h->b, h->p, i, h->fp32, dst, h->stream)) != cudaSuccess) return cuda_fail(h, e, "walk");

@@ -41,10 +41,20 @@ struct Ctrl {
     unsigned long long n_active;   // |M| after deactivation
     double theta_prev;   // theta_{r-1}: k-th largest lower bound of the previous iteration
     double theta;        // theta_r
-    int32_t theta_id;    // id of the k-th node (ties of l broken by smaller id)
+    int32_t theta_id;    // original id of the k-th node (ties of l broken by smaller id)
     int32_t k_eff;       // entries in the top-k list
     double tau;          // candidate filter used by the select (diagnostic)
     unsigned long long body_runs;  // loop bodies executed (finalize calls that did work)
+    // FP32-certified mode (unused in FP64 mode): levels >= f32_from are FP32
+    int32_t f32_from;    // first FP32 level (INT32_MAX: none yet)
+    int32_t stall;       // 1: rounding widening dominates; more iterations cannot certify
+    double e_cur;        // relative error bound of the stored s_r of the current level
+    double e64;          // largest relative error bound over the FP64 levels
+    double lo64, hi64;   // c64 * lo64 <= exact FP64-level part <= c64 * hi64
+    double lo32, hi32;   // same for c32, the FP32-level part
+    double los, his;     // same for the stored s_r of the current level
+    unsigned long long smax_bits, smax_prev_bits;  // max s_r over M (this / previous level)
+    unsigned long long tailw_bits, roundw_bits;    // max tail width / rounding width over M
 };
 
 // Per-call constants.
@@ -54,22 +64,45 @@ struct IterParams {
     double eps;        // separation slack of Eq. (3)
     int64_t n;
     int64_t k;         // effective k
-    int64_t stride;    // elements per walk slot
+    int64_t stride;    // elements per walk slot (8-byte units)
     int32_t slots;     // walk slots (ring of `slots` levels)
     int32_t undirected;
     int32_t r_max;
-    int32_t pad;
+    int32_t cert;      // 1: FP32-certified mode (rigorous widening, FP32 levels)
+    double ag_hi;      // an upper bound of alpha*gamma (cert mode)
+    float alpha_f;     // alpha rounded to FP32 (cert mode, FP32 levels)
+    int32_t depth;     // longest chain of additions in one row sum of the SpMV
+    int32_t fp32_from; // cert mode: forced first FP32 level (0: automatic)
 };
 
-// Lower and upper bound of Alg. 1 from c_r and s_r = alpha^r omega_r:
+// Lower and upper bound of Alg. 1 from the Katz partial sum and s_r:
 //   l_r = c_r + alpha * s_r   (undirected; Sec. 3.1)      l_r = c_r (directed)
 //   u_r = c_r + alpha*gamma * s_r                          (Theorem 1)
-// Explicit round-to-nearest intrinsics: every kernel that re-derives the
-// bounds gets bit-identical values (no contraction into FMA).
-__device__ __forceinline__ void node_bounds(double c_r, double s_r, const IterParams& p, double& l,
-                                            double& u) {
-    l = p.undirected ? __dadd_rn(c_r, __dmul_rn(p.alpha, s_r)) : c_r;
-    u = __dadd_rn(c_r, __dmul_rn(p.ag, s_r));
+// FP64 mode: c_r = c64, with round-to-nearest as the paper.  FP32-certified
+// mode: the partial sum is c64 (FP64 levels) + c32 (FP32 levels) and every
+// stored quantity carries a proven relative error; the bounds are widened by
+// it and evaluated with directed rounding, so l_r <= Katz <= u_r holds for the
+// exact Katz score.  Explicit rounding intrinsics: every kernel that re-derives
+// the bounds gets bit-identical values (no contraction into FMA).
+struct BState {
+    double lo64, hi64, lo32, hi32, los, his;
+};
+
+__device__ __forceinline__ BState bstate(const Ctrl* c) {
+    return BState{c->lo64, c->hi64, c->lo32, c->hi32, c->los, c->his};
+}
+
+__device__ __forceinline__ void node_bounds(double c64, double c32, double s_r, const IterParams& p,
+                                            const BState& b, double& l, double& u) {
+    if (!p.cert) {
+        l = p.undirected ? __dadd_rn(c64, __dmul_rn(p.alpha, s_r)) : c64;
+        u = __dadd_rn(c64, __dmul_rn(p.ag, s_r));
+        return;
+    }
+    const double c_lo = __dadd_rd(__dmul_rd(c64, b.lo64), __dmul_rd(c32, b.lo32));
+    const double c_hi = __dadd_ru(__dmul_ru(c64, b.hi64), __dmul_ru(c32, b.hi32));
+    l = p.undirected ? __dadd_rd(c_lo, __dmul_rd(__dmul_rd(p.alpha, s_r), b.los)) : c_lo;
+    u = __dadd_ru(c_hi, __dmul_ru(__dmul_ru(p.ag_hi, s_r), b.his));
 }
 
 // Position order of converged()'s partial sort: larger l first, ties by smaller id.
@@ -80,6 +113,14 @@ __device__ __forceinline__ bool ranks_before(double la, int32_t ia, double lb, i
 template <typename T>
 __device__ __forceinline__ T* walk_slot(T* base, const IterParams& p, int level) {
     return base + (size_t)(level % p.slots) * (size_t)p.stride;
+}
+
+// s_level(u) as FP64, whatever the level's storage type (slots are 8-byte
+// units; an FP32 level uses the first half of its slot)
+__device__ __forceinline__ double walk_value(const double* walk, const IterParams& p, int f32_from, int level,
+                                             int64_t u) {
+    const double* slot = walk_slot(walk, p, level);
+    return level >= f32_from ? (double)((const float*)slot)[u] : slot[u];
 }
 
 // ---- launchers (katz_kernels.cu) -------------------------------------------
@@ -109,7 +150,8 @@ struct DeviceGraph {
 
 struct IterBuffers {
     void* walk = nullptr;     // double* or float*
-    double* c = nullptr;
+    double* c = nullptr;       // c64: Katz partial sum over the FP64 levels
+    double* c32 = nullptr;     // FP32-certified mode: partial sum over the FP32 levels
     uint8_t* active = nullptr;
     double* cand_l = nullptr;
     double* cand_u = nullptr;
@@ -151,7 +193,9 @@ cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterP
 cudaError_t launch_finalize(const IterBuffers& b, const IterParams& p, cudaStream_t st);
 // outputs in original vertex order
 cudaError_t launch_bounds_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
-                              double* lower, double* upper, cudaStream_t st);
+                              double* lower, double* upper, double* err, cudaStream_t st);
+cudaError_t launch_cert_init(const IterBuffers& b, const IterParams& p, cudaStream_t st);
+int max_sum_depth(const SpmvLayout& L, int64_t max_chunks_per_row);
 cudaError_t launch_walk_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
                             double* out, cudaStream_t st);
 // radix select over candidates (large candidate sets): one pass of 8-bit digits

@@ -18,6 +18,8 @@ struct katz_handle {
     katz::DeviceGraph g;
     int64_t deg_max = 0;
     int64_t D = 0;  // degree bound used for gamma
+    int sum_depth = 1;   // longest addition chain of one SpMV row sum
+    int f32_from = 0x7fffffff;  // first FP32 level of the last ranking
     katz::IterBuffers b;
     katz::IterParams p{};
     int walk_slots = 0;

@@ -54,12 +54,13 @@ __global__ void validate_kernel(const Off* __restrict__ rowptr, const int32_t* _
 }
 
 template <typename T>
-__global__ void init_walk_kernel(T* walk, double* c, uint8_t* active, IterParams p) {
+__global__ void init_walk_kernel(T* walk, double* c, double* c32, uint8_t* active, IterParams p) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = tid; v < p.n; v += stride) {
         walk[v] = (T)1;  // s_0 = omega_0 = 1 (Alg. 1)
         c[v] = 0.0;      // c_0 = 0
+        if (c32) c32[v] = 0.0;
         active[v] = 1;   // M = V
     }
     for (int64_t s = tid; s < p.slots; s += stride) walk[(size_t)s * p.stride + p.n] = (T)0;  // sentinel
@@ -111,10 +112,11 @@ __global__ void kth_degree_kernel(const uint32_t* __restrict__ hist, int64_t D, 
     }
     __syncthreads();
     if (tid == 0) {
+        // level 1 is always FP64: s_1 = alpha * deg, c64 = 0 + s_1, c32 = 0
         const T s1 = scale<T>(p.alpha, (T)found);
         const double sd = (double)s1;
         double l, u;
-        node_bounds(add<double>(0.0, sd), sd, p, l, u);
+        node_bounds(add<double>(0.0, sd), 0.0, sd, p, bstate(ctrl), l, u);
         ctrl->theta_prev = l;
     }
 }
@@ -136,8 +138,8 @@ __device__ __forceinline__ bool sel_before(const SelEntry& a, const SelEntry& b)
 template <typename T>
 __global__ void __launch_bounds__(SELECT_THREADS)
 select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, const int32_t* __restrict__ cid,
-              const T* walk, const double* c, const int32_t* __restrict__ inv, int32_t* topk_id, double* topk_l,
-              double* topk_u, Ctrl* ctrl, IterParams p) {
+              const T* walk, const double* c, const double* c32, const int32_t* __restrict__ inv, int32_t* topk_id,
+              double* topk_l, double* topk_u, Ctrl* ctrl, IterParams p) {
     extern __shared__ SelEntry sel[];
     __shared__ unsigned int s_cnt;
     __shared__ double s_tau;
@@ -160,12 +162,13 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
         if (r_cur <= 1 || kprev < (int)p.k) {
             if (tid == 0) s_big = 1;
         } else {
-            const T* s = walk_slot(walk, p, r_cur);
+            const BState bs = bstate(ctrl);
+            const int f32_from = ctrl->f32_from;
             double m = 1.0 / 0.0;
             for (int q = tid; q < kprev; q += SELECT_THREADS) {
                 const int32_t v = inv[topk_id[q]];
                 double l, u;
-                node_bounds(c[v], (double)s[v], p, l, u);
+                node_bounds(c[v], c32 ? c32[v] : 0.0, walk_value(walk, p, f32_from, r_cur, v), p, bs, l, u);
                 m = fmin(m, l);
             }
             for (int off = 16; off; off >>= 1) m = fmin(m, __shfl_xor_sync(FULL, m, off));
@@ -240,19 +243,23 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
 // count the ones that remain (converged() returns false if any remain).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void count_kernel(const T* walk, const double* __restrict__ c, const int32_t* __restrict__ perm,
-                             uint8_t* active, Ctrl* ctrl, IterParams p) {
+__global__ void count_kernel(const T* walk, const double* __restrict__ c, const double* __restrict__ c32,
+                             const int32_t* __restrict__ perm, uint8_t* active, Ctrl* ctrl, IterParams p) {
     if (ctrl->stop || (ctrl->flags & F_NEED_BIG)) return;
     const int r_cur = ctrl->r + 1;
-    const T* __restrict__ s = walk_slot(walk, p, r_cur);
+    const int f32_from = ctrl->f32_from;
+    const BState bs = bstate(ctrl);
     const double th = ctrl->theta;
     const int32_t thid = ctrl->theta_id;
     unsigned long long cross = 0, act = 0;
+    double smax = 0.0, tailw = 0.0, roundw = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
         if (!active[v]) continue;
+        const double sv = walk_value(walk, p, f32_from, r_cur, v);
+        const double c64v = c[v], c32v = c32 ? c32[v] : 0.0;
         double l, u;
-        node_bounds(c[v], (double)s[v], p, l, u);
+        node_bounds(c64v, c32v, sv, p, bs, l, u);
         const int32_t ov = perm[v];  // ties are broken by the original id
         if (!ranks_before(l, ov, th, thid) && !(l == th && ov == thid)) {
             if (__dsub_rn(u, p.eps) < th) {
@@ -262,15 +269,69 @@ __global__ void count_kernel(const T* walk, const double* __restrict__ c, const 
             ++cross;
         }
         ++act;
+        if (p.cert) {
+            smax = fmax(smax, sv);
+            tailw = fmax(tailw, p.ag * sv);
+            roundw = fmax(roundw, c64v * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32));
+        }
     }
     for (int off = 16; off; off >>= 1) {
         cross += __shfl_xor_sync(FULL, cross, off);
         act += __shfl_xor_sync(FULL, act, off);
+        smax = fmax(smax, __shfl_xor_sync(FULL, smax, off));
+        tailw = fmax(tailw, __shfl_xor_sync(FULL, tailw, off));
+        roundw = fmax(roundw, __shfl_xor_sync(FULL, roundw, off));
     }
     if ((threadIdx.x & 31) == 0) {
         if (cross) atomicAdd(&ctrl->cnt_cross, cross);
         if (act) atomicAdd(&ctrl->n_active, act);
+        if (p.cert) {  // non-negative doubles order like their bit patterns
+            atomicMax(&ctrl->smax_bits, (unsigned long long)__double_as_longlong(smax));
+            atomicMax(&ctrl->tailw_bits, (unsigned long long)__double_as_longlong(tailw));
+            atomicMax(&ctrl->roundw_bits, (unsigned long long)__double_as_longlong(roundw));
+        }
     }
+}
+
+// gamma_m = m u / (1 - m u) (Higham), rounded up
+__device__ __forceinline__ double gamma_up(double m, double u) {
+    const double mu = __dmul_ru(m, u);
+    return __ddiv_ru(mu, __dsub_rd(1.0, mu));
+}
+
+// FP32-certified mode: error bounds and widening factors of level `lvl`
+// (relative error e_lvl of its stored s, the largest error e64 of the FP64
+// levels, and how many terms the FP64 accumulations of c64 / c32 hold).
+__device__ void set_level_state(Ctrl* ctrl, const IterParams& p, int lvl, double e_lvl) {
+    const double u64 = 0x1p-53;
+    const int f32_from = ctrl->f32_from;
+    ctrl->e_cur = e_lvl;
+    if (lvl < f32_from) ctrl->e64 = e_lvl;
+    const int n64 = lvl < f32_from ? lvl : f32_from - 1;
+    const int n32 = lvl < f32_from ? 0 : lvl - f32_from + 1;
+    // c_hat = sum of stored terms with relative errors <= e, accumulated in
+    // FP64 (relative error <= (terms + 1) u64 for non-negative terms)
+    const double w64 = __dadd_ru(ctrl->e64, __dmul_ru((double)(n64 + 2), u64));
+    const double w32 = __dadd_ru(e_lvl, __dmul_ru((double)(n32 + 2), u64));
+    ctrl->lo64 = __dsub_rd(1.0, w64);
+    ctrl->hi64 = __dadd_ru(1.0, __dmul_ru(2.0, w64));
+    ctrl->lo32 = n32 ? __dsub_rd(1.0, w32) : 1.0;
+    ctrl->hi32 = n32 ? __dadd_ru(1.0, __dmul_ru(2.0, w32)) : 1.0;
+    ctrl->los = __dsub_rd(1.0, e_lvl);
+    ctrl->his = __dadd_ru(1.0, __dmul_ru(2.0, e_lvl));
+}
+
+// error bound of level lvl from the bound of level lvl - 1
+__device__ double next_error(const Ctrl* ctrl, const IterParams& p, int lvl, double e_prev) {
+    const double g = lvl >= ctrl->f32_from ? gamma_up((double)(p.depth + 3), 0x1p-24)
+                                          : gamma_up((double)(p.depth + 1), 0x1p-53);
+    return __dsub_ru(__dmul_ru(__dadd_ru(1.0, e_prev), __dadd_ru(1.0, g)), 1.0);
+}
+
+__global__ void cert_init_kernel(Ctrl* ctrl, IterParams p) {
+    ctrl->f32_from = (p.cert && p.fp32_from >= 2) ? p.fp32_from : 0x7fffffff;
+    ctrl->e64 = 0.0;
+    set_level_state(ctrl, p, 1, p.cert ? next_error(ctrl, p, 1, 0.0) : 0.0);
 }
 
 __global__ void finalize_kernel(const double* __restrict__ topk_l, const double* __restrict__ topk_u,
@@ -305,31 +366,71 @@ __global__ void finalize_kernel(const double* __restrict__ topk_l, const double*
         ctrl->n_cand = 0;
         ctrl->cnt_cross = 0;
         ctrl->n_active = 0;
-        const int stop = conv || r_cur >= p.r_max;
+        int stop = conv || r_cur >= p.r_max;
+        if (p.cert) {
+            const double smax = __longlong_as_double((long long)ctrl->smax_bits);
+            const double sprev = __longlong_as_double((long long)ctrl->smax_prev_bits);
+            const double tailw = __longlong_as_double((long long)ctrl->tailw_bits);
+            const double roundw = __longlong_as_double((long long)ctrl->roundw_bits);
+            // stall: over the active set the rounding widening is wider than the
+            // Theorem-1 tail term, so further iterations cannot separate it
+            if (!conv && r_cur >= ctrl->f32_from && tailw < roundw) {
+                ctrl->stall = 1;
+                stop = 1;
+            }
+            if (!stop) {
+                const int next = r_cur + 1;
+                // switch to FP32 once the terms still to come (predicted from the
+                // decay of max s_r over M) carry a rounding widening below eps/16
+                if (ctrl->f32_from == 0x7fffffff && p.fp32_from == 0 && r_cur >= 2 && sprev > 0.0 &&
+                    smax < 0.5 * sprev) {
+                    const double rho = smax / sprev;
+                    const double tail_est = smax * rho / (1.0 - rho);
+                    const double e32 = ctrl->e_cur + 64.0 * gamma_up((double)(p.depth + 3), 0x1p-24);
+                    if (2.0 * tail_est * e32 <= p.eps / 16.0) ctrl->f32_from = next;
+                }
+                set_level_state(ctrl, p, next, next_error(ctrl, p, next, ctrl->e_cur));
+            }
+            ctrl->smax_prev_bits = ctrl->smax_bits;
+            ctrl->smax_bits = 0;
+            ctrl->tailw_bits = 0;
+            ctrl->roundw_bits = 0;
+        }
         ctrl->stop = stop;
         if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, stop ? 0u : 1u);
     }
 }
 
 template <typename T>
-__global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, const int32_t* __restrict__ inv,
-                                  IterParams p, int level, double* lower, double* upper) {
-    const T* s = walk_slot(walk, p, level);
+__global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, const double* __restrict__ c32,
+                                  const int32_t* __restrict__ inv, const Ctrl* ctrl, IterParams p, int level,
+                                  double* lower, double* upper, double* err) {
+    const BState bs = bstate(ctrl);
+    const int f32_from = ctrl->f32_from;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
         const int32_t w = inv[v];
+        const double sv = walk_value(walk, p, f32_from, level, w);
+        const double c32v = c32 ? c32[w] : 0.0;
         double l, u;
-        node_bounds(c[w], (double)s[w], p, l, u);
+        node_bounds(c[w], c32v, sv, p, bs, l, u);
+        if (err) {  // widening added for rounding (zero in FP64 mode)
+            err[v] = p.cert ? c[w] * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32) +
+                                  p.ag_hi * sv * (bs.his - 1.0) + p.alpha * sv * (1.0 - bs.los)
+                            : 0.0;
+        }
         if (lower) lower[v] = l;
         if (upper) upper[v] = u;
     }
 }
 
 template <typename T>
-__global__ void walk_out_kernel(const T* walk, const int32_t* __restrict__ inv, IterParams p, int level, double* out) {
-    const T* s = walk_slot(walk, p, level);
+__global__ void walk_out_kernel(const T* walk, const int32_t* __restrict__ inv, const Ctrl* ctrl, IterParams p,
+                                int level, double* out) {
+    const int f32_from = ctrl->f32_from;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) out[v] = (double)s[inv[v]];
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride)
+        out[v] = walk_value(walk, p, f32_from, level, inv[v]);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,8 +516,13 @@ cudaError_t launch_validate_csr(const DeviceGraph& g, unsigned long long* d_bad,
 cudaError_t launch_init_walk(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                              cudaStream_t st) {
     (void)g;
-    if (fp32) return cudaErrorNotSupported;
-    init_walk_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((double*)b.walk, b.c, b.active, p);
+    (void)fp32;
+    init_walk_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((double*)b.walk, b.c, b.c32, b.active, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cert_init(const IterBuffers& b, const IterParams& p, cudaStream_t st) {
+    cert_init_kernel<<<1, 1, 0, st>>>(b.ctrl, p);
     return cudaGetLastError();
 }
 
@@ -440,17 +546,18 @@ cudaError_t prepare_kernels() {
 
 cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const double* cl,
                           const double* cu, const int32_t* cid, bool fp32, cudaStream_t st) {
-    if (fp32) return cudaErrorNotSupported;
+    (void)fp32;
     const int smem = SELECT_CAP * (int)sizeof(SelEntry);
-    select_kernel<double><<<1, SELECT_THREADS, smem, st>>>(cl, cu, cid, (const double*)b.walk, b.c, g.inv,
+    select_kernel<double><<<1, SELECT_THREADS, smem, st>>>(cl, cu, cid, (const double*)b.walk, b.c, b.c32, g.inv,
                                                            b.topk_id, b.topk_l, b.topk_u, b.ctrl, p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                          cudaStream_t st) {
-    if (fp32) return cudaErrorNotSupported;
-    count_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, g.perm, b.active, b.ctrl, p);
+    (void)fp32;
+    count_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, g.perm, b.active,
+                                                             b.ctrl, p);
     return cudaGetLastError();
 }
 
@@ -460,17 +567,17 @@ cudaError_t launch_finalize(const IterBuffers& b, const IterParams& p, cudaStrea
 }
 
 cudaError_t launch_bounds_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
-                              double* lower, double* upper, cudaStream_t st) {
-    if (fp32) return cudaErrorNotSupported;
-    bounds_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, g.inv, p, level, lower,
-                                                                 upper);
+                              double* lower, double* upper, double* err, cudaStream_t st) {
+    (void)fp32;
+    bounds_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, g.inv, b.ctrl, p,
+                                                                 level, lower, upper, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_walk_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
                             double* out, cudaStream_t st) {
-    if (fp32) return cudaErrorNotSupported;
-    walk_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, g.inv, p, level, out);
+    (void)fp32;
+    walk_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, g.inv, b.ctrl, p, level, out);
     return cudaGetLastError();
 }
 

@@ -13,11 +13,23 @@
 //   OCTET   16 < deg <= 128   eight lanes per row
 //   WARP    128 < deg <= 2048 one warp per row
 //   CHUNK   deg > 2048        one warp per 2048-arc chunk; spmv_chunk_fixup adds
-//                             a row's chunk sums in chunk order and finishes it
+//                             a row's chunk sums as a pairwise tree and finishes it
 // The walk vector is gathered with read-only loads (one L2 request per arc:
 // this access, not HBM bandwidth, bounds the kernel on power-law graphs).
-// Every row sum is accumulated in a fixed order, so results are reproducible.
+//
+// Row sums use a fixed order: each lane adds its terms eight at a time as a
+// pairwise tree and chains the eight-term sums; lanes then meet in a shuffle
+// tree.  Results are reproducible, and the longest chain of additions in any
+// row sum (max_sum_depth) is small; the FP32-certified mode needs it for its
+// rounding-error bound.
+//
+// Level types: FP64 mode computes every level in FP64.  The FP32-certified
+// mode starts in FP64 and computes the levels from Ctrl::f32_from on in FP32
+// (FP32 storage, FP32 sums, FP32 multiply by alpha), adding them to the
+// separate partial sum c32.
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "katz_common.cuh"
 
@@ -30,8 +42,9 @@ constexpr int BLOCK = 256;
 constexpr int WARPS = BLOCK / 32;
 
 struct Epi {
-    double* y;
-    double* c;
+    void* y;          // level r slot (double or float)
+    double* c64;
+    double* c32;
     uint8_t* active;
     const int32_t* perm;
     double* cand_l;
@@ -40,18 +53,32 @@ struct Epi {
     int64_t cand_cap;
     Ctrl* ctrl;
     double theta_prev;
+    BState bs;
 };
 
-// Finish row u: s_r(u) = alpha * sum, c_r = c_{r-1} + s_r, bounds, candidate
-// (candidates carry the original id).
-__device__ __forceinline__ void finish_row(int64_t u, double sum, const Epi& e, const IterParams& p) {
-    const double s = __dmul_rn(p.alpha, sum);
-    e.y[u] = s;
-    const double cn = __dadd_rn(e.c[u], s);
-    e.c[u] = cn;
+// Finish row u of an FP64 level: s = alpha * sum, c64 += s, bounds, candidate.
+// Finish row u of an FP32 level: s = fl32(alpha_f * sum), c32 += s, bounds, candidate.
+// Candidates carry the original id.
+template <typename Acc>
+__device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, const IterParams& p) {
+    double sd, c64, c32 = 0.0;
+    if constexpr (sizeof(Acc) == 8) {
+        sd = __dmul_rn(p.alpha, (double)sum);
+        ((double*)e.y)[u] = sd;
+        c64 = __dadd_rn(e.c64[u], sd);
+        e.c64[u] = c64;
+        if (e.c32) c32 = e.c32[u];
+    } else {
+        const float sf = __fmul_rn(p.alpha_f, (float)sum);
+        ((float*)e.y)[u] = sf;
+        sd = (double)sf;
+        c32 = __dadd_rn(e.c32[u], sd);
+        e.c32[u] = c32;
+        c64 = e.c64[u];
+    }
     if (e.active[u]) {
         double l, up;
-        node_bounds(cn, s, p, l, up);
+        node_bounds(c64, c32, sd, p, e.bs, l, up);
         if (l >= e.theta_prev) {
             const unsigned long long pos = atomicAdd(&e.ctrl->n_cand, 1ULL);
             if (pos < (unsigned long long)e.cand_cap) {
@@ -63,107 +90,168 @@ __device__ __forceinline__ void finish_row(int64_t u, double sum, const Epi& e, 
     }
 }
 
-// sum of x[col[j]] for j in [a, b) with stride `step` starting at a + first,
-// eight independent loads in flight, added in index order
-__device__ __forceinline__ double strided_sum(const int32_t* __restrict__ col, const double* __restrict__ x,
-                                              int64_t a, int64_t b, int first, int step) {
-    double s = 0.0;
+template <typename Acc>
+__device__ __forceinline__ Acc addA(Acc a, Acc b);
+template <>
+__device__ __forceinline__ double addA<double>(double a, double b) { return __dadd_rn(a, b); }
+template <>
+__device__ __forceinline__ float addA<float>(float a, float b) { return __fadd_rn(a, b); }
+
+// Sum of x[col[j]] for j in [a, b) with stride `step` from a + first: eight
+// loads in flight, each group of eight added as a pairwise tree (depth 3),
+// groups chained in index order.
+template <typename Tin, typename Acc>
+__device__ __forceinline__ Acc strided_sum(const int32_t* __restrict__ col, const Tin* __restrict__ x, int64_t a,
+                                           int64_t b, int first, int step) {
+    Acc s = (Acc)0;
     for (int64_t j = a + first; j < b; j += 8 * (int64_t)step) {
-        double v[8];
+        Acc v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int64_t jj = j + (int64_t)q * step;
-            v[q] = jj < b ? __ldg(x + col[jj]) : 0.0;
+            v[q] = jj < b ? (Acc)__ldg(x + col[jj]) : (Acc)0;
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) s = __dadd_rn(s, v[q]);
+        const Acc t = addA<Acc>(addA<Acc>(addA<Acc>(v[0], v[1]), addA<Acc>(v[2], v[3])),
+                                addA<Acc>(addA<Acc>(v[4], v[5]), addA<Acc>(v[6], v[7])));
+        s = addA<Acc>(s, t);
     }
     return s;
+}
+
+// One level: Tin = type of level r-1, Tout = type of level r (Acc = Tout).
+template <typename Off, typename Tin, typename Tout>
+__device__ __forceinline__ void spmv_rows(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                          const SpmvLayout& L, const Tin* __restrict__ x, const Epi& ep,
+                                          const int32_t* __restrict__ chunk_row,
+                                          const int64_t* __restrict__ chunk_first, double* chunk_part,
+                                          const IterParams& p) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t b = blockIdx.x;
+    typedef Tout Acc;
+    if (b >= L.blk_thread) {  // THREAD rows
+        const int64_t u = L.row_thread + (b - L.blk_thread) * BLOCK + tid;
+        if (u < L.n) finish_row<Acc>(u, strided_sum<Tin, Acc>(col, x, rowptr[u], rowptr[u + 1], 0, 1), ep, p);
+    } else if (b >= L.blk_octet) {  // OCTET rows
+        const int64_t u = L.row_octet + (b - L.blk_octet) * (BLOCK / 8) + (tid >> 3);
+        const int sub = tid & 7;
+        Acc s = (Acc)0;
+        if (u < L.row_thread) s = strided_sum<Tin, Acc>(col, x, rowptr[u], rowptr[u + 1], sub, 8);
+#pragma unroll
+        for (int off = 4; off; off >>= 1) s = addA<Acc>(s, __shfl_down_sync(FULL, s, off, 8));
+        if (sub == 0 && u < L.row_thread) finish_row<Acc>(u, s, ep, p);
+    } else if (b >= L.blk_warp) {  // WARP rows
+        const int64_t u = L.row_warp + (b - L.blk_warp) * WARPS + wid;
+        Acc s = (Acc)0;
+        if (u < L.row_octet) s = strided_sum<Tin, Acc>(col, x, rowptr[u], rowptr[u + 1], lane, 32);
+#pragma unroll
+        for (int off = 16; off; off >>= 1) s = addA<Acc>(s, __shfl_down_sync(FULL, s, off));
+        if (lane == 0 && u < L.row_octet) finish_row<Acc>(u, s, ep, p);
+    } else {  // CHUNK rows: one warp per chunk of CHUNK_ARCS arcs
+        const int64_t ch = b * WARPS + wid;
+        Acc s = (Acc)0;
+        if (ch < L.chunks) {
+            const int64_t u = chunk_row[ch];
+            const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+            const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+            s = strided_sum<Tin, Acc>(col, x, j0, j1, lane, 32);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) s = addA<Acc>(s, __shfl_down_sync(FULL, s, off));
+        if (lane == 0 && ch < L.chunks) chunk_part[ch] = (double)s;  // exact for FP32 sums
+    }
+}
+
+__device__ __forceinline__ Epi make_epi(void* y, double* c64, double* c32, uint8_t* active, const int32_t* perm,
+                                        double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap,
+                                        Ctrl* ctrl) {
+    return Epi{y, c64, c32, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl, ctrl->theta_prev, bstate(ctrl)};
 }
 
 template <typename Off>
 __global__ void __launch_bounds__(BLOCK)
 spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L, double* walk,
-                 double* c, uint8_t* active, const int32_t* __restrict__ perm, const int32_t* __restrict__ chunk_row,
-                 const int64_t* __restrict__ chunk_first, double* chunk_part, double* cand_l, double* cand_u,
-                 int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
+                 double* c64, double* c32, uint8_t* active, const int32_t* __restrict__ perm,
+                 const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first, double* chunk_part,
+                 double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
     if (ctrl->stop) return;
     const int r_cur = ctrl->r + 1;
-    const double* __restrict__ x = walk_slot(walk, p, r_cur - 1);
-    double* y = walk_slot(walk, p, r_cur);
-    const Epi ep{y, c, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl, ctrl->theta_prev};
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t b = blockIdx.x;
-
-    if (b >= L.blk_thread) {  // THREAD rows
-        const int64_t u = L.row_thread + (b - L.blk_thread) * BLOCK + tid;
-        if (u < L.n) finish_row(u, strided_sum(col, x, rowptr[u], rowptr[u + 1], 0, 1), ep, p);
-    } else if (b >= L.blk_octet) {  // OCTET rows
-        const int64_t u = L.row_octet + (b - L.blk_octet) * (BLOCK / 8) + (tid >> 3);
-        const int sub = tid & 7;
-        double s = 0.0;
-        if (u < L.row_thread) s = strided_sum(col, x, rowptr[u], rowptr[u + 1], sub, 8);
-#pragma unroll
-        for (int off = 4; off; off >>= 1) s = __dadd_rn(s, __shfl_down_sync(FULL, s, off, 8));
-        if (sub == 0 && u < L.row_thread) finish_row(u, s, ep, p);
-    } else if (b >= L.blk_warp) {  // WARP rows
-        const int64_t u = L.row_warp + (b - L.blk_warp) * WARPS + wid;
-        double s = 0.0;
-        if (u < L.row_octet) s = strided_sum(col, x, rowptr[u], rowptr[u + 1], lane, 32);
-#pragma unroll
-        for (int off = 16; off; off >>= 1) s = __dadd_rn(s, __shfl_down_sync(FULL, s, off));
-        if (lane == 0 && u < L.row_octet) finish_row(u, s, ep, p);
-    } else {  // CHUNK rows: one warp per chunk of CHUNK_ARCS arcs
-        const int64_t ch = b * WARPS + wid;
-        double s = 0.0;
-        if (ch < L.chunks) {
-            const int64_t u = chunk_row[ch];
-            const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
-            const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
-            s = strided_sum(col, x, j0, j1, lane, 32);
-        }
-#pragma unroll
-        for (int off = 16; off; off >>= 1) s = __dadd_rn(s, __shfl_down_sync(FULL, s, off));
-        if (lane == 0 && ch < L.chunks) chunk_part[ch] = s;
-    }
+    const int f32_from = ctrl->f32_from;
+    const double* xs = walk_slot(walk, p, r_cur - 1);
+    double* ys = walk_slot(walk, p, r_cur);
+    const Epi ep = make_epi(ys, c64, c32, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
+    if (r_cur < f32_from)
+        spmv_rows<Off, double, double>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
+    else if (r_cur == f32_from)
+        spmv_rows<Off, double, float>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
+    else
+        spmv_rows<Off, float, float>(rowptr, col, L, (const float*)xs, ep, chunk_row, chunk_first, chunk_part, p);
 }
 
-// CHUNK rows: add the chunk sums of each row in chunk order, then finish it.
-__global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c, uint8_t* active,
+// CHUNK rows: add the chunk sums of each row as a pairwise tree (in the
+// level's precision), then finish the row.
+template <typename Acc>
+__device__ __forceinline__ Acc chunk_tree(const double* __restrict__ part, int64_t first, int64_t count) {
+    Acc buf[64];
+    Acc total = (Acc)0;
+    for (int64_t base = 0; base < count; base += 64) {
+        const int m = (int)min((int64_t)64, count - base);
+        for (int q = 0; q < 64; ++q) buf[q] = q < m ? (Acc)part[first + base + q] : (Acc)0;
+        for (int w = 32; w >= 1; w >>= 1)
+            for (int q = 0; q < w; ++q) buf[q] = addA<Acc>(buf[2 * q], buf[2 * q + 1]);
+        total = addA<Acc>(total, buf[0]);
+    }
+    return total;
+}
+
+__global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double* c32, uint8_t* active,
                                  const int32_t* __restrict__ perm, const int64_t* __restrict__ chunk_first,
                                  const double* __restrict__ chunk_part, double* cand_l, double* cand_u,
                                  int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
     if (ctrl->stop) return;
     const int r_cur = ctrl->r + 1;
-    double* y = walk_slot(walk, p, r_cur);
-    const Epi ep{y, c, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl, ctrl->theta_prev};
+    double* ys = walk_slot(walk, p, r_cur);
+    const Epi ep = make_epi(ys, c64, c32, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= L.row_warp) return;
-    double s = 0.0;
-    for (int64_t ch = chunk_first[u]; ch < chunk_first[u + 1]; ++ch) s = __dadd_rn(s, chunk_part[ch]);
-    finish_row(u, s, ep, p);
+    const int64_t first = chunk_first[u], count = chunk_first[u + 1] - first;
+    if (r_cur < ctrl->f32_from)
+        finish_row<double>(u, chunk_tree<double>(chunk_part, first, count), ep, p);
+    else
+        finish_row<float>(u, chunk_tree<float>(chunk_part, first, count), ep, p);
 }
 
 }  // namespace
 
+// Longest chain of additions in one row sum: ceil(per-lane terms / 8) chained
+// groups + 3 (tree of 8) + shuffle levels + tree over chunks.
+int max_sum_depth(const SpmvLayout& L, int64_t max_chunks_per_row) {
+    auto lane_depth = [](int64_t terms) { return (int)((terms + 7) / 8) + 3; };
+    int d = lane_depth(16);                                   // THREAD
+    if (L.row_thread > L.row_octet) d = std::max(d, lane_depth(128 / 8) + 3);   // OCTET
+    if (L.row_octet > L.row_warp) d = std::max(d, lane_depth(2048 / 32) + 5);   // WARP
+    if (L.row_warp > 0)                                       // CHUNK: + tree of 64 + chained groups
+        d = std::max(d, lane_depth(CHUNK_ARCS / 32) + 5 + 6 + (int)((max_chunks_per_row + 63) / 64));
+    return d;
+}
+
 cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                         cudaStream_t st) {
-    if (fp32) return cudaErrorNotSupported;
+    (void)fp32;
     const SpmvLayout& L = g.layout;
     if (L.blocks_total > 0) {
         if (g.off64)
             spmv_rows_kernel<int64_t><<<(unsigned)L.blocks_total, BLOCK, 0, st>>>(
-                (const int64_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.active, g.perm, g.chunk_row,
+                (const int64_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.active, g.perm, g.chunk_row,
                 g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
         else
             spmv_rows_kernel<int32_t><<<(unsigned)L.blocks_total, BLOCK, 0, st>>>(
-                (const int32_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.active, g.perm, g.chunk_row,
+                (const int32_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.active, g.perm, g.chunk_row,
                 g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
     }
     if (L.row_warp > 0)
         spmv_chunk_fixup<<<(unsigned)((L.row_warp + 127) / 128), 128, 0, st>>>(
-            L, (double*)b.walk, b.c, b.active, g.perm, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id,
-            b.cand_cap, b.ctrl, p);
+            L, (double*)b.walk, b.c, b.c32, b.active, g.perm, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u,
+            b.cand_id, b.cand_cap, b.ctrl, p);
     return cudaGetLastError();
 }
 

@@ -6,13 +6,13 @@ import numpy as np
 REL_TOL = 1e-12  # FP64 mode: omega, l, u within 1e-12 relative of the oracle
 
 
-def tie_groups(ranking, l_ref, tol=REL_TOL):
+def tie_groups(ranking, l_ref, tol=REL_TOL, atol=0.0):
     """Split a ranking into runs of nodes whose reference lower bounds agree
-    to within rounding (relative tol); the order inside a run is not unique."""
+    to within tol (relative) + atol; the order inside a run is not unique."""
     groups, cur = [], [int(ranking[0])] if len(ranking) else []
     for a, b in zip(ranking, ranking[1:]):
         la, lb = l_ref[a], l_ref[b]
-        if abs(la - lb) <= tol * max(abs(la), abs(lb)):
+        if abs(la - lb) <= tol * max(abs(la), abs(lb)) + atol:
             cur.append(int(b))
         else:
             groups.append(cur)
@@ -22,7 +22,7 @@ def tie_groups(ranking, l_ref, tol=REL_TOL):
     return groups
 
 
-def assert_same_ranking(got, ref, l_ref, tol=REL_TOL):
+def assert_same_ranking(got, ref, l_ref, tol=REL_TOL, atol=0.0):
     """Identical certified order, up to permutations inside runs of
     rounding-level ties (compared as sets); the last run may be cut by k, so
     there the GPU's members must be tied with the oracle's k-th node."""
@@ -31,7 +31,7 @@ def assert_same_ranking(got, ref, l_ref, tol=REL_TOL):
     assert got.shape == ref.shape, (got.shape, ref.shape)
     if np.array_equal(got, ref):
         return 0
-    gref = tie_groups(ref, l_ref, tol)
+    gref = tie_groups(ref, l_ref, tol, atol)
     pos = 0
     for gi, grp in enumerate(gref):
         seg = got[pos:pos + len(grp)]
@@ -40,7 +40,7 @@ def assert_same_ranking(got, ref, l_ref, tol=REL_TOL):
         else:
             lk = l_ref[grp[0]]
             for v in seg:
-                assert abs(l_ref[v] - lk) <= tol * abs(lk), f"rank {pos}: node {v} not tied with {grp[0]}"
+                assert abs(l_ref[v] - lk) <= tol * abs(lk) + atol, f"rank {pos}: node {v} not tied with {grp[0]}"
         pos += len(grp)
     return sum(len(g) > 1 for g in gref)
 

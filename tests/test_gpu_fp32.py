@@ -1,0 +1,100 @@
+"""FP32-certified mode: walk levels from Ctrl::f32_from on are carried in FP32
+and the bounds are widened by a proven rounding-error bound, evaluated with
+directed rounding.  Checks: the certified bounds bracket the exact Katz score
+(exact rational arithmetic) at every iteration, the certified ranking agrees
+with the FP64 oracle up to eps-ties, each node's deviation from the oracle's
+bounds stays inside the reported widening, and FP32 levels are really used."""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import sympy
+
+import graphgen as gg
+import oracle
+from tests.parity import assert_same_ranking
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+K = pytest.importorskip("paper_1807_03847_gb300")
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _exact_katz(rowptr, col, alpha: Fraction):
+    n = len(rowptr) - 1
+    A = sympy.zeros(n, n)
+    for v in range(n):
+        for j in range(rowptr[v], rowptr[v + 1]):
+            A[v, int(col[j])] += 1
+    a = sympy.Rational(alpha.numerator, alpha.denominator)
+    z = (sympy.eye(n) - a * A).LUsolve(sympy.ones(n, 1))
+    return [Fraction(int(sympy.fraction(x)[0]), int(sympy.fraction(x)[1])) for x in a * A * z]
+
+
+def _cert(g, k, eps, fp32_from=0, r_max=256, alpha=0.0, check=True):
+    opts = K.katz_default_opts(precision=K.KATZ_FP32_CERT, fp32_from=fp32_from, r_max=r_max, keep_history=1)
+    h = K.Katz(_dev(g.rowptr), _dev(g.col), opts)
+    info = h.rank(alpha, k, eps, check=check)
+    out = dict(info=info, ranking=h.ranking(min(k, g.n)) if info.status in (0,) else None)
+    out["l"], out["u"], out["err"] = h.bounds()
+    h.close()
+    return out
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("fp32_from", [2, 3])
+def test_certified_bounds_bracket_exact_katz(seed, fp32_from):
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(6, 12))
+    pairs = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < 0.4] or [(0, 1)]
+    u, v = zip(*pairs)
+    g = gg.from_edges(n, np.array(u), np.array(v))
+    D = g.deg_max()
+    alpha = Fraction(1, D + 1)
+    cx = np.array([float(x) for x in _exact_katz(g.rowptr, g.col, alpha)])
+    for r_max in (fp32_from, fp32_from + 1, fp32_from + 4, 40):
+        got = _cert(g, n, 1e-300, fp32_from=fp32_from, r_max=r_max, alpha=float(alpha), check=False)
+        assert got["info"].r <= r_max
+        assert np.all(got["l"] <= cx) and np.all(got["u"] >= cx), (r_max, got["l"] - cx, got["u"] - cx)
+
+
+@pytest.mark.parametrize("wl,k", [("er16k", 100), ("rmat14", 200)])
+def test_fp32_certified_ranking_matches_oracle(wl, k):
+    g = gg.workload("er16k") if wl == "er16k" else gg.rmat(14, 16, seed=77)
+    eps = 1e-9
+    ref = oracle.katz_static(g.rowptr, g.col, 0.0, k, eps, r_max=256)
+    got = _cert(g, k, eps)
+    info = got["info"]
+    assert info.converged == 1 and info.r >= ref["r"]
+    # identical certified order up to pairs closer than eps (both are certified)
+    assert_same_ranking(got["ranking"], ref["ranking"], ref["l"], atol=eps)
+    # per-node deviation from the FP64 oracle's bounds lies within the
+    # reported rounding widening (plus the oracle's own FP64 rounding)
+    if info.r == ref["r"]:
+        slack = got["err"] + 1e-12 * np.abs(ref["l"]) + 1e-300
+        assert np.all(np.abs(got["l"] - ref["l"]) <= slack)
+        assert np.all(np.abs(got["u"] - ref["u"]) <= slack)
+    assert np.all(got["l"] <= got["u"])
+
+
+def test_fp32_levels_are_used_and_certify():
+    g = gg.rmat(16, 16, seed=16)
+    got = _cert(g, 1000, 1e-9)
+    assert got["info"].converged == 1
+    assert got["info"].fp32_levels >= 1
+    ref = oracle.katz_static(g.rowptr, g.col, 0.0, 1000, 1e-9, r_max=256)
+    assert_same_ranking(got["ranking"], ref["ranking"], ref["l"], atol=1e-9)
+
+
+def test_stall_reports_precision_error():
+    # all levels in FP32 and an eps far below what FP32 can separate on a
+    # graph with near-ties: the widening overtakes the tail, EPRECISION
+    g = gg.rmat(12, 16, seed=3)
+    got = _cert(g, 400, 1e-15, fp32_from=2, check=False)
+    assert got["info"].status == 6  # KATZ_EPRECISION
+    assert np.all(got["l"] <= got["u"])
