@@ -39,6 +39,12 @@ WORKLOADS = {
                    desc="undirected R-MAT scale 21 (2,097,152 vertices), edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), "
                         "symmetrised and deduplicated, int32 CSR; alpha=1/(deg_max+1); certified top-1000; eps=1e-9 "
                         "(profiling case: col array larger than L2, a few GB on the device)"),
+    "rmat24": dict(graph="rmat24", k=1000, eps=1e-9, alpha=0.0, precision=0,
+                   desc="undirected R-MAT scale 24 (16,777,216 vertices), edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), "
+                        "symmetrised and deduplicated, int32 CSR; alpha=1/(deg_max+1); certified top-1000; eps=1e-9"),
+    "rmat24-halfalpha": dict(graph="rmat24", k=1000, eps=1e-9, alpha="half", precision=0,
+                             desc="undirected R-MAT scale 24, edge factor 16; alpha=0.5/deg_max; certified top-1000; "
+                                  "eps=1e-9"),
     "er16k": dict(graph="er16k", k=100, eps=1e-9, alpha=0.0, precision=0,
                   desc="undirected Erdos-Renyi n=16384, m=131072, int32 CSR; alpha=1/(deg_max+1); certified top-100; "
                        "eps=1e-9"),
@@ -266,6 +272,8 @@ def main():
     fp32 = wl["precision"] == 1
     g = gg.workload(wl["graph"])
     n, nnz = g.n, g.nnz
+    if wl["alpha"] == "half":
+        wl["alpha"] = 0.5 / g.deg_max()
     stream = torch.cuda.current_stream()
     rowptr_d = torch.from_numpy(g.rowptr).cuda()
     col_d = torch.from_numpy(g.col).cuda()
@@ -373,6 +381,7 @@ def main():
                        "l2": "flushed between steps (256 MB write); col array alone is larger than L2"},
             "time_to_certified_ms": 1e3 * total_s_max / args.steps,
             "spmv_gteps": nnz / t_launch / 1e9,
+            "fp32_levels": int(infos[-1].fp32_levels),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "ranking_head": [int(x) for x in ranking[:5]],
         }

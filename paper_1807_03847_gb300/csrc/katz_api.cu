@@ -60,6 +60,8 @@ void free_iter(katz_handle* h) {
     cudaFree(b.walk);
     cudaFree(b.c);
     cudaFree(b.c32);
+    cudaFree(b.lb);
+    cudaFree(b.ub);
     cudaFree(b.active);
     cudaFree(b.cand_l);
     cudaFree(b.cand_u);
@@ -93,7 +95,11 @@ katz_status ensure_iter_buffers(katz_handle* h) {
     KALLOC(walk, (size_t)slots * stride * esz);
     b.walk = walk;
     KALLOC(b.c, n);
-    if (h->fp32) KALLOC(b.c32, n);
+    if (h->fp32) {
+        KALLOC(b.c32, n);
+        KALLOC(b.lb, n);
+        KALLOC(b.ub, n);
+    }
     KALLOC(b.active, n);
     KALLOC(b.cand_l, n);
     KALLOC(b.cand_u, n);

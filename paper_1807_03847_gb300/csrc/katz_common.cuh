@@ -152,6 +152,8 @@ struct IterBuffers {
     void* walk = nullptr;     // double* or float*
     double* c = nullptr;       // c64: Katz partial sum over the FP64 levels
     double* c32 = nullptr;     // FP32-certified mode: partial sum over the FP32 levels
+    double* lb = nullptr;      // FP32-certified mode: stored bounds of active nodes, kept
+    double* ub = nullptr;      //   monotone (l = max over levels, u = min over levels)
     uint8_t* active = nullptr;
     double* cand_l = nullptr;
     double* cand_u = nullptr;

@@ -54,13 +54,18 @@ __global__ void validate_kernel(const Off* __restrict__ rowptr, const int32_t* _
 }
 
 template <typename T>
-__global__ void init_walk_kernel(T* walk, double* c, double* c32, uint8_t* active, IterParams p) {
+__global__ void init_walk_kernel(T* walk, double* c, double* c32, double* lb, double* ub, uint8_t* active,
+                                 IterParams p) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = tid; v < p.n; v += stride) {
         walk[v] = (T)1;  // s_0 = omega_0 = 1 (Alg. 1)
         c[v] = 0.0;      // c_0 = 0
         if (c32) c32[v] = 0.0;
+        if (lb) {
+            lb[v] = 0.0;
+            ub[v] = 1.0 / 0.0;
+        }
         active[v] = 1;   // M = V
     }
     for (int64_t s = tid; s < p.slots; s += stride) walk[(size_t)s * p.stride + p.n] = (T)0;  // sentinel
@@ -138,8 +143,8 @@ __device__ __forceinline__ bool sel_before(const SelEntry& a, const SelEntry& b)
 template <typename T>
 __global__ void __launch_bounds__(SELECT_THREADS)
 select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, const int32_t* __restrict__ cid,
-              const T* walk, const double* c, const double* c32, const int32_t* __restrict__ inv, int32_t* topk_id,
-              double* topk_l, double* topk_u, Ctrl* ctrl, IterParams p) {
+              const T* walk, const double* c, const double* c32, const double* lb, const int32_t* __restrict__ inv,
+              int32_t* topk_id, double* topk_l, double* topk_u, Ctrl* ctrl, IterParams p) {
     extern __shared__ SelEntry sel[];
     __shared__ unsigned int s_cnt;
     __shared__ double s_tau;
@@ -168,7 +173,8 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
             for (int q = tid; q < kprev; q += SELECT_THREADS) {
                 const int32_t v = inv[topk_id[q]];
                 double l, u;
-                node_bounds(c[v], c32 ? c32[v] : 0.0, walk_value(walk, p, f32_from, r_cur, v), p, bs, l, u);
+                if (p.cert) l = lb[v];
+                else node_bounds(c[v], 0.0, walk_value(walk, p, f32_from, r_cur, v), p, bs, l, u);
                 m = fmin(m, l);
             }
             for (int off = 16; off; off >>= 1) m = fmin(m, __shfl_xor_sync(FULL, m, off));
@@ -244,6 +250,7 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void count_kernel(const T* walk, const double* __restrict__ c, const double* __restrict__ c32,
+                             const double* __restrict__ lb, const double* __restrict__ ub,
                              const int32_t* __restrict__ perm, uint8_t* active, Ctrl* ctrl, IterParams p) {
     if (ctrl->stop || (ctrl->flags & F_NEED_BIG)) return;
     const int r_cur = ctrl->r + 1;
@@ -259,7 +266,12 @@ __global__ void count_kernel(const T* walk, const double* __restrict__ c, const 
         const double sv = walk_value(walk, p, f32_from, r_cur, v);
         const double c64v = c[v], c32v = c32 ? c32[v] : 0.0;
         double l, u;
-        node_bounds(c64v, c32v, sv, p, bs, l, u);
+        if (p.cert) {
+            l = lb[v];
+            u = ub[v];
+        } else {
+            node_bounds(c64v, c32v, sv, p, bs, l, u);
+        }
         const int32_t ov = perm[v];  // ties are broken by the original id
         if (!ranks_before(l, ov, th, thid) && !(l == th && ov == thid)) {
             if (__dsub_rn(u, p.eps) < th) {
@@ -403,8 +415,10 @@ __global__ void finalize_kernel(const double* __restrict__ topk_l, const double*
 
 template <typename T>
 __global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, const double* __restrict__ c32,
-                                  const int32_t* __restrict__ inv, const Ctrl* ctrl, IterParams p, int level,
-                                  double* lower, double* upper, double* err) {
+                                  const double* __restrict__ lb, const double* __restrict__ ub,
+                                  const uint8_t* __restrict__ active, const int32_t* __restrict__ inv,
+                                  const Ctrl* ctrl, IterParams p, int level, double* lower, double* upper,
+                                  double* err) {
     const BState bs = bstate(ctrl);
     const int f32_from = ctrl->f32_from;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -414,6 +428,10 @@ __global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, c
         const double c32v = c32 ? c32[w] : 0.0;
         double l, u;
         node_bounds(c[w], c32v, sv, p, bs, l, u);
+        if (p.cert && active[w]) {
+            l = fmax(l, lb[w]);
+            u = fmin(u, ub[w]);
+        }
         if (err) {  // widening added for rounding (zero in FP64 mode)
             err[v] = p.cert ? c[w] * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32) +
                                   p.ag_hi * sv * (bs.his - 1.0) + p.alpha * sv * (1.0 - bs.los)
@@ -517,7 +535,7 @@ cudaError_t launch_init_walk(const DeviceGraph& g, const IterBuffers& b, const I
                              cudaStream_t st) {
     (void)g;
     (void)fp32;
-    init_walk_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((double*)b.walk, b.c, b.c32, b.active, p);
+    init_walk_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, p);
     return cudaGetLastError();
 }
 
@@ -548,7 +566,7 @@ cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const Iter
                           const double* cu, const int32_t* cid, bool fp32, cudaStream_t st) {
     (void)fp32;
     const int smem = SELECT_CAP * (int)sizeof(SelEntry);
-    select_kernel<double><<<1, SELECT_THREADS, smem, st>>>(cl, cu, cid, (const double*)b.walk, b.c, b.c32, g.inv,
+    select_kernel<double><<<1, SELECT_THREADS, smem, st>>>(cl, cu, cid, (const double*)b.walk, b.c, b.c32, b.lb, g.inv,
                                                            b.topk_id, b.topk_l, b.topk_u, b.ctrl, p);
     return cudaGetLastError();
 }
@@ -556,8 +574,8 @@ cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const Iter
 cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                          cudaStream_t st) {
     (void)fp32;
-    count_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, g.perm, b.active,
-                                                             b.ctrl, p);
+    count_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, b.lb, b.ub, g.perm,
+                                                             b.active, b.ctrl, p);
     return cudaGetLastError();
 }
 
@@ -569,8 +587,8 @@ cudaError_t launch_finalize(const IterBuffers& b, const IterParams& p, cudaStrea
 cudaError_t launch_bounds_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
                               double* lower, double* upper, double* err, cudaStream_t st) {
     (void)fp32;
-    bounds_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, g.inv, b.ctrl, p,
-                                                                 level, lower, upper, err);
+    bounds_out_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, b.lb, b.ub,
+                                                                 b.active, g.inv, b.ctrl, p, level, lower, upper, err);
     return cudaGetLastError();
 }
 

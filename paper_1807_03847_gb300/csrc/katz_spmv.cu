@@ -45,6 +45,8 @@ struct Epi {
     void* y;          // level r slot (double or float)
     double* c64;
     double* c32;
+    double* lb;       // cert mode: monotone stored bounds
+    double* ub;
     uint8_t* active;
     const int32_t* perm;
     double* cand_l;
@@ -79,6 +81,12 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
     if (e.active[u]) {
         double l, up;
         node_bounds(c64, c32, sd, p, e.bs, l, up);
+        if (p.cert) {  // both the new and the stored bounds are valid: keep the tighter ones
+            l = fmax(l, e.lb[u]);
+            up = fmin(up, e.ub[u]);
+            e.lb[u] = l;
+            e.ub[u] = up;
+        }
         if (l >= e.theta_prev) {
             const unsigned long long pos = atomicAdd(&e.ctrl->n_cand, 1ULL);
             if (pos < (unsigned long long)e.cand_cap) {
@@ -161,16 +169,17 @@ __device__ __forceinline__ void spmv_rows(const Off* __restrict__ rowptr, const 
     }
 }
 
-__device__ __forceinline__ Epi make_epi(void* y, double* c64, double* c32, uint8_t* active, const int32_t* perm,
-                                        double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap,
-                                        Ctrl* ctrl) {
-    return Epi{y, c64, c32, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl, ctrl->theta_prev, bstate(ctrl)};
+__device__ __forceinline__ Epi make_epi(void* y, double* c64, double* c32, double* lb, double* ub, uint8_t* active,
+                                        const int32_t* perm, double* cand_l, double* cand_u, int32_t* cand_id,
+                                        int64_t cand_cap, Ctrl* ctrl) {
+    return Epi{y,      c64,     c32,     lb,       ub,    active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl,
+               ctrl->theta_prev, bstate(ctrl)};
 }
 
 template <typename Off>
 __global__ void __launch_bounds__(BLOCK)
 spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L, double* walk,
-                 double* c64, double* c32, uint8_t* active, const int32_t* __restrict__ perm,
+                 double* c64, double* c32, double* lb, double* ub, uint8_t* active, const int32_t* __restrict__ perm,
                  const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first, double* chunk_part,
                  double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
     if (ctrl->stop) return;
@@ -178,7 +187,7 @@ spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col
     const int f32_from = ctrl->f32_from;
     const double* xs = walk_slot(walk, p, r_cur - 1);
     double* ys = walk_slot(walk, p, r_cur);
-    const Epi ep = make_epi(ys, c64, c32, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
+    const Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
     if (r_cur < f32_from)
         spmv_rows<Off, double, double>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
     else if (r_cur == f32_from)
@@ -203,14 +212,15 @@ __device__ __forceinline__ Acc chunk_tree(const double* __restrict__ part, int64
     return total;
 }
 
-__global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double* c32, uint8_t* active,
+__global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double* c32, double* lb, double* ub,
+                                 uint8_t* active,
                                  const int32_t* __restrict__ perm, const int64_t* __restrict__ chunk_first,
                                  const double* __restrict__ chunk_part, double* cand_l, double* cand_u,
                                  int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
     if (ctrl->stop) return;
     const int r_cur = ctrl->r + 1;
     double* ys = walk_slot(walk, p, r_cur);
-    const Epi ep = make_epi(ys, c64, c32, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
+    const Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= L.row_warp) return;
     const int64_t first = chunk_first[u], count = chunk_first[u + 1] - first;
@@ -241,16 +251,16 @@ cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterPa
     if (L.blocks_total > 0) {
         if (g.off64)
             spmv_rows_kernel<int64_t><<<(unsigned)L.blocks_total, BLOCK, 0, st>>>(
-                (const int64_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.active, g.perm, g.chunk_row,
+                (const int64_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, g.chunk_row,
                 g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
         else
             spmv_rows_kernel<int32_t><<<(unsigned)L.blocks_total, BLOCK, 0, st>>>(
-                (const int32_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.active, g.perm, g.chunk_row,
+                (const int32_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, g.chunk_row,
                 g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
     }
     if (L.row_warp > 0)
         spmv_chunk_fixup<<<(unsigned)((L.row_warp + 127) / 128), 128, 0, st>>>(
-            L, (double*)b.walk, b.c, b.c32, b.active, g.perm, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u,
+            L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u,
             b.cand_id, b.cand_cap, b.ctrl, p);
     return cudaGetLastError();
 }

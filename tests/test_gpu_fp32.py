@@ -98,3 +98,27 @@ def test_stall_reports_precision_error():
     got = _cert(g, 400, 1e-15, fp32_from=2, check=False)
     assert got["info"].status == 6  # KATZ_EPRECISION
     assert np.all(got["l"] <= got["u"])
+
+
+def test_certified_bounds_monotone_across_the_fp32_switch():
+    """Lemma 2 must hold for the certified bounds (the candidate filter and
+    permanent deactivation rely on it), also where the widening grows at the
+    switch to FP32 levels."""
+    g = gg.rmat(15, 16, seed=5)
+    k, eps = 300, 1e-9
+    full = _cert(g, k, eps, fp32_from=3)
+    assert full["info"].converged == 1 and len(full["ranking"]) == k
+    top = full["ranking"]
+    prev_l = prev_u = None
+    for R in range(1, full["info"].r + 1):
+        got = _cert(g, k, eps, fp32_from=3, r_max=R, check=False)
+        l, u = got["l"][top], got["u"][top]
+        if prev_l is not None:
+            assert np.all(l >= prev_l) and np.all(u <= prev_u), R
+        prev_l, prev_u = l, u
+
+
+def test_fp32_switch_keeps_k_candidates_on_a_larger_graph():
+    g = gg.rmat(18, 16, seed=18)
+    got = _cert(g, 1000, 1e-9)
+    assert got["info"].converged == 1 and got["info"].k == 1000 and len(got["ranking"]) == 1000
