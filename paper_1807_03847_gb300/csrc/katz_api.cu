@@ -337,6 +337,18 @@ void katz_destroy(katz_h h) {
     cudaFree(h->d_hist256);
     cudaFree(h->d_count);
     cudaFree(h->d_scratch);
+    {
+        DynBuffers& d = h->dyn;
+        for (void* ptr : {(void*)d.src, (void*)d.dst, (void*)d.ins, (void*)d.pos_a, (void*)d.pos_b, (void*)d.table,
+                          (void*)d.err, (void*)d.delta, (void*)d.ins_cnt, (void*)d.cursor, (void*)d.touched,
+                          (void*)d.ins_start, (void*)d.ins_rows, (void*)d.n_ins_rows, (void*)d.bucket,
+                          (void*)d.vbits, (void*)d.frontier, (void*)d.fsize})
+            cudaFree(ptr);
+        cudaFree(h->col_spare);
+        cudaFree(h->rp_new);
+        cudaFree(h->deg_tmp);
+        cudaFree(h->scan_sums);
+    }
     cudaFreeHost(h->h_ctrl);
     drop_graph(h);
     for (cudaEvent_t ev : h->sp_ev) cudaEventDestroy(ev);
@@ -684,15 +696,250 @@ katz_status katz_get_trace(katz_h h, int64_t* active_per_iter, int32_t cap) {
     return KATZ_OK;
 }
 
+// Algorithm 2 on the device: validate, apply, repair s_1..s_r, re-derive the
+// active set and continue iterating until converged() holds again.
 katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t* dst, const uint8_t* is_insert,
                                     int64_t m, katz_info* info) {
-    (void)src;
-    (void)dst;
-    (void)is_insert;
-    (void)m;
-    (void)info;
     if (!h) return KATZ_EINVAL;
-    return fail(h, KATZ_ESTATE, "dynamic updates are not available in this build");
+    h->err.clear();
+    if (!h->ranked) return fail(h, KATZ_ESTATE, "rank the graph before updating it");
+    if (!h->opts.keep_history) return fail(h, KATZ_ESTATE, "dynamic updates need keep_history = 1");
+    if (h->fp32) return fail(h, KATZ_ESTATE, "dynamic updates run in FP64 mode");
+    if (!h->opts.undirected) return fail(h, KATZ_ESTATE, "dynamic updates take undirected handles");
+    if (m < 0 || (m > 0 && (!src || !dst || !is_insert))) return fail(h, KATZ_EINVAL, "bad batch arguments");
+    cudaError_t e;
+    DeviceGraph& g = h->g;
+    DynBuffers& d = h->dyn;
+    const int64_t n = g.n;
+    const int r = h->r;
+    if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+    // ---- buffers --------------------------------------------------------------
+#define DALLOC(ptr, cnt)                                                      \
+    if ((e = dmalloc(&(ptr), (size_t)(cnt))) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc " #ptr);
+    if (!d.delta) {
+        DALLOC(d.delta, n);
+        DALLOC(d.ins_cnt, n);
+        DALLOC(d.cursor, n);
+        DALLOC(d.touched, n);
+        DALLOC(d.ins_start, n);
+        DALLOC(d.vbits, (n + 31) / 32);
+        DALLOC(d.frontier, n);
+        DALLOC(d.fsize, 1);
+        DALLOC(d.n_ins_rows, 1);
+        DALLOC(d.err, 1);
+        DALLOC(h->rp_new, n + 1);
+        DALLOC(h->deg_tmp, n + 1);
+        DALLOC(h->scan_sums, scan_blocks(n + 1));
+        if ((e = cudaMemsetAsync(d.delta, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.ins_cnt, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.cursor, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.touched, 0, (size_t)n, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "memset dynamic scratch");
+        h->col_cap = g.nnz;
+    }
+    if (m > d.cap) {
+        cudaFree(d.src);
+        cudaFree(d.dst);
+        cudaFree(d.ins);
+        cudaFree(d.pos_a);
+        cudaFree(d.pos_b);
+        cudaFree(d.ins_rows);
+        cudaFree(d.bucket);
+        cudaFree(d.table);
+        d = DynBuffers{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, d.err, d.delta, d.ins_cnt,
+                       d.cursor, d.touched, d.ins_start, nullptr, d.n_ins_rows, nullptr, d.vbits, d.frontier,
+                       d.fsize};
+        const int64_t cap = std::max<int64_t>(m, 1024);
+        DALLOC(d.src, cap);
+        DALLOC(d.dst, cap);
+        DALLOC(d.ins, cap);
+        DALLOC(d.pos_a, cap);
+        DALLOC(d.pos_b, cap);
+        DALLOC(d.ins_rows, 2 * cap);
+        DALLOC(d.bucket, 2 * cap);
+        int64_t tsize = 1;
+        while (tsize < 4 * cap) tsize <<= 1;
+        DALLOC(d.table, tsize);
+        d.table_mask = tsize - 1;
+        d.cap = cap;
+        if ((e = cudaMemsetAsync(d.table, 0, (size_t)tsize * sizeof(unsigned long long), h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "memset table");
+    }
+#undef DALLOC
+    if (m > 0) {
+        if ((e = cudaMemcpyAsync(d.src, src, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, h->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d.dst, dst, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, h->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d.ins, is_insert, (size_t)m, cudaMemcpyDefault, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "copy batch");
+    }
+    int64_t full_levels = 0, affected = 0;
+    if (m > 0) {
+        // ---- validate (nothing changes unless the whole batch is valid) ----------
+        if ((e = cudaMemsetAsync(d.err, 0, sizeof(int32_t), h->stream)) != cudaSuccess ||
+            (e = dyn_validate(g, d, m, h->D, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "validate batch");
+        int32_t err = 0;
+        if ((e = cudaMemcpyAsync(&err, d.err, sizeof(err), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "validate sync");
+        if (err) {
+            if ((e = dyn_clear(g, d, m, h->stream)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+                return cuda_fail(h, e, "clear batch");
+            if (err & DYN_E_INVAL)
+                return fail(h, KATZ_EINVAL, "batch violates the preconditions (range, self-loop, duplicate pair, "
+                                            "inserted edge present or deleted edge absent)");
+            return fail(h, KATZ_EALPHA, "a row would exceed the degree bound D");
+        }
+        // ---- apply: new offsets, rows rebuilt into the spare col buffer -----------
+        if ((e = dyn_prepare(g, d, m, h->rp_new, h->deg_tmp, h->scan_sums, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "prepare rebuild");
+        int64_t nnz_new = 0;
+        if ((e = cudaMemcpyAsync(&nnz_new, h->rp_new + n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "rebuild size");
+        if (!g.off64 && n + nnz_new >= 0x7fffffffLL) {
+            dyn_clear(g, d, m, h->stream);
+            return fail(h, KATZ_EINVAL, "the graph would outgrow 32-bit offsets; create it with more headroom");
+        }
+        if (nnz_new > h->col_spare_cap) {
+            cudaFree(h->col_spare);
+            h->col_spare = nullptr;
+            const int64_t cap = nnz_new + nnz_new / 16 + 1024;
+            if ((e = dmalloc(&h->col_spare, (size_t)cap)) != cudaSuccess) {
+                h->col_spare_cap = 0;
+                dyn_clear(g, d, m, h->stream);
+                return cuda_fail(h, e, "cudaMalloc col");
+            }
+            h->col_spare_cap = cap;
+        }
+        if ((e = dyn_rebuild(g, d, m, h->rp_new, h->col_spare, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "rebuild rows");
+        std::swap(g.col, h->col_spare);
+        std::swap(h->col_cap, h->col_spare_cap);
+        g.nnz = nnz_new;
+        if ((e = dyn_clear(g, d, m, h->stream)) != cudaSuccess) return cuda_fail(h, e, "clear batch");
+        // chunk table of the CHUNK rows from their new degrees
+        {
+            const int64_t rw = g.layout.row_warp;
+            std::vector<int64_t> hrp((size_t)rw + 1);
+            if ((e = cudaMemcpyAsync(hrp.data(), h->rp_new, hrp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                     h->stream)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+                return cuda_fail(h, e, "copy rowptr head");
+            std::vector<int64_t> first((size_t)rw + 1, 0);
+            for (int64_t u = 0; u < rw; ++u)
+                first[u + 1] = first[u] + (hrp[u + 1] - hrp[u] + CHUNK_ARCS - 1) / CHUNK_ARCS;
+            const int64_t chunks = first[rw];
+            if (chunks > g.layout.chunks) {
+                cudaFree(g.chunk_row);
+                cudaFree(g.chunk_part);
+                g.chunk_row = nullptr;
+                g.chunk_part = nullptr;
+                if ((e = dmalloc(&g.chunk_row, (size_t)chunks)) != cudaSuccess ||
+                    (e = dmalloc(&g.chunk_part, (size_t)chunks)) != cudaSuccess)
+                    return cuda_fail(h, e, "cudaMalloc chunks");
+            }
+            std::vector<int32_t> crow((size_t)std::max<int64_t>(chunks, 1));
+            for (int64_t u = 0; u < rw; ++u)
+                for (int64_t q = first[u]; q < first[u + 1]; ++q) crow[q] = (int32_t)u;
+            if ((e = cudaMemcpyAsync(g.chunk_first, first.data(), first.size() * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+                (chunks > 0 && (e = cudaMemcpyAsync(g.chunk_row, crow.data(), (size_t)chunks * sizeof(int32_t),
+                                                    cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) ||
+                (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+                return cuda_fail(h, e, "copy chunks");
+            g.layout = make_layout(n, g.layout.row_warp, g.layout.row_octet, g.layout.row_thread, chunks);
+        }
+        drop_graph(h);  // captured launches hold the old arrays and layout
+        // ---- repair s_1..s_r: affected rows only, or whole levels once the
+        //      affected set is large (Sec. 4) ------------------------------------------
+        if ((e = dyn_seed(g, d, m, h->stream)) != cudaSuccess) return cuda_fail(h, e, "seed frontier");
+        unsigned long long fs = 0;
+        if ((e = cudaMemcpyAsync(&fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "frontier size");
+        const double tau = h->opts.frontier_abort_frac > 0 ? h->opts.frontier_abort_frac : 0.05;
+        int64_t lo = 0, hi = (int64_t)fs;
+        bool full = false;
+        for (int i = 1; i <= r; ++i) {
+            if (!full && (double)hi > tau * (double)n) full = true;
+            if (full) {
+                if ((e = launch_spmv_store(g, h->b, h->p, i, h->stream)) != cudaSuccess)
+                    return cuda_fail(h, e, "full level");
+                ++full_levels;
+                continue;
+            }
+            if ((e = launch_rows_store(g, h->b, h->p, d.frontier, d.fsize, hi, i, h->stream)) != cudaSuccess)
+                return cuda_fail(h, e, "repair rows");
+            if (i < r) {
+                if ((e = dyn_expand(g, d, lo, hi, h->stream)) != cudaSuccess) return cuda_fail(h, e, "expand");
+                if ((e = cudaMemcpyAsync(&fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+                    (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+                    return cuda_fail(h, e, "frontier size");
+                lo = hi;
+                hi = (int64_t)fs;
+            }
+        }
+        affected = full ? n : hi;
+        if ((e = dyn_recompute_c(g, h->b, d, h->p, r, full, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "recompute c");
+    }
+    // ---- bounds, reactivation, converged() at level r, then more iterations ------
+    h->launches = 0;
+    h->big_paths = 0;
+    if ((e = dyn_reactivate(g, h->b, h->p, r, h->stream)) != cudaSuccess ||
+        (e = launch_select(g, h->b, h->p, h->b.cand_l, h->b.cand_u, h->b.cand_id, h->fp32, h->stream)) != cudaSuccess ||
+        (e = launch_count(g, h->b, h->p, h->fp32, h->stream)) != cudaSuccess ||
+        (e = launch_finalize(h->b, h->p, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "re-check");
+    if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "re-check sync");
+    katz_status st = KATZ_OK;
+    if (h->h_ctrl->flags & F_NEED_BIG) {
+        st = big_select(h);
+        if (st != KATZ_OK) return st;
+        if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "re-check sync");
+    }
+    if (!h->h_ctrl->stop) {
+        st = run_loop(h);
+        if (st != KATZ_OK) return st;
+    }
+    if ((e = cudaEventRecord(h->ev1, h->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "sync");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    const Ctrl& hc = *h->h_ctrl;
+    h->r = hc.r;
+    h->converged = hc.converged;
+    h->k_eff = hc.k_eff;
+    h->last_ms = ms;
+    std::vector<int64_t> tr((size_t)h->opts.r_max + 2, 0);
+    if ((e = cudaMemcpy(tr.data(), h->b.trace, tr.size() * sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "copy trace");
+    h->trace.assign(tr.begin() + 1, tr.begin() + 1 + std::max(0, h->r));
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->r = h->r;
+        info->converged = h->converged;
+        info->active = h->trace.empty() ? n : h->trace.back();
+        info->k = h->k_eff;
+        info->alpha = h->alpha;
+        info->gamma = h->gamma;
+        info->time_ms = ms;
+        info->nnz = g.nnz;
+        info->affected = affected;
+        info->full_levels = (int32_t)full_levels;
+        info->launches = h->launches;
+    }
+    if (!h->converged) return fail(h, KATZ_ENOTCONV, "r_max reached before the top-k criterion held");
+    return KATZ_OK;
 }
 
 }  // extern "C"

@@ -28,6 +28,7 @@ constexpr int SELECT_CAP = KATZ_MAX_K;
 constexpr int SELECT_THREADS = 1024;
 
 enum : int32_t { F_NEED_BIG = 1 };
+enum : int32_t { DYN_E_INVAL = 1, DYN_E_ALPHA = 2 };  // batch validation failures
 
 // Iteration state kept on the device so that a captured graph can loop
 // without host round trips.
@@ -168,6 +169,43 @@ struct IterBuffers {
     int32_t use_cond = 0;
 };
 
+// Scratch of the dynamic update (katz_dynamic.cu); per-node arrays are zero
+// between batches.
+struct DynBuffers {
+    int64_t cap = 0;                 // updates the batch arrays hold
+    int32_t* src = nullptr;          // batch, original ids
+    int32_t* dst = nullptr;
+    uint8_t* ins = nullptr;
+    int64_t* pos_a = nullptr;        // position of arc src->dst in the old col (deletions)
+    int64_t* pos_b = nullptr;
+    unsigned long long* table = nullptr;  // open-addressing set of unordered pairs
+    int64_t table_mask = 0;
+    int32_t* err = nullptr;
+    int32_t* delta = nullptr;        // [n] degree change
+    int32_t* ins_cnt = nullptr;      // [n] inserted arcs per row
+    int32_t* cursor = nullptr;       // [n]
+    uint8_t* touched = nullptr;      // [n]
+    int64_t* ins_start = nullptr;    // [n] bucket offset
+    int32_t* ins_rows = nullptr;     // [2 cap] rows receiving insertions
+    unsigned long long* n_ins_rows = nullptr;
+    int32_t* bucket = nullptr;       // [2 cap] inserted arcs grouped by row
+    uint32_t* vbits = nullptr;       // [n/32] frontier visit marks
+    int32_t* frontier = nullptr;     // [n] affected nodes, in order of discovery
+    unsigned long long* fsize = nullptr;
+};
+
+cudaError_t dyn_validate(const DeviceGraph& g, const DynBuffers& d, int64_t m, int64_t D, cudaStream_t st);
+cudaError_t dyn_clear(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st);
+cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, int64_t* rowptr_new, int64_t* deg,
+                        int64_t* sums, cudaStream_t st);
+cudaError_t dyn_rebuild(DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new, int32_t* col_new,
+                        cudaStream_t st);
+cudaError_t dyn_seed(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st);
+cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, int64_t hi, cudaStream_t st);
+cudaError_t dyn_recompute_c(const DeviceGraph& g, const IterBuffers& b, const DynBuffers& d, const IterParams& p,
+                            int r, bool all, cudaStream_t st);
+cudaError_t dyn_reactivate(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int r, cudaStream_t st);
+
 cudaError_t prepare_kernels();  // one-time function attributes (outside any capture)
 SpmvLayout make_layout(int64_t n, int64_t row_warp, int64_t row_octet, int64_t row_thread, int64_t chunks);
 // create-time relabelling (katz_relabel.cu)
@@ -188,6 +226,10 @@ cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const Iter
                           uint32_t* d_deghist, int64_t D, cudaStream_t st);
 cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                         cudaStream_t st);
+cudaError_t launch_spmv_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level,
+                              cudaStream_t st);
+cudaError_t launch_rows_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const int32_t* rows,
+                              const unsigned long long* nrows_dev, int64_t nrows_max, int level, cudaStream_t st);
 cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const double* cl,
                           const double* cu, const int32_t* cid, bool fp32, cudaStream_t st);
 cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,

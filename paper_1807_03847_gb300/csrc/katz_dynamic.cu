@@ -1,0 +1,464 @@
+// Dynamic graphs (Sec. 4, Algorithm 2): a batch of undirected edge
+// insertions and deletions is validated, applied to the device CSR, and the
+// stored walk vectors s_1..s_r are repaired level by level.
+//
+// Repair (the pull form of Algorithm 2's update, see katz_api.cu):
+//   F_1 = endpoints of the batch (their rows changed);
+//   F_i = F_{i-1} + neighbours of the nodes that joined F_{i-1}   (reverse BFS;
+//         in-neighbours = neighbours for undirected graphs);
+//   s_i(w) is recomputed for w in F_i from the already repaired level i-1
+//   with the same row kernel order as the static SpMV, so the repaired
+//   vectors equal a full recomputation on the updated graph.  Once |F_i|
+//   exceeds frontier_abort_frac * n the level is recomputed for all nodes
+//   (the paper aborts the BFS when S becomes large).
+// Nothing is changed unless the whole batch passes validation.
+#include <stdint.h>
+
+#include "katz_common.cuh"
+
+namespace katz {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// position of `target` in row u (first match), -1 if absent; one warp
+template <typename Off>
+__device__ __forceinline__ int64_t find_in_row(const Off* rowptr, const int32_t* col, int64_t u, int32_t target) {
+    const int lane = threadIdx.x & 31;
+    const int64_t a = rowptr[u], b = rowptr[u + 1];
+    for (int64_t base = a; base < b; base += 32) {
+        const int64_t j = base + lane;
+        const bool hit = j < b && col[j] == target;
+        const unsigned m = __ballot_sync(FULL, hit);
+        if (m) return base + (__ffs(m) - 1);
+    }
+    return -1;
+}
+
+// One warp per update: range, self-loop, duplicate (hash of the unordered
+// pair), presence (I and E disjoint, D a subset of E) and the degree deltas.
+template <typename Off>
+__global__ void validate_batch_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                      const int32_t* __restrict__ inv, int64_t n, const int32_t* __restrict__ src,
+                                      const int32_t* __restrict__ dst, const uint8_t* __restrict__ ins, int64_t m,
+                                      unsigned long long* table, int64_t table_mask, int32_t* delta,
+                                      int64_t* pos_a, int64_t* pos_b, int32_t* err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; e < m; e += warps) {
+        const int32_t a = src[e], b = dst[e];
+        if (a < 0 || b < 0 || a >= n || b >= n || a == b) {
+            if (lane == 0) atomicOr(err, DYN_E_INVAL);
+            continue;
+        }
+        if (lane == 0) {  // duplicate pair inside the batch
+            const unsigned long long key = ((unsigned long long)min(a, b) << 32 | (unsigned)max(a, b)) + 1ull;
+            int64_t h = (int64_t)(mix64(key) & (unsigned long long)table_mask);
+            for (int64_t probe = 0; probe <= table_mask; ++probe) {
+                const unsigned long long old = atomicCAS(&table[h], 0ull, key);
+                if (old == 0ull) break;
+                if (old == key) {
+                    atomicOr(err, DYN_E_INVAL);
+                    break;
+                }
+                h = (h + 1) & table_mask;
+            }
+        }
+        const int32_t ua = inv[a], ub = inv[b];
+        const int64_t pa = find_in_row(rowptr, col, ua, ub);
+        const int64_t pb = find_in_row(rowptr, col, ub, ua);
+        if (lane == 0) {
+            const bool present = pa >= 0 && pb >= 0;
+            if (ins[e] ? (pa >= 0 || pb >= 0) : !present) atomicOr(err, DYN_E_INVAL);
+            pos_a[e] = pa;
+            pos_b[e] = pb;
+            const int d = ins[e] ? 1 : -1;
+            atomicAdd(&delta[ua], d);
+            atomicAdd(&delta[ub], d);
+        }
+    }
+}
+
+template <typename Off>
+__global__ void degree_check_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ inv,
+                                    const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                                    int64_t n, const int32_t* __restrict__ delta, int64_t D, int32_t* err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t a = src[e], b = dst[e];
+        if (a < 0 || b < 0 || a >= n || b >= n) continue;
+        const int32_t ends[2] = {inv[a], inv[b]};
+        for (int q = 0; q < 2; ++q) {
+            const int64_t u = ends[q];
+            if ((int64_t)rowptr[u + 1] - (int64_t)rowptr[u] + delta[u] > D) atomicOr(err, DYN_E_ALPHA);
+        }
+    }
+}
+
+// undo the per-node scratch of a batch (delta, insertion counters, marks)
+__global__ void clear_batch_kernel(const int32_t* __restrict__ inv, const int32_t* __restrict__ src,
+                                   const int32_t* __restrict__ dst, int64_t m, int64_t n, int32_t* delta,
+                                   int32_t* ins_cnt, int32_t* cursor, uint8_t* touched) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t a = src[e], b = dst[e];
+        if (a < 0 || b < 0 || a >= n || b >= n) continue;
+        const int32_t ends[2] = {inv[a], inv[b]};
+        for (int q = 0; q < 2; ++q) {
+            delta[ends[q]] = 0;
+            ins_cnt[ends[q]] = 0;
+            cursor[ends[q]] = 0;
+            touched[ends[q]] = 0;
+        }
+    }
+}
+
+// insertions: count per row and list the rows that receive arcs
+__global__ void count_inserts_kernel(const int32_t* __restrict__ inv, const int32_t* __restrict__ src,
+                                     const int32_t* __restrict__ dst, const uint8_t* __restrict__ ins, int64_t m,
+                                     int32_t* ins_cnt, int32_t* ins_rows, unsigned long long* n_ins_rows) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        if (!ins[e]) continue;
+        const int32_t ends[2] = {inv[src[e]], inv[dst[e]]};
+        for (int q = 0; q < 2; ++q)
+            if (atomicAdd(&ins_cnt[ends[q]], 1) == 0) ins_rows[atomicAdd(n_ins_rows, 1ULL)] = ends[q];
+    }
+}
+
+// deletions: mark both arcs in the old col (read once more by the rebuild)
+__global__ void mark_deletes_kernel(const uint8_t* __restrict__ ins, int64_t m, const int64_t* __restrict__ pos_a,
+                                    const int64_t* __restrict__ pos_b, int32_t* col) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        if (ins[e]) continue;
+        col[pos_a[e]] = -1;
+        col[pos_b[e]] = -1;
+    }
+}
+
+// exclusive offsets of the insertion buckets (one block; the row list is short)
+__global__ void bucket_offsets_kernel(const int32_t* __restrict__ ins_rows, const unsigned long long* n_ins_rows,
+                                      const int32_t* __restrict__ ins_cnt, int64_t* ins_start) {
+    __shared__ long long part[1024];
+    const int tid = threadIdx.x;
+    const int64_t cnt = (int64_t)*n_ins_rows;
+    const int64_t chunk = (cnt + 1023) / 1024;
+    long long s = 0;
+    for (int64_t q = tid * chunk; q < min(cnt, (int64_t)(tid + 1) * chunk); ++q) s += ins_cnt[ins_rows[q]];
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const long long a = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += a;
+        __syncthreads();
+    }
+    long long run = tid ? part[tid - 1] : 0;
+    for (int64_t q = tid * chunk; q < min(cnt, (int64_t)(tid + 1) * chunk); ++q) {
+        ins_start[ins_rows[q]] = run;
+        run += ins_cnt[ins_rows[q]];
+    }
+}
+
+// place the inserted arcs (original id of the target kept for the sort)
+__global__ void bucket_fill_kernel(const int32_t* __restrict__ inv, const int32_t* __restrict__ src,
+                                   const int32_t* __restrict__ dst, const uint8_t* __restrict__ ins, int64_t m,
+                                   const int64_t* __restrict__ ins_start, int32_t* cursor, int32_t* bucket) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        if (!ins[e]) continue;
+        const int32_t a = src[e], b = dst[e];
+        const int32_t ua = inv[a], ub = inv[b];
+        bucket[ins_start[ua] + atomicAdd(&cursor[ua], 1)] = b;
+        bucket[ins_start[ub] + atomicAdd(&cursor[ub], 1)] = a;
+    }
+}
+
+// each bucket sorted by original id (deterministic row contents), then
+// renamed to internal ids
+__global__ void bucket_sort_kernel(const int32_t* __restrict__ ins_rows, const unsigned long long* n_ins_rows,
+                                   const int32_t* __restrict__ ins_cnt, const int64_t* __restrict__ ins_start,
+                                   const int32_t* __restrict__ inv, int32_t* bucket) {
+    const int64_t cnt = (int64_t)*n_ins_rows;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += stride) {
+        const int32_t u = ins_rows[q];
+        int32_t* bkt = bucket + ins_start[u];
+        const int c = ins_cnt[u];
+        for (int i = 1; i < c; ++i) {
+            const int32_t v = bkt[i];
+            int j = i - 1;
+            while (j >= 0 && bkt[j] > v) {
+                bkt[j + 1] = bkt[j];
+                --j;
+            }
+            bkt[j + 1] = v;
+        }
+        for (int i = 0; i < c; ++i) bkt[i] = inv[bkt[i]];
+    }
+}
+
+template <typename Off>
+__global__ void new_degrees_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ delta, int64_t n,
+                                   int64_t* deg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
+        deg[u] = (int64_t)rowptr[u + 1] - (int64_t)rowptr[u] + delta[u];
+}
+
+// one warp per row: kept entries in their order, then the row's inserted arcs
+template <typename Off>
+__global__ void rebuild_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                    const int64_t* __restrict__ rowptr_new, const int32_t* __restrict__ ins_cnt,
+                                    const int64_t* __restrict__ ins_start, const int32_t* __restrict__ bucket,
+                                    int64_t n, int32_t* col_new) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; u < n; u += warps) {
+        const int64_t a = rowptr[u], b = rowptr[u + 1];
+        int64_t o = rowptr_new[u];
+        for (int64_t base = a; base < b; base += 32) {
+            const int64_t j = base + lane;
+            const int32_t x = j < b ? col[j] : -1;
+            const unsigned keep = __ballot_sync(FULL, x >= 0);
+            if (x >= 0) col_new[o + __popc(keep & ((1u << lane) - 1u))] = x;
+            o += __popc(keep);
+        }
+        const int c = ins_cnt[u];
+        if (c) {
+            const int32_t* bkt = bucket + ins_start[u];
+            for (int q = lane; q < c; q += 32) col_new[o + q] = bkt[q];
+        }
+    }
+}
+
+template <typename Off>
+__global__ void narrow_kernel(const int64_t* __restrict__ in, Off* __restrict__ out, int64_t count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) out[q] = (Off)in[q];
+}
+
+// test-and-set of u's visit bit; true if u was not visited before
+__device__ __forceinline__ bool visit(uint32_t* vbits, int32_t u) {
+    const uint32_t bit = 1u << (u & 31);
+    return !(atomicOr(&vbits[u >> 5], bit) & bit);
+}
+
+// F_1: the endpoints of every update
+__global__ void seed_frontier_kernel(const int32_t* __restrict__ inv, const int32_t* __restrict__ src,
+                                     const int32_t* __restrict__ dst, int64_t m, uint32_t* vbits, int32_t* frontier,
+                                     unsigned long long* fsize) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t ends[2] = {inv[src[e]], inv[dst[e]]};
+        for (int q = 0; q < 2; ++q)
+            if (visit(vbits, ends[q])) frontier[atomicAdd(fsize, 1ULL)] = ends[q];
+    }
+}
+
+// the neighbours of frontier[lo, hi) join the frontier; one warp per node
+template <typename Off>
+__global__ void expand_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t* frontier,
+                              int64_t lo, int64_t hi, uint32_t* vbits, unsigned long long* fsize) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t q = lo + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; q < hi; q += warps) {
+        const int64_t w = frontier[q];
+        for (int64_t j = (int64_t)rowptr[w] + lane; j < (int64_t)rowptr[w + 1]; j += 32) {
+            const int32_t x = col[j];
+            if (visit(vbits, x)) frontier[atomicAdd(fsize, 1ULL)] = x;
+        }
+    }
+}
+
+// c_r = s_1 + ... + s_r in level order (the order the static iteration adds them)
+__global__ void recompute_c_kernel(const double* walk, IterParams p, int r, const int32_t* __restrict__ rows,
+                                   const unsigned long long* nrows, int64_t n, double* c) {
+    const int64_t cnt = rows ? (int64_t)*nrows : n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += stride) {
+        const int64_t v = rows ? rows[q] : q;
+        double acc = 0.0;
+        for (int i = 1; i <= r; ++i) acc = __dadd_rn(acc, walk_slot(walk, p, i)[v]);
+        c[v] = acc;
+    }
+}
+
+// a valid candidate threshold after the update: min of the new l_r over the
+// previous top-k (at least k nodes reach it)
+__global__ void theta_lb_kernel(const int32_t* __restrict__ topk_id, const int32_t* __restrict__ inv,
+                                const double* walk, const double* __restrict__ c, IterParams p, int r, Ctrl* ctrl) {
+    __shared__ double wmin[32];
+    const int kk = ctrl->k_eff;
+    const double* s = walk_slot(walk, p, r);
+    const BState bs = bstate(ctrl);
+    double m = 1.0 / 0.0;
+    for (int q = threadIdx.x; q < kk; q += blockDim.x) {
+        const int32_t v = inv[topk_id[q]];
+        double l, u;
+        node_bounds(c[v], 0.0, s[v], p, bs, l, u);
+        m = fmin(m, l);
+    }
+    for (int off = 16; off; off >>= 1) m = fmin(m, __shfl_xor_sync(FULL, m, off));
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 1.0 / 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) mm = fmin(mm, wmin[w]);
+        ctrl->theta_prev = kk > 0 ? mm : 0.0;
+        ctrl->r = r - 1;  // the check that follows evaluates level r
+        ctrl->n_cand = 0;
+        ctrl->cnt_cross = 0;
+        ctrl->n_active = 0;
+        ctrl->stop = 0;
+        ctrl->flags = 0;
+        ctrl->converged = 0;
+    }
+}
+
+// Reactivation: the active set is re-derived from all of V (a node outside
+// it satisfies the paper's reactivation test exactly when converged() would
+// keep it), and the candidates of the check at level r are collected.
+__global__ void reactivate_kernel(const double* walk, const double* __restrict__ c,
+                                  const int32_t* __restrict__ perm, IterParams p, int r, uint8_t* active,
+                                  double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl) {
+    const double* s = walk_slot(walk, p, r);
+    const double th = ctrl->theta_prev;
+    const BState bs = bstate(ctrl);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
+        active[v] = 1;
+        double l, u;
+        node_bounds(c[v], 0.0, s[v], p, bs, l, u);
+        if (l >= th) {
+            const unsigned long long pos = atomicAdd(&ctrl->n_cand, 1ULL);
+            if (pos < (unsigned long long)cand_cap) {
+                cand_l[pos] = l;
+                cand_u[pos] = u;
+                cand_id[pos] = perm[v];
+            }
+        }
+    }
+}
+
+int grid_for(int64_t n, int threads, int max_blocks = 152 * 16) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+}  // namespace
+
+// ---- launchers ---------------------------------------------------------------
+
+cudaError_t dyn_validate(const DeviceGraph& g, const DynBuffers& d, int64_t m, int64_t D, cudaStream_t st) {
+    const int wblocks = grid_for(m * 32, 256);
+    if (g.off64)
+        validate_batch_kernel<int64_t><<<wblocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, g.inv, g.n, d.src,
+                                                               d.dst, d.ins, m, d.table, d.table_mask, d.delta,
+                                                               d.pos_a, d.pos_b, d.err);
+    else
+        validate_batch_kernel<int32_t><<<wblocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, g.inv, g.n, d.src,
+                                                               d.dst, d.ins, m, d.table, d.table_mask, d.delta,
+                                                               d.pos_a, d.pos_b, d.err);
+    if (g.off64)
+        degree_check_kernel<int64_t><<<grid_for(m, 256), 256, 0, st>>>((const int64_t*)g.rowptr, g.inv, d.src, d.dst,
+                                                                      m, g.n, d.delta, D, d.err);
+    else
+        degree_check_kernel<int32_t><<<grid_for(m, 256), 256, 0, st>>>((const int32_t*)g.rowptr, g.inv, d.src, d.dst,
+                                                                      m, g.n, d.delta, D, d.err);
+    return cudaGetLastError();
+}
+
+cudaError_t dyn_clear(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st) {
+    clear_batch_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, m, g.n, d.delta, d.ins_cnt, d.cursor,
+                                                          d.touched);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(d.table, 0, (size_t)(d.table_mask + 1) * sizeof(unsigned long long), st);
+}
+
+// sorted insertion buckets and the new row offsets
+// (int64, n+1 entries, into rowptr_new); the total is rowptr_new[n]
+cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, int64_t* rowptr_new, int64_t* deg,
+                        int64_t* sums, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(d.n_ins_rows, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    count_inserts_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, d.ins, m, d.ins_cnt, d.ins_rows,
+                                                           d.n_ins_rows);
+    bucket_offsets_kernel<<<1, 1024, 0, st>>>(d.ins_rows, d.n_ins_rows, d.ins_cnt, d.ins_start);
+    bucket_fill_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, d.ins, m, d.ins_start, d.cursor,
+                                                         d.bucket);
+    bucket_sort_kernel<<<grid_for(2 * m, 128), 128, 0, st>>>(d.ins_rows, d.n_ins_rows, d.ins_cnt, d.ins_start, g.inv,
+                                                            d.bucket);
+    if (g.off64)
+        new_degrees_kernel<int64_t><<<grid_for(g.n, 256), 256, 0, st>>>((const int64_t*)g.rowptr, d.delta, g.n, deg);
+    else
+        new_degrees_kernel<int32_t><<<grid_for(g.n, 256), 256, 0, st>>>((const int32_t*)g.rowptr, d.delta, g.n, deg);
+    e = cudaMemsetAsync(deg + g.n, 0, sizeof(int64_t), st);
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return exclusive_scan_i64(deg, g.n + 1, rowptr_new, sums, st);
+}
+
+// rows into col_new, then the new offsets over the old ones
+cudaError_t dyn_rebuild(DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new, int32_t* col_new,
+                        cudaStream_t st) {
+    mark_deletes_kernel<<<grid_for(m, 256), 256, 0, st>>>(d.ins, m, d.pos_a, d.pos_b, g.col);
+    if (g.off64)
+        rebuild_rows_kernel<int64_t><<<grid_for(g.n * 32, 256), 256, 0, st>>>(
+            (const int64_t*)g.rowptr, g.col, rowptr_new, d.ins_cnt, d.ins_start, d.bucket, g.n, col_new);
+    else
+        rebuild_rows_kernel<int32_t><<<grid_for(g.n * 32, 256), 256, 0, st>>>(
+            (const int32_t*)g.rowptr, g.col, rowptr_new, d.ins_cnt, d.ins_start, d.bucket, g.n, col_new);
+    if (g.off64)
+        narrow_kernel<int64_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int64_t*)g.rowptr, g.n + 1);
+    else
+        narrow_kernel<int32_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int32_t*)g.rowptr, g.n + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t dyn_seed(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(d.vbits, 0, (size_t)((g.n + 31) / 32) * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.fsize, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    seed_frontier_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, m, d.vbits, d.frontier, d.fsize);
+    return cudaGetLastError();
+}
+
+cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, int64_t hi, cudaStream_t st) {
+    if (hi <= lo) return cudaSuccess;
+    if (g.off64)
+        expand_kernel<int64_t><<<grid_for((hi - lo) * 32, 256), 256, 0, st>>>((const int64_t*)g.rowptr, g.col,
+                                                                             d.frontier, lo, hi, d.vbits, d.fsize);
+    else
+        expand_kernel<int32_t><<<grid_for((hi - lo) * 32, 256), 256, 0, st>>>((const int32_t*)g.rowptr, g.col,
+                                                                             d.frontier, lo, hi, d.vbits, d.fsize);
+    return cudaGetLastError();
+}
+
+cudaError_t dyn_recompute_c(const DeviceGraph& g, const IterBuffers& b, const DynBuffers& d, const IterParams& p,
+                            int r, bool all, cudaStream_t st) {
+    recompute_c_kernel<<<grid_for(g.n, 256), 256, 0, st>>>((const double*)b.walk, p, r, all ? nullptr : d.frontier,
+                                                           d.fsize, g.n, b.c);
+    return cudaGetLastError();
+}
+
+cudaError_t dyn_reactivate(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int r, cudaStream_t st) {
+    theta_lb_kernel<<<1, 1024, 0, st>>>(b.topk_id, g.inv, (const double*)b.walk, b.c, p, r, b.ctrl);
+    reactivate_kernel<<<grid_for(g.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, g.perm, p, r, b.active,
+                                                          b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl);
+    return cudaGetLastError();
+}
+
+}  // namespace katz

@@ -44,6 +44,14 @@ struct katz_handle {
     cudaGraphExec_t graph_exec = nullptr;
     katz::IterParams graph_params{};
     bool graph_fp32 = false;
+    // dynamic updates
+    katz::DynBuffers dyn;
+    int32_t* col_spare = nullptr;     // rebuilt col is written here, then swapped
+    int64_t col_spare_cap = 0;
+    int64_t col_cap = 0;              // capacity of g.col
+    int64_t* rp_new = nullptr;        // [n+1]
+    int64_t* deg_tmp = nullptr;       // [n+1]
+    int64_t* scan_sums = nullptr;
     // result of the last rank/update call
     bool ranked = false;
     int r = 0;

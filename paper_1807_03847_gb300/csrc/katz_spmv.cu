@@ -56,6 +56,7 @@ struct Epi {
     Ctrl* ctrl;
     double theta_prev;
     BState bs;
+    int store_only;   // dynamic repair: write s_r only (c and bounds are rebuilt afterwards)
 };
 
 // Finish row u of an FP64 level: s = alpha * sum, c64 += s, bounds, candidate.
@@ -63,6 +64,12 @@ struct Epi {
 // Candidates carry the original id.
 template <typename Acc>
 __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, const IterParams& p) {
+    if constexpr (sizeof(Acc) == 8) {
+        if (e.store_only) {
+            ((double*)e.y)[u] = __dmul_rn(p.alpha, (double)sum);
+            return;
+        }
+    }
     double sd, c64, c32 = 0.0;
     if constexpr (sizeof(Acc) == 8) {
         sd = __dmul_rn(p.alpha, (double)sum);
@@ -173,7 +180,7 @@ __device__ __forceinline__ Epi make_epi(void* y, double* c64, double* c32, doubl
                                         const int32_t* perm, double* cand_l, double* cand_u, int32_t* cand_id,
                                         int64_t cand_cap, Ctrl* ctrl) {
     return Epi{y,      c64,     c32,     lb,       ub,    active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl,
-               ctrl->theta_prev, bstate(ctrl)};
+               ctrl->theta_prev, bstate(ctrl), 0};
 }
 
 template <typename Off>
@@ -181,13 +188,16 @@ __global__ void __launch_bounds__(BLOCK)
 spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L, double* walk,
                  double* c64, double* c32, double* lb, double* ub, uint8_t* active, const int32_t* __restrict__ perm,
                  const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first, double* chunk_part,
-                 double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
-    if (ctrl->stop) return;
-    const int r_cur = ctrl->r + 1;
-    const int f32_from = ctrl->f32_from;
+                 double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p,
+                 int store_level) {
+    // store_level > 0: dynamic repair of one FP64 level, s only
+    if (!store_level && ctrl->stop) return;
+    const int r_cur = store_level ? store_level : ctrl->r + 1;
+    const int f32_from = store_level ? 0x7fffffff : ctrl->f32_from;
     const double* xs = walk_slot(walk, p, r_cur - 1);
     double* ys = walk_slot(walk, p, r_cur);
-    const Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
+    Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
+    ep.store_only = store_level > 0;
     if (r_cur < f32_from)
         spmv_rows<Off, double, double>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
     else if (r_cur == f32_from)
@@ -216,15 +226,16 @@ __global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double
                                  uint8_t* active,
                                  const int32_t* __restrict__ perm, const int64_t* __restrict__ chunk_first,
                                  const double* __restrict__ chunk_part, double* cand_l, double* cand_u,
-                                 int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
-    if (ctrl->stop) return;
-    const int r_cur = ctrl->r + 1;
+                                 int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p, int store_level) {
+    if (!store_level && ctrl->stop) return;
+    const int r_cur = store_level ? store_level : ctrl->r + 1;
     double* ys = walk_slot(walk, p, r_cur);
-    const Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
+    Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
+    ep.store_only = store_level > 0;
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= L.row_warp) return;
     const int64_t first = chunk_first[u], count = chunk_first[u + 1] - first;
-    if (r_cur < ctrl->f32_from)
+    if (store_level || r_cur < ctrl->f32_from)
         finish_row<double>(u, chunk_tree<double>(chunk_part, first, count), ep, p);
     else
         finish_row<float>(u, chunk_tree<float>(chunk_part, first, count), ep, p);
@@ -244,24 +255,95 @@ int max_sum_depth(const SpmvLayout& L, int64_t max_chunks_per_row) {
     return d;
 }
 
-cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
-                        cudaStream_t st) {
-    (void)fp32;
+static cudaError_t spmv_launch(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int store_level,
+                               cudaStream_t st) {
     const SpmvLayout& L = g.layout;
     if (L.blocks_total > 0) {
         if (g.off64)
             spmv_rows_kernel<int64_t><<<(unsigned)L.blocks_total, BLOCK, 0, st>>>(
-                (const int64_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, g.chunk_row,
-                g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
+                (const int64_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm,
+                g.chunk_row, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p,
+                store_level);
         else
             spmv_rows_kernel<int32_t><<<(unsigned)L.blocks_total, BLOCK, 0, st>>>(
-                (const int32_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, g.chunk_row,
-                g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
+                (const int32_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm,
+                g.chunk_row, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p,
+                store_level);
     }
     if (L.row_warp > 0)
         spmv_chunk_fixup<<<(unsigned)((L.row_warp + 127) / 128), 128, 0, st>>>(
-            L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u,
-            b.cand_id, b.cand_cap, b.ctrl, p);
+            L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, g.chunk_first, g.chunk_part, b.cand_l,
+            b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p, store_level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
+                        cudaStream_t st) {
+    (void)fp32;
+    return spmv_launch(g, b, p, 0, st);
+}
+
+cudaError_t launch_spmv_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level,
+                              cudaStream_t st) {
+    return spmv_launch(g, b, p, level, st);
+}
+
+// One warp per listed row: the row's s_level recomputed with the same
+// summation order as spmv_rows_kernel uses for that row (its row mode is set
+// by its internal index), so a repaired level equals a full recomputation.
+template <typename Off>
+__global__ void rows_store_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L,
+                                  const int32_t* __restrict__ rows, const unsigned long long* nrows_ptr,
+                                  double* walk, const int64_t* __restrict__ chunk_first, double* chunk_part,
+                                  IterParams p, int level) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t nrows = (int64_t)*nrows_ptr;
+    const double* __restrict__ x = walk_slot(walk, p, level - 1);
+    double* y = walk_slot(walk, p, level);
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < nrows; w += warps) {
+        const int64_t u = rows[w];
+        const int64_t a = rowptr[u], e = rowptr[u + 1];
+        double s = 0.0;
+        if (u >= L.row_thread) {          // THREAD: lane 0 alone, step 1
+            if (lane == 0) s = strided_sum<double, double>(col, x, a, e, 0, 1);
+        } else if (u >= L.row_octet) {    // OCTET: lanes 0..7, step 8, tree of width 8
+            if (lane < 8) s = strided_sum<double, double>(col, x, a, e, lane, 8);
+#pragma unroll
+            for (int off = 4; off; off >>= 1) s = __dadd_rn(s, __shfl_down_sync(FULL, s, off, 8));
+        } else if (u >= L.row_warp) {     // WARP
+            s = strided_sum<double, double>(col, x, a, e, lane, 32);
+#pragma unroll
+            for (int off = 16; off; off >>= 1) s = __dadd_rn(s, __shfl_down_sync(FULL, s, off));
+        } else {                          // CHUNK: chunk sums, then the tree over them
+            for (int64_t ch = chunk_first[u]; ch < chunk_first[u + 1]; ++ch) {
+                const int64_t j0 = a + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+                const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, e);
+                double t = strided_sum<double, double>(col, x, j0, j1, lane, 32);
+#pragma unroll
+                for (int off = 16; off; off >>= 1) t = __dadd_rn(t, __shfl_down_sync(FULL, t, off));
+                if (lane == 0) chunk_part[ch] = t;
+            }
+            __syncwarp();
+            if (lane == 0) s = chunk_tree<double>(chunk_part, chunk_first[u], chunk_first[u + 1] - chunk_first[u]);
+        }
+        if (lane == 0) y[u] = __dmul_rn(p.alpha, s);
+    }
+}
+
+cudaError_t launch_rows_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const int32_t* rows,
+                              const unsigned long long* nrows_dev, int64_t nrows_max, int level, cudaStream_t st) {
+    if (nrows_max <= 0) return cudaSuccess;
+    int64_t blocks = (nrows_max + 7) / 8;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (g.off64)
+        rows_store_kernel<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, g.layout, rows,
+                                                                    nrows_dev, (double*)b.walk, g.chunk_first,
+                                                                    g.chunk_part, p, level);
+    else
+        rows_store_kernel<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, g.layout, rows,
+                                                                    nrows_dev, (double*)b.walk, g.chunk_first,
+                                                                    g.chunk_part, p, level);
     return cudaGetLastError();
 }
 
