@@ -183,6 +183,45 @@ katz_status katz_get_trace(katz_h h, int64_t* active_per_iter, int32_t cap);
 katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t* dst,
                                     const uint8_t* is_insert, int64_t m, katz_info* info);
 
+/*
+ * katz_certify_topk_noalloc - the paper has no counterpart to this entry
+ * point.  It is for callers that must not have a library allocate device
+ * memory: a process whose own caching allocator holds all device memory, a
+ * latency-bound loop that cannot take the device-wide wait of cudaFree, a
+ * host that forbids device allocation by the code it loads.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Given per-node bounds lower[v] <= c(v) <= upper[v] for v in [0, n) (two
+ * arrays of n doubles in device memory, e.g. from katz_get_bounds; no NaN),
+ * writes ids_out[0..k) = the k nodes with the largest lower bounds in
+ * decreasing order (ties by smaller id) and *certified_out = 1 if the top-k
+ * criterion that katz_rank_static stops on holds for these bounds (each
+ * adjacent top-k pair and the k-th node against every other node
+ * eps-separated), else 0.  ids_out (k int32) and certified_out (one int32)
+ * are device memory owned by the caller.
+ *
+ * Working memory: one fixed array of at most 420 KiB in the library's device image,
+ * present on every device that loads the library until the process exits.
+ * It holds at most KATZ_MAX_K candidates, so the limits are
+ * 1 <= k <= KATZ_MAX_K, k <= n <= 2^31 - 2, eps > 0: anything beyond them
+ * returns KATZ_EINVAL before any work is queued.
+ *
+ * The work is queued on cuda_stream (NULL: the default stream) and the call
+ * returns without waiting for it.  The first call on a device, with that
+ * device current, looks up the array's device address and raises the sort
+ * kernel's shared-memory limit; make that first call before any stream
+ * capture begins on that device.  Every call on a device uses the same
+ * array, which keeps the contents of the last call; each call clears what
+ * must start at zero.  Calls whose work overlaps on the GPU (streams with no
+ * ordering between them) race on the array and give wrong results.
+ * No handle: errors are reported by the return value alone.
+ * Errors: KATZ_EINVAL (NULL pointer, sizes above the limits), KATZ_ECUDA
+ * (device lookup or a launch failed).
+ */
+katz_status katz_certify_topk_noalloc(const double* lower, const double* upper, int64_t n, int64_t k,
+                                      double eps, int32_t* ids_out, int32_t* certified_out,
+                                      void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

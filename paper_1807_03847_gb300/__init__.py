@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "KatzError", "katz_opts", "katz_info", "katz_default_opts", "katz_create_csr", "katz_destroy",
     "katz_rank_static", "katz_get_ranking", "katz_get_bounds", "katz_get_walk", "katz_get_trace",
-    "katz_apply_update_batch", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT",
+    "katz_apply_update_batch", "katz_certify_topk_noalloc", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT",
     "KATZ_MAX_K", "library_path",
 ]
 
@@ -81,6 +81,7 @@ def _load():
         "katz_get_walk": (ctypes.c_int, [P, i32, P]),
         "katz_get_trace": (ctypes.c_int, [P, P, i32]),
         "katz_apply_update_batch": (ctypes.c_int, [P, P, P, P, i64, ctypes.POINTER(katz_info)]),
+        "katz_certify_topk_noalloc": (ctypes.c_int, [P, P, i64, i64, dbl, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -190,6 +191,17 @@ def katz_apply_update_batch(h, src, dst, is_insert, m: int | None = None, check:
         _check(h, st, "katz_apply_update_batch")
     info.status = st
     return info
+
+
+def katz_certify_topk_noalloc(lower, upper, k: int, eps: float, ids_out, certified_out, stream=None) -> None:
+    """Top-k ids and the separation verdict from device bounds, with no
+    allocation by the library; lower/upper/ids_out/certified_out are device
+    tensors the caller owns; stream: a torch.cuda.Stream or raw handle."""
+    n = lower.shape[0]
+    handle = getattr(stream, "cuda_stream", stream)
+    st = _load().katz_certify_topk_noalloc(_ptr(lower), _ptr(upper), int(n), int(k), float(eps), _ptr(ids_out),
+                                           _ptr(certified_out), handle)
+    _check(None, st, "katz_certify_topk_noalloc")
 
 
 class Katz:
