@@ -50,6 +50,12 @@ WORKLOADS = {
                        "eps=1e-9"),
 }
 
+SERVING = dict(graph="rmat23", k=100, eps=1e-9, rate=200.0, min_size=1, max_size=10000, p_insert=0.5,
+               desc="undirected R-MAT scale 23 base graph (8,388,608 vertices, edge factor 16); update batches of "
+                    "log-uniform size in [1, 10^4], 50% inserts of uniform non-edges / 50% deletes of uniform existing "
+                    "edges; Poisson arrivals at 200 batches/s; deg_bound = deg_max + 64, alpha = 1/(deg_bound+1); "
+                    "certified top-100 after every batch; eps=1e-9")
+
 HBM_PEAK_FALLBACK = 6800.0  # GB/s, used only if MEASURED_PEAKS.json is absent
 FP64_ADD_PEAK_TFLOPS = 0.625  # 1.25 TFLOP/s FP64 (FMA = 2 FLOP) -> 0.625 T additions/s
 
@@ -60,12 +66,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat22")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve-rmat23"], default="rmat22")
     ap.add_argument("--precision", choices=["fp64", "fp32cert"], default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--serve-batches", type=int, default=400,
+                    help="batches of the serving stream measured beside the static line (0: skip)")
     return ap.parse_args()
 
 
@@ -138,7 +146,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha1()
-    for fn in ("katz_kernels.cu", "katz_common.cuh"):
+    for fn in ("katz_spmv.cu", "katz_common.cuh"):
         with open(os.path.join(ROOT, "paper_1807_03847_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -220,6 +228,72 @@ def cpu_baseline(g, wl, iters):
                       f"{dt:.2f} s"}, dt
 
 
+def run_serving(batches, workers=2, slots=8):
+    """Open-loop serving run: the batches of the stream are submitted at their
+    arrival times to a katz_server holding one R-MAT23 handle; latency is
+    submit -> certified top-k on the host.  Then the static recomputation of
+    the final graph (katz_rank_static on the same handle) as the baseline."""
+    import torch
+
+    import graphgen as gg
+    import paper_1807_03847_gb300 as K
+
+    cfg = SERVING
+    g = gg.workload(cfg["graph"])
+    D = g.deg_max() + 64
+    st = gg.stream(g, batches, seed=gg.SEED_BASE + 230, min_size=cfg["min_size"], max_size=cfg["max_size"],
+                   p_insert=cfg["p_insert"], rate=cfg["rate"], deg_bound=D)
+    h = K.Katz(torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.col).cuda(),
+               K.katz_default_opts(keep_history=1, deg_bound=D))
+    info0 = h.rank(0.0, cfg["k"], cfg["eps"])
+    srv = K.Server(workers=workers, slots=slots, slot_updates=cfg["max_size"])
+    srv.attach(h, cfg["k"])
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    tickets = []
+    t0 = time.perf_counter()
+    for j in range(len(st)):
+        delay = t0 + st.arrival[j] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(h, *st.batch(j)))
+    results = [srv.wait(t, timeout_ms=600000) for t in tickets]
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    srv.close()
+    bad = [r[0] for r in results if r[0] != 0]
+    lat = np.array([r[2].latency_ms for r in results])
+    svc = np.array([r[2].service_ms for r in results])
+    dev = np.array([r[2].info.time_ms for r in results])
+    aff = np.array([r[2].info.affected for r in results], np.float64)
+    full = np.array([r[2].info.full_levels for r in results], np.float64)
+    launches = int(sum(r[2].info.launches for r in results))
+    sizes = st.sizes()
+    # full static recomputation of the final graph, same handle (graph resident)
+    rec_dev, rec_wall = [], []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        inf = h.rank(0.0, cfg["k"], cfg["eps"])
+        rec_wall.append(1e3 * (time.perf_counter() - t1))
+        rec_dev.append(inf.time_ms)
+    h.close()
+    small = sizes <= 100
+    return {
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "service_p50_ms": float(np.percentile(svc, 50)), "service_p99_ms": float(np.percentile(svc, 99)),
+        "device_p50_ms": float(np.percentile(dev, 50)),
+        "p50_ms_batches_le_100": float(np.percentile(lat[small], 50)) if small.any() else None,
+        "recompute_ms": float(np.median(rec_wall)), "recompute_device_ms": float(np.median(rec_dev)),
+        "batches": int(len(st)), "updates": int(sizes.sum()), "rejected": len(bad),
+        "offered_rate": cfg["rate"], "achieved_rate": len(st) / wall,
+        "affected_mean_frac": float(aff.mean() / g.n), "full_levels_mean": float(full.mean()),
+        "r_initial": int(info0.r), "gpu_launches": launches, "workers": workers, "slots": slots,
+        "clocks": clocks, "n": g.n, "nnz": g.nnz, "deg_bound": D, "desc": cfg["desc"],
+        "latency": "submit (at the batch's arrival time) -> certified top-100 copied to the host",
+    }
+
+
 def run_reference(args):
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -260,6 +334,25 @@ def main():
         run_reference(args)
         return
     import torch
+
+    if args.workload == "serve-rmat23":
+        rank = int(os.environ.get("RANK", "0"))
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        sv = run_serving(max(args.serve_batches, 2000) if args.serve_batches else 2000)
+        if rank == 0:
+            print(json.dumps({
+                "metric": "update-to-certified top-100 latency p99 (serving, dynamic R-MAT23)",
+                "value": sv["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": sv["batches"], "warmup": 0,
+                "ms_per_step": sv["p50_ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "serve-rmat23-top100-fp64", "graph": sv["desc"],
+                           "l2": "not flushed: requests run back to back as they arrive"},
+                "serving": sv, "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"],
+                "e2e": {"value": sv["p99_ms"], "unit": "ms",
+                        "h2d_bytes_per_step": int(9 * sv["updates"] / sv["batches"]),
+                        "d2h_bytes_per_step": 400},
+            }), flush=True)
+        return
 
     import graphgen as gg
     import paper_1807_03847_gb300 as K
@@ -365,6 +458,14 @@ def main():
                "ms_per_step": 1e3 * e2e_t / len(e2e_times),
                "api": "katz_create_csr(host pinned CSR) + katz_rank_static + katz_get_ranking(host) + katz_destroy"}
 
+    serving = None
+    if args.serve_batches > 0:
+        h.close()
+        del rowptr_d, col_d, flush
+        torch.cuda.empty_cache()
+        serving = run_serving(args.serve_batches)
+        h = None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _ = cpu_baseline(g, wl, args.cpu_iters)
@@ -384,9 +485,11 @@ def main():
             "fp32_levels": int(infos[-1].fp32_levels),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "ranking_head": [int(x) for x in ranking[:5]],
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    h.close()
+    if h is not None:
+        h.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

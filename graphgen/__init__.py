@@ -62,6 +62,10 @@ def _load():
             lib.gg_max_threads.restype = ctypes.c_int
             lib.gg_update_batch.restype = i64
             lib.gg_update_batch.argtypes = [i64, P, P, i64, dbl, u64, P, P, P]
+            lib.gg_stream_total.restype = i64
+            lib.gg_stream_total.argtypes = [i64, i64, i64, u64]
+            lib.gg_stream.restype = i64
+            lib.gg_stream.argtypes = [i64, P, P, i64, i64, i64, i64, dbl, dbl, u64, i64, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -166,6 +170,45 @@ def update_batch(g: Graph, m: int, seed: int, p_insert: float = 0.5):
     got = lib.gg_update_batch(g.n, g.rowptr.ctypes.data, g.col.ctypes.data, m, p_insert, seed,
                               src.ctypes.data, dst.ctypes.data, ins.ctypes.data)
     return src[:got], dst[:got], ins[:got]
+
+
+class Stream:
+    """A sequence of update batches with arrival times (seconds)."""
+
+    def __init__(self, offsets, src, dst, is_insert, arrival):
+        self.offsets, self.src, self.dst, self.is_insert, self.arrival = offsets, src, dst, is_insert, arrival
+
+    def __len__(self) -> int:
+        return len(self.arrival)
+
+    def batch(self, j: int):
+        a, b = self.offsets[j], self.offsets[j + 1]
+        return self.src[a:b], self.dst[a:b], self.is_insert[a:b]
+
+    def sizes(self) -> np.ndarray:
+        return np.diff(self.offsets)
+
+
+def stream(g: Graph, batches: int, seed: int, min_size: int = 1, max_size: int = 10000, p_insert: float = 0.5,
+           rate: float = 200.0, deg_bound: int | None = None) -> Stream:
+    """Update batches applied one after another to g: sizes log-uniform in
+    [min_size, max_size]; inserts are uniform non-edges (degrees kept at or
+    below deg_bound), deletes uniform existing edges, no pair twice within a
+    batch; Poisson arrivals at `rate` batches per second."""
+    lib = _load()
+    total = lib.gg_stream_total(batches, min_size, max_size, seed)
+    offsets = np.zeros(batches + 1, np.int64)
+    src = np.empty(max(total, 1), np.int32)
+    dst = np.empty(max(total, 1), np.int32)
+    ins = np.empty(max(total, 1), np.uint8)
+    arrival = np.empty(max(batches, 1), np.float64)
+    D = int(deg_bound) if deg_bound is not None else g.deg_max() + 64
+    got = lib.gg_stream(g.n, g.rowptr.ctypes.data, g.col.ctypes.data, D, batches, min_size, max_size, p_insert,
+                        rate, seed, total, offsets.ctypes.data, src.ctypes.data, dst.ctypes.data, ins.ctypes.data,
+                        arrival.ctypes.data)
+    if got < 0:
+        raise MemoryError("gg_stream: out of memory")
+    return Stream(offsets, src[:got], dst[:got], ins[:got], arrival[:batches])
 
 
 def apply_batch(g: Graph, src, dst, is_insert) -> Graph:

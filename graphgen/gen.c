@@ -368,3 +368,219 @@ int64_t gg_update_batch(int64_t n, const int64_t *rowptr, const int32_t *col, in
     free(set);
     return e;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Request stream for the serving workload                                    */
+/* ------------------------------------------------------------------------- */
+/*
+ * gg_stream: `batches` update batches applied one after another to a base
+ * graph (sorted symmetric CSR).  Batch j has m_j updates, m_j log-uniform in
+ * [min_size, max_size]; each update is an insert with probability p_insert,
+ * else a delete.  Every batch is drawn against the graph after batches
+ * 0..j-1:
+ *   insert: a uniform pair {a,b}, a != b, that is not an edge, not used
+ *           earlier in the batch, with both degrees below deg_bound counting
+ *           the batch's earlier inserts;
+ *   delete: a uniform existing edge not used earlier in the batch.
+ * Arrival times are a Poisson process of the given rate (exponential gaps,
+ * first arrival at the first gap).
+ *
+ * The evolving edge set is the base CSR minus a set of deleted base edges
+ * plus a list of inserted edges (with a map from edge to list slot, so an
+ * inserted edge can be drawn uniformly and removed in O(1)).
+ *
+ * Output: offsets[batches+1] into src/dst/is_insert (capacity `cap`) and
+ * arrival[batches] in seconds.  Returns the number of updates written, or -1
+ * if cap is too small or memory runs out.
+ */
+typedef struct {
+    uint64_t *key;   /* ~0 empty, ~1 tombstone */
+    int64_t *val;
+    uint64_t mask;
+} gg_map;
+
+#define GG_EMPTY (~0ULL)
+#define GG_TOMB (~1ULL)
+
+static int map_init(gg_map *m, uint64_t items) {
+    uint64_t cap = 16;
+    while (cap < 4 * items + 16) cap <<= 1;
+    m->key = (uint64_t *)malloc(cap * sizeof(uint64_t));
+    m->val = (int64_t *)malloc(cap * sizeof(int64_t));
+    if (!m->key || !m->val) return -1;
+    memset(m->key, 0xff, cap * sizeof(uint64_t));
+    m->mask = cap - 1;
+    return 0;
+}
+
+static void map_free(gg_map *m) {
+    free(m->key);
+    free(m->val);
+}
+
+/* slot of key, or -1 */
+static int64_t map_find(const gg_map *m, uint64_t key) {
+    uint64_t h = mix64(key) & m->mask;
+    while (m->key[h] != GG_EMPTY) {
+        if (m->key[h] == key) return (int64_t)h;
+        h = (h + 1) & m->mask;
+    }
+    return -1;
+}
+
+static void map_put(gg_map *m, uint64_t key, int64_t val) {
+    int64_t s = map_find(m, key);
+    if (s >= 0) {
+        m->val[s] = val;
+        return;
+    }
+    uint64_t h = mix64(key) & m->mask;
+    while (m->key[h] != GG_EMPTY && m->key[h] != GG_TOMB) h = (h + 1) & m->mask;
+    m->key[h] = key;
+    m->val[h] = val;
+}
+
+static void map_del(gg_map *m, uint64_t key) {
+    int64_t s = map_find(m, key);
+    if (s >= 0) m->key[s] = GG_TOMB;
+}
+
+static inline uint64_t pair_key(uint64_t a, uint64_t b) {
+    return a < b ? (a << 32) | b : (b << 32) | a;
+}
+
+/* size of batch j: log-uniform in [min_size, max_size] */
+static int64_t stream_size(int64_t j, int64_t min_size, int64_t max_size, uint64_t seed) {
+    const double lo = log((double)min_size), hi = log((double)max_size + 1.0);
+    int64_t m = (int64_t)floor(exp(lo + (hi - lo) * unit(draw(seed, 21, (uint64_t)j))));
+    if (m < min_size) m = min_size;
+    if (m > max_size) m = max_size;
+    return m;
+}
+
+/* total number of updates gg_stream draws (the capacity it needs) */
+int64_t gg_stream_total(int64_t batches, int64_t min_size, int64_t max_size, uint64_t seed) {
+    int64_t s = 0;
+    for (int64_t j = 0; j < batches; ++j) s += stream_size(j, min_size, max_size, seed);
+    return s;
+}
+
+int64_t gg_stream(int64_t n, const int64_t *rowptr, const int32_t *col, int64_t deg_bound, int64_t batches,
+                  int64_t min_size, int64_t max_size, double p_insert, double rate, uint64_t seed,
+                  int64_t cap, int64_t *offsets, int32_t *src, int32_t *dst, uint8_t *is_insert,
+                  double *arrival) {
+    const int64_t nnz = rowptr[n];
+    int64_t *deg = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    uint64_t *ins_list = (uint64_t *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(uint64_t));
+    int32_t *bdeg = (int32_t *)calloc((size_t)n, sizeof(int32_t));  /* inserts so far in the batch */
+    gg_map deleted = {0}, inserted = {0}, in_batch = {0};
+    int64_t n_ins = 0, out = 0, rc = 0;
+    double t_arr = 0.0;
+    uint64_t t = 0;
+    if (!deg || !ins_list || !bdeg || map_init(&deleted, (uint64_t)cap) || map_init(&inserted, (uint64_t)cap) ||
+        map_init(&in_batch, (uint64_t)(max_size > 0 ? max_size : 1))) {
+        rc = -1;
+        goto done;
+    }
+    for (int64_t v = 0; v < n; ++v) deg[v] = rowptr[v + 1] - rowptr[v];
+    offsets[0] = 0;
+    for (int64_t j = 0; j < batches; ++j) {
+        /* arrival and size */
+        t_arr += -log(1.0 - unit(draw(seed, 20, (uint64_t)j))) / rate;
+        arrival[j] = t_arr;
+        const int64_t m = stream_size(j, min_size, max_size, seed);
+        if (out + m > cap) {
+            rc = -1;
+            goto done;
+        }
+        const int64_t b0 = out;
+        int64_t guard = 0;
+        while (out - b0 < m && guard < 1000 * (m + 10)) {
+            ++guard;
+            ++t;
+            const int ins = unit(draw(seed, 22, t)) < p_insert;
+            uint64_t a, b;
+            if (ins) {
+                a = below(draw(seed, 23, t), (uint64_t)n);
+                b = below(draw(seed, 24, t), (uint64_t)n);
+                if (a == b) continue;
+                if (deg[a] + bdeg[a] >= deg_bound || deg[b] + bdeg[b] >= deg_bound) continue;
+                const uint64_t key = pair_key(a, b);
+                const int in_base = has_arc(rowptr, col, (int32_t)a, (int32_t)b);
+                const int alive = (in_base && map_find(&deleted, key) < 0) || map_find(&inserted, key) >= 0;
+                if (alive || map_find(&in_batch, key) >= 0) continue;
+                map_put(&in_batch, key, 1);
+                ++bdeg[a];
+                ++bdeg[b];
+            } else {
+                const uint64_t slots = (uint64_t)nnz + 2 * (uint64_t)n_ins;
+                if (slots == 0) continue;
+                const uint64_t x = below(draw(seed, 25, t), slots);
+                if (x < (uint64_t)nnz) {
+                    int64_t l = 0, h = n;
+                    while (h - l > 1) {
+                        int64_t mid = (l + h) >> 1;
+                        if ((uint64_t)rowptr[mid] <= x) l = mid; else h = mid;
+                    }
+                    a = (uint64_t)l;
+                    b = (uint64_t)col[x];
+                    if (map_find(&deleted, pair_key(a, b)) >= 0) continue;
+                } else {
+                    const uint64_t key = ins_list[(x - (uint64_t)nnz) / 2];
+                    a = key >> 32;
+                    b = key & 0xffffffffULL;
+                }
+                const uint64_t key = pair_key(a, b);
+                if (map_find(&in_batch, key) >= 0) continue;
+                map_put(&in_batch, key, 0);
+            }
+            src[out] = (int32_t)a;
+            dst[out] = (int32_t)b;
+            is_insert[out] = (uint8_t)ins;
+            ++out;
+        }
+        /* apply the batch to the evolving edge set */
+        memset(in_batch.key, 0xff, (in_batch.mask + 1) * sizeof(uint64_t));
+        for (int64_t e = b0; e < out; ++e) {
+            const uint64_t a = (uint64_t)src[e], b = (uint64_t)dst[e], key = pair_key(a, b);
+            if (is_insert[e]) {
+                bdeg[a] = 0;
+                bdeg[b] = 0;
+                ++deg[a];
+                ++deg[b];
+                if (map_find(&deleted, key) >= 0) {
+                    map_del(&deleted, key);        /* a deleted base edge comes back */
+                } else {
+                    ins_list[n_ins] = key;
+                    map_put(&inserted, key, n_ins);
+                    ++n_ins;
+                }
+            } else {
+                --deg[a];
+                --deg[b];
+                const int64_t s = map_find(&inserted, key);
+                if (s >= 0) {                      /* swap-remove from the inserted list */
+                    const int64_t slot = inserted.val[s];
+                    map_del(&inserted, key);
+                    --n_ins;
+                    if (slot != n_ins) {
+                        ins_list[slot] = ins_list[n_ins];
+                        map_put(&inserted, ins_list[slot], slot);
+                    }
+                } else {
+                    map_put(&deleted, key, 1);
+                }
+            }
+        }
+        offsets[j + 1] = out;
+    }
+    rc = out;
+done:
+    free(deg);
+    free(ins_list);
+    free(bdeg);
+    if (deleted.key) map_free(&deleted);
+    if (inserted.key) map_free(&inserted);
+    if (in_batch.key) map_free(&in_batch);
+    return rc;
+}

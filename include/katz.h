@@ -184,6 +184,82 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
                                     const uint8_t* is_insert, int64_t m, katz_info* info);
 
 /*
+ * Serving loop for dynamic graphs (Sec. 4 applied to a stream of batches).
+ *
+ * A server takes update batches for one or more attached handles as they
+ * arrive and answers each with the certified top-k of its graph after that
+ * batch.  Requests on one handle run in arrival order, each on the graph the
+ * previous ones left; requests on different handles run at the same time on
+ * their handles' streams.  Submitted batches wait in arrival order until one
+ * of `slots` staging slots is free and the admitted updates stay within
+ * `admit_updates`; admission copies the batch to the device on the slot's own
+ * stream, overlapping the work in flight.  `workers` host threads drive the
+ * admitted requests through katz_apply_update_batch and katz_get_ranking.
+ * Attaching a handle reserves its device buffers for batches of up to
+ * slot_updates updates (and adjacency headroom), so a request allocates
+ * nothing on the device unless its graph grows past that headroom.
+ */
+typedef struct katz_server* katz_server_h;
+
+typedef struct {
+    int32_t workers;        /* host threads driving requests (default 4) */
+    int32_t slots;          /* requests admitted at once (default 8) */
+    int64_t slot_updates;   /* largest batch accepted, in updates (default 10000) */
+    int64_t admit_updates;  /* admitted updates in total at most (0: slots * slot_updates) */
+} katz_server_opts;
+
+typedef struct {
+    int32_t status;         /* katz_status of the request (KATZ_EINVAL: batch rejected,
+                               graph and ranking unchanged) */
+    int32_t reserved;
+    int64_t k;              /* ids written to ids_out */
+    katz_info info;         /* katz_apply_update_batch's info */
+    double queue_ms;        /* submit -> admitted into a slot */
+    double wait_ms;         /* admitted -> a worker started it */
+    double service_ms;      /* started -> ranking copied to the host */
+    double latency_ms;      /* submit -> ranking copied to the host */
+} katz_request_result;
+
+void katz_server_default_opts(katz_server_opts* opts);
+
+/* Create a server on the current device (opts NULL: defaults).
+ * Errors: KATZ_EINVAL, KATZ_ENOMEM. */
+katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts);
+
+/*
+ * Serve handle h, answering with its top k (1 <= k <= the ranked k).  h must
+ * have ranked with keep_history = 1 in FP64 mode on an undirected graph and
+ * should own its stream (katz_opts.cuda_stream = NULL), so that its work can
+ * overlap other handles'.  While attached, h belongs to the server: the caller
+ * makes no other call on it until the server is destroyed.
+ * Errors: KATZ_EINVAL, KATZ_ESTATE, KATZ_ENOMEM, KATZ_ECUDA.
+ */
+katz_status katz_server_attach(katz_server_h s, katz_h h, int64_t k);
+
+/*
+ * Queue a batch of m undirected updates for h (host arrays, copied before the
+ * call returns; m <= slot_updates).  *ticket identifies the request.
+ * Errors: KATZ_EINVAL, KATZ_ESTATE (h not attached).
+ */
+katz_status katz_server_submit(katz_server_h s, katz_h h, const int32_t* src, const int32_t* dst,
+                               const uint8_t* is_insert, int64_t m, uint64_t* ticket);
+
+/*
+ * Wait up to timeout_ms (0: just look) for a request.  Once it has finished,
+ * writes its ranking to ids_out (host, k entries; NULL skips it) and its
+ * result to res (nullable), forgets the ticket and returns KATZ_OK; the
+ * request's own outcome is res->status.  Each ticket is collected by one
+ * call.  Errors: KATZ_ETIMEOUT (not finished yet), KATZ_EINVAL (unknown
+ * ticket).
+ */
+katz_status katz_server_wait(katz_server_h s, uint64_t ticket, int64_t timeout_ms, int32_t* ids_out,
+                             katz_request_result* res);
+
+/* Finish the requests that are running, drop the queued ones, release the
+ * server (NULL is ignored).  Attached handles stay valid. */
+void katz_server_destroy(katz_server_h s);
+
+/*
  * katz_certify_topk_noalloc - the paper has no counterpart to this entry
  * point.  It is for callers that must not have a library allocate device
  * memory: a process whose own caching allocator holds all device memory, a

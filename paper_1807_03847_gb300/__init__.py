@@ -18,7 +18,8 @@ from . import build as _build
 __all__ = [
     "KatzError", "katz_opts", "katz_info", "katz_default_opts", "katz_create_csr", "katz_destroy",
     "katz_rank_static", "katz_get_ranking", "katz_get_bounds", "katz_get_walk", "katz_get_trace",
-    "katz_apply_update_batch", "katz_certify_topk_noalloc", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT",
+    "katz_apply_update_batch", "katz_certify_topk_noalloc", "katz_server_opts", "katz_request_result",
+    "katz_server_default_opts", "Server", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT",
     "KATZ_MAX_K", "library_path",
 ]
 
@@ -44,6 +45,17 @@ class katz_info(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class katz_server_opts(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("slots", ctypes.c_int32), ("slot_updates", ctypes.c_int64),
+                ("admit_updates", ctypes.c_int64)]
+
+
+class katz_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("k", ctypes.c_int64),
+                ("info", katz_info), ("queue_ms", ctypes.c_double), ("wait_ms", ctypes.c_double),
+                ("service_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
 
 
 class KatzError(RuntimeError):
@@ -82,6 +94,12 @@ def _load():
         "katz_get_trace": (ctypes.c_int, [P, P, i32]),
         "katz_apply_update_batch": (ctypes.c_int, [P, P, P, P, i64, ctypes.POINTER(katz_info)]),
         "katz_certify_topk_noalloc": (ctypes.c_int, [P, P, i64, i64, dbl, P, P, P]),
+        "katz_server_default_opts": (None, [ctypes.POINTER(katz_server_opts)]),
+        "katz_server_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(katz_server_opts)]),
+        "katz_server_attach": (ctypes.c_int, [P, P, i64]),
+        "katz_server_submit": (ctypes.c_int, [P, P, P, P, P, i64, ctypes.POINTER(ctypes.c_uint64)]),
+        "katz_server_wait": (ctypes.c_int, [P, ctypes.c_uint64, i64, P, ctypes.POINTER(katz_request_result)]),
+        "katz_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -202,6 +220,68 @@ def katz_certify_topk_noalloc(lower, upper, k: int, eps: float, ids_out, certifi
     st = _load().katz_certify_topk_noalloc(_ptr(lower), _ptr(upper), int(n), int(k), float(eps), _ptr(ids_out),
                                            _ptr(certified_out), handle)
     _check(None, st, "katz_certify_topk_noalloc")
+
+
+def katz_server_default_opts(**kw) -> katz_server_opts:
+    o = katz_server_opts()
+    _load().katz_server_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Server:
+    """Owning wrapper around a katz_server (destroyed with the object)."""
+
+    def __init__(self, opts: katz_server_opts | None = None, **kw):
+        if opts is None:
+            opts = katz_server_default_opts(**kw)
+        self.opts = opts
+        h = ctypes.c_void_p()
+        st = _load().katz_server_create(ctypes.byref(h), ctypes.byref(opts))
+        if st != 0:
+            raise KatzError(st, "katz_server_create")
+        self.s = h.value
+        self.k = {}
+
+    def attach(self, katz, k: int) -> None:
+        hh = katz.h if isinstance(katz, Katz) else katz
+        _check(hh, _load().katz_server_attach(self.s, hh, int(k)), "katz_server_attach")
+        self.k[hh] = int(k)
+
+    def submit(self, katz, src, dst, is_insert) -> int:
+        hh = katz.h if isinstance(katz, Katz) else katz
+        src = np.ascontiguousarray(src, np.int32)
+        dst = np.ascontiguousarray(dst, np.int32)
+        ins = np.ascontiguousarray(is_insert, np.uint8)
+        t = ctypes.c_uint64()
+        st = _load().katz_server_submit(self.s, hh, _ptr(src), _ptr(dst), _ptr(ins), len(src), ctypes.byref(t))
+        if st != 0:
+            raise KatzError(st, "katz_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        """(status, ids, result) of a finished request; raises KatzError
+        (KATZ_ETIMEOUT) if it does not finish in time."""
+        ids = np.empty(KATZ_MAX_K, np.int32)
+        res = katz_request_result()
+        st = _load().katz_server_wait(self.s, int(ticket), int(timeout_ms), _ptr(ids), ctypes.byref(res))
+        if st != 0:
+            raise KatzError(st, "katz_server_wait")
+        return res.status, ids[: res.k].copy(), res
+
+    def close(self):
+        if getattr(self, "s", None):
+            _load().katz_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Katz:

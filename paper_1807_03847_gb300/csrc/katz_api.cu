@@ -294,6 +294,80 @@ katz_status run_loop(katz_handle* h) {
 
 }  // namespace katz
 
+namespace katz {
+
+// Device buffers of the dynamic path for batches of up to m updates and a
+// rebuilt adjacency of up to nnz_cap arcs (0: no spare adjacency yet).  A
+// batch within these sizes allocates and frees nothing.
+katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
+    cudaError_t e;
+    DeviceGraph& g = h->g;
+    DynBuffers& d = h->dyn;
+    const int64_t n = g.n;
+#define DALLOC(ptr, cnt)                                                      \
+    if ((e = dmalloc(&(ptr), (size_t)(cnt))) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc " #ptr);
+    if (!d.delta) {
+        DALLOC(d.delta, n);
+        DALLOC(d.ins_cnt, n);
+        DALLOC(d.cursor, n);
+        DALLOC(d.touched, n);
+        DALLOC(d.ins_start, n);
+        DALLOC(d.vbits, (n + 31) / 32);
+        DALLOC(d.frontier, n);
+        DALLOC(d.fsize, 1);
+        DALLOC(d.n_ins_rows, 1);
+        DALLOC(d.err, 1);
+        DALLOC(h->rp_new, n + 1);
+        DALLOC(h->deg_tmp, n + 1);
+        DALLOC(h->scan_sums, scan_blocks(n + 1));
+        if ((e = cudaMemsetAsync(d.delta, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.ins_cnt, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.cursor, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.touched, 0, (size_t)n, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "memset dynamic scratch");
+        h->col_cap = g.nnz;
+    }
+    if (m > d.cap) {
+        cudaFree(d.src);
+        cudaFree(d.dst);
+        cudaFree(d.ins);
+        cudaFree(d.pos_a);
+        cudaFree(d.pos_b);
+        cudaFree(d.ins_rows);
+        cudaFree(d.bucket);
+        cudaFree(d.table);
+        d = DynBuffers{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, d.err, d.delta, d.ins_cnt,
+                       d.cursor, d.touched, d.ins_start, nullptr, d.n_ins_rows, nullptr, d.vbits, d.frontier,
+                       d.fsize};
+        const int64_t cap = std::max<int64_t>(m, 1024);
+        DALLOC(d.src, cap);
+        DALLOC(d.dst, cap);
+        DALLOC(d.ins, cap);
+        DALLOC(d.pos_a, cap);
+        DALLOC(d.pos_b, cap);
+        DALLOC(d.ins_rows, 2 * cap);
+        DALLOC(d.bucket, 2 * cap);
+        int64_t tsize = 1;
+        while (tsize < 4 * cap) tsize <<= 1;
+        DALLOC(d.table, tsize);
+        d.table_mask = tsize - 1;
+        d.cap = cap;
+        if ((e = cudaMemsetAsync(d.table, 0, (size_t)tsize * sizeof(unsigned long long), h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "memset table");
+    }
+    if (nnz_cap > h->col_spare_cap) {
+        cudaFree(h->col_spare);
+        h->col_spare = nullptr;
+        h->col_spare_cap = 0;
+        DALLOC(h->col_spare, nnz_cap);
+        h->col_spare_cap = nnz_cap;
+    }
+#undef DALLOC
+    return KATZ_OK;
+}
+
+}  // namespace katz
+
 extern "C" {
 
 void katz_default_opts(katz_opts* o) {
@@ -591,7 +665,9 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
     h->ranked = true;
     h->last_ms = ms;
     std::vector<int64_t> tr((size_t)h->opts.r_max + 2, 0);
-    if ((e = cudaMemcpy(tr.data(), h->b.trace, tr.size() * sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(tr.data(), h->b.trace, tr.size() * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "copy trace");
     h->trace.assign(tr.begin() + 1, tr.begin() + 1 + std::max(0, h->r));
     if (h->opts.use_graph && !h->opts.profile)
@@ -714,58 +790,10 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
     const int r = h->r;
     if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
     // ---- buffers --------------------------------------------------------------
-#define DALLOC(ptr, cnt)                                                      \
-    if ((e = dmalloc(&(ptr), (size_t)(cnt))) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc " #ptr);
-    if (!d.delta) {
-        DALLOC(d.delta, n);
-        DALLOC(d.ins_cnt, n);
-        DALLOC(d.cursor, n);
-        DALLOC(d.touched, n);
-        DALLOC(d.ins_start, n);
-        DALLOC(d.vbits, (n + 31) / 32);
-        DALLOC(d.frontier, n);
-        DALLOC(d.fsize, 1);
-        DALLOC(d.n_ins_rows, 1);
-        DALLOC(d.err, 1);
-        DALLOC(h->rp_new, n + 1);
-        DALLOC(h->deg_tmp, n + 1);
-        DALLOC(h->scan_sums, scan_blocks(n + 1));
-        if ((e = cudaMemsetAsync(d.delta, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(d.ins_cnt, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(d.cursor, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(d.touched, 0, (size_t)n, h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "memset dynamic scratch");
-        h->col_cap = g.nnz;
+    {
+        const katz_status rs = katz::dyn_reserve(h, m, 0);
+        if (rs != KATZ_OK) return rs;
     }
-    if (m > d.cap) {
-        cudaFree(d.src);
-        cudaFree(d.dst);
-        cudaFree(d.ins);
-        cudaFree(d.pos_a);
-        cudaFree(d.pos_b);
-        cudaFree(d.ins_rows);
-        cudaFree(d.bucket);
-        cudaFree(d.table);
-        d = DynBuffers{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, d.err, d.delta, d.ins_cnt,
-                       d.cursor, d.touched, d.ins_start, nullptr, d.n_ins_rows, nullptr, d.vbits, d.frontier,
-                       d.fsize};
-        const int64_t cap = std::max<int64_t>(m, 1024);
-        DALLOC(d.src, cap);
-        DALLOC(d.dst, cap);
-        DALLOC(d.ins, cap);
-        DALLOC(d.pos_a, cap);
-        DALLOC(d.pos_b, cap);
-        DALLOC(d.ins_rows, 2 * cap);
-        DALLOC(d.bucket, 2 * cap);
-        int64_t tsize = 1;
-        while (tsize < 4 * cap) tsize <<= 1;
-        DALLOC(d.table, tsize);
-        d.table_mask = tsize - 1;
-        d.cap = cap;
-        if ((e = cudaMemsetAsync(d.table, 0, (size_t)tsize * sizeof(unsigned long long), h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "memset table");
-    }
-#undef DALLOC
     if (m > 0) {
         if ((e = cudaMemcpyAsync(d.src, src, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, h->stream)) != cudaSuccess ||
             (e = cudaMemcpyAsync(d.dst, dst, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, h->stream)) != cudaSuccess ||
@@ -921,7 +949,9 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
     h->k_eff = hc.k_eff;
     h->last_ms = ms;
     std::vector<int64_t> tr((size_t)h->opts.r_max + 2, 0);
-    if ((e = cudaMemcpy(tr.data(), h->b.trace, tr.size() * sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(tr.data(), h->b.trace, tr.size() * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "copy trace");
     h->trace.assign(tr.begin() + 1, tr.begin() + 1 + std::max(0, h->r));
     if (info) {

@@ -69,4 +69,5 @@ katz_status cuda_fail(katz_handle* h, cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
 void drop_graph(katz_handle* h);
 cudaError_t launch_narrow_rowptr(const int64_t* in, int32_t* out, int64_t count, cudaStream_t st);
+katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap);
 }  // namespace katz

@@ -1,0 +1,340 @@
+// Serving loop for dynamic graphs: update batches arrive over time, each one
+// is applied to its graph with Algorithm 2 (Sec. 4) and answered with the
+// certified top-k of the graph after it.
+//
+// The state a request works on (the CSR, the stored walk vectors s_1..s_r,
+// the bounds) stays on the device in its handle.  The host side is a small
+// scheduler:
+//   - submit() copies the batch into host memory the server owns and queues
+//     it in arrival order;
+//   - admission moves queued requests, oldest first, into one of `slots`
+//     staging slots while a slot is free and the admitted updates stay within
+//     the update budget; admission starts the host-to-device copy of the batch
+//     on the slot's copy stream, so it overlaps whatever runs on the device;
+//   - `workers` threads take admitted requests, oldest first, skipping those
+//     whose handle is busy with an earlier request (requests on one handle run
+//     in arrival order, requests on different handles run at the same time,
+//     each on its handle's stream);
+//   - a finished request releases its slot, which admits the next one, and
+//     its result (status, info, ranking, timestamps) waits for wait().
+// Every request sees exactly the graph that the requests on its handle before
+// it produced, so its answer does not depend on what else is in flight.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/katz.h"
+#include "katz_handle.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+enum RequestState { WAITING, ADMITTED, RUNNING, DONE };
+
+struct Request {
+    uint64_t ticket = 0;
+    katz_handle* h = nullptr;
+    int64_t m = 0;
+    std::vector<int32_t> src, dst;
+    std::vector<uint8_t> ins;
+    RequestState state = WAITING;
+    int slot = -1;
+    Clock::time_point t_submit, t_admit, t_start, t_done;
+    katz_status status = KATZ_OK;
+    katz_info info{};
+    std::vector<int32_t> ids;
+};
+
+struct Slot {
+    int32_t* d_src = nullptr;
+    int32_t* d_dst = nullptr;
+    uint8_t* d_ins = nullptr;
+    int32_t* h_src = nullptr;   // pinned staging
+    int32_t* h_dst = nullptr;
+    uint8_t* h_ins = nullptr;
+    int32_t* h_ids = nullptr;   // pinned, KATZ_MAX_K
+    cudaStream_t copy = nullptr;
+    cudaEvent_t h2d_done = nullptr;
+};
+
+struct Lane {
+    int64_t k = 0;
+    bool busy = false;
+};
+
+}  // namespace
+
+struct katz_server {
+    katz_server_opts opts{};
+    int dev = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> waiting;    // submitted, not yet admitted (arrival order)
+    std::deque<Request*> admitted;   // admitted, not yet started (admission order)
+    std::unordered_map<uint64_t, Request*> requests;  // until wait() collects them
+    std::unordered_map<katz_handle*, Lane> lanes;
+    std::vector<Slot> slots;
+    std::vector<int> free_slots;
+    int64_t admitted_updates = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::vector<std::thread> workers;
+};
+
+namespace {
+
+void free_slot_memory(Slot& s) {
+    cudaFree(s.d_src);
+    cudaFree(s.d_dst);
+    cudaFree(s.d_ins);
+    cudaFreeHost(s.h_src);
+    cudaFreeHost(s.h_dst);
+    cudaFreeHost(s.h_ins);
+    cudaFreeHost(s.h_ids);
+    if (s.h2d_done) cudaEventDestroy(s.h2d_done);
+    if (s.copy) cudaStreamDestroy(s.copy);
+    s = Slot{};
+}
+
+// Move queued requests into free slots, oldest first (caller holds mu).
+void admit_locked(katz_server* s) {
+    while (!s->waiting.empty() && !s->free_slots.empty()) {
+        Request* q = s->waiting.front();
+        if (s->admitted_updates > 0 && s->admitted_updates + q->m > s->opts.admit_updates) break;
+        s->waiting.pop_front();
+        const int si = s->free_slots.back();
+        s->free_slots.pop_back();
+        Slot& sl = s->slots[(size_t)si];
+        q->slot = si;
+        q->state = ADMITTED;
+        q->t_admit = Clock::now();
+        s->admitted_updates += q->m;
+        if (q->m > 0) {
+            std::memcpy(sl.h_src, q->src.data(), (size_t)q->m * sizeof(int32_t));
+            std::memcpy(sl.h_dst, q->dst.data(), (size_t)q->m * sizeof(int32_t));
+            std::memcpy(sl.h_ins, q->ins.data(), (size_t)q->m);
+            cudaMemcpyAsync(sl.d_src, sl.h_src, (size_t)q->m * sizeof(int32_t), cudaMemcpyHostToDevice, sl.copy);
+            cudaMemcpyAsync(sl.d_dst, sl.h_dst, (size_t)q->m * sizeof(int32_t), cudaMemcpyHostToDevice, sl.copy);
+            cudaMemcpyAsync(sl.d_ins, sl.h_ins, (size_t)q->m, cudaMemcpyHostToDevice, sl.copy);
+        }
+        cudaEventRecord(sl.h2d_done, sl.copy);
+        q->src.clear();
+        q->src.shrink_to_fit();
+        q->dst.clear();
+        q->dst.shrink_to_fit();
+        q->ins.clear();
+        q->ins.shrink_to_fit();
+        s->admitted.push_back(q);
+        s->cv_work.notify_one();
+    }
+}
+
+void run_request(katz_server* s, Request* q, int64_t k) {
+    Slot& sl = s->slots[(size_t)q->slot];
+    katz_handle* h = q->h;
+    cudaError_t e = cudaStreamWaitEvent(h->stream, sl.h2d_done, 0);
+    if (e != cudaSuccess) {
+        q->status = KATZ_ECUDA;
+        return;
+    }
+    q->status = katz_apply_update_batch(h, sl.d_src, sl.d_dst, sl.d_ins, q->m, &q->info);
+    // the ranking of the graph the handle now holds (after a rejected batch
+    // the graph is unchanged and so is the ranking)
+    if (q->status == KATZ_OK || q->status == KATZ_EINVAL || q->status == KATZ_EALPHA) {
+        const int64_t kk = std::min<int64_t>(k, h->k_eff);
+        if (kk > 0 && katz_get_ranking(h, sl.h_ids, kk) == KATZ_OK) q->ids.assign(sl.h_ids, sl.h_ids + kk);
+    }
+}
+
+void worker_main(katz_server* s) {
+    cudaSetDevice(s->dev);
+    std::unique_lock<std::mutex> lock(s->mu);
+    for (;;) {
+        Request* q = nullptr;
+        for (;;) {
+            if (s->stop) return;
+            for (auto it = s->admitted.begin(); it != s->admitted.end(); ++it) {
+                if (!s->lanes[(*it)->h].busy) {
+                    q = *it;
+                    s->admitted.erase(it);
+                    break;
+                }
+            }
+            if (q) break;
+            s->cv_work.wait(lock);
+        }
+        Lane& lane = s->lanes[q->h];
+        lane.busy = true;
+        q->state = RUNNING;
+        q->t_start = Clock::now();
+        const int64_t k = lane.k;
+        lock.unlock();
+        run_request(s, q, k);
+        lock.lock();
+        q->t_done = Clock::now();
+        q->state = DONE;
+        s->lanes[q->h].busy = false;
+        s->free_slots.push_back(q->slot);
+        s->admitted_updates -= q->m;
+        admit_locked(s);
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void katz_server_default_opts(katz_server_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->workers = 4;
+    o->slots = 8;
+    o->slot_updates = 10000;
+    o->admit_updates = 0;
+}
+
+katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts) {
+    if (!out) return KATZ_EINVAL;
+    *out = nullptr;
+    katz_server_opts o;
+    katz_server_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.workers < 1 || o.workers > 64 || o.slots < 1 || o.slots > 1024 || o.slot_updates < 1)
+        return KATZ_EINVAL;
+    if (o.admit_updates <= 0) o.admit_updates = (int64_t)o.slots * o.slot_updates;
+    katz_server* s = new katz_server();
+    s->opts = o;
+    cudaGetDevice(&s->dev);
+    s->slots.resize((size_t)o.slots);
+    bool ok = true;
+    for (int i = 0; i < o.slots && ok; ++i) {
+        Slot& sl = s->slots[(size_t)i];
+        const size_t m = (size_t)o.slot_updates;
+        ok = cudaMalloc((void**)&sl.d_src, m * sizeof(int32_t)) == cudaSuccess &&
+             cudaMalloc((void**)&sl.d_dst, m * sizeof(int32_t)) == cudaSuccess &&
+             cudaMalloc((void**)&sl.d_ins, m) == cudaSuccess &&
+             cudaMallocHost((void**)&sl.h_src, m * sizeof(int32_t)) == cudaSuccess &&
+             cudaMallocHost((void**)&sl.h_dst, m * sizeof(int32_t)) == cudaSuccess &&
+             cudaMallocHost((void**)&sl.h_ins, m) == cudaSuccess &&
+             cudaMallocHost((void**)&sl.h_ids, (size_t)KATZ_MAX_K * sizeof(int32_t)) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&sl.copy, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&sl.h2d_done, cudaEventDisableTiming) == cudaSuccess;
+        s->free_slots.push_back(o.slots - 1 - i);
+    }
+    if (!ok) {
+        for (Slot& sl : s->slots) free_slot_memory(sl);
+        delete s;
+        return KATZ_ENOMEM;
+    }
+    for (int i = 0; i < o.workers; ++i) s->workers.emplace_back(worker_main, s);
+    *out = s;
+    return KATZ_OK;
+}
+
+katz_status katz_server_attach(katz_server_h s, katz_h h, int64_t k) {
+    if (!s || !h) return KATZ_EINVAL;
+    if (!h->ranked) return katz::fail(h, KATZ_ESTATE, "rank the graph before attaching it");
+    if (!h->opts.keep_history || h->fp32 || !h->opts.undirected)
+        return katz::fail(h, KATZ_ESTATE, "served handles need keep_history = 1, FP64 and an undirected graph");
+    if (k < 1 || k > h->k_eff) return katz::fail(h, KATZ_EINVAL, "k must lie in [1, ranked k]");
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->lanes.count(h)) return katz::fail(h, KATZ_EINVAL, "handle already attached");
+    }
+    // device buffers for the largest batch and a rebuilt adjacency with headroom,
+    // so that serving allocates nothing per request
+    const int64_t nnz_cap = h->g.nnz + h->g.nnz / 16 + 2 * s->opts.slot_updates + 1024;
+    const katz_status st = katz::dyn_reserve(h, s->opts.slot_updates, nnz_cap);
+    if (st != KATZ_OK) return st;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return katz::fail(h, KATZ_ECUDA, "attach sync");
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->lanes[h] = Lane{k, false};
+    return KATZ_OK;
+}
+
+katz_status katz_server_submit(katz_server_h s, katz_h h, const int32_t* src, const int32_t* dst,
+                               const uint8_t* is_insert, int64_t m, uint64_t* ticket) {
+    if (!s || !h || !ticket || m < 0 || m > s->opts.slot_updates) return KATZ_EINVAL;
+    if (m > 0 && (!src || !dst || !is_insert)) return KATZ_EINVAL;
+    Request* q = new Request();
+    q->h = h;
+    q->m = m;
+    q->src.assign(src, src + m);
+    q->dst.assign(dst, dst + m);
+    q->ins.assign(is_insert, is_insert + m);
+    q->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (!s->lanes.count(h)) {
+        delete q;
+        return KATZ_ESTATE;
+    }
+    q->ticket = s->next_ticket++;
+    s->requests[q->ticket] = q;
+    s->waiting.push_back(q);
+    admit_locked(s);
+    *ticket = q->ticket;
+    return KATZ_OK;
+}
+
+katz_status katz_server_wait(katz_server_h s, uint64_t ticket, int64_t timeout_ms, int32_t* ids_out,
+                             katz_request_result* res) {
+    if (!s) return KATZ_EINVAL;
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->requests.find(ticket);
+    if (it == s->requests.end()) return KATZ_EINVAL;
+    Request* q = it->second;
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (q->state != DONE) {
+        if (s->cv_done.wait_until(lock, deadline) == std::cv_status::timeout && q->state != DONE)
+            return KATZ_ETIMEOUT;
+    }
+    if (res) {
+        std::memset(res, 0, sizeof(*res));
+        res->status = q->status;
+        res->k = (int64_t)q->ids.size();
+        res->info = q->info;
+        res->queue_ms = ms_between(q->t_submit, q->t_admit);
+        res->wait_ms = ms_between(q->t_admit, q->t_start);
+        res->service_ms = ms_between(q->t_start, q->t_done);
+        res->latency_ms = ms_between(q->t_submit, q->t_done);
+    }
+    if (ids_out && !q->ids.empty()) std::memcpy(ids_out, q->ids.data(), q->ids.size() * sizeof(int32_t));
+    s->requests.erase(it);
+    delete q;
+    return KATZ_OK;
+}
+
+void katz_server_destroy(katz_server_h s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (std::thread& t : s->workers) t.join();
+    for (auto& kv : s->requests) delete kv.second;
+    for (auto& kv : s->lanes) cudaStreamSynchronize(kv.first->stream);
+    for (Slot& sl : s->slots) {
+        if (sl.copy) cudaStreamSynchronize(sl.copy);
+        free_slot_memory(sl);
+    }
+    delete s;
+}
+
+}  // extern "C"

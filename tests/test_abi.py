@@ -48,13 +48,15 @@ def test_struct_layout_matches_the_header(tmp_path):
 
     src = tmp_path / "sz.c"
     src.write_text('#include "katz.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(katz_opts), sizeof(katz_info),'
-                   ' offsetof(katz_opts, cuda_stream), offsetof(katz_info, affected));return 0;}\n')
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(katz_opts), sizeof(katz_info),'
+                   ' offsetof(katz_opts, cuda_stream), offsetof(katz_info, affected), sizeof(katz_server_opts),'
+                   ' sizeof(katz_request_result), offsetof(katz_request_result, latency_ms));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     assert got == [ctypes.sizeof(K.katz_opts), ctypes.sizeof(K.katz_info), K.katz_opts.cuda_stream.offset,
-                   K.katz_info.affected.offset]
+                   K.katz_info.affected.offset, ctypes.sizeof(K.katz_server_opts),
+                   ctypes.sizeof(K.katz_request_result), K.katz_request_result.latency_ms.offset]
 
 
 def test_create_rejects_bad_arguments_without_touching_the_device():

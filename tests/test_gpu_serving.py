@@ -1,0 +1,126 @@
+"""The serving loop (katz_server_*): update batches for several graphs,
+submitted in arrival order and run concurrently, give each request the same
+answer as applying that graph's batches one by one alone, and the last state
+of every graph matches the oracle session fed the same batches."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from tests.parity import assert_same_ranking
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+K = pytest.importorskip("paper_1807_03847_gb300")
+
+EPS = 1e-9
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _handle(g, k, D):
+    h = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(keep_history=1, deg_bound=D, r_max=128))
+    h.rank(0.0, k, EPS)
+    return h
+
+
+def _workloads():
+    out = []
+    for i, (scale, k, max_size) in enumerate([(12, 50, 400), (13, 32, 2000), (11, 100, 60)]):
+        g = gg.rmat(scale, 16, seed=300 + i)
+        D = g.deg_max() + 64
+        st = gg.stream(g, 12, seed=500 + i, max_size=max_size, rate=2000.0, deg_bound=D)
+        out.append((g, k, D, st))
+    return out
+
+
+def _alone(g, k, D, st):
+    """Each batch applied in order with katz_apply_update_batch, no server."""
+    h = _handle(g, k, D)
+    res = []
+    for j in range(len(st)):
+        info = h.update(*st.batch(j))
+        res.append((info.r, h.ranking(k).copy()))
+    h.close()
+    return res
+
+
+def test_same_result_alone_and_in_the_mix():
+    wl = _workloads()
+    alone = [_alone(*w) for w in wl]
+    handles = [_handle(g, k, D) for g, k, D, _ in wl]
+    srv = K.Server(workers=3, slots=4, slot_updates=2000)
+    for h, (g, k, D, st) in zip(handles, wl):
+        srv.attach(h, k)
+    # all requests in one arrival order (merged Poisson streams), submitted at once
+    order = sorted(((st.arrival[j], w, j) for w, (_, _, _, st) in enumerate(wl) for j in range(len(st))))
+    tickets = {}
+    for _, w, j in order:
+        tickets[(w, j)] = srv.submit(handles[w], *wl[w][3].batch(j))
+    for (w, j), t in tickets.items():
+        status, ids, res = srv.wait(t)
+        assert status == 0, (w, j, status)
+        r_alone, ids_alone = alone[w][j]
+        assert res.info.r == r_alone, (w, j)
+        np.testing.assert_array_equal(ids, ids_alone, err_msg=f"graph {w} batch {j}")
+    srv.close()
+    # the final state of each graph against the oracle fed the same batches
+    for h, (g, k, D, st) in zip(handles, wl):
+        s = oracle.Session(g.rowptr, g.col, True, D)
+        assert s.rank_static(0.0, k, EPS, 128) == oracle.OK
+        for j in range(len(st)):
+            assert s.apply_update(*st.batch(j)) == oracle.OK
+        c, l, u = s.bounds()
+        assert_same_ranking(h.ranking(k), s.ranking(), l)
+        h.close()
+
+
+def test_rejected_batch_leaves_the_graph_and_later_requests_intact():
+    g = gg.rmat(11, 16, seed=31)
+    D, k = g.deg_max() + 64, 20
+    st = gg.stream(g, 4, seed=32, max_size=50, deg_bound=D)
+    h = _handle(g, k, D)
+    ref = _alone(g, k, D, st)
+    srv = K.Server(workers=2, slots=2, slot_updates=100)
+    srv.attach(h, k)
+    # a delete of a pair that is not an edge (0 has no self-loop) is invalid
+    t0 = srv.submit(h, *st.batch(0))
+    bad = srv.submit(h, np.array([0], np.int32), np.array([0], np.int32), np.array([0], np.uint8))
+    rest = [srv.submit(h, *st.batch(j)) for j in range(1, len(st))]
+    s0, ids0, _ = srv.wait(t0)
+    sb, idsb, _ = srv.wait(bad)
+    assert s0 == 0 and sb == 1  # KATZ_EINVAL
+    np.testing.assert_array_equal(idsb, ids0)  # unchanged ranking
+    for j, t in enumerate(rest, start=1):
+        status, ids, _ = srv.wait(t)
+        assert status == 0
+        np.testing.assert_array_equal(ids, ref[j][1])
+    with pytest.raises(K.KatzError):  # larger than a slot
+        srv.submit(h, np.zeros(101, np.int32), np.ones(101, np.int32), np.ones(101, np.uint8))
+    srv.close()
+    h.close()
+
+
+def test_wait_times_out_and_one_slot_serialises_admission():
+    g = gg.rmat(12, 16, seed=41)
+    D, k = g.deg_max() + 64, 10
+    st = gg.stream(g, 6, seed=42, max_size=500, deg_bound=D)
+    ref = _alone(g, k, D, st)
+    h = _handle(g, k, D)
+    srv = K.Server(workers=4, slots=1, slot_updates=500)
+    srv.attach(h, k)
+    ts = [srv.submit(h, *st.batch(j)) for j in range(len(st))]
+    with pytest.raises(K.KatzError) as e:
+        srv.wait(ts[-1], timeout_ms=0)
+    assert e.value.name == "KATZ_ETIMEOUT"
+    for j, t in enumerate(ts):
+        status, ids, res = srv.wait(t)
+        assert status == 0
+        np.testing.assert_array_equal(ids, ref[j][1])
+        assert res.latency_ms >= res.service_ms
+    srv.close()
+    h.close()

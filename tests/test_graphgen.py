@@ -66,3 +66,30 @@ def test_update_batch_preconditions():
     g2 = gg.apply_batch(g, src, dst, ins)
     _check(g2)
     assert g2.nnz == g.nnz + 2 * int(ins.sum()) - 2 * int((1 - ins).sum())
+
+
+def test_stream_batches_are_valid_against_the_evolving_graph():
+    g = gg.rmat(10, 8, seed=3)
+    D = g.deg_max() + 4
+    st = gg.stream(g, 40, seed=7, max_size=300, rate=200.0, deg_bound=D)
+    sizes = st.sizes()
+    assert len(st) == 40 and sizes.min() >= 1 and sizes.max() <= 300
+    assert np.all(np.diff(st.arrival) > 0) and st.arrival[0] > 0
+    again = gg.stream(g, 40, seed=7, max_size=300, rate=200.0, deg_bound=D)
+    assert np.array_equal(st.src, again.src) and np.array_equal(st.is_insert, again.is_insert)
+    cur = g
+    for j in range(len(st)):
+        src, dst, ins = st.batch(j)
+        pairs = set()
+        for a, b, i in zip(src.tolist(), dst.tolist(), ins.tolist()):
+            assert a != b
+            key = (min(a, b), max(a, b))
+            assert key not in pairs
+            pairs.add(key)
+            present = b in cur.col[cur.rowptr[a]:cur.rowptr[a + 1]]
+            assert present != bool(i), (j, a, b, i)
+        cur = gg.apply_batch(cur, src, dst, ins)
+        assert cur.deg_max() <= D
+    # both kinds of update occur, and the mean gap matches the rate
+    assert 0 < st.is_insert.mean() < 1
+    assert 0.002 < st.arrival[-1] / len(st) < 0.01
