@@ -568,7 +568,7 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
             for (int64_t q = first[u]; q < first[u + 1]; ++q) crow[q] = (int32_t)u;
         KCHK2(dmalloc(&g.chunk_first, first.size()), "cudaMalloc");
         KCHK2(dmalloc(&g.chunk_row, crow.size()), "cudaMalloc");
-        KCHK2(dmalloc(&g.chunk_part, crow.size()), "cudaMalloc");
+        KCHK2(dmalloc(&g.chunk_part, 3 * crow.size()), "cudaMalloc");
         KCHK2(cudaMemcpyAsync(g.chunk_first, first.data(), first.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                               h->stream), "copy chunks");
         KCHK2(cudaMemcpyAsync(g.chunk_row, crow.data(), crow.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
@@ -866,7 +866,7 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
                 g.chunk_row = nullptr;
                 g.chunk_part = nullptr;
                 if ((e = dmalloc(&g.chunk_row, (size_t)chunks)) != cudaSuccess ||
-                    (e = dmalloc(&g.chunk_part, (size_t)chunks)) != cudaSuccess)
+                    (e = dmalloc(&g.chunk_part, 3 * (size_t)chunks)) != cudaSuccess)
                     return cuda_fail(h, e, "cudaMalloc chunks");
             }
             std::vector<int32_t> crow((size_t)std::max<int64_t>(chunks, 1));

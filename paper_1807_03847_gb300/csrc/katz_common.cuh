@@ -145,7 +145,7 @@ struct DeviceGraph {
     int32_t* inv = nullptr;   // original -> internal id
     int32_t* chunk_row = nullptr;     // [chunks] row of each chunk
     int64_t* chunk_first = nullptr;   // [row_warp + 1] first chunk of each CHUNK row
-    double* chunk_part = nullptr;     // [chunks] chunk sums
+    double* chunk_part = nullptr;     // [3 chunks] chunk partial sums (three words per chunk)
     SpmvLayout layout{};
 };
 

@@ -17,11 +17,22 @@
 // The walk vector is gathered with read-only loads (one L2 request per arc:
 // this access, not HBM bandwidth, bounds the kernel on power-law graphs).
 //
-// Row sums use a fixed order: each lane adds its terms eight at a time as a
-// pairwise tree and chains the eight-term sums; lanes then meet in a shuffle
-// tree.  Results are reproducible, and the longest chain of additions in any
-// row sum (max_sum_depth) is small; the FP32-certified mode needs it for its
-// rounding-error bound.
+// Row sums of an FP64 level are exact: each lane adds its terms into a
+// 128-bit fixed-point accumulator whose scale follows the largest exponent
+// seen (XAcc below), lanes and chunks merge their accumulators, and the
+// total is rounded once to FP64.  A row sum is therefore the correctly
+// rounded sum of its terms (up to a truncation near 2^-90 relative), for any
+// order and any split of the terms over lanes, warps or chunks: the full
+// SpMV, the repair of single rows and the chunked hub rows all give the same
+// bits.  The adds run on the integer pipes; GB300 executes FP64 additions at
+// a small fraction of its integer rate, and one FP64 add per arc was the
+// limit of the kernel.
+//
+// FP32 levels (FP32-certified mode) add in FP32 in a fixed order: each lane
+// adds its terms eight at a time as a pairwise tree and chains the
+// eight-term sums; lanes then meet in a shuffle tree.  The longest chain of
+// additions in a row sum (max_sum_depth) enters that mode's rounding-error
+// bound.
 //
 // Level types: FP64 mode computes every level in FP64.  The FP32-certified
 // mode starts in FP64 and computes the levels from Ctrl::f32_from on in FP32
@@ -108,9 +119,232 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
 template <typename Acc>
 __device__ __forceinline__ Acc addA(Acc a, Acc b);
 template <>
-__device__ __forceinline__ double addA<double>(double a, double b) { return __dadd_rn(a, b); }
-template <>
 __device__ __forceinline__ float addA<float>(float a, float b) { return __fadd_rn(a, b); }
+
+// ---------------------------------------------------------------------------
+// Exact accumulation of non-negative doubles.
+//
+// A term x = m * 2^(e - 1075) (m < 2^53 its integer mantissa, e >= 1 its
+// biased exponent, e = 1 for subnormals and zero) is added to
+// W * 2^(E - 1075 - XF), W a 128-bit integer in four 32-bit words and E the
+// largest exponent the accumulator has seen, as the integer
+// m * 2^(XF - (E - e)).  With XF = 31 a term with E - e <= 31 spans at most
+// three words after its shift, so the common case is three funnel shifts and
+// one carry chain; a term more than 2^31 below E is truncated at W's last
+// bit (slow path), and a larger exponent shifts W right (slow path).  W stays
+// below 2^85 per 2^1 terms of the top binade, so no sum of a row can carry
+// out of 128 bits.  E = 0 marks an empty accumulator.
+// ---------------------------------------------------------------------------
+constexpr int XF = 31;
+
+struct XAcc {
+    uint32_t w0, w1, w2, w3;
+    int E;
+};
+
+__device__ __forceinline__ XAcc xacc_zero() { return XAcc{0u, 0u, 0u, 0u, 0}; }
+
+__device__ __forceinline__ unsigned long long lo64(const XAcc& a) {
+    return ((unsigned long long)a.w1 << 32) | a.w0;
+}
+__device__ __forceinline__ unsigned long long hi64(const XAcc& a) {
+    return ((unsigned long long)a.w3 << 32) | a.w2;
+}
+__device__ __forceinline__ void set128(XAcc& a, unsigned long long lo, unsigned long long hi) {
+    a.w0 = (uint32_t)lo;
+    a.w1 = (uint32_t)(lo >> 32);
+    a.w2 = (uint32_t)hi;
+    a.w3 = (uint32_t)(hi >> 32);
+}
+
+// W >>= d (truncating), d >= 0
+__device__ __forceinline__ void shr128(XAcc& a, int d) {
+    if (d <= 0) return;
+    unsigned long long lo = lo64(a), hi = hi64(a);
+    if (d >= 128) {
+        lo = 0ull;
+        hi = 0ull;
+    } else if (d >= 64) {
+        lo = hi >> (d - 64);
+        hi = 0ull;
+    } else {
+        lo = (lo >> d) | (hi << (64 - d));
+        hi >>= d;
+    }
+    set128(a, lo, hi);
+}
+
+// W += (p2:p1:p0)
+__device__ __forceinline__ void add96(XAcc& a, uint32_t p0, uint32_t p1, uint32_t p2) {
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2), "+r"(a.w3)
+        : "r"(p0), "r"(p1), "r"(p2));
+}
+
+// W += V (128 bits)
+__device__ __forceinline__ void add128(XAcc& a, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32 %3, %3, %7;"
+        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2), "+r"(a.w3)
+        : "r"(v0), "r"(v1), "r"(v2), "r"(v3));
+}
+
+__device__ __forceinline__ int exp_of(double x) { return max((int)((uint32_t)__double2hiint(x) >> 20), 1); }
+
+// the rare cases of xacc_add: E < e (rescale first) or E - e > XF (truncate)
+__device__ __noinline__ XAcc xacc_add_slow(XAcc a, int e, uint32_t m0, uint32_t m1) {
+    int d = a.E - e;
+    if (d < 0) {
+        shr128(a, -d);
+        a.E = e;
+        d = 0;
+    }
+    if (d <= XF) {
+        const uint32_t sh = (uint32_t)(XF - d);
+        add96(a, m0 << sh, __funnelshift_l(m0, m1, sh), __funnelshift_l(m1, 0u, sh));
+    } else {
+        const int rs = d - XF;  // m * 2^-rs, truncated
+        if (rs < 53) {
+            const unsigned long long m = (((unsigned long long)m1 << 32) | m0) >> rs;
+            add96(a, (uint32_t)m, (uint32_t)(m >> 32), 0u);
+        }
+    }
+    return a;
+}
+
+__device__ __forceinline__ void xacc_add(XAcc& a, double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int eb = (int)(hi >> 20);
+    const int e = (hi | lo) ? max(eb, 1) : a.E;  // a zero term (padding) adds nothing on the fast path
+    const uint32_t m1 = (hi & 0xFFFFFu) | (eb ? 0x100000u : 0u);
+    const int d = a.E - e;
+    if ((unsigned)d > (unsigned)XF) {
+        a = xacc_add_slow(a, e, lo, m1);
+        return;
+    }
+    const uint32_t sh = (uint32_t)(XF - d);
+    add96(a, lo << sh, __funnelshift_l(lo, m1, sh), __funnelshift_l(m1, 0u, sh));
+}
+
+// a += b (any exponents)
+__device__ __forceinline__ void xacc_merge(XAcc& a, XAcc b) {
+    if (b.E > a.E) {
+        const XAcc t = a;
+        a = b;
+        b = t;
+    }
+    shr128(b, a.E - b.E);
+    add128(a, b.w0, b.w1, b.w2, b.w3);
+}
+
+// Sum over groups of `width` lanes (8 or 32): every lane aligns to the
+// group's largest exponent, then the aligned integers meet in a shuffle tree.
+template <int width>
+__device__ __forceinline__ XAcc xacc_group_sum(XAcc a) {
+    int E = a.E;
+    if constexpr (width == 32) {
+        E = __reduce_max_sync(FULL, E);
+    } else {
+#pragma unroll
+        for (int off = width / 2; off; off >>= 1) E = max(E, __shfl_xor_sync(FULL, E, off, width));
+    }
+    shr128(a, E - a.E);
+    a.E = E;
+#pragma unroll
+    for (int off = width / 2; off; off >>= 1) {
+        const uint32_t v0 = __shfl_down_sync(FULL, a.w0, off, width);
+        const uint32_t v1 = __shfl_down_sync(FULL, a.w1, off, width);
+        const uint32_t v2 = __shfl_down_sync(FULL, a.w2, off, width);
+        const uint32_t v3 = __shfl_down_sync(FULL, a.w3, off, width);
+        add128(a, v0, v1, v2, v3);
+    }
+    return a;
+}
+
+// W * 2^(E - 1075 - XF) rounded to the nearest double (ties to even)
+__device__ __forceinline__ double xacc_to_double(const XAcc& a) {
+    const unsigned long long L = lo64(a), H = hi64(a);
+    if ((L | H) == 0ull) return 0.0;
+    const int p = H ? 127 - __clzll((long long)H) : 63 - __clzll((long long)L);  // top bit
+    int be = p - 52 + a.E - XF;
+    unsigned long long T;
+    bool rnd = false, sticky = false;
+    if (p <= 52) {
+        T = L << (52 - p);
+    } else {
+        const int sft = p - 52;  // 1..75
+        const int rb = sft - 1;  // round bit; sticky = the bits below it
+        if (rb < 64) {
+            rnd = (L >> rb) & 1ull;
+            sticky = rb ? (L & ((1ull << rb) - 1ull)) != 0ull : false;
+        } else {
+            rnd = (H >> (rb - 64)) & 1ull;
+            sticky = L != 0ull || (rb > 64 && (H & ((1ull << (rb - 64)) - 1ull)) != 0ull);
+        }
+        XAcc t = a;
+        shr128(t, sft);
+        T = lo64(t);
+    }
+    if (rnd && (sticky || (T & 1ull))) {
+        T += 1ull;
+        if (T >> 53) {
+            T >>= 1;
+            be += 1;
+        }
+    }
+    if (be >= 1) return __longlong_as_double((long long)(((unsigned long long)be << 52) | (T & 0xFFFFFFFFFFFFFull)));
+    return ldexp((double)T, be - 1075);  // subnormal result
+}
+
+// Exact sum of x[col[j]] for j in [a, b) with stride `step` from a + first:
+// groups of G loads in flight (past the end: zero, which the fast path adds
+// as nothing).  G = 8 for rows whose lanes see many terms, G = 4 for short
+// rows (fewer padded slots).  An empty accumulator starts at the largest
+// exponent of its first group, so it rarely has to rescale.
+template <int G>
+__device__ __forceinline__ XAcc strided_xsum(const int32_t* __restrict__ col, const double* __restrict__ x,
+                                             int64_t a, int64_t b, int first, int step) {
+    XAcc s = xacc_zero();
+    for (int64_t j = a + first; j < b; j += G * (int64_t)step) {
+        double v[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int64_t jj = j + (int64_t)q * step;
+            v[q] = jj < b ? __ldg(x + col[jj]) : 0.0;
+        }
+        if (s.E == 0) {
+            int em = exp_of(v[0]);
+#pragma unroll
+            for (int q = 1; q < G; ++q) em = max(em, exp_of(v[q]));
+            s.E = em;
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) xacc_add(s, v[q]);
+    }
+    return s;
+}
+
+// chunk partials: three words per chunk (W low, W high, E) for FP64 levels;
+// the first word holds the FP32 sum (exact in FP64) for FP32 levels
+__device__ __forceinline__ void store_part(double* part, int64_t ch, const XAcc& a) {
+    unsigned long long* w = (unsigned long long*)part + 3 * ch;
+    w[0] = lo64(a);
+    w[1] = hi64(a);
+    w[2] = (unsigned long long)(unsigned)a.E;
+}
+
+__device__ __forceinline__ XAcc load_part(const double* part, int64_t ch) {
+    const unsigned long long* w = (const unsigned long long*)part + 3 * ch;
+    XAcc a;
+    set128(a, w[0], w[1]);
+    a.E = (int)w[2];
+    return a;
+}
 
 // Sum of x[col[j]] for j in [a, b) with stride `step` from a + first: eight
 // loads in flight, each group of eight added as a pairwise tree (depth 3),
@@ -133,7 +367,8 @@ __device__ __forceinline__ Acc strided_sum(const int32_t* __restrict__ col, cons
     return s;
 }
 
-// One level: Tin = type of level r-1, Tout = type of level r (Acc = Tout).
+// One level: Tin = type of level r-1, Tout = type of level r.  FP64 levels
+// sum exactly (XAcc); FP32 levels add in FP32 (fixed pairwise order).
 template <typename Off, typename Tin, typename Tout>
 __device__ __forceinline__ void spmv_rows(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
                                           const SpmvLayout& L, const Tin* __restrict__ x, const Epi& ep,
@@ -142,37 +377,69 @@ __device__ __forceinline__ void spmv_rows(const Off* __restrict__ rowptr, const 
                                           const IterParams& p) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t b = blockIdx.x;
-    typedef Tout Acc;
-    if (b >= L.blk_thread) {  // THREAD rows
-        const int64_t u = L.row_thread + (b - L.blk_thread) * BLOCK + tid;
-        if (u < L.n) finish_row<Acc>(u, strided_sum<Tin, Acc>(col, x, rowptr[u], rowptr[u + 1], 0, 1), ep, p);
-    } else if (b >= L.blk_octet) {  // OCTET rows
-        const int64_t u = L.row_octet + (b - L.blk_octet) * (BLOCK / 8) + (tid >> 3);
-        const int sub = tid & 7;
-        Acc s = (Acc)0;
-        if (u < L.row_thread) s = strided_sum<Tin, Acc>(col, x, rowptr[u], rowptr[u + 1], sub, 8);
-#pragma unroll
-        for (int off = 4; off; off >>= 1) s = addA<Acc>(s, __shfl_down_sync(FULL, s, off, 8));
-        if (sub == 0 && u < L.row_thread) finish_row<Acc>(u, s, ep, p);
-    } else if (b >= L.blk_warp) {  // WARP rows
-        const int64_t u = L.row_warp + (b - L.blk_warp) * WARPS + wid;
-        Acc s = (Acc)0;
-        if (u < L.row_octet) s = strided_sum<Tin, Acc>(col, x, rowptr[u], rowptr[u + 1], lane, 32);
-#pragma unroll
-        for (int off = 16; off; off >>= 1) s = addA<Acc>(s, __shfl_down_sync(FULL, s, off));
-        if (lane == 0 && u < L.row_octet) finish_row<Acc>(u, s, ep, p);
-    } else {  // CHUNK rows: one warp per chunk of CHUNK_ARCS arcs
-        const int64_t ch = b * WARPS + wid;
-        Acc s = (Acc)0;
-        if (ch < L.chunks) {
-            const int64_t u = chunk_row[ch];
-            const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
-            const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
-            s = strided_sum<Tin, Acc>(col, x, j0, j1, lane, 32);
+    if constexpr (sizeof(Tout) == 8) {
+        static_assert(sizeof(Tin) == 8, "FP64 levels follow FP64 levels");
+        if (b >= L.blk_thread) {  // THREAD rows
+            const int64_t u = L.row_thread + (b - L.blk_thread) * BLOCK + tid;
+            if (u < L.n) finish_row<double>(u, xacc_to_double(strided_xsum<4>(col, x, rowptr[u], rowptr[u + 1], 0, 1)), ep, p);
+        } else if (b >= L.blk_octet) {  // OCTET rows
+            const int64_t u = L.row_octet + (b - L.blk_octet) * (BLOCK / 8) + (tid >> 3);
+            const int sub = tid & 7;
+            XAcc s = xacc_zero();
+            if (u < L.row_thread) s = strided_xsum<4>(col, x, rowptr[u], rowptr[u + 1], sub, 8);
+            s = xacc_group_sum<8>(s);
+            if (sub == 0 && u < L.row_thread) finish_row<double>(u, xacc_to_double(s), ep, p);
+        } else if (b >= L.blk_warp) {  // WARP rows
+            const int64_t u = L.row_warp + (b - L.blk_warp) * WARPS + wid;
+            XAcc s = xacc_zero();
+            if (u < L.row_octet) s = strided_xsum<8>(col, x, rowptr[u], rowptr[u + 1], lane, 32);
+            s = xacc_group_sum<32>(s);
+            if (lane == 0 && u < L.row_octet) finish_row<double>(u, xacc_to_double(s), ep, p);
+        } else {  // CHUNK rows: one warp per chunk of CHUNK_ARCS arcs
+            const int64_t ch = b * WARPS + wid;
+            XAcc s = xacc_zero();
+            if (ch < L.chunks) {
+                const int64_t u = chunk_row[ch];
+                const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+                const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+                s = strided_xsum<8>(col, x, j0, j1, lane, 32);
+            }
+            s = xacc_group_sum<32>(s);
+            if (lane == 0 && ch < L.chunks) store_part(chunk_part, ch, s);
         }
+    } else {
+        typedef float Acc;
+        if (b >= L.blk_thread) {  // THREAD rows
+            const int64_t u = L.row_thread + (b - L.blk_thread) * BLOCK + tid;
+            if (u < L.n) finish_row<Acc>(u, strided_sum<Tin, Acc>(col, x, rowptr[u], rowptr[u + 1], 0, 1), ep, p);
+        } else if (b >= L.blk_octet) {  // OCTET rows
+            const int64_t u = L.row_octet + (b - L.blk_octet) * (BLOCK / 8) + (tid >> 3);
+            const int sub = tid & 7;
+            Acc s = (Acc)0;
+            if (u < L.row_thread) s = strided_sum<Tin, Acc>(col, x, rowptr[u], rowptr[u + 1], sub, 8);
 #pragma unroll
-        for (int off = 16; off; off >>= 1) s = addA<Acc>(s, __shfl_down_sync(FULL, s, off));
-        if (lane == 0 && ch < L.chunks) chunk_part[ch] = (double)s;  // exact for FP32 sums
+            for (int off = 4; off; off >>= 1) s = addA<Acc>(s, __shfl_down_sync(FULL, s, off, 8));
+            if (sub == 0 && u < L.row_thread) finish_row<Acc>(u, s, ep, p);
+        } else if (b >= L.blk_warp) {  // WARP rows
+            const int64_t u = L.row_warp + (b - L.blk_warp) * WARPS + wid;
+            Acc s = (Acc)0;
+            if (u < L.row_octet) s = strided_sum<Tin, Acc>(col, x, rowptr[u], rowptr[u + 1], lane, 32);
+#pragma unroll
+            for (int off = 16; off; off >>= 1) s = addA<Acc>(s, __shfl_down_sync(FULL, s, off));
+            if (lane == 0 && u < L.row_octet) finish_row<Acc>(u, s, ep, p);
+        } else {  // CHUNK rows: one warp per chunk of CHUNK_ARCS arcs
+            const int64_t ch = b * WARPS + wid;
+            Acc s = (Acc)0;
+            if (ch < L.chunks) {
+                const int64_t u = chunk_row[ch];
+                const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+                const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+                s = strided_sum<Tin, Acc>(col, x, j0, j1, lane, 32);
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) s = addA<Acc>(s, __shfl_down_sync(FULL, s, off));
+            if (lane == 0 && ch < L.chunks) chunk_part[3 * ch] = (double)s;  // exact for FP32 sums
+        }
     }
 }
 
@@ -206,15 +473,15 @@ spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col
         spmv_rows<Off, float, float>(rowptr, col, L, (const float*)xs, ep, chunk_row, chunk_first, chunk_part, p);
 }
 
-// CHUNK rows: add the chunk sums of each row as a pairwise tree (in the
-// level's precision), then finish the row.
+// CHUNK rows of an FP32 level: add the chunk sums of each row as a pairwise
+// tree in FP32, then finish the row.
 template <typename Acc>
 __device__ __forceinline__ Acc chunk_tree(const double* __restrict__ part, int64_t first, int64_t count) {
     Acc buf[64];
     Acc total = (Acc)0;
     for (int64_t base = 0; base < count; base += 64) {
         const int m = (int)min((int64_t)64, count - base);
-        for (int q = 0; q < 64; ++q) buf[q] = q < m ? (Acc)part[first + base + q] : (Acc)0;
+        for (int q = 0; q < 64; ++q) buf[q] = q < m ? (Acc)part[3 * (first + base + q)] : (Acc)0;
         for (int w = 32; w >= 1; w >>= 1)
             for (int q = 0; q < w; ++q) buf[q] = addA<Acc>(buf[2 * q], buf[2 * q + 1]);
         total = addA<Acc>(total, buf[0]);
@@ -235,10 +502,13 @@ __global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= L.row_warp) return;
     const int64_t first = chunk_first[u], count = chunk_first[u + 1] - first;
-    if (store_level || r_cur < ctrl->f32_from)
-        finish_row<double>(u, chunk_tree<double>(chunk_part, first, count), ep, p);
-    else
+    if (store_level || r_cur < ctrl->f32_from) {
+        XAcc t = xacc_zero();  // chunk partials merged in chunk order
+        for (int64_t ch = first; ch < first + count; ++ch) xacc_merge(t, load_part(chunk_part, ch));
+        finish_row<double>(u, xacc_to_double(t), ep, p);
+    } else {
         finish_row<float>(u, chunk_tree<float>(chunk_part, first, count), ep, p);
+    }
 }
 
 }  // namespace
@@ -288,14 +558,14 @@ cudaError_t launch_spmv_store(const DeviceGraph& g, const IterBuffers& b, const 
     return spmv_launch(g, b, p, level, st);
 }
 
-// One warp per listed row: the row's s_level recomputed with the same
-// summation order as spmv_rows_kernel uses for that row (its row mode is set
-// by its internal index), so a repaired level equals a full recomputation.
+// One warp per listed row: the row's s_level recomputed with the lane
+// partition spmv_rows_kernel uses for that row (its row mode is set by its
+// internal index) and the same merges, so a repaired level has the bits of a
+// full recomputation.
 template <typename Off>
 __global__ void rows_store_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L,
                                   const int32_t* __restrict__ rows, const unsigned long long* nrows_ptr,
-                                  double* walk, const int64_t* __restrict__ chunk_first, double* chunk_part,
-                                  IterParams p, int level) {
+                                  double* walk, const int64_t* __restrict__ chunk_first, IterParams p, int level) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     const int64_t nrows = (int64_t)*nrows_ptr;
@@ -304,30 +574,24 @@ __global__ void rows_store_kernel(const Off* __restrict__ rowptr, const int32_t*
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < nrows; w += warps) {
         const int64_t u = rows[w];
         const int64_t a = rowptr[u], e = rowptr[u + 1];
-        double s = 0.0;
+        XAcc s = xacc_zero();
         if (u >= L.row_thread) {          // THREAD: lane 0 alone, step 1
-            if (lane == 0) s = strided_sum<double, double>(col, x, a, e, 0, 1);
-        } else if (u >= L.row_octet) {    // OCTET: lanes 0..7, step 8, tree of width 8
-            if (lane < 8) s = strided_sum<double, double>(col, x, a, e, lane, 8);
-#pragma unroll
-            for (int off = 4; off; off >>= 1) s = __dadd_rn(s, __shfl_down_sync(FULL, s, off, 8));
+            if (lane == 0) s = strided_xsum<4>(col, x, a, e, 0, 1);
+        } else if (u >= L.row_octet) {    // OCTET: lanes 0..7, step 8
+            if (lane < 8) s = strided_xsum<4>(col, x, a, e, lane, 8);
+            s = xacc_group_sum<8>(s);
         } else if (u >= L.row_warp) {     // WARP
-            s = strided_sum<double, double>(col, x, a, e, lane, 32);
-#pragma unroll
-            for (int off = 16; off; off >>= 1) s = __dadd_rn(s, __shfl_down_sync(FULL, s, off));
-        } else {                          // CHUNK: chunk sums, then the tree over them
+            s = strided_xsum<8>(col, x, a, e, lane, 32);
+            s = xacc_group_sum<32>(s);
+        } else {                          // CHUNK: chunk partials merged in chunk order
             for (int64_t ch = chunk_first[u]; ch < chunk_first[u + 1]; ++ch) {
                 const int64_t j0 = a + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
                 const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, e);
-                double t = strided_sum<double, double>(col, x, j0, j1, lane, 32);
-#pragma unroll
-                for (int off = 16; off; off >>= 1) t = __dadd_rn(t, __shfl_down_sync(FULL, t, off));
-                if (lane == 0) chunk_part[ch] = t;
+                const XAcc t = xacc_group_sum<32>(strided_xsum<8>(col, x, j0, j1, lane, 32));
+                if (lane == 0) xacc_merge(s, t);
             }
-            __syncwarp();
-            if (lane == 0) s = chunk_tree<double>(chunk_part, chunk_first[u], chunk_first[u + 1] - chunk_first[u]);
         }
-        if (lane == 0) y[u] = __dmul_rn(p.alpha, s);
+        if (lane == 0) y[u] = __dmul_rn(p.alpha, xacc_to_double(s));
     }
 }
 
@@ -338,12 +602,12 @@ cudaError_t launch_rows_store(const DeviceGraph& g, const IterBuffers& b, const 
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (g.off64)
         rows_store_kernel<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, g.layout, rows,
-                                                                    nrows_dev, (double*)b.walk, g.chunk_first,
-                                                                    g.chunk_part, p, level);
+                                                                    nrows_dev, (double*)b.walk, g.chunk_first, p,
+                                                                    level);
     else
         rows_store_kernel<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, g.layout, rows,
-                                                                    nrows_dev, (double*)b.walk, g.chunk_first,
-                                                                    g.chunk_part, p, level);
+                                                                    nrows_dev, (double*)b.walk, g.chunk_first, p,
+                                                                    level);
     return cudaGetLastError();
 }
 
