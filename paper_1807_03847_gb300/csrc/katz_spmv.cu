@@ -450,8 +450,10 @@ __device__ __forceinline__ Epi make_epi(void* y, double* c64, double* c32, doubl
                ctrl->theta_prev, bstate(ctrl), 0};
 }
 
+// Six 256-thread blocks per SM (40 registers): the gathers need the warps in
+// flight more than the lanes need registers.
 template <typename Off>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, 6)
 spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L, double* walk,
                  double* c64, double* c32, double* lb, double* ub, uint8_t* active, const int32_t* __restrict__ perm,
                  const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first, double* chunk_part,
