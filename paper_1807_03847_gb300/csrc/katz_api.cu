@@ -95,11 +95,9 @@ katz_status ensure_iter_buffers(katz_handle* h) {
     KALLOC(walk, (size_t)slots * stride * esz);
     b.walk = walk;
     KALLOC(b.c, n);
-    if (h->fp32) {
-        KALLOC(b.c32, n);
-        KALLOC(b.lb, n);
-        KALLOC(b.ub, n);
-    }
+    KALLOC(b.lb, n);  // bounds of the active nodes at the last level (cert mode: monotone)
+    KALLOC(b.ub, n);
+    if (h->fp32) KALLOC(b.c32, n);
     KALLOC(b.active, n);
     KALLOC(b.cand_l, n);
     KALLOC(b.cand_u, n);
@@ -314,7 +312,8 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
         DALLOC(d.ins_start, n);
         DALLOC(d.vbits, (n + 31) / 32);
         DALLOC(d.frontier, n);
-        DALLOC(d.fsize, 1);
+        DALLOC(d.fsize, 2);
+        DALLOC(d.hub_epoch, std::max<int64_t>(g.layout.row_warp, 1));
         DALLOC(d.n_ins_rows, 1);
         DALLOC(d.err, 1);
         DALLOC(h->rp_new, n + 1);
@@ -331,20 +330,21 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
         cudaFree(d.src);
         cudaFree(d.dst);
         cudaFree(d.ins);
-        cudaFree(d.pos_a);
-        cudaFree(d.pos_b);
         cudaFree(d.ins_rows);
         cudaFree(d.bucket);
         cudaFree(d.table);
-        d = DynBuffers{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, d.err, d.delta, d.ins_cnt,
-                       d.cursor, d.touched, d.ins_start, nullptr, d.n_ins_rows, nullptr, d.vbits, d.frontier,
-                       d.fsize};
+        d.src = nullptr;
+        d.dst = nullptr;
+        d.ins = nullptr;
+        d.ins_rows = nullptr;
+        d.bucket = nullptr;
+        d.table = nullptr;
+        d.table_mask = 0;
+        d.cap = 0;
         const int64_t cap = std::max<int64_t>(m, 1024);
         DALLOC(d.src, cap);
         DALLOC(d.dst, cap);
         DALLOC(d.ins, cap);
-        DALLOC(d.pos_a, cap);
-        DALLOC(d.pos_b, cap);
         DALLOC(d.ins_rows, 2 * cap);
         DALLOC(d.bucket, 2 * cap);
         int64_t tsize = 1;
@@ -413,7 +413,7 @@ void katz_destroy(katz_h h) {
     cudaFree(h->d_scratch);
     {
         DynBuffers& d = h->dyn;
-        for (void* ptr : {(void*)d.src, (void*)d.dst, (void*)d.ins, (void*)d.pos_a, (void*)d.pos_b, (void*)d.table,
+        for (void* ptr : {(void*)d.src, (void*)d.dst, (void*)d.ins, (void*)d.hub_epoch, (void*)d.table,
                           (void*)d.err, (void*)d.delta, (void*)d.ins_cnt, (void*)d.cursor, (void*)d.touched,
                           (void*)d.ins_start, (void*)d.ins_rows, (void*)d.n_ins_rows, (void*)d.bucket,
                           (void*)d.vbits, (void*)d.frontier, (void*)d.fsize})
@@ -789,6 +789,9 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
     const int64_t n = g.n;
     const int r = h->r;
     if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+    h->launches = 0;
+    h->big_paths = 0;
+    const bool hubs = g.layout.row_warp > 0;
     // ---- buffers --------------------------------------------------------------
     {
         const katz_status rs = katz::dyn_reserve(h, m, 0);
@@ -806,6 +809,7 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
         if ((e = cudaMemsetAsync(d.err, 0, sizeof(int32_t), h->stream)) != cudaSuccess ||
             (e = dyn_validate(g, d, m, h->D, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "validate batch");
+        h->launches += 2;
         int32_t err = 0;
         if ((e = cudaMemcpyAsync(&err, d.err, sizeof(err), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
@@ -822,6 +826,7 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
         // ---- apply: new offsets, rows rebuilt into the spare col buffer -----------
         if ((e = dyn_prepare(g, d, m, h->rp_new, h->deg_tmp, h->scan_sums, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "prepare rebuild");
+        h->launches += 8;  // 5 bucket/degree kernels + 3 scan passes
         int64_t nnz_new = 0;
         if ((e = cudaMemcpyAsync(&nnz_new, h->rp_new + n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream)) !=
                 cudaSuccess ||
@@ -844,10 +849,12 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
         }
         if ((e = dyn_rebuild(g, d, m, h->rp_new, h->col_spare, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "rebuild rows");
+        h->launches += (g.n > g.layout.row_warp ? 1 : 0) + (g.layout.chunks > 0 ? 1 : 0) + (hubs ? 1 : 0) + 1;
         std::swap(g.col, h->col_spare);
         std::swap(h->col_cap, h->col_spare_cap);
         g.nnz = nnz_new;
         if ((e = dyn_clear(g, d, m, h->stream)) != cudaSuccess) return cuda_fail(h, e, "clear batch");
+        h->launches += 1;
         // chunk table of the CHUNK rows from their new degrees
         {
             const int64_t rw = g.layout.row_warp;
@@ -884,39 +891,48 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
         // ---- repair s_1..s_r: affected rows only, or whole levels once the
         //      affected set is large (Sec. 4) ------------------------------------------
         if ((e = dyn_seed(g, d, m, h->stream)) != cudaSuccess) return cuda_fail(h, e, "seed frontier");
-        unsigned long long fs = 0;
-        if ((e = cudaMemcpyAsync(&fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+        h->launches += 1;
+        unsigned long long fs[2] = {0, 0};  // frontier size, sum of its degrees
+        if ((e = cudaMemcpyAsync(fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "frontier size");
         const double tau = h->opts.frontier_abort_frac > 0 ? h->opts.frontier_abort_frac : 0.05;
-        int64_t lo = 0, hi = (int64_t)fs;
-        bool full = false;
+        // a level goes full once the frontier holds more than tau of the nodes
+        // or of the arcs (its rows' arcs are the work of a frontier level)
+        auto too_big = [&](unsigned long long cnt, unsigned long long vol) {
+            return (double)cnt > tau * (double)n || (double)vol > tau * (double)g.nnz;
+        };
+        int64_t lo = 0, hi = (int64_t)fs[0];
+        bool full = too_big(fs[0], fs[1]);
         for (int i = 1; i <= r; ++i) {
-            if (!full && (double)hi > tau * (double)n) full = true;
             if (full) {
                 if ((e = launch_spmv_store(g, h->b, h->p, i, h->stream)) != cudaSuccess)
                     return cuda_fail(h, e, "full level");
                 ++full_levels;
+                h->launches += hubs ? 2 : 1;
                 continue;
             }
-            if ((e = launch_rows_store(g, h->b, h->p, d.frontier, d.fsize, hi, i, h->stream)) != cudaSuccess)
+            if ((e = launch_rows_store(g, h->b, h->p, d.frontier, d.fsize, hi, d.vbits, i, h->stream)) != cudaSuccess)
                 return cuda_fail(h, e, "repair rows");
+            h->launches += (hi > 0 ? 1 : 0) + (hi > 0 && g.layout.chunks > 0 ? 2 : 0);
             if (i < r) {
-                if ((e = dyn_expand(g, d, lo, hi, h->stream)) != cudaSuccess) return cuda_fail(h, e, "expand");
-                if ((e = cudaMemcpyAsync(&fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+                if ((e = dyn_expand(g, d, lo, hi, i, h->stream)) != cudaSuccess) return cuda_fail(h, e, "expand");
+                h->launches += hi > lo ? 1 + (g.layout.chunks > 0 ? 1 : 0) : 0;
+                if ((e = cudaMemcpyAsync(fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
                     (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
                     return cuda_fail(h, e, "frontier size");
                 lo = hi;
-                hi = (int64_t)fs;
+                hi = (int64_t)fs[0];
+                full = too_big(fs[0], fs[1]);
             }
         }
         affected = full ? n : hi;
         if ((e = dyn_recompute_c(g, h->b, d, h->p, r, full, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "recompute c");
+        h->launches += 1;
     }
     // ---- bounds, reactivation, converged() at level r, then more iterations ------
-    h->launches = 0;
-    h->big_paths = 0;
+    h->launches += 5;  // theta_lb, reactivate, select, count, finalize
     if ((e = dyn_reactivate(g, h->b, h->p, r, h->stream)) != cudaSuccess ||
         (e = launch_select(g, h->b, h->p, h->b.cand_l, h->b.cand_u, h->b.cand_id, h->fp32, h->stream)) != cudaSuccess ||
         (e = launch_count(g, h->b, h->p, h->fp32, h->stream)) != cudaSuccess ||

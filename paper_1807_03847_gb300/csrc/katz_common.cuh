@@ -106,11 +106,6 @@ __device__ __forceinline__ void node_bounds(double c64, double c32, double s_r, 
     u = __dadd_ru(c_hi, __dmul_ru(__dmul_ru(p.ag_hi, s_r), b.his));
 }
 
-// Position order of converged()'s partial sort: larger l first, ties by smaller id.
-__device__ __forceinline__ bool ranks_before(double la, int32_t ia, double lb, int32_t ib) {
-    return la > lb || (la == lb && ia < ib);
-}
-
 template <typename T>
 __device__ __forceinline__ T* walk_slot(T* base, const IterParams& p, int level) {
     return base + (size_t)(level % p.slots) * (size_t)p.stride;
@@ -176,22 +171,21 @@ struct DynBuffers {
     int32_t* src = nullptr;          // batch, original ids
     int32_t* dst = nullptr;
     uint8_t* ins = nullptr;
-    int64_t* pos_a = nullptr;        // position of arc src->dst in the old col (deletions)
-    int64_t* pos_b = nullptr;
-    unsigned long long* table = nullptr;  // open-addressing set of unordered pairs
+    unsigned long long* table = nullptr;  // open-addressing set of unordered internal-id pairs (bit 63: delete)
     int64_t table_mask = 0;
     int32_t* err = nullptr;
     int32_t* delta = nullptr;        // [n] degree change
     int32_t* ins_cnt = nullptr;      // [n] inserted arcs per row
     int32_t* cursor = nullptr;       // [n]
-    uint8_t* touched = nullptr;      // [n]
+    uint8_t* touched = nullptr;      // [n] rows of the batch's endpoints
     int64_t* ins_start = nullptr;    // [n] bucket offset
     int32_t* ins_rows = nullptr;     // [2 cap] rows receiving insertions
     unsigned long long* n_ins_rows = nullptr;
     int32_t* bucket = nullptr;       // [2 cap] inserted arcs grouped by row
     uint32_t* vbits = nullptr;       // [n/32] frontier visit marks
     int32_t* frontier = nullptr;     // [n] affected nodes, in order of discovery
-    unsigned long long* fsize = nullptr;
+    unsigned long long* fsize = nullptr;  // [2] frontier size, sum of the frontier's degrees
+    int32_t* hub_epoch = nullptr;    // [row_warp] level at which a CHUNK row joined the frontier
 };
 
 cudaError_t dyn_validate(const DeviceGraph& g, const DynBuffers& d, int64_t m, int64_t D, cudaStream_t st);
@@ -201,7 +195,8 @@ cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, in
 cudaError_t dyn_rebuild(DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new, int32_t* col_new,
                         cudaStream_t st);
 cudaError_t dyn_seed(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st);
-cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, int64_t hi, cudaStream_t st);
+cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, int64_t hi, int level,
+                       cudaStream_t st);
 cudaError_t dyn_recompute_c(const DeviceGraph& g, const IterBuffers& b, const DynBuffers& d, const IterParams& p,
                             int r, bool all, cudaStream_t st);
 cudaError_t dyn_reactivate(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int r, cudaStream_t st);
@@ -228,8 +223,11 @@ cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterPa
                         cudaStream_t st);
 cudaError_t launch_spmv_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level,
                               cudaStream_t st);
+// s_level recomputed for the listed rows (CHUNK rows excepted) and for the
+// CHUNK rows whose visit bit is set, with the lane partition of the SpMV
 cudaError_t launch_rows_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const int32_t* rows,
-                              const unsigned long long* nrows_dev, int64_t nrows_max, int level, cudaStream_t st);
+                              const unsigned long long* nrows_dev, int64_t nrows_max, const uint32_t* vbits,
+                              int level, cudaStream_t st);
 cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const double* cl,
                           const double* cu, const int32_t* cid, bool fp32, cudaStream_t st);
 cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,

@@ -7,12 +7,21 @@
 //   F_i = F_{i-1} + neighbours of the nodes that joined F_{i-1}   (reverse BFS;
 //         in-neighbours = neighbours for undirected graphs);
 //   s_i(w) is recomputed for w in F_i from the already repaired level i-1
-//   with the same row kernel order as the static SpMV, so the repaired
-//   vectors equal a full recomputation on the updated graph.  Once |F_i|
-//   exceeds frontier_abort_frac * n the level is recomputed for all nodes
-//   (the paper aborts the BFS when S becomes large).
+//   with the lane partition of the static SpMV, so the repaired vectors equal
+//   a full recomputation on the updated graph.  Once F_i holds more than
+//   frontier_abort_frac of the nodes or of the arcs, the remaining levels are
+//   recomputed for all nodes (the paper aborts the BFS when S becomes large;
+//   on graphs with hubs the arcs of S, not its size, measure the work).
 // Nothing is changed unless the whole batch passes validation.
+//
+// The adjacency is rebuilt into a spare array: runs of untouched rows move as
+// one contiguous copy (their offsets shift by a constant), touched rows drop
+// their deleted arcs (looked up in the batch's pair table) and append their
+// inserted ones; CHUNK rows (the hubs) are copied chunk-parallel or compacted
+// by a whole block.
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "katz_common.cuh"
 
@@ -42,14 +51,36 @@ __device__ __forceinline__ int64_t find_in_row(const Off* rowptr, const int32_t*
     return -1;
 }
 
-// One warp per update: range, self-loop, duplicate (hash of the unordered
-// pair), presence (I and E disjoint, D a subset of E) and the degree deltas.
+constexpr unsigned long long DEL_BIT = 1ull << 63;
+
+// key of the unordered pair {u, v} of internal ids (never 0, bit 63 clear)
+__device__ __forceinline__ unsigned long long pair_key(int32_t u, int32_t v) {
+    return (((unsigned long long)(uint32_t)min(u, v) << 32) | (uint32_t)max(u, v)) + 1ull;
+}
+
+// the stored entry of `key` (with its delete bit), 0 if absent
+__device__ __forceinline__ unsigned long long table_find(const unsigned long long* __restrict__ table, int64_t mask,
+                                                         unsigned long long key) {
+    int64_t h = (int64_t)(mix64(key) & (unsigned long long)mask);
+    for (int64_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long t = table[h];
+        if (t == 0ull) return 0ull;
+        if ((t & ~DEL_BIT) == key) return t;
+        h = (h + 1) & mask;
+    }
+    return 0ull;
+}
+
+// One warp per update: range, self-loop, duplicate (the pair table, which
+// also records deletions for the rebuild), presence (I and E disjoint, D a
+// subset of E; the graph is symmetric, so the shorter of the two rows
+// decides), degree deltas and the touched rows.
 template <typename Off>
 __global__ void validate_batch_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
                                       const int32_t* __restrict__ inv, int64_t n, const int32_t* __restrict__ src,
                                       const int32_t* __restrict__ dst, const uint8_t* __restrict__ ins, int64_t m,
                                       unsigned long long* table, int64_t table_mask, int32_t* delta,
-                                      int64_t* pos_a, int64_t* pos_b, int32_t* err) {
+                                      uint8_t* touched, int32_t* err) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; e < m; e += warps) {
@@ -58,30 +89,31 @@ __global__ void validate_batch_kernel(const Off* __restrict__ rowptr, const int3
             if (lane == 0) atomicOr(err, DYN_E_INVAL);
             continue;
         }
+        const int32_t ua = inv[a], ub = inv[b];
         if (lane == 0) {  // duplicate pair inside the batch
-            const unsigned long long key = ((unsigned long long)min(a, b) << 32 | (unsigned)max(a, b)) + 1ull;
+            const unsigned long long key = pair_key(ua, ub);
+            const unsigned long long entry = key | (ins[e] ? 0ull : DEL_BIT);
             int64_t h = (int64_t)(mix64(key) & (unsigned long long)table_mask);
             for (int64_t probe = 0; probe <= table_mask; ++probe) {
-                const unsigned long long old = atomicCAS(&table[h], 0ull, key);
+                const unsigned long long old = atomicCAS(&table[h], 0ull, entry);
                 if (old == 0ull) break;
-                if (old == key) {
+                if ((old & ~DEL_BIT) == key) {
                     atomicOr(err, DYN_E_INVAL);
                     break;
                 }
                 h = (h + 1) & table_mask;
             }
         }
-        const int32_t ua = inv[a], ub = inv[b];
-        const int64_t pa = find_in_row(rowptr, col, ua, ub);
-        const int64_t pb = find_in_row(rowptr, col, ub, ua);
+        const int64_t da = (int64_t)rowptr[ua + 1] - (int64_t)rowptr[ua];
+        const int64_t db = (int64_t)rowptr[ub + 1] - (int64_t)rowptr[ub];
+        const int64_t pos = da <= db ? find_in_row(rowptr, col, ua, ub) : find_in_row(rowptr, col, ub, ua);
         if (lane == 0) {
-            const bool present = pa >= 0 && pb >= 0;
-            if (ins[e] ? (pa >= 0 || pb >= 0) : !present) atomicOr(err, DYN_E_INVAL);
-            pos_a[e] = pa;
-            pos_b[e] = pb;
+            if (ins[e] ? pos >= 0 : pos < 0) atomicOr(err, DYN_E_INVAL);
             const int d = ins[e] ? 1 : -1;
             atomicAdd(&delta[ua], d);
             atomicAdd(&delta[ub], d);
+            touched[ua] = 1;
+            touched[ub] = 1;
         }
     }
 }
@@ -130,17 +162,6 @@ __global__ void count_inserts_kernel(const int32_t* __restrict__ inv, const int3
         const int32_t ends[2] = {inv[src[e]], inv[dst[e]]};
         for (int q = 0; q < 2; ++q)
             if (atomicAdd(&ins_cnt[ends[q]], 1) == 0) ins_rows[atomicAdd(n_ins_rows, 1ULL)] = ends[q];
-    }
-}
-
-// deletions: mark both arcs in the old col (read once more by the rebuild)
-__global__ void mark_deletes_kernel(const uint8_t* __restrict__ ins, int64_t m, const int64_t* __restrict__ pos_a,
-                                    const int64_t* __restrict__ pos_b, int32_t* col) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        if (ins[e]) continue;
-        col[pos_a[e]] = -1;
-        col[pos_b[e]] = -1;
     }
 }
 
@@ -214,29 +235,122 @@ __global__ void new_degrees_kernel(const Off* __restrict__ rowptr, const int32_t
         deg[u] = (int64_t)rowptr[u + 1] - (int64_t)rowptr[u] + delta[u];
 }
 
-// one warp per row: kept entries in their order, then the row's inserted arcs
+// a touched row: its arcs minus the deleted ones (in their order), then its
+// inserted arcs; one warp
 template <typename Off>
-__global__ void rebuild_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                    const int64_t* __restrict__ rowptr_new, const int32_t* __restrict__ ins_cnt,
-                                    const int64_t* __restrict__ ins_start, const int32_t* __restrict__ bucket,
-                                    int64_t n, int32_t* col_new) {
+__device__ __forceinline__ void rebuild_touched_row(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                                    int64_t v, int64_t o, const int32_t* __restrict__ ins_cnt,
+                                                    const int64_t* __restrict__ ins_start,
+                                                    const int32_t* __restrict__ bucket,
+                                                    const unsigned long long* __restrict__ table, int64_t mask,
+                                                    int32_t* col_new) {
+    const int lane = threadIdx.x & 31;
+    const int64_t a = rowptr[v], b = rowptr[v + 1];
+    for (int64_t base = a; base < b; base += 32) {
+        const int64_t j = base + lane;
+        const int32_t x = j < b ? col[j] : -1;
+        const bool keep = x >= 0 && !(table_find(table, mask, pair_key((int32_t)v, x)) & DEL_BIT);
+        const unsigned kb = __ballot_sync(FULL, keep);
+        if (keep) col_new[o + __popc(kb & ((1u << lane) - 1u))] = x;
+        o += __popc(kb);
+    }
+    const int c = ins_cnt[v];
+    const int32_t* bkt = bucket + ins_start[v];
+    for (int q = lane; q < c; q += 32) col_new[o + q] = bkt[q];
+}
+
+// rows from row_lo on (no CHUNK rows): one warp per 32 consecutive rows; a
+// run without touched rows is one contiguous copy
+template <typename Off>
+__global__ void rebuild_groups_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                      const int64_t* __restrict__ rowptr_new, const uint8_t* __restrict__ touched,
+                                      const int32_t* __restrict__ ins_cnt, const int64_t* __restrict__ ins_start,
+                                      const int32_t* __restrict__ bucket, const unsigned long long* __restrict__ table,
+                                      int64_t mask, int64_t row_lo, int64_t n, int32_t* col_new) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; u < n; u += warps) {
+    const int64_t groups = (n - row_lo + 31) / 32;
+    for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; gi < groups; gi += warps) {
+        const int64_t u0 = row_lo + gi * 32, u1 = min(u0 + 32, n);
+        const bool t = u0 + lane < u1 && touched[u0 + lane];
+        const unsigned tb = __ballot_sync(FULL, t);
+        if (!tb) {
+            const int64_t a = rowptr[u0], b = rowptr[u1], o = rowptr_new[u0];
+            for (int64_t j = a + lane; j < b; j += 32) col_new[o + (j - a)] = col[j];
+            continue;
+        }
+        for (int64_t v = u0; v < u1; ++v) {
+            const int64_t o = rowptr_new[v];
+            if ((tb >> (v - u0)) & 1u) {
+                rebuild_touched_row(rowptr, col, v, o, ins_cnt, ins_start, bucket, table, mask, col_new);
+            } else {
+                const int64_t a = rowptr[v], b = rowptr[v + 1];
+                for (int64_t j = a + lane; j < b; j += 32) col_new[o + (j - a)] = col[j];
+            }
+        }
+    }
+}
+
+// untouched CHUNK rows: one warp per chunk copies it to its new place
+template <typename Off>
+__global__ void rebuild_chunks_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                      const int64_t* __restrict__ rowptr_new, const uint8_t* __restrict__ touched,
+                                      const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first,
+                                      int64_t chunks, int32_t* col_new) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < chunks; ch += warps) {
+        const int64_t u = chunk_row[ch];
+        if (touched[u]) continue;
+        const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+        const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+        const int64_t o = rowptr_new[u] + (j0 - (int64_t)rowptr[u]);
+        for (int64_t j = j0 + lane; j < j1; j += 32) col_new[o + (j - j0)] = col[j];
+    }
+}
+
+// touched CHUNK rows: one block of HUB_THREADS per row compacts it tile by tile
+constexpr int HUB_THREADS = 1024;
+template <typename Off>
+__global__ void __launch_bounds__(HUB_THREADS)
+rebuild_hub_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                        const int64_t* __restrict__ rowptr_new, const uint8_t* __restrict__ touched,
+                        const int32_t* __restrict__ ins_cnt, const int64_t* __restrict__ ins_start,
+                        const int32_t* __restrict__ bucket, const unsigned long long* __restrict__ table, int64_t mask,
+                        int64_t row_warp, int32_t* col_new) {
+    __shared__ int wsum[HUB_THREADS / 32];
+    __shared__ int total;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int64_t u = blockIdx.x; u < row_warp; u += gridDim.x) {
+        if (!touched[u]) continue;  // the same for the whole block
         const int64_t a = rowptr[u], b = rowptr[u + 1];
         int64_t o = rowptr_new[u];
-        for (int64_t base = a; base < b; base += 32) {
-            const int64_t j = base + lane;
+        for (int64_t base = a; base < b; base += HUB_THREADS) {
+            const int64_t j = base + tid;
             const int32_t x = j < b ? col[j] : -1;
-            const unsigned keep = __ballot_sync(FULL, x >= 0);
-            if (x >= 0) col_new[o + __popc(keep & ((1u << lane) - 1u))] = x;
-            o += __popc(keep);
+            const bool keep = x >= 0 && !(table_find(table, mask, pair_key((int32_t)u, x)) & DEL_BIT);
+            const unsigned kb = __ballot_sync(FULL, keep);
+            if (lane == 0) wsum[wid] = __popc(kb);
+            __syncthreads();
+            if (wid == 0) {  // exclusive scan of the warp counts
+                const int c = wsum[lane];
+                int inc = c;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(FULL, inc, off);
+                    if (lane >= off) inc += y;
+                }
+                wsum[lane] = inc - c;
+                if (lane == 31) total = inc;
+            }
+            __syncthreads();
+            if (keep) col_new[o + wsum[wid] + __popc(kb & ((1u << lane) - 1u))] = x;
+            o += total;
+            __syncthreads();
         }
         const int c = ins_cnt[u];
-        if (c) {
-            const int32_t* bkt = bucket + ins_start[u];
-            for (int q = lane; q < c; q += 32) col_new[o + q] = bkt[q];
-        }
+        const int32_t* bkt = bucket + ins_start[u];
+        for (int q = tid; q < c; q += HUB_THREADS) col_new[o + q] = bkt[q];
     }
 }
 
@@ -252,31 +366,94 @@ __device__ __forceinline__ bool visit(uint32_t* vbits, int32_t u) {
     return !(atomicOr(&vbits[u >> 5], bit) & bit);
 }
 
+template <typename Off>
+__device__ __forceinline__ int64_t degree(const Off* __restrict__ rowptr, int64_t u) {
+    return (int64_t)rowptr[u + 1] - (int64_t)rowptr[u];
+}
+
+// a node joins the frontier: listed, its degree counted by the caller, a
+// CHUNK row remembers the level it joined at
+__device__ __forceinline__ void join(int32_t x, int level, int64_t row_warp, int32_t* frontier,
+                                     unsigned long long* fsize, int32_t* hub_epoch) {
+    frontier[atomicAdd(&fsize[0], 1ULL)] = x;
+    if (x < row_warp) hub_epoch[x] = level;
+}
+
 // F_1: the endpoints of every update
-__global__ void seed_frontier_kernel(const int32_t* __restrict__ inv, const int32_t* __restrict__ src,
-                                     const int32_t* __restrict__ dst, int64_t m, uint32_t* vbits, int32_t* frontier,
-                                     unsigned long long* fsize) {
+template <typename Off>
+__global__ void seed_frontier_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ inv,
+                                     const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                                     int64_t row_warp, uint32_t* vbits, int32_t* frontier, unsigned long long* fsize,
+                                     int32_t* hub_epoch) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         const int32_t ends[2] = {inv[src[e]], inv[dst[e]]};
-        for (int q = 0; q < 2; ++q)
-            if (visit(vbits, ends[q])) frontier[atomicAdd(fsize, 1ULL)] = ends[q];
+        for (int q = 0; q < 2; ++q) {
+            if (visit(vbits, ends[q])) {
+                join(ends[q], 1, row_warp, frontier, fsize, hub_epoch);
+                atomicAdd(&fsize[1], (unsigned long long)degree(rowptr, ends[q]));
+            }
+        }
     }
 }
 
-// the neighbours of frontier[lo, hi) join the frontier; one warp per node
+// neighbours of the arcs [j0, j1) join F_{level+1}; returns the degrees added
 template <typename Off>
-__global__ void expand_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t* frontier,
-                              int64_t lo, int64_t hi, uint32_t* vbits, unsigned long long* fsize) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-    for (int64_t q = lo + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; q < hi; q += warps) {
-        const int64_t w = frontier[q];
-        for (int64_t j = (int64_t)rowptr[w] + lane; j < (int64_t)rowptr[w + 1]; j += 32) {
-            const int32_t x = col[j];
-            if (visit(vbits, x)) frontier[atomicAdd(fsize, 1ULL)] = x;
+__device__ __forceinline__ unsigned long long expand_arcs(const Off* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ col, int64_t j0, int64_t j1,
+                                                          int level, int64_t row_warp, uint32_t* vbits,
+                                                          int32_t* frontier, unsigned long long* fsize,
+                                                          int32_t* hub_epoch) {
+    unsigned long long vol = 0;
+    for (int64_t j = j0 + (threadIdx.x & 31); j < j1; j += 32) {
+        const int32_t x = col[j];
+        if (visit(vbits, x)) {
+            join(x, level + 1, row_warp, frontier, fsize, hub_epoch);
+            vol += (unsigned long long)degree(rowptr, x);
         }
     }
+    return vol;
+}
+
+__device__ __forceinline__ void add_warp_volume(unsigned long long vol, unsigned long long* fsize) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) vol += __shfl_xor_sync(FULL, vol, off);
+    if ((threadIdx.x & 31) == 0 && vol) atomicAdd(&fsize[1], vol);
+}
+
+// the neighbours of frontier[lo, hi) join the frontier; one warp per node
+// (CHUNK rows are expanded chunk by chunk by expand_hubs_kernel)
+template <typename Off>
+__global__ void expand_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t* frontier,
+                              int64_t lo, int64_t hi, int level, int64_t row_warp, uint32_t* vbits,
+                              unsigned long long* fsize, int32_t* hub_epoch) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    unsigned long long vol = 0;
+    for (int64_t q = lo + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; q < hi; q += warps) {
+        const int64_t w = frontier[q];
+        if (w < row_warp) continue;
+        vol += expand_arcs(rowptr, col, (int64_t)rowptr[w], (int64_t)rowptr[w + 1], level, row_warp, vbits, frontier,
+                           fsize, hub_epoch);
+    }
+    add_warp_volume(vol, fsize);
+}
+
+// CHUNK rows that joined at `level`: one warp per chunk
+template <typename Off>
+__global__ void expand_hubs_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                   const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first,
+                                   int64_t chunks, int32_t* frontier, int level, int64_t row_warp, uint32_t* vbits,
+                                   unsigned long long* fsize, int32_t* hub_epoch) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    unsigned long long vol = 0;
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < chunks; ch += warps) {
+        const int64_t u = chunk_row[ch];
+        if (hub_epoch[u] != level) continue;
+        const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+        const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+        vol += expand_arcs(rowptr, col, j0, j1, level, row_warp, vbits, frontier, fsize, hub_epoch);
+    }
+    add_warp_volume(vol, fsize);
 }
 
 // c_r = s_1 + ... + s_r in level order (the order the static iteration adds them)
@@ -329,7 +506,8 @@ __global__ void theta_lb_kernel(const int32_t* __restrict__ topk_id, const int32
 // keep it), and the candidates of the check at level r are collected.
 __global__ void reactivate_kernel(const double* walk, const double* __restrict__ c,
                                   const int32_t* __restrict__ perm, IterParams p, int r, uint8_t* active,
-                                  double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl) {
+                                  double* lb, double* ub, double* cand_l, double* cand_u, int32_t* cand_id,
+                                  int64_t cand_cap, Ctrl* ctrl) {
     const double* s = walk_slot(walk, p, r);
     const double th = ctrl->theta_prev;
     const BState bs = bstate(ctrl);
@@ -338,6 +516,8 @@ __global__ void reactivate_kernel(const double* walk, const double* __restrict__
         active[v] = 1;
         double l, u;
         node_bounds(c[v], 0.0, s[v], p, bs, l, u);
+        lb[v] = l;  // the bounds the deactivation count reads
+        ub[v] = u;
         if (l >= th) {
             const unsigned long long pos = atomicAdd(&ctrl->n_cand, 1ULL);
             if (pos < (unsigned long long)cand_cap) {
@@ -365,11 +545,11 @@ cudaError_t dyn_validate(const DeviceGraph& g, const DynBuffers& d, int64_t m, i
     if (g.off64)
         validate_batch_kernel<int64_t><<<wblocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, g.inv, g.n, d.src,
                                                                d.dst, d.ins, m, d.table, d.table_mask, d.delta,
-                                                               d.pos_a, d.pos_b, d.err);
+                                                               d.touched, d.err);
     else
         validate_batch_kernel<int32_t><<<wblocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, g.inv, g.n, d.src,
                                                                d.dst, d.ins, m, d.table, d.table_mask, d.delta,
-                                                               d.pos_a, d.pos_b, d.err);
+                                                               d.touched, d.err);
     if (g.off64)
         degree_check_kernel<int64_t><<<grid_for(m, 256), 256, 0, st>>>((const int64_t*)g.rowptr, g.inv, d.src, d.dst,
                                                                       m, g.n, d.delta, D, d.err);
@@ -411,16 +591,34 @@ cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, in
     return exclusive_scan_i64(deg, g.n + 1, rowptr_new, sums, st);
 }
 
-// rows into col_new, then the new offsets over the old ones
+template <typename Off>
+static void rebuild_launch(DeviceGraph& g, const DynBuffers& d, const int64_t* rowptr_new, int32_t* col_new,
+                           cudaStream_t st) {
+    const Off* rp = (const Off*)g.rowptr;
+    const SpmvLayout& L = g.layout;
+    const int64_t groups = (g.n - L.row_warp + 31) / 32;
+    if (groups > 0)
+        rebuild_groups_kernel<Off><<<grid_for(groups * 32, 256), 256, 0, st>>>(
+            rp, g.col, rowptr_new, d.touched, d.ins_cnt, d.ins_start, d.bucket, d.table, d.table_mask, L.row_warp,
+            g.n, col_new);
+    if (L.chunks > 0)
+        rebuild_chunks_kernel<Off><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
+            rp, g.col, rowptr_new, d.touched, g.chunk_row, g.chunk_first, L.chunks, col_new);
+    if (L.row_warp > 0)
+        rebuild_hub_rows_kernel<Off><<<(unsigned)std::min<int64_t>(L.row_warp, 152 * 2), HUB_THREADS, 0, st>>>(
+            rp, g.col, rowptr_new, d.touched, d.ins_cnt, d.ins_start, d.bucket, d.table, d.table_mask, L.row_warp,
+            col_new);
+}
+
+// rows into col_new (old layout and chunk table), then the new offsets over
+// the old ones
 cudaError_t dyn_rebuild(DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new, int32_t* col_new,
                         cudaStream_t st) {
-    mark_deletes_kernel<<<grid_for(m, 256), 256, 0, st>>>(d.ins, m, d.pos_a, d.pos_b, g.col);
+    (void)m;
     if (g.off64)
-        rebuild_rows_kernel<int64_t><<<grid_for(g.n * 32, 256), 256, 0, st>>>(
-            (const int64_t*)g.rowptr, g.col, rowptr_new, d.ins_cnt, d.ins_start, d.bucket, g.n, col_new);
+        rebuild_launch<int64_t>(g, d, rowptr_new, col_new, st);
     else
-        rebuild_rows_kernel<int32_t><<<grid_for(g.n * 32, 256), 256, 0, st>>>(
-            (const int32_t*)g.rowptr, g.col, rowptr_new, d.ins_cnt, d.ins_start, d.bucket, g.n, col_new);
+        rebuild_launch<int32_t>(g, d, rowptr_new, col_new, st);
     if (g.off64)
         narrow_kernel<int64_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int64_t*)g.rowptr, g.n + 1);
     else
@@ -428,22 +626,44 @@ cudaError_t dyn_rebuild(DeviceGraph& g, const DynBuffers& d, int64_t m, const in
     return cudaGetLastError();
 }
 
+// F_1 on the updated graph; fsize = {|F_1|, sum of degrees}
 cudaError_t dyn_seed(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(d.vbits, 0, (size_t)((g.n + 31) / 32) * sizeof(uint32_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.fsize, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.fsize, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess && g.layout.row_warp > 0)
+        e = cudaMemsetAsync(d.hub_epoch, 0, (size_t)g.layout.row_warp * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    seed_frontier_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, m, d.vbits, d.frontier, d.fsize);
+    if (g.off64)
+        seed_frontier_kernel<int64_t><<<grid_for(m, 256), 256, 0, st>>>((const int64_t*)g.rowptr, g.inv, d.src, d.dst,
+                                                                       m, g.layout.row_warp, d.vbits, d.frontier,
+                                                                       d.fsize, d.hub_epoch);
+    else
+        seed_frontier_kernel<int32_t><<<grid_for(m, 256), 256, 0, st>>>((const int32_t*)g.rowptr, g.inv, d.src, d.dst,
+                                                                       m, g.layout.row_warp, d.vbits, d.frontier,
+                                                                       d.fsize, d.hub_epoch);
     return cudaGetLastError();
 }
 
-cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, int64_t hi, cudaStream_t st) {
+// F_{level+1} from the nodes that joined at `level` (frontier[lo, hi))
+cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, int64_t hi, int level,
+                       cudaStream_t st) {
     if (hi <= lo) return cudaSuccess;
-    if (g.off64)
-        expand_kernel<int64_t><<<grid_for((hi - lo) * 32, 256), 256, 0, st>>>((const int64_t*)g.rowptr, g.col,
-                                                                             d.frontier, lo, hi, d.vbits, d.fsize);
-    else
-        expand_kernel<int32_t><<<grid_for((hi - lo) * 32, 256), 256, 0, st>>>((const int32_t*)g.rowptr, g.col,
-                                                                             d.frontier, lo, hi, d.vbits, d.fsize);
+    const SpmvLayout& L = g.layout;
+    if (g.off64) {
+        expand_kernel<int64_t><<<grid_for((hi - lo) * 32, 256), 256, 0, st>>>(
+            (const int64_t*)g.rowptr, g.col, d.frontier, lo, hi, level, L.row_warp, d.vbits, d.fsize, d.hub_epoch);
+        if (L.chunks > 0)
+            expand_hubs_kernel<int64_t><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
+                (const int64_t*)g.rowptr, g.col, g.chunk_row, g.chunk_first, L.chunks, d.frontier, level, L.row_warp,
+                d.vbits, d.fsize, d.hub_epoch);
+    } else {
+        expand_kernel<int32_t><<<grid_for((hi - lo) * 32, 256), 256, 0, st>>>(
+            (const int32_t*)g.rowptr, g.col, d.frontier, lo, hi, level, L.row_warp, d.vbits, d.fsize, d.hub_epoch);
+        if (L.chunks > 0)
+            expand_hubs_kernel<int32_t><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
+                (const int32_t*)g.rowptr, g.col, g.chunk_row, g.chunk_first, L.chunks, d.frontier, level, L.row_warp,
+                d.vbits, d.fsize, d.hub_epoch);
+    }
     return cudaGetLastError();
 }
 
@@ -456,8 +676,8 @@ cudaError_t dyn_recompute_c(const DeviceGraph& g, const IterBuffers& b, const Dy
 
 cudaError_t dyn_reactivate(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int r, cudaStream_t st) {
     theta_lb_kernel<<<1, 1024, 0, st>>>(b.topk_id, g.inv, (const double*)b.walk, b.c, p, r, b.ctrl);
-    reactivate_kernel<<<grid_for(g.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, g.perm, p, r, b.active,
-                                                          b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl);
+    reactivate_kernel<<<grid_for(g.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, g.perm, p, r, b.active, b.lb,
+                                                          b.ub, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl);
     return cudaGetLastError();
 }
 

@@ -261,19 +261,15 @@ __global__ void count_kernel(const T* walk, const double* __restrict__ c, const 
     unsigned long long cross = 0, act = 0;
     double smax = 0.0, tailw = 0.0, roundw = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // l, th >= 0 (sums of non-negative terms): they order like their bit patterns
+    const long long th_bits = __double_as_longlong(th);
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
         if (!active[v]) continue;
-        const double sv = walk_value(walk, p, f32_from, r_cur, v);
-        const double c64v = c[v], c32v = c32 ? c32[v] : 0.0;
-        double l, u;
-        if (p.cert) {
-            l = lb[v];
-            u = ub[v];
-        } else {
-            node_bounds(c64v, c32v, sv, p, bs, l, u);
-        }
+        const double l = lb[v], u = ub[v];  // stored by the SpMV epilogue of this level
+        const long long l_bits = __double_as_longlong(l);
         const int32_t ov = perm[v];  // ties are broken by the original id
-        if (!ranks_before(l, ov, th, thid) && !(l == th && ov == thid)) {
+        const bool top = l_bits > th_bits || (l_bits == th_bits && ov <= thid);
+        if (!top) {
             if (__dsub_rn(u, p.eps) < th) {
                 active[v] = 0;
                 continue;
@@ -282,11 +278,17 @@ __global__ void count_kernel(const T* walk, const double* __restrict__ c, const 
         }
         ++act;
         if (p.cert) {
+            const double sv = walk_value(walk, p, f32_from, r_cur, v);
+            const double c64v = c[v], c32v = c32 ? c32[v] : 0.0;
             smax = fmax(smax, sv);
             tailw = fmax(tailw, p.ag * sv);
             roundw = fmax(roundw, c64v * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32));
         }
     }
+    // block totals first: one atomic per block and counter (same-address
+    // atomics from every warp were the cost of this pass)
+    __shared__ unsigned long long s_cross[32], s_act[32];
+    __shared__ double s_smax[32], s_tailw[32], s_roundw[32];
     for (int off = 16; off; off >>= 1) {
         cross += __shfl_xor_sync(FULL, cross, off);
         act += __shfl_xor_sync(FULL, act, off);
@@ -294,13 +296,36 @@ __global__ void count_kernel(const T* walk, const double* __restrict__ c, const 
         tailw = fmax(tailw, __shfl_xor_sync(FULL, tailw, off));
         roundw = fmax(roundw, __shfl_xor_sync(FULL, roundw, off));
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (cross) atomicAdd(&ctrl->cnt_cross, cross);
-        if (act) atomicAdd(&ctrl->n_active, act);
-        if (p.cert) {  // non-negative doubles order like their bit patterns
-            atomicMax(&ctrl->smax_bits, (unsigned long long)__double_as_longlong(smax));
-            atomicMax(&ctrl->tailw_bits, (unsigned long long)__double_as_longlong(tailw));
-            atomicMax(&ctrl->roundw_bits, (unsigned long long)__double_as_longlong(roundw));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        s_cross[wid] = cross;
+        s_act[wid] = act;
+        s_smax[wid] = smax;
+        s_tailw[wid] = tailw;
+        s_roundw[wid] = roundw;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        cross = lane < nw ? s_cross[lane] : 0ull;
+        act = lane < nw ? s_act[lane] : 0ull;
+        smax = lane < nw ? s_smax[lane] : 0.0;
+        tailw = lane < nw ? s_tailw[lane] : 0.0;
+        roundw = lane < nw ? s_roundw[lane] : 0.0;
+        for (int off = 16; off; off >>= 1) {
+            cross += __shfl_xor_sync(FULL, cross, off);
+            act += __shfl_xor_sync(FULL, act, off);
+            smax = fmax(smax, __shfl_xor_sync(FULL, smax, off));
+            tailw = fmax(tailw, __shfl_xor_sync(FULL, tailw, off));
+            roundw = fmax(roundw, __shfl_xor_sync(FULL, roundw, off));
+        }
+        if (lane == 0) {
+            if (cross) atomicAdd(&ctrl->cnt_cross, cross);
+            if (act) atomicAdd(&ctrl->n_active, act);
+            if (p.cert) {  // non-negative doubles order like their bit patterns
+                atomicMax(&ctrl->smax_bits, (unsigned long long)__double_as_longlong(smax));
+                atomicMax(&ctrl->tailw_bits, (unsigned long long)__double_as_longlong(tailw));
+                atomicMax(&ctrl->roundw_bits, (unsigned long long)__double_as_longlong(roundw));
+            }
         }
     }
 }
@@ -574,8 +599,8 @@ cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const Iter
 cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                          cudaStream_t st) {
     (void)fp32;
-    count_kernel<double><<<grid_for(p.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, b.lb, b.ub, g.perm,
-                                                             b.active, b.ctrl, p);
+    count_kernel<double><<<grid_for(p.n, 256, 152 * 16), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, b.lb, b.ub,
+                                                                       g.perm, b.active, b.ctrl, p);
     return cudaGetLastError();
 }
 

@@ -102,9 +102,9 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
         if (p.cert) {  // both the new and the stored bounds are valid: keep the tighter ones
             l = fmax(l, e.lb[u]);
             up = fmin(up, e.ub[u]);
-            e.lb[u] = l;
-            e.ub[u] = up;
         }
+        e.lb[u] = l;  // read by the deactivation count of this level
+        e.ub[u] = up;
         if (l >= e.theta_prev) {
             const unsigned long long pos = atomicAdd(&e.ctrl->n_cand, 1ULL);
             if (pos < (unsigned long long)e.cand_cap) {
@@ -346,6 +346,16 @@ __device__ __forceinline__ XAcc load_part(const double* part, int64_t ch) {
     return a;
 }
 
+// The partials of chunks [first, first + count) merged by one warp: lane l
+// merges chunks first + l, first + l + 32, ... in order, then the lanes meet.
+// A chunk partial stays below 2^95 (2048 terms below 2^84), a lane's merge
+// below 2^108 for any row that fits in memory, so 32 lanes cannot carry out.
+__device__ __forceinline__ XAcc merge_chunks_warp(const double* __restrict__ part, int64_t first, int64_t count) {
+    XAcc t = xacc_zero();
+    for (int64_t q = threadIdx.x & 31; q < count; q += 32) xacc_merge(t, load_part(part, first + q));
+    return xacc_group_sum<32>(t);
+}
+
 // Sum of x[col[j]] for j in [a, b) with stride `step` from a + first: eight
 // loads in flight, each group of eight added as a pairwise tree (depth 3),
 // groups chained in index order.
@@ -491,6 +501,8 @@ __device__ __forceinline__ Acc chunk_tree(const double* __restrict__ part, int64
     return total;
 }
 
+// CHUNK rows: one warp per row merges the row's chunk partials, then its
+// first lane finishes the row.
 __global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double* c32, double* lb, double* ub,
                                  uint8_t* active,
                                  const int32_t* __restrict__ perm, const int64_t* __restrict__ chunk_first,
@@ -501,14 +513,13 @@ __global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double
     double* ys = walk_slot(walk, p, r_cur);
     Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
     ep.store_only = store_level > 0;
-    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;  // one warp per CHUNK row
     if (u >= L.row_warp) return;
     const int64_t first = chunk_first[u], count = chunk_first[u + 1] - first;
     if (store_level || r_cur < ctrl->f32_from) {
-        XAcc t = xacc_zero();  // chunk partials merged in chunk order
-        for (int64_t ch = first; ch < first + count; ++ch) xacc_merge(t, load_part(chunk_part, ch));
-        finish_row<double>(u, xacc_to_double(t), ep, p);
-    } else {
+        const XAcc t = merge_chunks_warp(chunk_part, first, count);
+        if ((threadIdx.x & 31) == 0) finish_row<double>(u, xacc_to_double(t), ep, p);
+    } else if ((threadIdx.x & 31) == 0) {
         finish_row<float>(u, chunk_tree<float>(chunk_part, first, count), ep, p);
     }
 }
@@ -543,7 +554,7 @@ static cudaError_t spmv_launch(const DeviceGraph& g, const IterBuffers& b, const
                 store_level);
     }
     if (L.row_warp > 0)
-        spmv_chunk_fixup<<<(unsigned)((L.row_warp + 127) / 128), 128, 0, st>>>(
+        spmv_chunk_fixup<<<(unsigned)((L.row_warp * 32 + 127) / 128), 128, 0, st>>>(
             L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, g.chunk_first, g.chunk_part, b.cand_l,
             b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p, store_level);
     return cudaGetLastError();
@@ -563,11 +574,12 @@ cudaError_t launch_spmv_store(const DeviceGraph& g, const IterBuffers& b, const 
 // One warp per listed row: the row's s_level recomputed with the lane
 // partition spmv_rows_kernel uses for that row (its row mode is set by its
 // internal index) and the same merges, so a repaired level has the bits of a
-// full recomputation.
+// full recomputation.  CHUNK rows are left to the two hub kernels below,
+// which split them over warps as the SpMV does.
 template <typename Off>
 __global__ void rows_store_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L,
                                   const int32_t* __restrict__ rows, const unsigned long long* nrows_ptr,
-                                  double* walk, const int64_t* __restrict__ chunk_first, IterParams p, int level) {
+                                  double* walk, IterParams p, int level) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     const int64_t nrows = (int64_t)*nrows_ptr;
@@ -575,6 +587,7 @@ __global__ void rows_store_kernel(const Off* __restrict__ rowptr, const int32_t*
     double* y = walk_slot(walk, p, level);
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < nrows; w += warps) {
         const int64_t u = rows[w];
+        if (u < L.row_warp) continue;     // CHUNK row
         const int64_t a = rowptr[u], e = rowptr[u + 1];
         XAcc s = xacc_zero();
         if (u >= L.row_thread) {          // THREAD: lane 0 alone, step 1
@@ -582,34 +595,74 @@ __global__ void rows_store_kernel(const Off* __restrict__ rowptr, const int32_t*
         } else if (u >= L.row_octet) {    // OCTET: lanes 0..7, step 8
             if (lane < 8) s = strided_xsum<4>(col, x, a, e, lane, 8);
             s = xacc_group_sum<8>(s);
-        } else if (u >= L.row_warp) {     // WARP
+        } else {                          // WARP
             s = strided_xsum<8>(col, x, a, e, lane, 32);
             s = xacc_group_sum<32>(s);
-        } else {                          // CHUNK: chunk partials merged in chunk order
-            for (int64_t ch = chunk_first[u]; ch < chunk_first[u + 1]; ++ch) {
-                const int64_t j0 = a + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
-                const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, e);
-                const XAcc t = xacc_group_sum<32>(strided_xsum<8>(col, x, j0, j1, lane, 32));
-                if (lane == 0) xacc_merge(s, t);
-            }
         }
         if (lane == 0) y[u] = __dmul_rn(p.alpha, xacc_to_double(s));
     }
 }
 
+__device__ __forceinline__ bool visited(const uint32_t* vbits, int64_t u) {
+    return (vbits[u >> 5] >> (u & 31)) & 1u;
+}
+
+// chunk partials of the CHUNK rows in the frontier (one warp per chunk)
+template <typename Off>
+__global__ void hub_chunks_store_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L,
+                                        const int32_t* __restrict__ chunk_row,
+                                        const int64_t* __restrict__ chunk_first, double* chunk_part,
+                                        const uint32_t* __restrict__ vbits, const double* walk, IterParams p,
+                                        int level) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const double* __restrict__ x = walk_slot(walk, p, level - 1);
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < L.chunks; ch += warps) {
+        const int64_t u = chunk_row[ch];
+        if (!visited(vbits, u)) continue;
+        const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+        const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+        const XAcc t = xacc_group_sum<32>(strided_xsum<8>(col, x, j0, j1, lane, 32));
+        if (lane == 0) store_part(chunk_part, ch, t);
+    }
+}
+
+// the CHUNK rows in the frontier: partials merged as spmv_chunk_fixup merges them
+__global__ void hub_rows_store_kernel(SpmvLayout L, const int64_t* __restrict__ chunk_first,
+                                      const double* __restrict__ chunk_part, const uint32_t* __restrict__ vbits,
+                                      double* walk, IterParams p, int level) {
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;  // one warp per CHUNK row
+    if (u >= L.row_warp || !visited(vbits, u)) return;
+    const XAcc t = merge_chunks_warp(chunk_part, chunk_first[u], chunk_first[u + 1] - chunk_first[u]);
+    if ((threadIdx.x & 31) == 0) walk_slot(walk, p, level)[u] = __dmul_rn(p.alpha, xacc_to_double(t));
+}
+
 cudaError_t launch_rows_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const int32_t* rows,
-                              const unsigned long long* nrows_dev, int64_t nrows_max, int level, cudaStream_t st) {
+                              const unsigned long long* nrows_dev, int64_t nrows_max, const uint32_t* vbits,
+                              int level, cudaStream_t st) {
     if (nrows_max <= 0) return cudaSuccess;
     int64_t blocks = (nrows_max + 7) / 8;
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (g.off64)
         rows_store_kernel<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, g.layout, rows,
-                                                                    nrows_dev, (double*)b.walk, g.chunk_first, p,
-                                                                    level);
+                                                                    nrows_dev, (double*)b.walk, p, level);
     else
         rows_store_kernel<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, g.layout, rows,
-                                                                    nrows_dev, (double*)b.walk, g.chunk_first, p,
-                                                                    level);
+                                                                    nrows_dev, (double*)b.walk, p, level);
+    const SpmvLayout& L = g.layout;
+    if (L.chunks > 0) {
+        const unsigned cb = (unsigned)std::min<int64_t>((L.chunks + 7) / 8, 152 * 32);
+        if (g.off64)
+            hub_chunks_store_kernel<int64_t><<<cb, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, L, g.chunk_row,
+                                                                g.chunk_first, g.chunk_part, vbits,
+                                                                (const double*)b.walk, p, level);
+        else
+            hub_chunks_store_kernel<int32_t><<<cb, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, L, g.chunk_row,
+                                                                g.chunk_first, g.chunk_part, vbits,
+                                                                (const double*)b.walk, p, level);
+        hub_rows_store_kernel<<<(unsigned)((L.row_warp * 32 + 127) / 128), 128, 0, st>>>(
+            L, g.chunk_first, g.chunk_part, vbits, (double*)b.walk, p, level);
+    }
     return cudaGetLastError();
 }
 
