@@ -45,6 +45,11 @@ WORKLOADS = {
     "rmat24-halfalpha": dict(graph="rmat24", k=1000, eps=1e-9, alpha="half", precision=0,
                              desc="undirected R-MAT scale 24, edge factor 16; alpha=0.5/deg_max; certified top-1000; "
                                   "eps=1e-9"),
+    "chunglu27": dict(graph="chunglu27", k=100, eps=1e-9, alpha=0.0, precision=0,
+                      desc="undirected Chung-Lu graph, n=2^27 (134,217,728) vertices, expected degrees Pareto with "
+                           "exponent 2.1 and mean 16 (about 2^30 endpoint pairs before symmetrising and "
+                           "deduplicating), int64 rowptr / int32 col CSR; alpha=1/(deg_max+1); certified top-100; "
+                           "eps=1e-9"),
     "er16k": dict(graph="er16k", k=100, eps=1e-9, alpha=0.0, precision=0,
                   desc="undirected Erdos-Renyi n=16384, m=131072, int32 CSR; alpha=1/(deg_max+1); certified top-100; "
                        "eps=1e-9"),
@@ -73,8 +78,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=3, help="--impl reference: oracle iterations per step")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU work of the cpu_baseline sample")
-    ap.add_argument("--serve-batches", type=int, default=400,
-                    help="batches of the serving stream measured beside the static line (0: skip)")
+    ap.add_argument("--serve-batches", type=int, default=None,
+                    help="batches of the serving stream (default: 400 beside the static line, 2000 for "
+                         "--workload serve-rmat23; 0 skips it beside the static line)")
     return ap.parse_args()
 
 
@@ -193,24 +199,32 @@ def barrier(world):
         dist.barrier()
 
 
-def allreduce_max(x, world):
+def _reduce(x, world, op):
+    """x reduced over the ranks (NCCL: on the GPU; gloo: on the host)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def allreduce_max(x, world):
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.MAX if world > 1 else None)
 
 
 def allreduce_sum(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.SUM if world > 1 else None)
+
+
+def replica_throughput(units_local, seconds_local, world):
+    """Whole-job value of N independent replicas: the units all ranks
+    processed over the slowest rank's time (barrier-bracketed regions)."""
+    return allreduce_sum(units_local, world) / allreduce_max(seconds_local, world)
 
 
 def cpu_baseline(g, wl, seconds):
@@ -359,7 +373,7 @@ def main():
     if args.workload == "serve-rmat23":
         rank = int(os.environ.get("RANK", "0"))
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        sv = run_serving(max(args.serve_batches, 2000) if args.serve_batches else 2000)
+        sv = run_serving(args.serve_batches or 2000)
         if rank == 0:
             print(json.dumps({
                 "metric": "update-to-certified top-100 latency p99 (serving, dynamic R-MAT23)",
@@ -418,8 +432,7 @@ def main():
     total_s = sum(step_ms) / 1e3
     edges_local = sum(inf.r * nnz for inf in infos)
     total_s_max = allreduce_max(total_s, world)
-    edges_all = allreduce_sum(edges_local, world)
-    value = edges_all / total_s_max / 1e9
+    value = replica_throughput(edges_local, total_s, world) / 1e9
     spmv_ms = sum(inf.spmv_ms for inf in infos)
     spmv_launches = sum(inf.spmv_launches for inf in infos)
     launches = sum(inf.launches for inf in infos)
@@ -473,6 +486,8 @@ def main():
                "api": "katz_create_csr(host pinned CSR) + katz_rank_static + katz_get_ranking(host) + katz_destroy"}
 
     serving = None
+    if args.serve_batches is None:
+        args.serve_batches = 400
     if args.serve_batches > 0:
         h.close()
         del rowptr_d, col_d, flush

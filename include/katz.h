@@ -6,7 +6,7 @@
  *
  *   Katz centrality (Eq. 1): c(v) = sum_{i>=1} alpha^i omega_i(v), omega_i(v)
  *   the number of walks of length i that start at v.  The library never
- *   forms c exactly; it iterates the walk recurrence of Eq. (4),
+ *   forms c exactly; it iterates the walk recurrence of Eq. (5),
  *   omega_i(v) = sum_{v->x} omega_{i-1}(x), and keeps per-node bounds
  *   l_r(v) <= c(v) <= u_r(v) (Sec. 3.1, Theorem 1) until the top-k
  *   criterion holds: the k nodes with the highest lower bounds are

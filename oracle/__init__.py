@@ -94,7 +94,7 @@ def max_threads() -> int:
 
 
 def walks_exact(rowptr, col, r: int) -> list[list[int]]:
-    """Exact omega_1..omega_r (Eq. 4 from omega_0 = 1) as Python ints."""
+    """Exact omega_1..omega_r (Eq. 5 from omega_0 = 1) as Python ints."""
     rowptr = np.ascontiguousarray(rowptr, np.int64)
     col = np.ascontiguousarray(col, np.int32)
     n = rowptr.shape[0] - 1

@@ -84,7 +84,7 @@ bool converged(std::vector<int32_t>& M, int64_t k, const std::vector<double>& l,
     return true;
 }
 
-// Eq. (4): omega_i(v) = sum over arcs v->x of omega_{i-1}(x), in CSR order.
+// Eq. (5): omega_i(v) = sum over arcs v->x of omega_{i-1}(x), in CSR order.
 void walk_step(int64_t n, const int64_t* rowptr, const int32_t* col, const std::vector<double>& prev,
                std::vector<double>& next) {
     next.assign((size_t)n, 0.0);
@@ -305,7 +305,7 @@ void oracle_set_threads(int t) {
 #endif
 }
 
-// Exact walk counts omega_1..omega_r of Eq. (4) from omega_0 = 1, as
+// Exact walk counts omega_1..omega_r of Eq. (5) from omega_0 = 1, as
 // unsigned 128-bit integers: out[(i-1)*n*2 + 2*v] = low 64 bits,
 // out[... + 1] = high 64 bits.  Returns EOVERFLOW_ if a count exceeds 2^128-1.
 int oracle_walks_u128(int64_t n, const int64_t* rowptr, const int32_t* col, int r, uint64_t* out) {

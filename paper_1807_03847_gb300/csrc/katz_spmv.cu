@@ -1,6 +1,6 @@
 // The walk-count SpMV of Algorithm 1, fused with the bound update:
 //
-//   s_r(u) = alpha * sum_{u->x} s_{r-1}(x)        (Eq. 4, scaled by alpha^r)
+//   s_r(u) = alpha * sum_{u->x} s_{r-1}(x)        (Eq. 5, scaled by alpha^r)
 //   c_r(u) = c_{r-1}(u) + s_r(u)
 //   l_r, u_r from c_r and s_r for u in M; u joins the candidate list when
 //   l_r(u) >= theta_{r-1}.

@@ -1,6 +1,6 @@
 """Pins of the CPU oracle against things other than itself (CPU only).
 
-* Eq. (1)/(4): exact walk counts against brute-force walk enumeration.
+* Eq. (1)/(5): exact walk counts against brute-force walk enumeration.
 * Eq. (2): the closed form c = alpha A (I - alpha A)^{-1} 1 solved in exact
   rational arithmetic; Theorem 1 (l_r <= c <= u_r) at every r, and l_r, u_r
   converge to c.
@@ -100,7 +100,7 @@ def _bounds_at(rowptr, col, alpha, k, eps, R, undirected=True):
 
 
 # ---------------------------------------------------------------------------
-# Eq. (4) against brute-force enumeration
+# Eq. (5) against brute-force enumeration
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("seed", range(6))
 @pytest.mark.parametrize("directed", [False, True])

@@ -1,0 +1,59 @@
+"""The N > 1 path of bench.py on CPU with gloo: N independent replicas (no
+data-path collective), whose whole-job value is the units every rank
+processed over the slowest rank's time; the reference arm runs on rank 0
+only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    bench.barrier(world)
+    units = 1000.0 * (rank + 1)        # rank r processed 1000 (r + 1) arcs ...
+    seconds = 0.5 + rank               # ... in 0.5 + r seconds
+    v = bench.replica_throughput(units, seconds, world)
+    out.put((rank, v, bench.allreduce_max(seconds, world), bench.allreduce_sum(units, world)))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_replicas_aggregate_over_all_ranks():
+    ctx = torch.multiprocessing.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, v, tmax, usum in got:
+        assert tmax == 1.5 and usum == 3000.0
+        assert v == pytest.approx(3000.0 / 1.5)  # every rank reports the same whole-job value
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "er16k", "--steps", "1", "--warmup", "0"], env=env, cwd=ROOT, capture_output=True,
+                         text=True, timeout=300)
+    assert res.returncode == 0 and res.stdout.strip() == ""
