@@ -21,9 +21,9 @@ def _dev(a):
 
 
 def run_gpu(g, alpha, k, eps, *, undirected=True, keep_history=True, r_max=256, on_device=True, use_graph=1,
-            precision=0):
+            precision=0, profile=0):
     opts = K.katz_default_opts(undirected=1 if undirected else 0, keep_history=1 if keep_history else 0,
-                               r_max=r_max, use_graph=use_graph, precision=precision)
+                               r_max=r_max, use_graph=use_graph, precision=precision, profile=profile)
     rp, cl = (_dev(g.rowptr), _dev(g.col)) if on_device else (g.rowptr, g.col)
     h = K.Katz(rp, cl, opts)
     info = h.rank(alpha, k, eps)
@@ -176,8 +176,10 @@ def test_repeat_call_is_deterministic():
 
 @pytest.mark.slow
 def test_rmat22_top1000_full_size():
-    """The benchmark workload at full size (R-MAT scale 22, top-1000, eps 1e-9)."""
+    """The benchmark workload at full size (R-MAT scale 22, top-1000, eps 1e-9)
+    in the configuration bench.py times (profiled host loop, two walk slots),
+    against a complete oracle run: same r, same ranking, every node's bounds."""
     g = gg.workload("rmat22")
     oracle.set_threads(0)
-    check_parity(g, 0.0, 1000, 1e-9, walks=False)
+    check_parity(g, 0.0, 1000, 1e-9, walks=False, profile=1)
 
