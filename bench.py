@@ -159,14 +159,14 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(precision: str):
+def ncu_traffic(workload: str, precision: str):
     """DRAM bytes per SpMV launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+    taken on this workload, in this precision, on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "spmv_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d.get(precision)
+        e = d.get(f"{workload}-{precision}")
         if e and e.get("source_hash") == kernel_source_hash():
             return e
     except Exception:
@@ -445,7 +445,7 @@ def main():
     bytes_alg = spmv_algorithmic_bytes(n, nnz, fp32, off64)
     t_launch = spmv_ms / 1e3 / max(spmv_launches, 1)
     hbm_ach = bytes_alg / t_launch / 1e9
-    tr = ncu_traffic("fp32cert" if fp32 else "fp64")
+    tr = ncu_traffic(args.workload, "fp32cert" if fp32 else "fp64")
     traffic = tr["bytes_per_launch"] if tr else None
     # The walk-count SpMV moves its compulsory bytes from HBM and sums on the
     # integer pipes (exact FP64 row sums), so DRAM bandwidth is the roofline

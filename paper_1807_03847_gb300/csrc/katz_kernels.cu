@@ -159,13 +159,13 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
         s_big = 0;
     }
     __syncthreads();
-    if (nc > (unsigned long long)SELECT_CAP) {
+    {
         // Narrow the candidates: the previous top-k nodes are still active and
         // each has l_r >= tau := min of their l_r, so the top-k of M lies in
-        // {l_r >= tau}.
+        // {l_r >= tau} (a far smaller sort than all of {l_r >= theta_{r-1}}).
         const int kprev = ctrl->k_eff;
         if (r_cur <= 1 || kprev < (int)p.k) {
-            if (tid == 0) s_big = 1;
+            if (tid == 0 && nc > (unsigned long long)SELECT_CAP) s_big = 1;
         } else {
             const BState bs = bstate(ctrl);
             const int f32_from = ctrl->f32_from;
@@ -263,26 +263,45 @@ __global__ void count_kernel(const T* walk, const double* __restrict__ c, const 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // l, th >= 0 (sums of non-negative terms): they order like their bit patterns
     const long long th_bits = __double_as_longlong(th);
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
-        if (!active[v]) continue;
-        const double l = lb[v], u = ub[v];  // stored by the SpMV epilogue of this level
-        const long long l_bits = __double_as_longlong(l);
-        const int32_t ov = perm[v];  // ties are broken by the original id
-        const bool top = l_bits > th_bits || (l_bits == th_bits && ov <= thid);
-        if (!top) {
-            if (__dsub_rn(u, p.eps) < th) {
-                active[v] = 0;
-                continue;
-            }
-            ++cross;
+    // four nodes per thread and pass, their loads issued before any decision
+    constexpr int U = 4;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v0 < p.n; v0 += U * stride) {
+        bool on[U];
+        double l[U], u[U];
+        int32_t ov[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int64_t v = v0 + q * stride;
+            on[q] = v < p.n && active[v];
         }
-        ++act;
-        if (p.cert) {
-            const double sv = walk_value(walk, p, f32_from, r_cur, v);
-            const double c64v = c[v], c32v = c32 ? c32[v] : 0.0;
-            smax = fmax(smax, sv);
-            tailw = fmax(tailw, p.ag * sv);
-            roundw = fmax(roundw, c64v * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32));
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int64_t v = v0 + q * stride;
+            l[q] = on[q] ? lb[v] : 0.0;  // stored by the SpMV epilogue of this level
+            u[q] = on[q] ? ub[v] : 0.0;
+            ov[q] = on[q] ? perm[v] : 0;  // ties are broken by the original id
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (!on[q]) continue;
+            const int64_t v = v0 + q * stride;
+            const long long l_bits = __double_as_longlong(l[q]);
+            const bool top = l_bits > th_bits || (l_bits == th_bits && ov[q] <= thid);
+            if (!top) {
+                if (__dsub_rn(u[q], p.eps) < th) {
+                    active[v] = 0;
+                    continue;
+                }
+                ++cross;
+            }
+            ++act;
+            if (p.cert) {
+                const double sv = walk_value(walk, p, f32_from, r_cur, v);
+                const double c64v = c[v], c32v = c32 ? c32[v] : 0.0;
+                smax = fmax(smax, sv);
+                tailw = fmax(tailw, p.ag * sv);
+                roundw = fmax(roundw, c64v * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32));
+            }
         }
     }
     // block totals first: one atomic per block and counter (same-address
