@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "katz_common.cuh"
@@ -26,6 +27,9 @@ const char* kStatusNames[] = {"KATZ_OK",     "KATZ_EINVAL",     "KATZ_EALPHA",  
 }  // namespace
 
 namespace katz {
+
+constexpr size_t CTRL_BYTES = (sizeof(Ctrl) + 255) / 256 * 256;
+constexpr size_t H_SMALL = 4096;
 
 katz_status fail(katz_handle* h, katz_status s, const std::string& msg) {
     if (h) h->err = msg;
@@ -48,29 +52,60 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory of the handles comes from one stream-ordered pool per
+// device that the library keeps for the life of the process (no release
+// threshold): destroying a handle returns its memory to the pool without a
+// device-wide synchronisation, and the next handle reuses it.
+cudaMemPool_t library_pool(int dev) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&pools[dev], &props) != cudaSuccess) {
+            pools[dev] = nullptr;
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    return pools[dev];
+}
+
+// count elements of X, ordered on the handle's stream
 template <typename X>
-cudaError_t dmalloc(X** p, size_t count) {
+cudaError_t dmalloc(katz_handle* h, X** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    return cudaMalloc((void**)p, count * sizeof(X));
+    cudaMemPool_t pool = library_pool(h->dev);
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync((void**)p, count * sizeof(X), pool, h->stream);
+}
+
+void dfree(katz_handle* h, void* p) {
+    if (p) cudaFreeAsync(p, h->stream);
 }
 
 void free_iter(katz_handle* h) {
     IterBuffers& b = h->b;
-    cudaFree(b.walk);
-    cudaFree(b.c);
-    cudaFree(b.c32);
-    cudaFree(b.lb);
-    cudaFree(b.ub);
-    cudaFree(b.active);
-    cudaFree(b.cand_l);
-    cudaFree(b.cand_u);
-    cudaFree(b.cand_id);
-    cudaFree(b.topk_id);
-    cudaFree(b.topk_l);
-    cudaFree(b.topk_u);
-    cudaFree(b.trace);
-    cudaFree(b.ctrl);
+    dfree(h, b.walk);
+    dfree(h, b.c);
+    dfree(h, b.c32);
+    dfree(h, b.lb);
+    dfree(h, b.ub);
+    dfree(h, b.active);
+    dfree(h, b.cand_l);
+    dfree(h, b.cand_u);
+    dfree(h, b.cand_id);
+    dfree(h, b.topk_id);
+    dfree(h, b.topk_l);
+    dfree(h, b.topk_u);
+    dfree(h, b.trace);
+    dfree(h, b.ctrl);
     b = IterBuffers();
     h->walk_slots = 0;
 }
@@ -87,7 +122,7 @@ katz_status ensure_iter_buffers(katz_handle* h) {
     const int64_t stride = ((n + 1) + 31) / 32 * 32;
     cudaError_t e;
 #define KALLOC(ptr, cnt)                                          \
-    if ((e = dmalloc(&(ptr), (size_t)(cnt))) != cudaSuccess) {    \
+    if ((e = dmalloc(h, &(ptr), (size_t)(cnt))) != cudaSuccess) {    \
         free_iter(h);                                             \
         return cuda_fail(h, e, "cudaMalloc " #ptr);               \
     }
@@ -303,7 +338,7 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
     DynBuffers& d = h->dyn;
     const int64_t n = g.n;
 #define DALLOC(ptr, cnt)                                                      \
-    if ((e = dmalloc(&(ptr), (size_t)(cnt))) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc " #ptr);
+    if ((e = dmalloc(h, &(ptr), (size_t)(cnt))) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc " #ptr);
     if (!d.delta) {
         DALLOC(d.delta, n);
         DALLOC(d.ins_cnt, n);
@@ -327,12 +362,12 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
         h->col_cap = g.nnz;
     }
     if (m > d.cap) {
-        cudaFree(d.src);
-        cudaFree(d.dst);
-        cudaFree(d.ins);
-        cudaFree(d.ins_rows);
-        cudaFree(d.bucket);
-        cudaFree(d.table);
+        dfree(h, d.src);
+        dfree(h, d.dst);
+        dfree(h, d.ins);
+        dfree(h, d.ins_rows);
+        dfree(h, d.bucket);
+        dfree(h, d.table);
         d.src = nullptr;
         d.dst = nullptr;
         d.ins = nullptr;
@@ -356,7 +391,7 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
             return cuda_fail(h, e, "memset table");
     }
     if (nnz_cap > h->col_spare_cap) {
-        cudaFree(h->col_spare);
+        dfree(h, h->col_spare);
         h->col_spare = nullptr;
         h->col_spare_cap = 0;
         DALLOC(h->col_spare, nnz_cap);
@@ -397,31 +432,31 @@ void katz_destroy(katz_h h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_iter(h);
-    cudaFree(h->g.rowptr);
-    cudaFree(h->g.col);
-    cudaFree(h->g.perm);
-    cudaFree(h->g.inv);
-    cudaFree(h->g.chunk_row);
-    cudaFree(h->g.chunk_first);
-    cudaFree(h->g.chunk_part);
-    cudaFree(h->d_deghist);
-    cudaFree(h->d_big_l);
-    cudaFree(h->d_big_u);
-    cudaFree(h->d_big_id);
-    cudaFree(h->d_hist256);
-    cudaFree(h->d_count);
-    cudaFree(h->d_scratch);
+    dfree(h, h->g.rowptr);
+    dfree(h, h->g.col);
+    dfree(h, h->g.perm);
+    dfree(h, h->g.inv);
+    dfree(h, h->g.chunk_row);
+    dfree(h, h->g.chunk_first);
+    dfree(h, h->g.chunk_part);
+    dfree(h, h->d_deghist);
+    dfree(h, h->d_big_l);
+    dfree(h, h->d_big_u);
+    dfree(h, h->d_big_id);
+    dfree(h, h->d_hist256);
+    dfree(h, h->d_count);
+    dfree(h, h->d_scratch);
     {
         DynBuffers& d = h->dyn;
         for (void* ptr : {(void*)d.src, (void*)d.dst, (void*)d.ins, (void*)d.hub_epoch, (void*)d.table,
                           (void*)d.err, (void*)d.delta, (void*)d.ins_cnt, (void*)d.cursor, (void*)d.touched,
                           (void*)d.ins_start, (void*)d.ins_rows, (void*)d.n_ins_rows, (void*)d.bucket,
                           (void*)d.vbits, (void*)d.frontier, (void*)d.fsize})
-            cudaFree(ptr);
-        cudaFree(h->col_spare);
-        cudaFree(h->rp_new);
-        cudaFree(h->deg_tmp);
-        cudaFree(h->scan_sums);
+            dfree(h, ptr);
+        dfree(h, h->col_spare);
+        dfree(h, h->rp_new);
+        dfree(h, h->deg_tmp);
+        dfree(h, h->scan_sums);
     }
     cudaFreeHost(h->h_ctrl);
     drop_graph(h);
@@ -465,33 +500,55 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     }
     KCHK(cudaEventCreate(&h->ev0), "cudaEventCreate");
     KCHK(cudaEventCreate(&h->ev1), "cudaEventCreate");
-    KCHK(cudaMallocHost((void**)&h->h_ctrl, sizeof(Ctrl)), "cudaMallocHost");
+    {  // one pinned block: the control block, then a small scratch for device-to-host reads
+        void* blk = nullptr;
+        KCHK(cudaMallocHost(&blk, CTRL_BYTES + H_SMALL), "cudaMallocHost");
+        h->h_ctrl = (Ctrl*)blk;
+        h->h_small = (unsigned char*)blk + CTRL_BYTES;
+    }
     DeviceGraph& g = h->g;
     g.n = n;
     g.nnz = nnz;
     g.off64 = (n + nnz) >= 0x7fffffffLL;
-    // copy the CSR as given (int64 rowptr), validate it, then store it in
-    // internal order (degree classes, largest first)
+    // Input: the row offsets are copied first and validated, and the
+    // degree-class relabelling (which needs only them) runs while the column
+    // array follows on a second stream in slices of rows; each slice is
+    // renamed into internal order as soon as it has arrived.
+    const bool host_rowptr = !is_device_ptr(rowptr);
+    const int slices = (host_rowptr && nnz >= (1 << 22)) ? 8 : 1;
+    std::vector<int64_t> vcut((size_t)slices + 1, 0), acut((size_t)slices + 1, 0);
+    vcut[slices] = n;
+    acut[slices] = nnz;
+    for (int i = 1; i < slices; ++i) {  // rows with about nnz / slices arcs each
+        const int64_t target = nnz / slices * i;
+        int64_t lo = vcut[i - 1], hi = n;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (rowptr[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        vcut[i] = lo;
+        // copy ranges come from the offsets as given, made monotone and kept
+        // inside [0, nnz], so that every copy stays in bounds even for a
+        // malformed CSR (which the device check then rejects)
+        acut[i] = std::min<int64_t>(std::max<int64_t>(rowptr[lo], acut[i - 1]), nnz);
+    }
     int64_t* rp64 = nullptr;
     int32_t* col0 = nullptr;
-    e = dmalloc(&rp64, (size_t)n + 1);
-    if (e == cudaSuccess) e = dmalloc(&col0, (size_t)nnz);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(rp64, rowptr, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDefault, h->stream);
-    if (e == cudaSuccess && nnz > 0)
-        e = cudaMemcpyAsync(col0, col, (size_t)nnz * sizeof(int32_t), cudaMemcpyDefault, h->stream);
+    cudaStream_t cs = nullptr;
+    std::vector<cudaEvent_t> ev((size_t)slices + 1, nullptr);
     auto drop_staging = [&]() {
-        cudaFree(rp64);
-        cudaFree(col0);
+        if (cs) cudaStreamSynchronize(cs);  // slices still in flight into col0
+        dfree(h, rp64);
+        dfree(h, col0);
         rp64 = nullptr;
         col0 = nullptr;
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+        ev.assign(ev.size(), nullptr);
+        if (cs) cudaStreamDestroy(cs);
+        cs = nullptr;
     };
-    if (e != cudaSuccess) {
-        drop_staging();
-        st = cuda_fail(h, e, "copy CSR");
-        katz_destroy(h);
-        return st;
-    }
 #define KCHK2(call, what)                      \
     if ((e = (call)) != cudaSuccess) {         \
         drop_staging();                        \
@@ -499,11 +556,25 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
         katz_destroy(h);                       \
         return st;                             \
     }
-    unsigned long long* d_bad = nullptr;
+    KCHK2(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (int i = 0; i <= slices; ++i) KCHK2(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming), "cudaEventCreate");
+    KCHK2(dmalloc(h, &rp64, (size_t)n + 1), "cudaMalloc rowptr");
+    KCHK2(dmalloc(h, &col0, (size_t)nnz), "cudaMalloc col");
+    KCHK2(cudaEventRecord(ev[slices], h->stream), "event");  // the allocations, for the copy stream
+    KCHK2(cudaStreamWaitEvent(cs, ev[slices], 0), "event");
+    KCHK2(cudaMemcpyAsync(rp64, rowptr, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDefault, h->stream), "copy rowptr");
+    for (int i = 0; i < slices; ++i) {
+        if (acut[i + 1] > acut[i])
+            KCHK2(cudaMemcpyAsync(col0 + acut[i], col + acut[i], (size_t)(acut[i + 1] - acut[i]) * sizeof(int32_t),
+                                  cudaMemcpyDefault, cs), "copy col");
+        KCHK2(cudaEventRecord(ev[i], cs), "event");
+    }
+    // offsets: monotone, rowptr[0] = 0, rowptr[n] = nnz, and deg_max
+    unsigned long long* d_bad = nullptr;  // [0] offsets malformed, [1] column entries out of range, [2] max chunks
     int64_t* d_degmax = nullptr;
-    KCHK2(dmalloc(&d_bad, 1), "cudaMalloc");
-    KCHK2(dmalloc(&d_degmax, 1), "cudaMalloc");
-    KCHK2(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), h->stream), "memset");
+    KCHK2(dmalloc(h, &d_bad, 3), "cudaMalloc");
+    KCHK2(dmalloc(h, &d_degmax, 1), "cudaMalloc");
+    KCHK2(cudaMemsetAsync(d_bad, 0, 3 * sizeof(unsigned long long), h->stream), "memset");
     KCHK2(cudaMemsetAsync(d_degmax, 0, sizeof(int64_t), h->stream), "memset");
     {
         DeviceGraph g64;
@@ -511,94 +582,100 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
         g64.nnz = nnz;
         g64.off64 = true;
         g64.rowptr = rp64;
-        g64.col = col0;
+        g64.col = nullptr;
         KCHK2(launch_validate_csr(g64, d_bad, d_degmax, h->stream), "validate");
     }
-    unsigned long long bad = 0;
-    int64_t degmax = 0;
-    KCHK2(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "copy");
-    KCHK2(cudaMemcpyAsync(&degmax, d_degmax, sizeof(degmax), cudaMemcpyDeviceToHost, h->stream), "copy");
+    // relabel: stable counting sort by degree class, then the new offsets
+    const int nb = relabel_blocks(n);
+    uint32_t* counts = nullptr;
+    uint64_t* class_start = nullptr;
+    int64_t* deg_new = nullptr;
+    int64_t* rp_new = nullptr;
+    int64_t* sums = nullptr;
+    KCHK2(dmalloc(h, &counts, (size_t)NUM_CLASSES * nb), "cudaMalloc counts");
+    KCHK2(dmalloc(h, &class_start, NUM_CLASSES), "cudaMalloc");
+    KCHK2(dmalloc(h, &g.perm, (size_t)n), "cudaMalloc perm");
+    KCHK2(dmalloc(h, &g.inv, (size_t)n), "cudaMalloc inv");
+    KCHK2(dmalloc(h, &deg_new, (size_t)n + 1), "cudaMalloc");
+    KCHK2(dmalloc(h, &rp_new, (size_t)n + 1), "cudaMalloc");
+    KCHK2(dmalloc(h, &sums, (size_t)scan_blocks(n + 1)), "cudaMalloc");
+    KCHK2(dmalloc(h, &g.col, (size_t)nnz), "cudaMalloc col");
+    KCHK2(relabel_by_degree_class(rp64, n, counts, nb, g.perm, g.inv, class_start, h->stream), "relabel");
+    KCHK2(relabel_offsets(rp64, g.perm, n, deg_new, rp_new, sums, h->stream), "relabel offsets");
+    // small reads go through pinned memory: a pageable copy would queue
+    // behind the column slices still in flight
+    struct HostVals {
+        unsigned long long bad, bad_col, max_chunks;
+        int64_t degmax, chunks;
+        uint64_t cs[NUM_CLASSES];
+    };
+    static_assert(sizeof(HostVals) <= H_SMALL, "pinned scratch");
+    HostVals& hv = *(HostVals*)h->h_small;
+    KCHK2(cudaMemcpyAsync(&hv.bad, d_bad, sizeof(hv.bad), cudaMemcpyDeviceToHost, h->stream), "copy");
+    KCHK2(cudaMemcpyAsync(&hv.degmax, d_degmax, sizeof(hv.degmax), cudaMemcpyDeviceToHost, h->stream), "copy");
+    KCHK2(cudaMemcpyAsync(hv.cs, class_start, sizeof(hv.cs), cudaMemcpyDeviceToHost, h->stream), "copy classes");
     KCHK2(cudaStreamSynchronize(h->stream), "validate sync");
-    cudaFree(d_bad);
-    cudaFree(d_degmax);
-    if (bad) {
+    if (hv.bad) {
         drop_staging();
         katz_destroy(h);
         return KATZ_EINVAL;
     }
-    h->deg_max = degmax;
-    h->D = std::max<int64_t>(h->opts.deg_bound, degmax);
-    // relabel: stable counting sort by degree class
-    {
-        const int nb = relabel_blocks(n);
-        uint32_t* counts = nullptr;
-        uint64_t* class_start = nullptr;
-        KCHK2(dmalloc(&counts, (size_t)NUM_CLASSES * nb), "cudaMalloc counts");
-        KCHK2(dmalloc(&class_start, NUM_CLASSES), "cudaMalloc");
-        KCHK2(dmalloc(&g.perm, (size_t)n), "cudaMalloc perm");
-        KCHK2(dmalloc(&g.inv, (size_t)n), "cudaMalloc inv");
-        KCHK2(relabel_by_degree_class(rp64, n, counts, nb, g.perm, g.inv, class_start, h->stream), "relabel");
-        uint64_t cs[NUM_CLASSES];
-        KCHK2(cudaMemcpyAsync(cs, class_start, sizeof(cs), cudaMemcpyDeviceToHost, h->stream), "copy classes");
-        KCHK2(cudaStreamSynchronize(h->stream), "relabel sync");
-        cudaFree(counts);
-        cudaFree(class_start);
-        // rows of degree > 2048 / > 128 / > 16 come first: classes >= 13 / >= 9 / >= 6
-        const int64_t row_warp = (int64_t)cs[12], row_octet = (int64_t)cs[8], row_thread = (int64_t)cs[5];
-        int64_t* deg_new = nullptr;
-        int64_t* rp_new = nullptr;
-        int64_t* sums = nullptr;
-        KCHK2(dmalloc(&deg_new, (size_t)n + 1), "cudaMalloc");
-        KCHK2(dmalloc(&rp_new, (size_t)n + 1), "cudaMalloc");
-        KCHK2(dmalloc(&sums, (size_t)scan_blocks(n + 1)), "cudaMalloc");
-        KCHK2(dmalloc(&g.col, (size_t)nnz), "cudaMalloc col");
-        KCHK2(cudaMemsetAsync(deg_new + n, 0, sizeof(int64_t), h->stream), "memset");
-        KCHK2(relabel_rows(rp64, col0, g.perm, g.inv, n, deg_new, rp_new, sums, g.col, h->stream), "relabel rows");
-        // chunk table of the CHUNK rows (host side; there are few of them)
-        std::vector<int64_t> hrp((size_t)row_warp + 1);
-        KCHK2(cudaMemcpyAsync(hrp.data(), rp_new, hrp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream),
-              "copy rowptr head");
-        KCHK2(cudaStreamSynchronize(h->stream), "relabel rows sync");
-        std::vector<int64_t> first((size_t)row_warp + 1, 0);
-        for (int64_t u = 0; u < row_warp; ++u)
-            first[u + 1] = first[u] + (hrp[u + 1] - hrp[u] + CHUNK_ARCS - 1) / CHUNK_ARCS;
-        const int64_t chunks = first[row_warp];
-        std::vector<int32_t> crow((size_t)std::max<int64_t>(chunks, 1));
-        for (int64_t u = 0; u < row_warp; ++u)
-            for (int64_t q = first[u]; q < first[u + 1]; ++q) crow[q] = (int32_t)u;
-        KCHK2(dmalloc(&g.chunk_first, first.size()), "cudaMalloc");
-        KCHK2(dmalloc(&g.chunk_row, crow.size()), "cudaMalloc");
-        KCHK2(dmalloc(&g.chunk_part, 3 * crow.size()), "cudaMalloc");
-        KCHK2(cudaMemcpyAsync(g.chunk_first, first.data(), first.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
-                              h->stream), "copy chunks");
-        KCHK2(cudaMemcpyAsync(g.chunk_row, crow.data(), crow.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                              h->stream), "copy chunks");
-        g.layout = make_layout(n, row_warp, row_octet, row_thread, chunks);
-        int64_t max_chunks = 0;
-        for (int64_t u = 0; u < row_warp; ++u) max_chunks = std::max<int64_t>(max_chunks, first[u + 1] - first[u]);
-        h->sum_depth = max_sum_depth(g.layout, max_chunks);
-        if (g.off64) {
-            g.rowptr = rp_new;
-            rp_new = nullptr;
-        } else {
-            int32_t* rp32 = nullptr;
-            KCHK2(dmalloc(&rp32, (size_t)n + 1), "cudaMalloc rowptr32");
-            KCHK2(launch_narrow_rowptr(rp_new, rp32, n + 1, h->stream), "narrow rowptr");
-            g.rowptr = rp32;
-        }
-        KCHK2(cudaStreamSynchronize(h->stream), "relabel sync");
-        cudaFree(deg_new);
-        cudaFree(rp_new);
-        cudaFree(sums);
+    h->deg_max = hv.degmax;
+    h->D = std::max<int64_t>(h->opts.deg_bound, hv.degmax);
+    // rows of degree > 2048 / > 128 / > 16 come first: classes >= 13 / >= 9 / >= 6
+    const int64_t row_warp = (int64_t)hv.cs[12], row_octet = (int64_t)hv.cs[8], row_thread = (int64_t)hv.cs[5];
+    // chunk table of the CHUNK rows, on the device (every CHUNK row holds more
+    // than CHUNK_ARCS arcs, so the count stays below nnz / CHUNK_ARCS + row_warp)
+    const int64_t chunks_cap = nnz / CHUNK_ARCS + row_warp + 1;
+    KCHK2(dmalloc(h, &g.chunk_first, (size_t)row_warp + 1), "cudaMalloc");
+    KCHK2(dmalloc(h, &g.chunk_row, (size_t)chunks_cap), "cudaMalloc");
+    KCHK2(dmalloc(h, &g.chunk_part, 3 * (size_t)chunks_cap), "cudaMalloc");
+    KCHK2(build_chunk_table(rp_new, row_warp, deg_new, sums, g.chunk_first, g.chunk_row, d_bad + 2, h->stream),
+          "chunk table");
+    // the column array, slice by slice as it arrives (entries range-checked);
+    // the CHUNK rows once all of it is there
+    for (int i = 0; i < slices; ++i) {
+        KCHK2(cudaStreamWaitEvent(h->stream, ev[i], 0), "event");
+        KCHK2(remap_src_rows(rp64, col0, g.inv, rp_new, vcut[i], vcut[i + 1], n, row_warp, g.col, d_bad + 1,
+                             h->stream), "relabel rows");
     }
+    KCHK2(remap_hub_chunks(rp64, col0, g.perm, g.inv, rp_new, g.chunk_row, g.chunk_first, row_warp, chunks_cap, n,
+                           g.col, d_bad + 1, h->stream), "relabel hub rows");
+    if (g.off64) {
+        g.rowptr = rp_new;
+        rp_new = nullptr;
+    } else {
+        int32_t* rp32 = nullptr;
+        KCHK2(dmalloc(h, &rp32, (size_t)n + 1), "cudaMalloc rowptr32");
+        KCHK2(launch_narrow_rowptr(rp_new, rp32, n + 1, h->stream), "narrow rowptr");
+        g.rowptr = rp32;
+    }
+    KCHK2(cudaMemcpyAsync(&hv.bad_col, d_bad + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream),
+          "copy");
+    KCHK2(cudaMemcpyAsync(&hv.chunks, g.chunk_first + row_warp, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream),
+          "copy");
+    KCHK2(cudaStreamSynchronize(h->stream), "relabel sync");
+    g.layout = make_layout(n, row_warp, row_octet, row_thread, hv.chunks);
+    h->sum_depth = max_sum_depth(g.layout, (int64_t)hv.max_chunks);
+    dfree(h, d_bad);
+    dfree(h, d_degmax);
+    dfree(h, counts);
+    dfree(h, class_start);
+    dfree(h, deg_new);
+    dfree(h, rp_new);
+    dfree(h, sums);
     drop_staging();
+    if (hv.bad_col) {  // a column entry outside [0, n)
+        katz_destroy(h);
+        return KATZ_EINVAL;
+    }
 #undef KCHK2
-    KCHK(dmalloc(&h->d_deghist, (size_t)h->D + 1), "cudaMalloc deghist");
-    KCHK(dmalloc(&h->d_big_l, SELECT_CAP), "cudaMalloc");
-    KCHK(dmalloc(&h->d_big_u, SELECT_CAP), "cudaMalloc");
-    KCHK(dmalloc(&h->d_big_id, SELECT_CAP), "cudaMalloc");
-    KCHK(dmalloc(&h->d_hist256, 256), "cudaMalloc");
-    KCHK(dmalloc(&h->d_count, 1), "cudaMalloc");
+    KCHK(dmalloc(h, &h->d_deghist, (size_t)h->D + 1), "cudaMalloc deghist");
+    KCHK(dmalloc(h, &h->d_big_l, SELECT_CAP), "cudaMalloc");
+    KCHK(dmalloc(h, &h->d_big_u, SELECT_CAP), "cudaMalloc");
+    KCHK(dmalloc(h, &h->d_big_id, SELECT_CAP), "cudaMalloc");
+    KCHK(dmalloc(h, &h->d_hist256, 256), "cudaMalloc");
+    KCHK(dmalloc(h, &h->d_count, 1), "cudaMalloc");
     KCHK(cudaStreamSynchronize(h->stream), "create sync");
 #undef KCHK
     *out = h;
@@ -724,7 +801,7 @@ katz_status katz_get_bounds(katz_h h, double* lower, double* upper, double* err)
     double* de = err;
     if (!dev) {
         if (!h->d_scratch) {
-            if ((e = dmalloc(&h->d_scratch, 3 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+            if ((e = dmalloc(h, &h->d_scratch, 3 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
         }
         dl = lower ? h->d_scratch : nullptr;
         du = upper ? h->d_scratch + n : nullptr;
@@ -754,7 +831,7 @@ katz_status katz_get_walk(katz_h h, int32_t i, double* s_out) {
     double* dst = s_out;
     const bool dev = is_device_ptr(s_out);
     if (!dev) {
-        if (!h->d_scratch && (e = dmalloc(&h->d_scratch, 3 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+        if (!h->d_scratch && (e = dmalloc(h, &h->d_scratch, 3 * (size_t)n)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
         dst = h->d_scratch;
     }
     if ((e = launch_walk_out(h->g, h->b, h->p, i, h->fp32, dst, h->stream)) != cudaSuccess) return cuda_fail(h, e, "walk");
@@ -837,10 +914,10 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
             return fail(h, KATZ_EINVAL, "the graph would outgrow 32-bit offsets; create it with more headroom");
         }
         if (nnz_new > h->col_spare_cap) {
-            cudaFree(h->col_spare);
+            dfree(h, h->col_spare);
             h->col_spare = nullptr;
             const int64_t cap = nnz_new + nnz_new / 16 + 1024;
-            if ((e = dmalloc(&h->col_spare, (size_t)cap)) != cudaSuccess) {
+            if ((e = dmalloc(h, &h->col_spare, (size_t)cap)) != cudaSuccess) {
                 h->col_spare_cap = 0;
                 dyn_clear(g, d, m, h->stream);
                 return cuda_fail(h, e, "cudaMalloc col");
@@ -868,12 +945,12 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
                 first[u + 1] = first[u] + (hrp[u + 1] - hrp[u] + CHUNK_ARCS - 1) / CHUNK_ARCS;
             const int64_t chunks = first[rw];
             if (chunks > g.layout.chunks) {
-                cudaFree(g.chunk_row);
-                cudaFree(g.chunk_part);
+                dfree(h, g.chunk_row);
+                dfree(h, g.chunk_part);
                 g.chunk_row = nullptr;
                 g.chunk_part = nullptr;
-                if ((e = dmalloc(&g.chunk_row, (size_t)chunks)) != cudaSuccess ||
-                    (e = dmalloc(&g.chunk_part, 3 * (size_t)chunks)) != cudaSuccess)
+                if ((e = dmalloc(h, &g.chunk_row, (size_t)chunks)) != cudaSuccess ||
+                    (e = dmalloc(h, &g.chunk_part, 3 * (size_t)chunks)) != cudaSuccess)
                     return cuda_fail(h, e, "cudaMalloc chunks");
             }
             std::vector<int32_t> crow((size_t)std::max<int64_t>(chunks, 1));

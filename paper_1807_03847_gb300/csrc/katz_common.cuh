@@ -209,10 +209,24 @@ int64_t scan_blocks(int64_t n);
 int degree_class_host(int64_t d);
 cudaError_t relabel_by_degree_class(const int64_t* rowptr64, int64_t n, uint32_t* counts_scratch, int nb,
                                     int32_t* perm, int32_t* inv, uint64_t* class_start_dev, cudaStream_t st);
-cudaError_t relabel_rows(const int64_t* rowptr64, const int32_t* col, const int32_t* perm, const int32_t* inv,
-                         int64_t n, int64_t* deg_new_scratch, int64_t* rowptr_new, int64_t* sums_scratch,
-                         int32_t* col_new, cudaStream_t st);
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* sums_scratch, cudaStream_t st);
+// new row offsets (int64, n+1) of the relabelled adjacency
+cudaError_t relabel_offsets(const int64_t* rowptr64, const int32_t* perm, int64_t n, int64_t* deg_new_scratch,
+                            int64_t* rowptr_new, int64_t* sums_scratch, cudaStream_t st);
+// arcs of the original rows [v0, v1) that do not become CHUNK rows, renamed
+// into their new rows; then those of the CHUNK rows, chunk by chunk
+cudaError_t remap_src_rows(const int64_t* rowptr64, const int32_t* col, const int32_t* inv, const int64_t* rowptr_new,
+                           int64_t v0, int64_t v1, int64_t n, int64_t row_warp, int32_t* col_new,
+                           unsigned long long* bad, cudaStream_t st);
+cudaError_t remap_hub_chunks(const int64_t* rowptr64, const int32_t* col, const int32_t* perm, const int32_t* inv,
+                             const int64_t* rowptr_new, const int32_t* chunk_row, const int64_t* chunk_first,
+                             int64_t row_warp, int64_t chunks_cap, int64_t n, int32_t* col_new,
+                             unsigned long long* bad, cudaStream_t st);
+// chunk table of the CHUNK rows from the new offsets: chunk_first (row_warp + 1
+// entries, exclusive scan of the chunk counts), chunk_row, and the largest count
+cudaError_t build_chunk_table(const int64_t* rowptr_new, int64_t row_warp, int64_t* cnt_scratch, int64_t* sums_scratch,
+                              int64_t* chunk_first, int32_t* chunk_row, unsigned long long* max_chunks,
+                              cudaStream_t st);
 cudaError_t launch_validate_csr(const DeviceGraph& g, unsigned long long* d_bad, int64_t* d_degmax,
                                 cudaStream_t st);
 cudaError_t launch_init_walk(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,

@@ -33,7 +33,8 @@ struct katz_handle {
     unsigned long long* d_hist256 = nullptr;
     unsigned long long* d_count = nullptr;
     double* d_scratch = nullptr;
-    katz::Ctrl* h_ctrl = nullptr;  // pinned
+    katz::Ctrl* h_ctrl = nullptr;  // pinned (one block with h_small)
+    unsigned char* h_small = nullptr;  // pinned scratch of H_SMALL bytes for small device-to-host reads
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // profiling: one event pair per SpMV launch
     std::vector<cudaEvent_t> sp_ev;

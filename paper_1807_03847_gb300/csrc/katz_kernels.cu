@@ -45,12 +45,20 @@ __global__ void validate_kernel(const Off* __restrict__ rowptr, const int32_t* _
         dm = max(dm, (long long)(b - a));
     }
     if (tid == 0 && ((int64_t)rowptr[0] != 0 || (int64_t)rowptr[n] != nnz)) ++nb;
-    for (int64_t j = tid; j < nnz; j += stride) {
-        const int32_t x = col[j];
-        if (x < 0 || (int64_t)x >= n) ++nb;
+    if (col) {  // NULL: the column entries are checked where they are first used
+        for (int64_t j = tid; j < nnz; j += stride) {
+            const int32_t x = col[j];
+            if (x < 0 || (int64_t)x >= n) ++nb;
+        }
     }
-    if (nb) atomicAdd(bad, nb);
-    atomicMax((unsigned long long*)degmax, (unsigned long long)dm);
+    for (int off = 16; off; off >>= 1) {
+        nb += __shfl_xor_sync(FULL, nb, off);
+        dm = max(dm, __shfl_xor_sync(FULL, dm, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (nb) atomicAdd(bad, nb);
+        if (dm) atomicMax((unsigned long long*)degmax, (unsigned long long)dm);
+    }
 }
 
 template <typename T>

@@ -169,19 +169,104 @@ __global__ void new_degree_kernel(const Off* __restrict__ rowptr, const int32_t*
     }
 }
 
-// one warp per new row: copy the original row, renaming its entries
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// Arcs of the original rows [v0, v1), renamed, into their new rows inv[v].
+// One warp per 32 consecutive rows: the lanes read the 32 rows' bounds and
+// targets at once, then the warp copies row after row.  Rows that become
+// CHUNK rows (inv[v] < row_warp) are left to remap_hub_chunks_kernel.  A
+// column entry outside [0, n) is counted in *bad and stored as 0 (the caller
+// rejects the graph).
 template <typename Off>
-__global__ void remap_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                  const int32_t* __restrict__ perm, const int32_t* __restrict__ inv,
-                                  const int64_t* __restrict__ rowptr_new, int64_t n, int32_t* col_new) {
+__global__ void remap_src_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                      const int32_t* __restrict__ inv, const int64_t* __restrict__ rowptr_new,
+                                      int64_t v0, int64_t v1, int64_t n, int64_t row_warp, int32_t* col_new,
+                                      unsigned long long* bad) {
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     const int lane = threadIdx.x & 31;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; u < n; u += warps) {
+    const int64_t groups = (v1 - v0 + 31) / 32;
+    unsigned long long nb = 0;
+    for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; gi < groups; gi += warps) {
+        const int64_t v = v0 + gi * 32 + lane;
+        int64_t a = 0, b = 0, o = 0;
+        if (v < v1) {
+            const int64_t u = inv[v];
+            if (u >= row_warp) {
+                a = rowptr[v];
+                b = rowptr[v + 1];
+                o = rowptr_new[u];
+            }
+        }
+        for (int q = 0; q < 32; ++q) {
+            const int64_t aq = __shfl_sync(FULL_MASK, a, q), bq = __shfl_sync(FULL_MASK, b, q);
+            const int64_t oq = __shfl_sync(FULL_MASK, o, q);
+            for (int64_t j = aq + lane; j < bq; j += 32) {
+                int32_t x = col[j];
+                if (x < 0 || (int64_t)x >= n) {
+                    ++nb;
+                    x = 0;
+                }
+                col_new[oq + (j - aq)] = inv[x];
+            }
+        }
+    }
+    for (int off = 16; off; off >>= 1) nb += __shfl_xor_sync(FULL_MASK, nb, off);
+    if (lane == 0 && nb) atomicAdd(bad, nb);
+}
+
+// CHUNK rows (new ids below row_warp): one warp per chunk of CHUNK_ARCS arcs
+// (the chunk count is chunk_first[row_warp])
+template <typename Off>
+__global__ void remap_hub_chunks_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                        const int32_t* __restrict__ perm, const int32_t* __restrict__ inv,
+                                        const int64_t* __restrict__ rowptr_new, const int32_t* __restrict__ chunk_row,
+                                        const int64_t* __restrict__ chunk_first, int64_t row_warp, int64_t n,
+                                        int32_t* col_new, unsigned long long* bad) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int lane = threadIdx.x & 31;
+    const int64_t chunks = chunk_first[row_warp];
+    unsigned long long nb = 0;
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < chunks; ch += warps) {
+        const int64_t u = chunk_row[ch];
         const int64_t v = perm[u];
         const int64_t a = rowptr[v], b = rowptr[v + 1];
-        const int64_t o = rowptr_new[u];
-        for (int64_t j = a + lane; j < b; j += 32) col_new[o + (j - a)] = inv[col[j]];
+        const int64_t j0 = a + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+        const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, b);
+        const int64_t o = rowptr_new[u] + (j0 - a);
+        for (int64_t j = j0 + lane; j < j1; j += 32) {
+            int32_t x = col[j];
+            if (x < 0 || (int64_t)x >= n) {
+                ++nb;
+                x = 0;
+            }
+            col_new[o + (j - j0)] = inv[x];
+        }
     }
+    for (int off = 16; off; off >>= 1) nb += __shfl_xor_sync(FULL_MASK, nb, off);
+    if (lane == 0 && nb) atomicAdd(bad, nb);
+}
+
+// chunks of each CHUNK row (u < row_warp) from its new degree; cnt[row_warp] = 0;
+// *max_chunks = the largest count
+__global__ void chunk_count_kernel(const int64_t* __restrict__ rowptr_new, int64_t row_warp, int64_t* cnt,
+                                   unsigned long long* max_chunks) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long mx = 0;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= row_warp; u += stride) {
+        const int64_t c = u < row_warp ? (rowptr_new[u + 1] - rowptr_new[u] + CHUNK_ARCS - 1) / CHUNK_ARCS : 0;
+        cnt[u] = c;
+        mx = max(mx, (unsigned long long)c);
+    }
+    for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(FULL_MASK, mx, off));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(max_chunks, mx);
+}
+
+// chunk_row[q] = u for the chunks q of row u (one warp per row)
+__global__ void chunk_fill_kernel(const int64_t* __restrict__ chunk_first, int64_t row_warp, int32_t* chunk_row) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; u < row_warp; u += warps)
+        for (int64_t q = chunk_first[u] + lane; q < chunk_first[u + 1]; q += 32) chunk_row[q] = (int32_t)u;
 }
 
 int grid_for(int64_t n, int threads, int max_blocks = 152 * 16) {
@@ -217,15 +302,40 @@ cudaError_t exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64
     return cudaGetLastError();
 }
 
-cudaError_t relabel_rows(const int64_t* rowptr64, const int32_t* col, const int32_t* perm, const int32_t* inv,
-                         int64_t n, int64_t* deg_new_scratch, int64_t* rowptr_new, int64_t* sums_scratch,
-                         int32_t* col_new, cudaStream_t st) {
+cudaError_t relabel_offsets(const int64_t* rowptr64, const int32_t* perm, int64_t n, int64_t* deg_new_scratch,
+                            int64_t* rowptr_new, int64_t* sums_scratch, cudaStream_t st) {
     new_degree_kernel<int64_t><<<grid_for(n, 256), 256, 0, st>>>(rowptr64, perm, n, deg_new_scratch);
-    // rowptr_new[0..n] = exclusive scan of the n degrees followed by the total
-    cudaError_t e = exclusive_scan_i64(deg_new_scratch, n + 1, rowptr_new, sums_scratch, st);
+    cudaError_t e = cudaMemsetAsync(deg_new_scratch + n, 0, sizeof(int64_t), st);
     if (e != cudaSuccess) return e;
-    remap_rows_kernel<int64_t><<<grid_for(n * 32, 256), 256, 0, st>>>(rowptr64, col, perm, inv, rowptr_new, n,
-                                                                      col_new);
+    return exclusive_scan_i64(deg_new_scratch, n + 1, rowptr_new, sums_scratch, st);
+}
+
+cudaError_t remap_src_rows(const int64_t* rowptr64, const int32_t* col, const int32_t* inv, const int64_t* rowptr_new,
+                           int64_t v0, int64_t v1, int64_t n, int64_t row_warp, int32_t* col_new,
+                           unsigned long long* bad, cudaStream_t st) {
+    if (v1 <= v0) return cudaSuccess;
+    remap_src_rows_kernel<int64_t><<<grid_for(v1 - v0, 256, 152 * 32), 256, 0, st>>>(
+        rowptr64, col, inv, rowptr_new, v0, v1, n, row_warp, col_new, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t remap_hub_chunks(const int64_t* rowptr64, const int32_t* col, const int32_t* perm, const int32_t* inv,
+                             const int64_t* rowptr_new, const int32_t* chunk_row, const int64_t* chunk_first,
+                             int64_t row_warp, int64_t chunks_cap, int64_t n, int32_t* col_new,
+                             unsigned long long* bad, cudaStream_t st) {
+    if (row_warp <= 0) return cudaSuccess;
+    remap_hub_chunks_kernel<int64_t><<<grid_for(chunks_cap * 32, 256, 152 * 32), 256, 0, st>>>(
+        rowptr64, col, perm, inv, rowptr_new, chunk_row, chunk_first, row_warp, n, col_new, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t build_chunk_table(const int64_t* rowptr_new, int64_t row_warp, int64_t* cnt_scratch, int64_t* sums_scratch,
+                              int64_t* chunk_first, int32_t* chunk_row, unsigned long long* max_chunks,
+                              cudaStream_t st) {
+    chunk_count_kernel<<<grid_for(row_warp + 1, 256), 256, 0, st>>>(rowptr_new, row_warp, cnt_scratch, max_chunks);
+    cudaError_t e = exclusive_scan_i64(cnt_scratch, row_warp + 1, chunk_first, sums_scratch, st);
+    if (e != cudaSuccess) return e;
+    if (row_warp > 0) chunk_fill_kernel<<<grid_for(row_warp * 32, 256), 256, 0, st>>>(chunk_first, row_warp, chunk_row);
     return cudaGetLastError();
 }
 

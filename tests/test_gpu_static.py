@@ -183,3 +183,30 @@ def test_rmat22_top1000_full_size():
     oracle.set_threads(0)
     check_parity(g, 0.0, 1000, 1e-9, walks=False, profile=1)
 
+
+
+def test_large_host_csr_is_copied_in_slices_and_matches_device_input():
+    # a host CSR of >= 2^22 arcs is copied slice by slice and renamed as it
+    # arrives: the handle must equal one created from device arrays
+    g = gg.rmat(18, 16, seed=61)
+    assert g.nnz >= 1 << 22
+    a = run_gpu(g, 0.0, 200, 1e-9, keep_history=False, on_device=False)
+    b = run_gpu(g, 0.0, 200, 1e-9, keep_history=False, on_device=True)
+    assert a["info"].r == b["info"].r
+    np.testing.assert_array_equal(a["ranking"], b["ranking"])
+    np.testing.assert_array_equal(a["l"], b["l"])
+    np.testing.assert_array_equal(a["u"], b["u"])
+
+
+def test_large_host_csr_with_a_bad_column_entry_in_a_late_slice_is_rejected():
+    g = gg.rmat(18, 16, seed=62)
+    col = g.col.copy()
+    col[-3] = g.n  # out of range, in the last slice
+    with pytest.raises(K.KatzError) as e:
+        K.Katz(g.rowptr, col)
+    assert e.value.name == "KATZ_EINVAL"
+    rp = g.rowptr.copy()
+    rp[g.n // 2] = rp[g.n // 2 + 1] + 5  # not monotone
+    with pytest.raises(K.KatzError) as e:
+        K.Katz(rp, g.col)
+    assert e.value.name == "KATZ_EINVAL"
