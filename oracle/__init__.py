@@ -32,6 +32,10 @@ OK, EINVAL, EALPHA, ENOTCONV, EOVERFLOW = 0, 1, 2, 3, 4
 _NAMES = {EINVAL: "EINVAL", EALPHA: "EALPHA", ENOTCONV: "ENOTCONV", EOVERFLOW: "EOVERFLOW"}
 
 
+# stopping criteria of Sec. 3.1
+TOPK, RANKING, SCORE, PAIR = 0, 1, 2, 3
+
+
 class OracleError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"oracle {what}: {_NAMES.get(code, code)}")
@@ -63,6 +67,7 @@ def _load():
                 "oracle_session_create": (P, [i64, P, P, ci, i64]),
                 "oracle_session_free": (None, [P]),
                 "oracle_session_rank": (ci, [P, dbl, i64, dbl, ci]),
+                "oracle_session_rank_criterion": (ci, [P, dbl, ci, i64, ctypes.c_int32, ctypes.c_int32, dbl, ci]),
                 "oracle_session_update": (ci, [P, i64, P, P, P]),
                 "oracle_session_info": (None, [P, P, P, P, P, P, P]),
                 "oracle_session_ranking": (i64, [P, P, i64]),
@@ -162,6 +167,12 @@ class Session:
     def rank_static(self, alpha: float, k: int, eps: float, r_max: int = 200) -> int:
         """Algorithm 1 with the top-k criterion; returns the status code."""
         return int(self._lib.oracle_session_rank(self._h, alpha, k, eps, r_max))
+
+    def rank(self, alpha: float, criterion: int, eps: float, k: int = 0, pair=(0, 1), r_max: int = 200) -> int:
+        """Algorithm 1 with a stopping criterion of Sec. 3.1 (TOPK, RANKING,
+        SCORE or PAIR); returns the status code."""
+        return int(self._lib.oracle_session_rank_criterion(self._h, alpha, int(criterion), int(k), int(pair[0]),
+                                                           int(pair[1]), eps, r_max))
 
     def apply_update(self, src, dst, ins) -> int:
         """Algorithm 2 semantics for an undirected batch {src[i], dst[i]}."""

@@ -30,6 +30,10 @@ namespace {
 
 enum { OK = 0, EINVAL_ = 1, EALPHA_ = 2, ENOTCONV_ = 3, EOVERFLOW_ = 4 };
 
+// Stopping criteria of Sec. 3.1.  The ranking criterion is the top-k
+// criterion with k = n (the paper says so), so it reuses converged().
+enum { CRIT_TOPK = 0, CRIT_RANKING = 1, CRIT_SCORE = 2, CRIT_PAIR = 3 };
+
 typedef unsigned __int128 u128;
 
 // Theorem 1: gamma = deg_max / (1 - alpha deg_max), valid for alpha < 1/deg_max.
@@ -84,6 +88,22 @@ bool converged(std::vector<int32_t>& M, int64_t k, const std::vector<double>& l,
     return true;
 }
 
+// Score criterion (Sec. 3.1): the upper and lower bound of every node differ
+// by less than eps.
+bool score_done(const std::vector<double>& l, const std::vector<double>& u, double eps) {
+    for (size_t v = 0; v < l.size(); ++v)
+        if (!(u[v] - l[v] < eps)) return false;
+    return true;
+}
+
+// Pair criterion (Sec. 3.1): nodes a and b are eps-separated (Eq. 3); w is the
+// one with the larger lower bound (ties: smaller id), v the other.
+bool pair_done(int32_t a, int32_t b, const std::vector<double>& l, const std::vector<double>& u, double eps) {
+    const bool a_first = l[a] > l[b] || (l[a] == l[b] && a < b);
+    const int32_t w = a_first ? a : b, v = a_first ? b : a;
+    return l[w] > u[v] - eps;
+}
+
 // Eq. (5): omega_i(v) = sum over arcs v->x of omega_{i-1}(x), in CSR order.
 void walk_step(int64_t n, const int64_t* rowptr, const int32_t* col, const std::vector<double>& prev,
                std::vector<double>& next) {
@@ -119,6 +139,15 @@ struct Session {
     std::vector<double> apow;                // apow[i] = alpha^i
     Bounds b;
     std::vector<int32_t> M;
+    int crit = CRIT_TOPK;
+    int32_t pa = 0, pb = 0;  // the pair of the pair criterion
+
+    // the stopping criterion of this ranking, after iteration r
+    bool check() {
+        if (crit == CRIT_SCORE) return score_done(b.l, b.u, eps);
+        if (crit == CRIT_PAIR) return pair_done(pa, pb, b.l, b.u, eps);
+        return converged(M, k, b.l, b.u, eps);
+    }
 
     void csr(std::vector<int64_t>& rp, std::vector<int32_t>& cl) const {
         rp.assign((size_t)n + 1, 0);
@@ -146,7 +175,19 @@ struct Session {
     // Algorithm 1.  The bounds are defined for r >= 1 (Theorem 1), so the
     // first convergence check follows the first iteration.
     int rank_static(double alpha_, int64_t k_, double eps_, int r_max_) {
+        return rank_criterion(alpha_, CRIT_TOPK, k_, 0, 0, eps_, r_max_);
+    }
+
+    // Algorithm 1 with any criterion of Sec. 3.1.
+    int rank_criterion(double alpha_, int crit_, int64_t k_, int32_t a, int32_t b2, double eps_, int r_max_) {
+        if (crit_ < CRIT_TOPK || crit_ > CRIT_PAIR) return EINVAL_;
+        if (crit_ == CRIT_RANKING) k_ = n;
+        if (crit_ == CRIT_PAIR && (a < 0 || b2 < 0 || a >= n || b2 >= n || a == b2)) return EINVAL_;
+        if (crit_ == CRIT_SCORE || crit_ == CRIT_PAIR) k_ = 1;
         if (!(eps_ > 0.0) || k_ < 1 || r_max_ < 1) return EINVAL_;
+        crit = crit_;
+        pa = a;
+        pb = b2;
         const int64_t dmax = [&] {
             int64_t d = 0;
             for (auto& a : adj) d = std::max<int64_t>(d, (int64_t)a.size());
@@ -173,7 +214,7 @@ struct Session {
             if (r >= r_max) return ENOTCONV_;
             int st = iterate(rp, cl);
             if (st) return st;
-        } while (!(conv = converged(M, k, b.l, b.u, eps)));
+        } while (!(conv = check()));
         return OK;
     }
 
@@ -269,7 +310,7 @@ struct Session {
         for (int64_t w = 0; w < n; ++w)
             if (!in[w] && b.u[w] >= lmin - eps) M.push_back((int32_t)w);  // reactivation
         conv = false;
-        while (!(conv = converged(M, k, b.l, b.u, eps))) {
+        while (!(conv = check())) {
             if (r >= r_max) return ENOTCONV_;
             st = iterate(rp, cl);
             if (st) return st;
@@ -410,6 +451,11 @@ int oracle_session_rank(void* p, double alpha, int64_t k, double eps, int r_max)
     return ((Session*)p)->rank_static(alpha, k, eps, r_max);
 }
 
+int oracle_session_rank_criterion(void* p, double alpha, int crit, int64_t k, int32_t a, int32_t b, double eps,
+                                   int r_max) {
+    return ((Session*)p)->rank_criterion(alpha, crit, k, a, b, eps, r_max);
+}
+
 int oracle_session_update(void* p, int64_t m, const int32_t* src, const int32_t* dst,
                           const uint8_t* ins) {
     return ((Session*)p)->apply_update(m, src, dst, ins);
@@ -430,6 +476,14 @@ void oracle_session_info(void* p, int* r, int64_t* active, int* conv, double* al
 // The first min(k, |M|) entries of M (the ranking once converged).
 int64_t oracle_session_ranking(void* p, int32_t* ids, int64_t cap) {
     Session* s = (Session*)p;
+    if (s->crit == CRIT_SCORE) return 0;  // certifies scores, not an order
+    if (s->crit == CRIT_PAIR) {            // the pair in its certified order
+        if (cap < 2) return 0;
+        const bool a_first = s->b.l[s->pa] > s->b.l[s->pb] || (s->b.l[s->pa] == s->b.l[s->pb] && s->pa < s->pb);
+        ids[0] = a_first ? s->pa : s->pb;
+        ids[1] = a_first ? s->pb : s->pa;
+        return 2;
+    }
     int64_t kk = std::min<int64_t>({s->k, (int64_t)s->M.size(), cap});
     for (int64_t i = 0; i < kk; ++i) ids[i] = s->M[i];
     return kk;

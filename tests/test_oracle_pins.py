@@ -332,3 +332,92 @@ def test_dynamic_batch_validation_is_atomic():
     after = s.bounds()
     assert all(np.array_equal(a, b) for a, b in zip(before, after))
     assert s.apply_update([0], [4], [1]) == oracle.OK
+
+
+# ---------------------------------------------------------------------------
+# The other stopping criteria of Sec. 3.1, each against a brute-force check
+# of its definition at every iteration
+# ---------------------------------------------------------------------------
+def _bounds_fixed(rowptr, col, R):
+    s = oracle.Session(rowptr, col)
+    assert s.run_fixed(0.0, R) == oracle.OK
+    c, l, u = s.bounds()
+    return l, u
+
+
+def _all_pairs_separated(l, u, eps):
+    """Ranking criterion: every pair eps-separated (Eq. 3), w the node the
+    order (l desc, id asc) puts first."""
+    order = sorted(range(len(l)), key=lambda v: (-l[v], v))
+    for i, j in itertools.combinations(range(len(order)), 2):
+        if not (l[order[i]] > u[order[j]] - eps):
+            return False, order
+    return True, order
+
+
+def _first_r(rowptr, col, test, r_max=60):
+    for R in range(1, r_max + 1):
+        l, u = _bounds_fixed(rowptr, col, R)
+        if test(l, u):
+            return R
+    return None
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_ranking_criterion_is_all_pairs_separated_first_time(seed):
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(10, 40))
+    rowptr, col = _random_graph(n, float(rng.uniform(0.08, 0.3)), rng)
+    eps = 1e-6
+    s = oracle.Session(rowptr, col)
+    assert s.rank(0.0, oracle.RANKING, eps) == oracle.OK
+    r = s.info()["r"]
+    assert r == _first_r(rowptr, col, lambda l, u: _all_pairs_separated(l, u, eps)[0])
+    c, l, u = s.bounds()
+    assert list(s.ranking()) == _all_pairs_separated(l, u, eps)[1]
+    # the ranking is the exact Katz order wherever two nodes differ by more than eps
+    D = int(np.diff(rowptr).max())
+    cx = _exact_katz(rowptr, col, Fraction(1, D + 1))
+    R = [int(v) for v in s.ranking()]
+    for i, j in itertools.combinations(range(n), 2):
+        assert cx[R[i]] >= cx[R[j]] - Fraction(eps)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_score_criterion_bounds_within_eps_first_time(seed):
+    rng = np.random.default_rng(800 + seed)
+    n = int(rng.integers(10, 60))
+    rowptr, col = _random_graph(n, float(rng.uniform(0.05, 0.3)), rng)
+    eps = 1e-7
+    s = oracle.Session(rowptr, col)
+    assert s.rank(0.0, oracle.SCORE, eps) == oracle.OK
+    r = s.info()["r"]
+    assert r == _first_r(rowptr, col, lambda l, u: bool(np.all(u - l < eps)))
+    assert len(s.ranking()) == 0
+    # every score is then known to within eps
+    D = int(np.diff(rowptr).max())
+    cx = _exact_katz(rowptr, col, Fraction(1, D + 1))
+    c, l, u = s.bounds()
+    for v in range(n):
+        assert abs(Fraction(float(l[v])) - cx[v]) < Fraction(eps)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pair_criterion_first_time(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(10, 60))
+    rowptr, col = _random_graph(n, float(rng.uniform(0.05, 0.3)), rng)
+    a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+    eps = 1e-8
+
+    def separated(l, u):
+        w, v = (a, b) if (l[a], -a) > (l[b], -b) else (b, a)
+        return l[w] > u[v] - eps
+
+    s = oracle.Session(rowptr, col)
+    assert s.rank(0.0, oracle.PAIR, eps, pair=(a, b)) == oracle.OK
+    r = s.info()["r"]
+    assert r == _first_r(rowptr, col, separated)
+    c, l, u = s.bounds()
+    w, v = (a, b) if (l[a], -a) > (l[b], -b) else (b, a)
+    assert list(s.ranking()) == [w, v]
