@@ -142,6 +142,35 @@ const char* katz_last_error(katz_h h);
 #define KATZ_MAX_K 8192
 katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz_info* info);
 
+/* Stopping criteria (Sec. 3.1). */
+enum {
+    KATZ_CRIT_TOPK = 0,     /* the top-k nodes eps-separated from each other and from all others */
+    KATZ_CRIT_RANKING = 1,  /* every pair of nodes eps-separated: the top-k criterion with k = n */
+    KATZ_CRIT_SCORE = 2,    /* u_r(v) - l_r(v) < eps for every node */
+    KATZ_CRIT_PAIR = 3      /* two given nodes eps-separated */
+};
+
+/*
+ * Algorithm 1 (Sec. 3.2) with any stopping criterion of Sec. 3.1.
+ * KATZ_CRIT_TOPK: the same as katz_rank_static(h, alpha, k, eps, info).
+ * The others run on FP64 handles and keep every node active:
+ *   KATZ_CRIT_RANKING: each iteration sorts all n nodes by (l desc, id asc)
+ *     and checks every adjacent pair (Eq. 3); afterwards katz_get_ranking
+ *     returns the full certified order (k up to n);
+ *   KATZ_CRIT_SCORE: stops once u_r - l_r < eps at every node; the bounds
+ *     (katz_get_bounds) then give every score to within eps, and there is
+ *     no ranking (katz_get_ranking returns KATZ_ESTATE);
+ *   KATZ_CRIT_PAIR: pair = host array of two distinct node ids; stops once
+ *     they are eps-separated; katz_get_ranking(h, ids, 2) returns them in
+ *     their certified order.
+ * k is read by KATZ_CRIT_TOPK only, pair by KATZ_CRIT_PAIR only.
+ * katz_apply_update_batch continues the top-k criterion only.
+ * Errors: KATZ_EINVAL, KATZ_EALPHA, KATZ_ENOTCONV, KATZ_ESTATE (another
+ * criterion on an FP32-certified handle), KATZ_ENOMEM, KATZ_ECUDA.
+ */
+katz_status katz_rank(katz_h h, double alpha, int32_t criterion, int64_t k, const int32_t* pair, double eps,
+                      katz_info* info);
+
 /*
  * The certified top-k after the last rank/update call: ids[0..k) in
  * decreasing order of lower bound (ties by smaller id).  k must equal the

@@ -17,13 +17,15 @@ from . import build as _build
 
 __all__ = [
     "KatzError", "katz_opts", "katz_info", "katz_default_opts", "katz_create_csr", "katz_destroy",
-    "katz_rank_static", "katz_get_ranking", "katz_get_bounds", "katz_get_walk", "katz_get_trace",
+    "katz_rank_static", "katz_rank", "KATZ_CRIT_TOPK", "KATZ_CRIT_RANKING", "KATZ_CRIT_SCORE", "KATZ_CRIT_PAIR",
+    "katz_get_ranking", "katz_get_bounds", "katz_get_walk", "katz_get_trace",
     "katz_apply_update_batch", "katz_certify_topk_noalloc", "katz_server_opts", "katz_request_result",
     "katz_server_default_opts", "Server", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT",
     "KATZ_MAX_K", "library_path",
 ]
 
 KATZ_FP64, KATZ_FP32_CERT = 0, 1
+KATZ_CRIT_TOPK, KATZ_CRIT_RANKING, KATZ_CRIT_SCORE, KATZ_CRIT_PAIR = 0, 1, 2, 3
 KATZ_MAX_K = 8192
 STATUS = ["KATZ_OK", "KATZ_EINVAL", "KATZ_EALPHA", "KATZ_ENOMEM", "KATZ_ECUDA", "KATZ_ENOTCONV",
           "KATZ_EPRECISION", "KATZ_ETIMEOUT", "KATZ_EBUSY", "KATZ_ESTATE"]
@@ -88,6 +90,7 @@ def _load():
         "katz_destroy": (None, [P]),
         "katz_last_error": (ctypes.c_char_p, [P]),
         "katz_rank_static": (ctypes.c_int, [P, dbl, i64, dbl, ctypes.POINTER(katz_info)]),
+        "katz_rank": (ctypes.c_int, [P, dbl, i32, i64, P, dbl, ctypes.POINTER(katz_info)]),
         "katz_get_ranking": (ctypes.c_int, [P, P, i64]),
         "katz_get_bounds": (ctypes.c_int, [P, P, P, P]),
         "katz_get_walk": (ctypes.c_int, [P, i32, P]),
@@ -169,6 +172,17 @@ def katz_rank_static(h, alpha: float, k: int, eps: float, check: bool = True) ->
     st = _load().katz_rank_static(h, float(alpha), int(k), float(eps), ctypes.byref(info))
     if check:
         _check(h, st, "katz_rank_static")
+    info.status = st
+    return info
+
+
+def katz_rank(h, alpha: float, criterion: int, eps: float, k: int = 0, pair=None, check: bool = True) -> katz_info:
+    """Algorithm 1 with a stopping criterion of Sec. 3.1 (KATZ_CRIT_*)."""
+    info = katz_info()
+    pa = np.ascontiguousarray(pair, np.int32) if pair is not None else None
+    st = _load().katz_rank(h, float(alpha), int(criterion), int(k), _ptr(pa), float(eps), ctypes.byref(info))
+    if check:
+        _check(h, st, "katz_rank")
     info.status = st
     return info
 
@@ -307,6 +321,9 @@ class Katz:
 
     def rank(self, alpha=0.0, k=100, eps=1e-9, check=True) -> katz_info:
         return katz_rank_static(self.h, alpha, k, eps, check)
+
+    def rank_by(self, criterion, alpha=0.0, eps=1e-9, k=0, pair=None, check=True) -> katz_info:
+        return katz_rank(self.h, alpha, criterion, eps, k, pair, check)
 
     def ranking(self, k):
         return katz_get_ranking(self.h, k)

@@ -332,6 +332,37 @@ namespace katz {
 // Device buffers of the dynamic path for batches of up to m updates and a
 // rebuilt adjacency of up to nnz_cap arcs (0: no spare adjacency yet).  A
 // batch within these sizes allocates and frees nothing.
+// alpha (Sec. 3.1: 1 / (D + 1) when not given), gamma of Theorem 1 and the
+// iteration parameters of a ranking; the iteration buffers
+katz_status setup_ranking(katz_handle* h, double alpha, int64_t k_eff, double eps, double& a, double& gamma) {
+    const double D = (double)h->D;
+    a = alpha > 0.0 ? alpha : 1.0 / (D + 1.0);
+    if (!(a * D < 1.0)) return fail(h, KATZ_EALPHA, "alpha * deg_bound >= 1");
+    katz_status st = ensure_iter_buffers(h);
+    if (st != KATZ_OK) return st;
+    gamma = D / (1.0 - a * D);
+    IterParams& p = h->p;
+    p.alpha = a;
+    p.ag = a * gamma;
+    p.eps = eps;
+    p.n = h->g.n;
+    p.k = k_eff;
+    p.stride = h->stride;
+    p.slots = h->walk_slots;
+    p.undirected = h->opts.undirected ? 1 : 0;
+    p.r_max = h->opts.r_max;
+    p.cert = h->fp32 ? 1 : 0;
+    {  // an upper bound of alpha * gamma: four ulps above the rounded product
+        double ag_hi = p.ag;
+        for (int q = 0; q < 4; ++q) ag_hi = std::nextafter(ag_hi, INFINITY);
+        p.ag_hi = ag_hi;
+    }
+    p.alpha_f = (float)a;
+    p.depth = h->sum_depth;
+    p.fp32_from = h->fp32 ? std::max(0, h->opts.fp32_from) : 0;
+    return KATZ_OK;
+}
+
 katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
     cudaError_t e;
     DeviceGraph& g = h->g;
@@ -446,6 +477,15 @@ void katz_destroy(katz_h h) {
     dfree(h, h->d_hist256);
     dfree(h, h->d_count);
     dfree(h, h->d_scratch);
+    dfree(h, h->rank_ids);
+    for (int q = 0; q < 2; ++q) {
+        dfree(h, h->rs.hi[q]);
+        dfree(h, h->rs.lo[q]);
+        dfree(h, h->rs.val[q]);
+    }
+    dfree(h, h->rs.counts);
+    dfree(h, h->rs.offs);
+    dfree(h, h->rs.sums);
     {
         DynBuffers& d = h->dyn;
         for (void* ptr : {(void*)d.src, (void*)d.dst, (void*)d.ins, (void*)d.hub_epoch, (void*)d.table,
@@ -689,31 +729,11 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
         return fail(h, KATZ_EINVAL, "need eps > 0, k >= 1, finite alpha");
     const int64_t k_eff = std::min<int64_t>(k, h->g.n);
     if (k_eff > KATZ_MAX_K) return fail(h, KATZ_EINVAL, "k exceeds KATZ_MAX_K");
-    const double D = (double)h->D;
-    const double a = alpha > 0.0 ? alpha : 1.0 / (D + 1.0);
-    if (!(a * D < 1.0)) return fail(h, KATZ_EALPHA, "alpha * deg_bound >= 1");
-    katz_status st = ensure_iter_buffers(h);
+    double a = 0.0, gamma = 0.0;
+    katz_status st = setup_ranking(h, alpha, k_eff, eps, a, gamma);
     if (st != KATZ_OK) return st;
-    const double gamma = D / (1.0 - a * D);
     IterParams& p = h->p;
-    p.alpha = a;
-    p.ag = a * gamma;
-    p.eps = eps;
-    p.n = h->g.n;
-    p.k = k_eff;
-    p.stride = h->stride;
-    p.slots = h->walk_slots;
-    p.undirected = h->opts.undirected ? 1 : 0;
-    p.r_max = h->opts.r_max;
-    p.cert = h->fp32 ? 1 : 0;
-    {  // an upper bound of alpha * gamma: four ulps above the rounded product
-        double ag_hi = p.ag;
-        for (int q = 0; q < 4; ++q) ag_hi = std::nextafter(ag_hi, INFINITY);
-        p.ag_hi = ag_hi;
-    }
-    p.alpha_f = (float)a;
-    p.depth = h->sum_depth;
-    p.fp32_from = h->fp32 ? std::max(0, h->opts.fp32_from) : 0;
+    h->criterion = KATZ_CRIT_TOPK;
     h->b.use_cond = 0;
     h->ranked = false;
     h->launches = 3;  // init_walk, deg_hist, kth_degree
@@ -779,12 +799,113 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
     return KATZ_OK;
 }
 
+katz_status katz_rank(katz_h h, double alpha, int32_t criterion, int64_t k, const int32_t* pair, double eps,
+                      katz_info* info) {
+    if (!h) return KATZ_EINVAL;
+    if (criterion == KATZ_CRIT_TOPK) return katz_rank_static(h, alpha, k, eps, info);
+    h->err.clear();
+    if (criterion != KATZ_CRIT_RANKING && criterion != KATZ_CRIT_SCORE && criterion != KATZ_CRIT_PAIR)
+        return fail(h, KATZ_EINVAL, "unknown criterion");
+    if (h->fp32) return fail(h, KATZ_ESTATE, "the ranking, score and pair criteria run on FP64 handles");
+    if (!(eps > 0.0) || !std::isfinite(eps) || !std::isfinite(alpha))
+        return fail(h, KATZ_EINVAL, "need eps > 0 and a finite alpha");
+    const int64_t n = h->g.n;
+    int32_t oa = 0, ob = 0;
+    if (criterion == KATZ_CRIT_PAIR) {
+        if (!pair) return fail(h, KATZ_EINVAL, "the pair criterion needs two node ids");
+        oa = pair[0];
+        ob = pair[1];
+        if (oa < 0 || ob < 0 || oa >= n || ob >= n || oa == ob)
+            return fail(h, KATZ_EINVAL, "the pair must be two distinct nodes");
+    }
+    const int64_t k_eff = criterion == KATZ_CRIT_RANKING ? n : (criterion == KATZ_CRIT_PAIR ? 2 : 0);
+    double a = 0.0, gamma = 0.0;
+    katz_status st = setup_ranking(h, alpha, std::max<int64_t>(k_eff, 1), eps, a, gamma);
+    if (st != KATZ_OK) return st;
+    IterParams& p = h->p;
+    cudaError_t e;
+    if (criterion == KATZ_CRIT_RANKING && !h->rank_ids) {
+        RadixBuffers& rs = h->rs;
+        const int64_t cnt = 256 * radix_tiles(n);
+        if ((e = dmalloc(h, &h->rank_ids, (size_t)n)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.hi[0], (size_t)n)) != cudaSuccess || (e = dmalloc(h, &rs.hi[1], (size_t)n)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.lo[0], (size_t)n)) != cudaSuccess || (e = dmalloc(h, &rs.lo[1], (size_t)n)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.val[0], (size_t)n)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.val[1], (size_t)n)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.counts, (size_t)cnt)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.offs, (size_t)cnt)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.sums, (size_t)scan_blocks(cnt))) != cudaSuccess)
+            return cuda_fail(h, e, "cudaMalloc ranking buffers");
+    }
+    h->criterion = criterion;
+    h->ranked = false;
+    h->launches = 0;
+    const int64_t spmv_kernels = h->g.layout.row_warp > 0 ? 2 : 1;
+    const int64_t check_kernels = criterion == KATZ_CRIT_RANKING ? 2 + 12 * 5 : 1;  // keys, 12 x (hist, scan 3, scatter), check
+    if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+    if ((e = cudaMemsetAsync(h->b.ctrl, 0, sizeof(Ctrl), h->stream)) != cudaSuccess ||
+        (e = launch_init_walk(h->g, h->b, p, false, h->stream)) != cudaSuccess ||
+        (e = launch_cert_init(h->b, p, h->stream)) != cudaSuccess ||
+        (e = launch_crit_init(h->b, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "init");
+    h->launches += 3;
+    for (int it = 0; it < p.r_max; ++it) {
+        if ((e = launch_spmv(h->g, h->b, p, false, h->stream)) != cudaSuccess) return cuda_fail(h, e, "spmv");
+        if (criterion == KATZ_CRIT_RANKING)
+            e = launch_ranking_check(h->g, h->b, p, h->rs, h->rank_ids, h->stream);
+        else if (criterion == KATZ_CRIT_SCORE)
+            e = launch_score_check(h->b, p, h->stream);
+        else
+            e = launch_pair_check(h->g, h->b, p, oa, ob, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "criterion");
+        if ((e = launch_finalize_crit(h->b, p, h->stream)) != cudaSuccess) return cuda_fail(h, e, "finalize");
+        h->launches += spmv_kernels + check_kernels + 1;
+        if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "sync");
+        if (h->h_ctrl->stop) break;
+    }
+    if ((e = cudaEventRecord(h->ev1, h->stream)) != cudaSuccess ||
+        (e = cudaEventSynchronize(h->ev1)) != cudaSuccess)
+        return cuda_fail(h, e, "event");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    const Ctrl& hc = *h->h_ctrl;
+    h->r = hc.r;
+    h->converged = hc.converged;
+    h->k_eff = k_eff;
+    h->alpha = a;
+    h->gamma = gamma;
+    h->eps = eps;
+    h->ranked = true;
+    h->last_ms = ms;
+    h->f32_from = 0x7fffffff;
+    h->trace.assign((size_t)std::max(0, h->r), n);
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->r = h->r;
+        info->converged = h->converged;
+        info->active = n;
+        info->k = k_eff;
+        info->alpha = a;
+        info->gamma = gamma;
+        info->time_ms = ms;
+        info->nnz = h->g.nnz;
+        info->launches = h->launches;
+        info->spmv_launches = h->r;
+    }
+    if (!h->converged) return fail(h, KATZ_ENOTCONV, "r_max reached before the criterion held");
+    return KATZ_OK;
+}
+
 katz_status katz_get_ranking(katz_h h, int32_t* ids, int64_t k) {
     if (!h || !ids) return KATZ_EINVAL;
     if (!h->ranked) return fail(h, KATZ_ESTATE, "no ranking yet");
+    if (h->criterion == KATZ_CRIT_SCORE) return fail(h, KATZ_ESTATE, "the score criterion certifies scores, not an order");
     if (k < 0 || k > h->k_eff) return fail(h, KATZ_EINVAL, "k larger than the ranked k");
     if (k == 0) return KATZ_OK;
-    cudaError_t e = cudaMemcpyAsync(ids, h->b.topk_id, (size_t)k * sizeof(int32_t), cudaMemcpyDefault, h->stream);
+    const int32_t* src = h->criterion == KATZ_CRIT_RANKING ? h->rank_ids : h->b.topk_id;
+    cudaError_t e = cudaMemcpyAsync(ids, src, (size_t)k * sizeof(int32_t), cudaMemcpyDefault, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return e == cudaSuccess ? KATZ_OK : cuda_fail(h, e, "copy ranking");
 }
@@ -856,6 +977,7 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
     if (!h) return KATZ_EINVAL;
     h->err.clear();
     if (!h->ranked) return fail(h, KATZ_ESTATE, "rank the graph before updating it");
+    if (h->criterion != KATZ_CRIT_TOPK) return fail(h, KATZ_ESTATE, "dynamic updates continue the top-k criterion");
     if (!h->opts.keep_history) return fail(h, KATZ_ESTATE, "dynamic updates need keep_history = 1");
     if (h->fp32) return fail(h, KATZ_ESTATE, "dynamic updates run in FP64 mode");
     if (!h->opts.undirected) return fail(h, KATZ_ESTATE, "dynamic updates take undirected handles");

@@ -188,6 +188,24 @@ struct DynBuffers {
     int32_t* hub_epoch = nullptr;    // [row_warp] level at which a CHUNK row joined the frontier
 };
 
+// ---- stopping criteria other than top-k (katz_criteria.cu) -------------------
+struct RadixBuffers {
+    uint64_t* hi[2] = {nullptr, nullptr};
+    uint32_t* lo[2] = {nullptr, nullptr};
+    int32_t* val[2] = {nullptr, nullptr};
+    int64_t* counts = nullptr;  // [256 * radix_tiles(n)]
+    int64_t* offs = nullptr;
+    int64_t* sums = nullptr;    // scan scratch
+};
+int64_t radix_tiles(int64_t n);
+cudaError_t launch_crit_init(const IterBuffers& b, cudaStream_t st);
+cudaError_t launch_score_check(const IterBuffers& b, const IterParams& p, cudaStream_t st);
+cudaError_t launch_pair_check(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int32_t oa, int32_t ob,
+                              cudaStream_t st);
+cudaError_t launch_ranking_check(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, RadixBuffers& rs,
+                                 int32_t* rank_ids, cudaStream_t st);
+cudaError_t launch_finalize_crit(const IterBuffers& b, const IterParams& p, cudaStream_t st);
+
 cudaError_t dyn_validate(const DeviceGraph& g, const DynBuffers& d, int64_t m, int64_t D, cudaStream_t st);
 cudaError_t dyn_clear(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st);
 cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, int64_t* rowptr_new, int64_t* deg,

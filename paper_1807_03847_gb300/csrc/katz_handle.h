@@ -53,6 +53,10 @@ struct katz_handle {
     int64_t* rp_new = nullptr;        // [n+1]
     int64_t* deg_tmp = nullptr;       // [n+1]
     int64_t* scan_sums = nullptr;
+    // stopping criteria other than top-k
+    int criterion = KATZ_CRIT_TOPK;
+    int32_t* rank_ids = nullptr;      // [n] ranking criterion: the order, original ids
+    katz::RadixBuffers rs;
     // result of the last rank/update call
     bool ranked = false;
     int r = 0;
