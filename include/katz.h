@@ -213,6 +213,23 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
                                     const uint8_t* is_insert, int64_t m, katz_info* info);
 
 /*
+ * Checkpoint and restore of a ranked handle (the state Sec. 4 keeps between
+ * batches: the walk history s_1..s_r, c_r, the active set M and r, with the
+ * graph and the last ranking).  katz_checkpoint_size gives the bytes of the
+ * image, katz_checkpoint writes it into a host buffer of that size, and
+ * katz_restore creates a handle on the current device from such a buffer
+ * (opts: only cuda_stream is read; NULL: a stream of its own).  The restored
+ * handle continues where the original stood: the same ranking, bounds and
+ * walks, and later calls give the same results.  The image is this library
+ * version's internal layout (checked on restore), not an exchange format.
+ * Errors: KATZ_EINVAL (NULL pointer, buffer too small, not an image of this
+ * version), KATZ_ESTATE (handle not ranked), KATZ_ENOMEM, KATZ_ECUDA.
+ */
+katz_status katz_checkpoint_size(katz_h h, uint64_t* bytes);
+katz_status katz_checkpoint(katz_h h, void* buf, uint64_t bytes);
+katz_status katz_restore(katz_h* out, const void* buf, uint64_t bytes, const katz_opts* opts);
+
+/*
  * Serving loop for dynamic graphs (Sec. 4 applied to a stream of batches).
  *
  * A server takes update batches for one or more attached handles as they

@@ -17,7 +17,7 @@ from . import build as _build
 
 __all__ = [
     "KatzError", "katz_opts", "katz_info", "katz_default_opts", "katz_create_csr", "katz_destroy",
-    "katz_rank_static", "katz_rank", "KATZ_CRIT_TOPK", "KATZ_CRIT_RANKING", "KATZ_CRIT_SCORE", "KATZ_CRIT_PAIR",
+    "katz_rank_static", "katz_rank", "katz_checkpoint", "katz_restore", "KATZ_CRIT_TOPK", "KATZ_CRIT_RANKING", "KATZ_CRIT_SCORE", "KATZ_CRIT_PAIR",
     "katz_get_ranking", "katz_get_bounds", "katz_get_walk", "katz_get_trace",
     "katz_apply_update_batch", "katz_certify_topk_noalloc", "katz_server_opts", "katz_request_result",
     "katz_server_default_opts", "Server", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT",
@@ -91,6 +91,9 @@ def _load():
         "katz_last_error": (ctypes.c_char_p, [P]),
         "katz_rank_static": (ctypes.c_int, [P, dbl, i64, dbl, ctypes.POINTER(katz_info)]),
         "katz_rank": (ctypes.c_int, [P, dbl, i32, i64, P, dbl, ctypes.POINTER(katz_info)]),
+        "katz_checkpoint_size": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint64)]),
+        "katz_checkpoint": (ctypes.c_int, [P, P, ctypes.c_uint64]),
+        "katz_restore": (ctypes.c_int, [ctypes.POINTER(P), P, ctypes.c_uint64, ctypes.POINTER(katz_opts)]),
         "katz_get_ranking": (ctypes.c_int, [P, P, i64]),
         "katz_get_bounds": (ctypes.c_int, [P, P, P, P]),
         "katz_get_walk": (ctypes.c_int, [P, i32, P]),
@@ -185,6 +188,26 @@ def katz_rank(h, alpha: float, criterion: int, eps: float, k: int = 0, pair=None
         _check(h, st, "katz_rank")
     info.status = st
     return info
+
+
+def katz_checkpoint(h) -> np.ndarray:
+    """The handle's state as a byte array (see katz_restore)."""
+    lib = _load()
+    size = ctypes.c_uint64()
+    _check(h, lib.katz_checkpoint_size(h, ctypes.byref(size)), "katz_checkpoint_size")
+    buf = np.empty(size.value, np.uint8)
+    _check(h, lib.katz_checkpoint(h, _ptr(buf), size.value), "katz_checkpoint")
+    return buf
+
+
+def katz_restore(image, opts: katz_opts | None = None) -> int:
+    """A new handle from a checkpoint image (byte array)."""
+    image = np.ascontiguousarray(image, np.uint8)
+    h = ctypes.c_void_p()
+    st = _load().katz_restore(ctypes.byref(h), _ptr(image), image.nbytes, ctypes.byref(opts) if opts else None)
+    if st != 0:
+        raise KatzError(st, "katz_restore")
+    return h.value
 
 
 def katz_get_ranking(h, k: int, out=None):
@@ -300,6 +323,19 @@ class Server:
 
 class Katz:
     """Owning wrapper around a handle (destroyed with the object)."""
+
+    @classmethod
+    def restore(cls, image, opts: katz_opts | None = None) -> "Katz":
+        """A handle from a checkpoint image (katz_restore)."""
+        obj = cls.__new__(cls)
+        obj.h = katz_restore(image, opts)
+        # n follows the image header's magic, version, layout word and options
+        off = 16 + ctypes.sizeof(katz_opts)
+        obj.n = int(np.frombuffer(np.ascontiguousarray(image[off:off + 8], np.uint8).tobytes(), np.int64)[0])
+        return obj
+
+    def checkpoint(self) -> np.ndarray:
+        return katz_checkpoint(self.h)
 
     def __init__(self, rowptr, col, opts: katz_opts | None = None):
         rowptr_np = rowptr

@@ -28,9 +28,6 @@ const char* kStatusNames[] = {"KATZ_OK",     "KATZ_EINVAL",     "KATZ_EALPHA",  
 
 namespace katz {
 
-constexpr size_t CTRL_BYTES = (sizeof(Ctrl) + 255) / 256 * 256;
-constexpr size_t H_SMALL = 4096;
-
 katz_status fail(katz_handle* h, katz_status s, const std::string& msg) {
     if (h) h->err = msg;
     return s;
@@ -76,18 +73,39 @@ cudaMemPool_t library_pool(int dev) {
     return pools[dev];
 }
 
-// count elements of X, ordered on the handle's stream
-template <typename X>
-cudaError_t dmalloc(katz_handle* h, X** p, size_t count) {
-    *p = nullptr;
-    if (count == 0) count = 1;
-    cudaMemPool_t pool = library_pool(h->dev);
-    if (!pool) return cudaErrorMemoryAllocation;
-    return cudaMallocFromPoolAsync((void**)p, count * sizeof(X), pool, h->stream);
+// The device, stream, events and pinned host block of a new handle.
+katz_status init_handle_runtime(katz_handle* h) {
+    cudaError_t e;
+    if ((e = cudaGetDevice(&h->dev)) != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+    if ((e = prepare_kernels()) != cudaSuccess) return cuda_fail(h, e, "prepare kernels");
+    if (h->opts.cuda_stream) {
+        h->stream = (cudaStream_t)h->opts.cuda_stream;
+        h->own_stream = false;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaStreamCreate");
+        h->own_stream = true;
+    }
+    if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaEventCreate");
+    // one pinned block: the control block, then a small scratch for device-to-host reads
+    void* blk = nullptr;
+    if ((e = cudaMallocHost(&blk, CTRL_BYTES + H_SMALL)) != cudaSuccess) return cuda_fail(h, e, "cudaMallocHost");
+    h->h_ctrl = (Ctrl*)blk;
+    h->h_small = (unsigned char*)blk + CTRL_BYTES;
+    return KATZ_OK;
 }
 
-void dfree(katz_handle* h, void* p) {
-    if (p) cudaFreeAsync(p, h->stream);
+// Scratch of the ranking loop that does not depend on the ranking's size.
+katz_status alloc_rank_scratch(katz_handle* h) {
+    cudaError_t e;
+    if ((e = dmalloc(h, &h->d_deghist, (size_t)h->D + 1)) != cudaSuccess ||
+        (e = dmalloc(h, &h->d_big_l, SELECT_CAP)) != cudaSuccess ||
+        (e = dmalloc(h, &h->d_big_u, SELECT_CAP)) != cudaSuccess ||
+        (e = dmalloc(h, &h->d_big_id, SELECT_CAP)) != cudaSuccess ||
+        (e = dmalloc(h, &h->d_hist256, 256)) != cudaSuccess || (e = dmalloc(h, &h->d_count, 1)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaMalloc rank scratch");
+    return KATZ_OK;
 }
 
 void free_iter(katz_handle* h) {
@@ -529,22 +547,9 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
         katz_destroy(h);                       \
         return st;                             \
     }
-    KCHK(cudaGetDevice(&h->dev), "cudaGetDevice");
-    KCHK(prepare_kernels(), "prepare kernels");
-    if (h->opts.cuda_stream) {
-        h->stream = (cudaStream_t)h->opts.cuda_stream;
-        h->own_stream = false;
-    } else {
-        KCHK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
-        h->own_stream = true;
-    }
-    KCHK(cudaEventCreate(&h->ev0), "cudaEventCreate");
-    KCHK(cudaEventCreate(&h->ev1), "cudaEventCreate");
-    {  // one pinned block: the control block, then a small scratch for device-to-host reads
-        void* blk = nullptr;
-        KCHK(cudaMallocHost(&blk, CTRL_BYTES + H_SMALL), "cudaMallocHost");
-        h->h_ctrl = (Ctrl*)blk;
-        h->h_small = (unsigned char*)blk + CTRL_BYTES;
+    if ((st = init_handle_runtime(h)) != KATZ_OK) {
+        katz_destroy(h);
+        return st;
     }
     DeviceGraph& g = h->g;
     g.n = n;
@@ -710,12 +715,10 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
         return KATZ_EINVAL;
     }
 #undef KCHK2
-    KCHK(dmalloc(h, &h->d_deghist, (size_t)h->D + 1), "cudaMalloc deghist");
-    KCHK(dmalloc(h, &h->d_big_l, SELECT_CAP), "cudaMalloc");
-    KCHK(dmalloc(h, &h->d_big_u, SELECT_CAP), "cudaMalloc");
-    KCHK(dmalloc(h, &h->d_big_id, SELECT_CAP), "cudaMalloc");
-    KCHK(dmalloc(h, &h->d_hist256, 256), "cudaMalloc");
-    KCHK(dmalloc(h, &h->d_count, 1), "cudaMalloc");
+    if ((st = alloc_rank_scratch(h)) != KATZ_OK) {
+        katz_destroy(h);
+        return st;
+    }
     KCHK(cudaStreamSynchronize(h->stream), "create sync");
 #undef KCHK
     *out = h;

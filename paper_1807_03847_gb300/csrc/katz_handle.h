@@ -69,6 +69,28 @@ struct katz_handle {
 };
 
 namespace katz {
+constexpr size_t CTRL_BYTES = (sizeof(Ctrl) + 255) / 256 * 256;
+constexpr size_t H_SMALL = 4096;
+
+cudaMemPool_t library_pool(int dev);
+
+// count elements of X from the library's pool, ordered on the handle's stream
+template <typename X>
+cudaError_t dmalloc(katz_handle* h, X** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaMemPool_t pool = library_pool(h->dev);
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync((void**)p, count * sizeof(X), pool, h->stream);
+}
+
+inline void dfree(katz_handle* h, void* p) {
+    if (p) cudaFreeAsync(p, h->stream);
+}
+
+katz_status init_handle_runtime(katz_handle* h);
+katz_status ensure_iter_buffers(katz_handle* h);
+katz_status alloc_rank_scratch(katz_handle* h);
 katz_status fail(katz_handle* h, katz_status s, const std::string& msg);
 katz_status cuda_fail(katz_handle* h, cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
