@@ -3,9 +3,11 @@ undirected SNAP/KONECT graphs; those are not available, so Erdos-Renyi, R-MAT
 and Chung-Lu graphs stand in for them).
 
 This package produces inputs only and holds none of the Katz arithmetic: the
-CPU oracle and the CUDA path both consume its CSR graphs.  Every graph is
-undirected, stored as a symmetric CSR (int64 ``rowptr``, int32 ``col``) with
-sorted rows, no self-loops and no duplicate arcs.
+CPU oracle and the CUDA path both consume its CSR graphs.  The generators'
+graphs are undirected, stored as a symmetric CSR (int64 ``rowptr``, int32
+``col``) with sorted rows, no self-loops and no duplicate arcs; ``orient`` and
+the ``directed_*`` helpers derive directed graphs (the same CSR, not
+symmetric) and directed update batches from them.
 """
 from __future__ import annotations
 
@@ -227,6 +229,78 @@ def apply_batch(g: Graph, src, dst, is_insert) -> Graph:
     v = (allk % n).astype(np.int32)
     sel = u < v
     return from_edges(n, u[sel], v[sel], g.name + "+batch")
+
+
+def directed_from_arcs(n: int, u, v, name: str = "arcs") -> Graph:
+    """CSR of the arcs u[i] -> v[i] (self-loops dropped, repeats merged)."""
+    u = np.asarray(u, np.int64)
+    v = np.asarray(v, np.int64)
+    keep = u != v
+    keys = np.unique(u[keep] * n + v[keep])
+    rows = keys // n
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return Graph(np.cumsum(rowptr), (keys % n).astype(np.int32), name)
+
+
+def orient(g: Graph, seed: int, p_keep: float = 0.5) -> Graph:
+    """A directed graph from an undirected one: each arc of the symmetric CSR
+    is kept independently with probability p_keep, so some edges stay
+    reciprocal, some become one-way and some vanish."""
+    rng = np.random.default_rng(seed)
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.rowptr))
+    keep = rng.random(g.nnz) < p_keep
+    return directed_from_arcs(g.n, rows[keep], g.col[keep], g.name + f"_dir{seed}")
+
+
+def directed_update_batch(g: Graph, m: int, seed: int, p_insert: float = 0.5, deg_bound: int | None = None):
+    """Draw m directed updates against the directed graph g: inserts are
+    uniform ordered non-arcs (out-degrees kept at or below deg_bound), deletes
+    uniform existing arcs; no ordered pair repeats within the batch (a -> b
+    and b -> a may both appear).  Returns (src, dst, is_insert)."""
+    rng = np.random.default_rng(seed)
+    n = g.n
+    D = int(deg_bound) if deg_bound is not None else (g.deg_max() if g.n else 0) + 64
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.rowptr))
+    present = rows * n + g.col.astype(np.int64)  # sorted: rows ascending, columns sorted
+    n_ins = int(rng.binomial(m, p_insert)) if m > 0 else 0
+    n_del = min(m - n_ins, len(present))
+    dels = rng.choice(present, size=n_del, replace=False) if n_del > 0 else np.zeros(0, np.int64)
+    outdeg = np.diff(g.rowptr).astype(np.int64)
+    ins_keys, seen = [], set()
+    tries = 0
+    while len(ins_keys) < n_ins and tries < 50 * (n_ins + 1):
+        tries += 1
+        a, b = int(rng.integers(0, n)), int(rng.integers(0, n))
+        key = a * n + b
+        if a == b or key in seen:
+            continue
+        pos = np.searchsorted(present, key)
+        if pos < len(present) and present[pos] == key:
+            continue
+        if outdeg[a] + 1 > D:
+            continue
+        seen.add(key)
+        outdeg[a] += 1
+        ins_keys.append(key)
+    keys = np.concatenate([np.array(ins_keys, np.int64), dels])
+    ins = np.concatenate([np.ones(len(ins_keys), np.uint8), np.zeros(len(dels), np.uint8)])
+    order = rng.permutation(len(keys))
+    keys, ins = keys[order], ins[order]
+    return (keys // n).astype(np.int32), (keys % n).astype(np.int32), ins
+
+
+def apply_directed_batch(g: Graph, src, dst, is_insert) -> Graph:
+    """The directed graph after an update batch (host-side, for test inputs)."""
+    n = g.n
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.rowptr))
+    keys = rows * n + g.col.astype(np.int64)
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    ins = np.asarray(is_insert).astype(bool)
+    keep = keys[~np.isin(keys, src[~ins] * n + dst[~ins])]
+    allk = np.concatenate([keep, src[ins] * n + dst[ins]])
+    return directed_from_arcs(n, allk // n, allk % n, g.name + "+batch")
 
 
 def workload(name: str) -> Graph:

@@ -246,15 +246,17 @@ struct Session {
     }
 
     // Preconditions of Alg. 2: I and E disjoint, D a subset of E; the batch
-    // itself names each unordered pair at most once and no self-loops; no row
-    // may exceed the degree bound the bounds were built with.
+    // itself names each edge at most once (an unordered pair when undirected,
+    // an ordered one when directed, Sec. 2.1) and no self-loops; no row may
+    // exceed the degree bound the bounds were built with (the out-degree of
+    // the source when directed).
     int validate(int64_t m, const int32_t* src, const int32_t* dst, const uint8_t* ins) const {
         std::vector<std::pair<int32_t, int32_t>> seen;
         std::vector<int64_t> dd((size_t)n, 0);
         for (int64_t e = 0; e < m; ++e) {
             int32_t a = src[e], x = dst[e];
             if (a < 0 || x < 0 || a >= n || x >= n || a == x) return EINVAL_;
-            seen.push_back({std::min(a, x), std::max(a, x)});
+            seen.push_back(undirected ? std::make_pair(std::min(a, x), std::max(a, x)) : std::make_pair(a, x));
             bool present = has(a, x);
             if (ins[e] ? present : !present) return EINVAL_;
             int delta = ins[e] ? 1 : -1;

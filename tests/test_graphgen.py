@@ -93,3 +93,31 @@ def test_stream_batches_are_valid_against_the_evolving_graph():
     # both kinds of update occur, and the mean gap matches the rate
     assert 0 < st.is_insert.mean() < 1
     assert 0.002 < st.arrival[-1] / len(st) < 0.01
+
+
+def test_directed_helpers_make_valid_graphs_and_batches():
+    g = gg.orient(gg.rmat(10, 8, seed=4), seed=9)
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    arcs = set(zip(rows.tolist(), g.col.tolist()))
+    assert all(a != b for a, b in arcs) and len(arcs) == g.nnz
+    assert any((b, a) not in arcs for a, b in arcs)  # not symmetric
+    assert any((b, a) in arcs for a, b in arcs)      # some edges reciprocal
+    for r in range(g.n):
+        row = g.col[g.rowptr[r]:g.rowptr[r + 1]]
+        assert np.all(np.diff(row) > 0)
+    D = g.deg_max() + 2
+    cur = g
+    for j in range(5):
+        src, dst, ins = gg.directed_update_batch(cur, 200, seed=j, deg_bound=D)
+        assert len(src) == 200 and 0 < ins.mean() < 1
+        seen = set()
+        cur_rows = np.repeat(np.arange(cur.n), np.diff(cur.rowptr))
+        cur_arcs = set(zip(cur_rows.tolist(), cur.col.tolist()))
+        for a, b, i in zip(src.tolist(), dst.tolist(), ins.tolist()):
+            assert a != b and (a, b) not in seen
+            seen.add((a, b))
+            assert ((a, b) in cur_arcs) != bool(i)
+        nxt = gg.apply_directed_batch(cur, src, dst, ins)
+        assert nxt.nnz == cur.nnz + int(ins.sum()) - int((1 - ins).sum())
+        assert nxt.deg_max() <= max(D, cur.deg_max())
+        cur = nxt

@@ -334,6 +334,83 @@ def test_dynamic_batch_validation_is_atomic():
     assert s.apply_update([0], [4], [1]) == oracle.OK
 
 
+# Directed graphs (Sec. 2.1: edges are ordered pairs; an update changes the
+# source's row only)
+@pytest.mark.parametrize("seed", range(6))
+def test_alg2_literal_directed_equals_static_recompute(seed):
+    rng = np.random.default_rng(450 + seed)
+    n = int(rng.integers(6, 14))
+    g = gg.orient(gg.from_edges(n, *zip(*[(a, b) for a in range(n) for b in range(a + 1, n)
+                                          if rng.random() < 0.4] or [(0, 1)])), seed)
+    r = 5
+    assert oracle.walks_exact(g.rowptr, g.col, r) == [list(x) for x in _brute_walks(g.rowptr, g.col, r)]
+    omega = oracle.walks_exact(g.rowptr, g.col, r)
+    src, dst, ins = gg.directed_update_batch(g, int(rng.integers(1, 6)), seed=seed)
+    new = oracle.alg2_update_exact(g.rowptr, g.col, omega, src, dst, ins)
+    g2 = gg.apply_directed_batch(g, src, dst, ins)
+    assert new == [list(x) for x in _brute_walks(g2.rowptr, g2.col, r)]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dynamic_session_directed_equals_static_recompute(seed):
+    g = gg.orient(gg.rmat(9, 8, seed=520 + seed), seed)
+    k, eps = 20, 1e-9
+    D = g.deg_max() + 8
+    s = oracle.Session(g.rowptr, g.col, False, D)
+    assert s.rank_static(0.0, k, eps) == oracle.OK
+    cur = g
+    for b in range(3):
+        src, dst, ins = gg.directed_update_batch(cur, 8 + 10 * b, seed=1000 * seed + b, deg_bound=D)
+        assert s.apply_update(src, dst, ins) == oracle.OK
+        cur = gg.apply_directed_batch(cur, src, dst, ins)
+        info = s.info()
+        t = oracle.Session(cur.rowptr, cur.col, False, D)
+        assert t.run_fixed(info["alpha"], info["r"]) == oracle.OK
+        for i in range(1, info["r"] + 1):
+            assert np.array_equal(s.omega(i), t.omega(i))
+        c, l, u = s.bounds()
+        c2, l2, u2 = t.bounds()
+        assert np.array_equal(c, c2) and np.array_equal(l, l2) and np.array_equal(u, u2)
+        assert np.array_equal(l, c)  # directed: l_r = c_r (Theorem 1)
+        ok, order = _criterion(l, u, k, eps)
+        assert ok and list(s.ranking()) == order[:k]
+
+
+def test_directed_batch_validation_uses_ordered_pairs():
+    # 0 -> 1 -> 2 -> 0 and 0 -> 2
+    g = gg.directed_from_arcs(4, [0, 1, 2, 0], [1, 2, 0, 2])
+    s = oracle.Session(g.rowptr, g.col, False, 3)
+    assert s.rank_static(0.0, 2, 1e-6) == oracle.OK
+    before = s.bounds()
+    cases = [
+        ([1], [2], [1]),            # insert an existing arc
+        ([2], [1], [0]),            # delete an absent arc (its reverse exists)
+        ([3, 3], [0, 0], [1, 1]),   # the same ordered pair twice
+        ([0, 0, 0], [3, 3, 1], [1, 1, 0]),
+    ]
+    for src, dst, ins in cases:
+        assert s.apply_update(src, dst, ins) == oracle.EINVAL
+    assert all(np.array_equal(a, b) for a, b in zip(before, s.bounds()))
+    # the degree bound applies to out-degrees: with D = 2, node 0 (out-degree
+    # 2) takes no further out-arc but any number of in-arcs
+    s3 = oracle.Session(g.rowptr, g.col, False, 2)
+    assert s3.rank_static(0.0, 2, 1e-6) == oracle.OK
+    assert s3.apply_update([0], [3], [1]) == oracle.EALPHA
+    assert s3.apply_update([3], [0], [1]) == oracle.OK
+    assert s.apply_update([0, 1], [3, 3], [1, 1]) == oracle.OK
+    assert s.apply_update([0], [3], [0]) == oracle.OK
+    assert s.apply_update([3, 0], [0, 3], [1, 1]) == oracle.OK  # a -> b and b -> a in one batch
+    g2 = gg.directed_from_arcs(4, [0, 1, 2, 0, 1, 3, 0], [1, 2, 0, 2, 3, 0, 3])
+    t = oracle.Session(g2.rowptr, g2.col, False, 3)
+    assert t.run_fixed(s.info()["alpha"], s.info()["r"]) == oracle.OK
+    assert all(np.array_equal(a, b) for a, b in zip(s.bounds(), t.bounds()))
+    s2 = oracle.Session(g.rowptr, g.col, False, 3)
+    assert s2.rank_static(0.0, 2, 1e-6) == oracle.OK
+    assert s2.apply_update([0, 0], [3, 1], [1, 0]) == oracle.OK
+    assert s2.apply_update([0], [1], [1]) == oracle.OK
+    assert s2.apply_update([0, 0], [3, 1], [0, 1]) == oracle.EINVAL  # 0 -> 1 present again
+
+
 # ---------------------------------------------------------------------------
 # The other stopping criteria of Sec. 3.1, each against a brute-force check
 # of its definition at every iteration
