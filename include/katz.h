@@ -197,15 +197,19 @@ katz_status katz_get_walk(katz_h h, int32_t i, double* s_out);
 katz_status katz_get_trace(katz_h h, int64_t* active_per_iter, int32_t cap);
 
 /*
- * Algorithm 2 (Sec. 4): apply a batch of m undirected edge updates
- * {src[e], dst[e]} (insert if is_insert[e] != 0, else delete) to the graph
- * of a handle that has ranked with keep_history = 1, repair the stored
- * walk vectors s_1..s_r, recompute the bounds, re-derive the active set
- * and continue iterating until the top-k criterion holds again.
+ * Algorithm 2 (Sec. 4): apply a batch of m edge updates (insert if
+ * is_insert[e] != 0, else delete) to the graph of a handle that has ranked
+ * with keep_history = 1 under the top-k criterion in FP64 mode, repair the
+ * stored walk vectors s_1..s_r, recompute the bounds, re-derive the active
+ * set and continue iterating until the top-k criterion holds again.
+ * On an undirected handle an update is the edge {src[e], dst[e]} (both arcs
+ * change); on a directed one (opts.undirected = 0) it is the arc
+ * src[e] -> dst[e] alone (Sec. 2.1), so a batch may name a -> b and b -> a.
  * Preconditions (checked, Sec. 4): inserted edges are absent, deleted
- * edges are present, no pair appears twice in the batch, no self-loops,
- * and no row exceeds the degree bound D afterwards.  Arrays may be host or
- * device pointers.
+ * edges are present, no edge appears twice in the batch (unordered pairs
+ * when undirected, ordered when directed), no self-loops, and no row
+ * exceeds the degree bound D afterwards (out-degrees when directed).
+ * Arrays may be host or device pointers.
  * Errors: KATZ_EINVAL (precondition), KATZ_EALPHA (a row would exceed D),
  * KATZ_ESTATE (no ranking / no history), KATZ_ENOMEM, KATZ_ECUDA.
  */
@@ -274,7 +278,7 @@ katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts)
 
 /*
  * Serve handle h, answering with its top k (1 <= k <= the ranked k).  h must
- * have ranked with keep_history = 1 in FP64 mode on an undirected graph and
+ * have ranked with keep_history = 1 in FP64 mode (directed or undirected) and
  * should own its stream (katz_opts.cuda_stream = NULL), so that its work can
  * overlap other handles'.  While attached, h belongs to the server: the caller
  * makes no other call on it until the server is destroyed.
@@ -283,8 +287,9 @@ katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts)
 katz_status katz_server_attach(katz_server_h s, katz_h h, int64_t k);
 
 /*
- * Queue a batch of m undirected updates for h (host arrays, copied before the
- * call returns; m <= slot_updates).  *ticket identifies the request.
+ * Queue a batch of m updates for h, read as katz_apply_update_batch reads
+ * them (host arrays, copied before the call returns; m <= slot_updates).
+ * *ticket identifies the request.
  * Errors: KATZ_EINVAL, KATZ_ESTATE (h not attached).
  */
 katz_status katz_server_submit(katz_server_h s, katz_h h, const int32_t* src, const int32_t* dst,

@@ -509,7 +509,7 @@ void katz_destroy(katz_h h) {
         for (void* ptr : {(void*)d.src, (void*)d.dst, (void*)d.ins, (void*)d.hub_epoch, (void*)d.table,
                           (void*)d.err, (void*)d.delta, (void*)d.ins_cnt, (void*)d.cursor, (void*)d.touched,
                           (void*)d.ins_start, (void*)d.ins_rows, (void*)d.n_ins_rows, (void*)d.bucket,
-                          (void*)d.vbits, (void*)d.frontier, (void*)d.fsize})
+                          (void*)d.vbits, (void*)d.frontier, (void*)d.fsize, (void*)d.rrowptr, (void*)d.rcol})
             dfree(h, ptr);
         dfree(h, h->col_spare);
         dfree(h, h->rp_new);
@@ -983,7 +983,6 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
     if (h->criterion != KATZ_CRIT_TOPK) return fail(h, KATZ_ESTATE, "dynamic updates continue the top-k criterion");
     if (!h->opts.keep_history) return fail(h, KATZ_ESTATE, "dynamic updates need keep_history = 1");
     if (h->fp32) return fail(h, KATZ_ESTATE, "dynamic updates run in FP64 mode");
-    if (!h->opts.undirected) return fail(h, KATZ_ESTATE, "dynamic updates take undirected handles");
     if (m < 0 || (m > 0 && (!src || !dst || !is_insert))) return fail(h, KATZ_EINVAL, "bad batch arguments");
     cudaError_t e;
     DeviceGraph& g = h->g;
@@ -999,6 +998,7 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
         const katz_status rs = katz::dyn_reserve(h, m, 0);
         if (rs != KATZ_OK) return rs;
     }
+    d.undirected = h->opts.undirected != 0;
     if (m > 0) {
         if ((e = cudaMemcpyAsync(d.src, src, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, h->stream)) != cudaSuccess ||
             (e = cudaMemcpyAsync(d.dst, dst, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, h->stream)) != cudaSuccess ||
@@ -1090,6 +1090,24 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
             g.layout = make_layout(n, g.layout.row_warp, g.layout.row_octet, g.layout.row_thread, chunks);
         }
         drop_graph(h);  // captured launches hold the old arrays and layout
+        // directed: the reverse BFS walks in-arcs, from the transposed CSR of
+        // the updated graph
+        if (!d.undirected) {
+            if (!d.rrowptr && (e = dmalloc(h, &d.rrowptr, (size_t)n + 1)) != cudaSuccess)
+                return cuda_fail(h, e, "cudaMalloc transposed offsets");
+            if (g.nnz > d.rcap) {
+                dfree(h, d.rcol);
+                d.rcol = nullptr;
+                d.rcap = 0;
+                const int64_t cap = g.nnz + g.nnz / 16 + 1024;
+                if ((e = dmalloc(h, &d.rcol, (size_t)cap)) != cudaSuccess)
+                    return cuda_fail(h, e, "cudaMalloc transposed arcs");
+                d.rcap = cap;
+            }
+            if ((e = dyn_transpose(g, d, h->deg_tmp, h->scan_sums, h->stream)) != cudaSuccess)
+                return cuda_fail(h, e, "transpose");
+            h->launches += 3 + (g.nnz > 0 ? 1 + (g.n > g.layout.row_warp ? 1 : 0) + (g.layout.chunks > 0 ? 1 : 0) : 0);
+        }
         // ---- repair s_1..s_r: affected rows only, or whole levels once the
         //      affected set is large (Sec. 4) ------------------------------------------
         if ((e = dyn_seed(g, d, m, h->stream)) != cudaSuccess) return cuda_fail(h, e, "seed frontier");
@@ -1119,7 +1137,7 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
             h->launches += (hi > 0 ? 1 : 0) + (hi > 0 && g.layout.chunks > 0 ? 2 : 0);
             if (i < r) {
                 if ((e = dyn_expand(g, d, lo, hi, i, h->stream)) != cudaSuccess) return cuda_fail(h, e, "expand");
-                h->launches += hi > lo ? 1 + (g.layout.chunks > 0 ? 1 : 0) : 0;
+                h->launches += hi > lo ? 1 + (d.undirected && g.layout.chunks > 0 ? 1 : 0) : 0;
                 if ((e = cudaMemcpyAsync(fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
                     (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
                     return cuda_fail(h, e, "frontier size");

@@ -171,7 +171,8 @@ struct DynBuffers {
     int32_t* src = nullptr;          // batch, original ids
     int32_t* dst = nullptr;
     uint8_t* ins = nullptr;
-    unsigned long long* table = nullptr;  // open-addressing set of unordered internal-id pairs (bit 63: delete)
+    bool undirected = true;          // edges are unordered pairs (both arcs) or ordered ones
+    unsigned long long* table = nullptr;  // open-addressing set of the batch's internal-id pairs (bit 63: delete)
     int64_t table_mask = 0;
     int32_t* err = nullptr;
     int32_t* delta = nullptr;        // [n] degree change
@@ -186,6 +187,9 @@ struct DynBuffers {
     int32_t* frontier = nullptr;     // [n] affected nodes, in order of discovery
     unsigned long long* fsize = nullptr;  // [2] frontier size, sum of the frontier's degrees
     int32_t* hub_epoch = nullptr;    // [row_warp] level at which a CHUNK row joined the frontier
+    int64_t* rrowptr = nullptr;      // [n+1] directed: transposed CSR (in-arcs) of the current graph
+    int32_t* rcol = nullptr;         // [rcap]
+    int64_t rcap = 0;
 };
 
 // ---- stopping criteria other than top-k (katz_criteria.cu) -------------------
@@ -215,6 +219,7 @@ cudaError_t dyn_rebuild(DeviceGraph& g, const DynBuffers& d, int64_t m, const in
 cudaError_t dyn_seed(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st);
 cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, int64_t hi, int level,
                        cudaStream_t st);
+cudaError_t dyn_transpose(const DeviceGraph& g, const DynBuffers& d, int64_t* cnt, int64_t* sums, cudaStream_t st);
 cudaError_t dyn_recompute_c(const DeviceGraph& g, const IterBuffers& b, const DynBuffers& d, const IterParams& p,
                             int r, bool all, cudaStream_t st);
 cudaError_t dyn_reactivate(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int r, cudaStream_t st);

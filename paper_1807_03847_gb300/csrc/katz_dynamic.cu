@@ -1,11 +1,15 @@
-// Dynamic graphs (Sec. 4, Algorithm 2): a batch of undirected edge
-// insertions and deletions is validated, applied to the device CSR, and the
-// stored walk vectors s_1..s_r are repaired level by level.
+// Dynamic graphs (Sec. 4, Algorithm 2): a batch of edge insertions and
+// deletions is validated, applied to the device CSR, and the stored walk
+// vectors s_1..s_r are repaired level by level.  An undirected edge {a, b} is
+// the two arcs a -> b and b -> a (Sec. 2.1); a directed update a -> b changes
+// the row of a alone.
 //
 // Repair (the pull form of Algorithm 2's update, see katz_api.cu):
-//   F_1 = endpoints of the batch (their rows changed);
-//   F_i = F_{i-1} + neighbours of the nodes that joined F_{i-1}   (reverse BFS;
-//         in-neighbours = neighbours for undirected graphs);
+//   F_1 = the rows the batch changed (both endpoints when undirected, the
+//         sources when directed);
+//   F_i = F_{i-1} + in-neighbours of the nodes that joined F_{i-1} (reverse
+//         BFS; in-neighbours = neighbours for undirected graphs, and a
+//         transposed CSR of the updated graph when directed);
 //   s_i(w) is recomputed for w in F_i from the already repaired level i-1
 //   with the lane partition of the static SpMV, so the repaired vectors equal
 //   a full recomputation on the updated graph.  Once F_i holds more than
@@ -53,9 +57,11 @@ __device__ __forceinline__ int64_t find_in_row(const Off* rowptr, const int32_t*
 
 constexpr unsigned long long DEL_BIT = 1ull << 63;
 
-// key of the unordered pair {u, v} of internal ids (never 0, bit 63 clear)
-__device__ __forceinline__ unsigned long long pair_key(int32_t u, int32_t v) {
-    return (((unsigned long long)(uint32_t)min(u, v) << 32) | (uint32_t)max(u, v)) + 1ull;
+// key of the edge u -> v of internal ids: the unordered pair {u, v} when
+// undirected, the ordered pair when directed (never 0, bit 63 clear)
+__device__ __forceinline__ unsigned long long pair_key(int32_t u, int32_t v, bool und) {
+    const int32_t a = und ? min(u, v) : u, b = und ? max(u, v) : v;
+    return (((unsigned long long)(uint32_t)a << 32) | (uint32_t)b) + 1ull;
 }
 
 // the stored entry of `key` (with its delete bit), 0 if absent
@@ -73,13 +79,14 @@ __device__ __forceinline__ unsigned long long table_find(const unsigned long lon
 
 // One warp per update: range, self-loop, duplicate (the pair table, which
 // also records deletions for the rebuild), presence (I and E disjoint, D a
-// subset of E; the graph is symmetric, so the shorter of the two rows
-// decides), degree deltas and the touched rows.
+// subset of E; an undirected graph is symmetric, so the shorter of the two
+// rows decides; a directed arc is looked up in its source's row), degree
+// deltas and the touched rows.
 template <typename Off>
 __global__ void validate_batch_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
                                       const int32_t* __restrict__ inv, int64_t n, const int32_t* __restrict__ src,
                                       const int32_t* __restrict__ dst, const uint8_t* __restrict__ ins, int64_t m,
-                                      unsigned long long* table, int64_t table_mask, int32_t* delta,
+                                      bool und, unsigned long long* table, int64_t table_mask, int32_t* delta,
                                       uint8_t* touched, int32_t* err) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
@@ -91,7 +98,7 @@ __global__ void validate_batch_kernel(const Off* __restrict__ rowptr, const int3
         }
         const int32_t ua = inv[a], ub = inv[b];
         if (lane == 0) {  // duplicate pair inside the batch
-            const unsigned long long key = pair_key(ua, ub);
+            const unsigned long long key = pair_key(ua, ub, und);
             const unsigned long long entry = key | (ins[e] ? 0ull : DEL_BIT);
             int64_t h = (int64_t)(mix64(key) & (unsigned long long)table_mask);
             for (int64_t probe = 0; probe <= table_mask; ++probe) {
@@ -106,28 +113,32 @@ __global__ void validate_batch_kernel(const Off* __restrict__ rowptr, const int3
         }
         const int64_t da = (int64_t)rowptr[ua + 1] - (int64_t)rowptr[ua];
         const int64_t db = (int64_t)rowptr[ub + 1] - (int64_t)rowptr[ub];
-        const int64_t pos = da <= db ? find_in_row(rowptr, col, ua, ub) : find_in_row(rowptr, col, ub, ua);
+        const int64_t pos =
+            (!und || da <= db) ? find_in_row(rowptr, col, ua, ub) : find_in_row(rowptr, col, ub, ua);
         if (lane == 0) {
             if (ins[e] ? pos >= 0 : pos < 0) atomicOr(err, DYN_E_INVAL);
             const int d = ins[e] ? 1 : -1;
             atomicAdd(&delta[ua], d);
-            atomicAdd(&delta[ub], d);
             touched[ua] = 1;
-            touched[ub] = 1;
+            if (und) {
+                atomicAdd(&delta[ub], d);
+                touched[ub] = 1;
+            }
         }
     }
 }
 
+// the rows the batch changes stay within D arcs (out-degrees when directed)
 template <typename Off>
 __global__ void degree_check_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ inv,
                                     const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                                    int64_t n, const int32_t* __restrict__ delta, int64_t D, int32_t* err) {
+                                    int64_t n, bool und, const int32_t* __restrict__ delta, int64_t D, int32_t* err) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         const int32_t a = src[e], b = dst[e];
         if (a < 0 || b < 0 || a >= n || b >= n) continue;
         const int32_t ends[2] = {inv[a], inv[b]};
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < (und ? 2 : 1); ++q) {
             const int64_t u = ends[q];
             if ((int64_t)rowptr[u + 1] - (int64_t)rowptr[u] + delta[u] > D) atomicOr(err, DYN_E_ALPHA);
         }
@@ -155,12 +166,13 @@ __global__ void clear_batch_kernel(const int32_t* __restrict__ inv, const int32_
 // insertions: count per row and list the rows that receive arcs
 __global__ void count_inserts_kernel(const int32_t* __restrict__ inv, const int32_t* __restrict__ src,
                                      const int32_t* __restrict__ dst, const uint8_t* __restrict__ ins, int64_t m,
-                                     int32_t* ins_cnt, int32_t* ins_rows, unsigned long long* n_ins_rows) {
+                                     bool und, int32_t* ins_cnt, int32_t* ins_rows,
+                                     unsigned long long* n_ins_rows) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         if (!ins[e]) continue;
         const int32_t ends[2] = {inv[src[e]], inv[dst[e]]};
-        for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < (und ? 2 : 1); ++q)
             if (atomicAdd(&ins_cnt[ends[q]], 1) == 0) ins_rows[atomicAdd(n_ins_rows, 1ULL)] = ends[q];
     }
 }
@@ -192,14 +204,15 @@ __global__ void bucket_offsets_kernel(const int32_t* __restrict__ ins_rows, cons
 // place the inserted arcs (original id of the target kept for the sort)
 __global__ void bucket_fill_kernel(const int32_t* __restrict__ inv, const int32_t* __restrict__ src,
                                    const int32_t* __restrict__ dst, const uint8_t* __restrict__ ins, int64_t m,
-                                   const int64_t* __restrict__ ins_start, int32_t* cursor, int32_t* bucket) {
+                                   bool und, const int64_t* __restrict__ ins_start, int32_t* cursor,
+                                   int32_t* bucket) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         if (!ins[e]) continue;
         const int32_t a = src[e], b = dst[e];
         const int32_t ua = inv[a], ub = inv[b];
         bucket[ins_start[ua] + atomicAdd(&cursor[ua], 1)] = b;
-        bucket[ins_start[ub] + atomicAdd(&cursor[ub], 1)] = a;
+        if (und) bucket[ins_start[ub] + atomicAdd(&cursor[ub], 1)] = a;
     }
 }
 
@@ -243,13 +256,13 @@ __device__ __forceinline__ void rebuild_touched_row(const Off* __restrict__ rowp
                                                     const int64_t* __restrict__ ins_start,
                                                     const int32_t* __restrict__ bucket,
                                                     const unsigned long long* __restrict__ table, int64_t mask,
-                                                    int32_t* col_new) {
+                                                    bool und, int32_t* col_new) {
     const int lane = threadIdx.x & 31;
     const int64_t a = rowptr[v], b = rowptr[v + 1];
     for (int64_t base = a; base < b; base += 32) {
         const int64_t j = base + lane;
         const int32_t x = j < b ? col[j] : -1;
-        const bool keep = x >= 0 && !(table_find(table, mask, pair_key((int32_t)v, x)) & DEL_BIT);
+        const bool keep = x >= 0 && !(table_find(table, mask, pair_key((int32_t)v, x, und)) & DEL_BIT);
         const unsigned kb = __ballot_sync(FULL, keep);
         if (keep) col_new[o + __popc(kb & ((1u << lane) - 1u))] = x;
         o += __popc(kb);
@@ -266,7 +279,7 @@ __global__ void rebuild_groups_kernel(const Off* __restrict__ rowptr, const int3
                                       const int64_t* __restrict__ rowptr_new, const uint8_t* __restrict__ touched,
                                       const int32_t* __restrict__ ins_cnt, const int64_t* __restrict__ ins_start,
                                       const int32_t* __restrict__ bucket, const unsigned long long* __restrict__ table,
-                                      int64_t mask, int64_t row_lo, int64_t n, int32_t* col_new) {
+                                      int64_t mask, bool und, int64_t row_lo, int64_t n, int32_t* col_new) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     const int64_t groups = (n - row_lo + 31) / 32;
@@ -282,7 +295,7 @@ __global__ void rebuild_groups_kernel(const Off* __restrict__ rowptr, const int3
         for (int64_t v = u0; v < u1; ++v) {
             const int64_t o = rowptr_new[v];
             if ((tb >> (v - u0)) & 1u) {
-                rebuild_touched_row(rowptr, col, v, o, ins_cnt, ins_start, bucket, table, mask, col_new);
+                rebuild_touched_row(rowptr, col, v, o, ins_cnt, ins_start, bucket, table, mask, und, col_new);
             } else {
                 const int64_t a = rowptr[v], b = rowptr[v + 1];
                 for (int64_t j = a + lane; j < b; j += 32) col_new[o + (j - a)] = col[j];
@@ -317,7 +330,7 @@ rebuild_hub_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restric
                         const int64_t* __restrict__ rowptr_new, const uint8_t* __restrict__ touched,
                         const int32_t* __restrict__ ins_cnt, const int64_t* __restrict__ ins_start,
                         const int32_t* __restrict__ bucket, const unsigned long long* __restrict__ table, int64_t mask,
-                        int64_t row_warp, int32_t* col_new) {
+                        bool und, int64_t row_warp, int32_t* col_new) {
     __shared__ int wsum[HUB_THREADS / 32];
     __shared__ int total;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -328,7 +341,7 @@ rebuild_hub_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restric
         for (int64_t base = a; base < b; base += HUB_THREADS) {
             const int64_t j = base + tid;
             const int32_t x = j < b ? col[j] : -1;
-            const bool keep = x >= 0 && !(table_find(table, mask, pair_key((int32_t)u, x)) & DEL_BIT);
+            const bool keep = x >= 0 && !(table_find(table, mask, pair_key((int32_t)u, x, und)) & DEL_BIT);
             const unsigned kb = __ballot_sync(FULL, keep);
             if (lane == 0) wsum[wid] = __popc(kb);
             __syncthreads();
@@ -379,16 +392,17 @@ __device__ __forceinline__ void join(int32_t x, int level, int64_t row_warp, int
     if (x < row_warp) hub_epoch[x] = level;
 }
 
-// F_1: the endpoints of every update
+// F_1: the rows every update changed (both endpoints when undirected, the
+// source when directed)
 template <typename Off>
 __global__ void seed_frontier_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ inv,
                                      const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                                     int64_t row_warp, uint32_t* vbits, int32_t* frontier, unsigned long long* fsize,
-                                     int32_t* hub_epoch) {
+                                     bool und, int64_t row_warp, uint32_t* vbits, int32_t* frontier,
+                                     unsigned long long* fsize, int32_t* hub_epoch) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         const int32_t ends[2] = {inv[src[e]], inv[dst[e]]};
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < (und ? 2 : 1); ++q) {
             if (visit(vbits, ends[q])) {
                 join(ends[q], 1, row_warp, frontier, fsize, hub_epoch);
                 atomicAdd(&fsize[1], (unsigned long long)degree(rowptr, ends[q]));
@@ -452,6 +466,64 @@ __global__ void expand_hubs_kernel(const Off* __restrict__ rowptr, const int32_t
         const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
         const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
         vol += expand_arcs(rowptr, col, j0, j1, level, row_warp, vbits, frontier, fsize, hub_epoch);
+    }
+    add_warp_volume(vol, fsize);
+}
+
+// ---- directed graphs: the transposed CSR of the updated graph ----------------
+// in-degree of every node (cnt must be zero on entry)
+__global__ void indegree_kernel(const int32_t* __restrict__ col, int64_t nnz, unsigned long long* cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += stride)
+        atomicAdd(&cnt[col[j]], 1ull);
+}
+
+// arcs of the rows from row_lo on into the transposed rows: one warp per 32
+// consecutive rows; cursor[x] starts at the first slot of x's in-arcs
+template <typename Off>
+__global__ void transpose_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t row_lo,
+                                      int64_t n, unsigned long long* cursor, int32_t* rcol) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t groups = (n - row_lo + 31) / 32;
+    for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; gi < groups; gi += warps) {
+        const int64_t u0 = row_lo + gi * 32, u1 = min(u0 + 32, n);
+        for (int64_t v = u0; v < u1; ++v) {
+            const int64_t a = rowptr[v], b = rowptr[v + 1];
+            for (int64_t j = a + lane; j < b; j += 32) rcol[atomicAdd(&cursor[col[j]], 1ull)] = (int32_t)v;
+        }
+    }
+}
+
+// the same for the CHUNK rows: one warp per chunk
+template <typename Off>
+__global__ void transpose_chunks_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                        const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first,
+                                        int64_t chunks, unsigned long long* cursor, int32_t* rcol) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < chunks; ch += warps) {
+        const int64_t u = chunk_row[ch];
+        const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+        const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+        for (int64_t j = j0 + lane; j < j1; j += 32) rcol[atomicAdd(&cursor[col[j]], 1ull)] = (int32_t)u;
+    }
+}
+
+// directed: the in-neighbours of frontier[lo, hi) join the frontier; one
+// warp per node, the in-arcs from the transposed CSR, the volume counted in
+// out-degrees (the rows a repair recomputes)
+template <typename Off>
+__global__ void expand_in_kernel(const Off* __restrict__ rowptr, const int64_t* __restrict__ rrowptr,
+                                 const int32_t* __restrict__ rcol, int32_t* frontier, int64_t lo, int64_t hi,
+                                 int level, int64_t row_warp, uint32_t* vbits, unsigned long long* fsize,
+                                 int32_t* hub_epoch) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    unsigned long long vol = 0;
+    for (int64_t q = lo + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; q < hi; q += warps) {
+        const int64_t w = frontier[q];
+        vol += expand_arcs(rowptr, rcol, rrowptr[w], rrowptr[w + 1], level, row_warp, vbits, frontier, fsize,
+                           hub_epoch);
     }
     add_warp_volume(vol, fsize);
 }
@@ -544,18 +616,18 @@ cudaError_t dyn_validate(const DeviceGraph& g, const DynBuffers& d, int64_t m, i
     const int wblocks = grid_for(m * 32, 256);
     if (g.off64)
         validate_batch_kernel<int64_t><<<wblocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, g.inv, g.n, d.src,
-                                                               d.dst, d.ins, m, d.table, d.table_mask, d.delta,
-                                                               d.touched, d.err);
+                                                               d.dst, d.ins, m, d.undirected, d.table, d.table_mask,
+                                                               d.delta, d.touched, d.err);
     else
         validate_batch_kernel<int32_t><<<wblocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, g.inv, g.n, d.src,
-                                                               d.dst, d.ins, m, d.table, d.table_mask, d.delta,
-                                                               d.touched, d.err);
+                                                               d.dst, d.ins, m, d.undirected, d.table, d.table_mask,
+                                                               d.delta, d.touched, d.err);
     if (g.off64)
         degree_check_kernel<int64_t><<<grid_for(m, 256), 256, 0, st>>>((const int64_t*)g.rowptr, g.inv, d.src, d.dst,
-                                                                      m, g.n, d.delta, D, d.err);
+                                                                      m, g.n, d.undirected, d.delta, D, d.err);
     else
         degree_check_kernel<int32_t><<<grid_for(m, 256), 256, 0, st>>>((const int32_t*)g.rowptr, g.inv, d.src, d.dst,
-                                                                      m, g.n, d.delta, D, d.err);
+                                                                      m, g.n, d.undirected, d.delta, D, d.err);
     return cudaGetLastError();
 }
 
@@ -573,11 +645,11 @@ cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, in
                         int64_t* sums, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(d.n_ins_rows, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    count_inserts_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, d.ins, m, d.ins_cnt, d.ins_rows,
-                                                           d.n_ins_rows);
+    count_inserts_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, d.ins, m, d.undirected, d.ins_cnt,
+                                                           d.ins_rows, d.n_ins_rows);
     bucket_offsets_kernel<<<1, 1024, 0, st>>>(d.ins_rows, d.n_ins_rows, d.ins_cnt, d.ins_start);
-    bucket_fill_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, d.ins, m, d.ins_start, d.cursor,
-                                                         d.bucket);
+    bucket_fill_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, d.ins, m, d.undirected, d.ins_start,
+                                                         d.cursor, d.bucket);
     bucket_sort_kernel<<<grid_for(2 * m, 128), 128, 0, st>>>(d.ins_rows, d.n_ins_rows, d.ins_cnt, d.ins_start, g.inv,
                                                             d.bucket);
     if (g.off64)
@@ -599,15 +671,15 @@ static void rebuild_launch(DeviceGraph& g, const DynBuffers& d, const int64_t* r
     const int64_t groups = (g.n - L.row_warp + 31) / 32;
     if (groups > 0)
         rebuild_groups_kernel<Off><<<grid_for(groups * 32, 256), 256, 0, st>>>(
-            rp, g.col, rowptr_new, d.touched, d.ins_cnt, d.ins_start, d.bucket, d.table, d.table_mask, L.row_warp,
-            g.n, col_new);
+            rp, g.col, rowptr_new, d.touched, d.ins_cnt, d.ins_start, d.bucket, d.table, d.table_mask, d.undirected,
+            L.row_warp, g.n, col_new);
     if (L.chunks > 0)
         rebuild_chunks_kernel<Off><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
             rp, g.col, rowptr_new, d.touched, g.chunk_row, g.chunk_first, L.chunks, col_new);
     if (L.row_warp > 0)
         rebuild_hub_rows_kernel<Off><<<(unsigned)std::min<int64_t>(L.row_warp, 152 * 2), HUB_THREADS, 0, st>>>(
-            rp, g.col, rowptr_new, d.touched, d.ins_cnt, d.ins_start, d.bucket, d.table, d.table_mask, L.row_warp,
-            col_new);
+            rp, g.col, rowptr_new, d.touched, d.ins_cnt, d.ins_start, d.bucket, d.table, d.table_mask, d.undirected,
+            L.row_warp, col_new);
 }
 
 // rows into col_new (old layout and chunk table), then the new offsets over
@@ -635,12 +707,12 @@ cudaError_t dyn_seed(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaS
     if (e != cudaSuccess) return e;
     if (g.off64)
         seed_frontier_kernel<int64_t><<<grid_for(m, 256), 256, 0, st>>>((const int64_t*)g.rowptr, g.inv, d.src, d.dst,
-                                                                       m, g.layout.row_warp, d.vbits, d.frontier,
-                                                                       d.fsize, d.hub_epoch);
+                                                                       m, d.undirected, g.layout.row_warp, d.vbits,
+                                                                       d.frontier, d.fsize, d.hub_epoch);
     else
         seed_frontier_kernel<int32_t><<<grid_for(m, 256), 256, 0, st>>>((const int32_t*)g.rowptr, g.inv, d.src, d.dst,
-                                                                       m, g.layout.row_warp, d.vbits, d.frontier,
-                                                                       d.fsize, d.hub_epoch);
+                                                                       m, d.undirected, g.layout.row_warp, d.vbits,
+                                                                       d.frontier, d.fsize, d.hub_epoch);
     return cudaGetLastError();
 }
 
@@ -649,6 +721,17 @@ cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, in
                        cudaStream_t st) {
     if (hi <= lo) return cudaSuccess;
     const SpmvLayout& L = g.layout;
+    if (!d.undirected) {
+        if (g.off64)
+            expand_in_kernel<int64_t><<<grid_for((hi - lo) * 32, 256), 256, 0, st>>>(
+                (const int64_t*)g.rowptr, d.rrowptr, d.rcol, d.frontier, lo, hi, level, L.row_warp, d.vbits, d.fsize,
+                d.hub_epoch);
+        else
+            expand_in_kernel<int32_t><<<grid_for((hi - lo) * 32, 256), 256, 0, st>>>(
+                (const int32_t*)g.rowptr, d.rrowptr, d.rcol, d.frontier, lo, hi, level, L.row_warp, d.vbits, d.fsize,
+                d.hub_epoch);
+        return cudaGetLastError();
+    }
     if (g.off64) {
         expand_kernel<int64_t><<<grid_for((hi - lo) * 32, 256), 256, 0, st>>>(
             (const int64_t*)g.rowptr, g.col, d.frontier, lo, hi, level, L.row_warp, d.vbits, d.fsize, d.hub_epoch);
@@ -663,6 +746,41 @@ cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, in
             expand_hubs_kernel<int32_t><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
                 (const int32_t*)g.rowptr, g.col, g.chunk_row, g.chunk_first, L.chunks, d.frontier, level, L.row_warp,
                 d.vbits, d.fsize, d.hub_epoch);
+    }
+    return cudaGetLastError();
+}
+
+// directed graphs: the transposed CSR of the current graph into d.rrowptr /
+// d.rcol (capacity d.rcap >= nnz); cnt: n + 1 int64 of scratch
+cudaError_t dyn_transpose(const DeviceGraph& g, const DynBuffers& d, int64_t* cnt, int64_t* sums, cudaStream_t st) {
+    const int64_t n = g.n;
+    const SpmvLayout& L = g.layout;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)(n + 1) * sizeof(int64_t), st);
+    if (e != cudaSuccess) return e;
+    if (g.nnz > 0)
+        indegree_kernel<<<grid_for(g.nnz, 256), 256, 0, st>>>(g.col, g.nnz, (unsigned long long*)cnt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = exclusive_scan_i64(cnt, n + 1, d.rrowptr, sums, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(cnt, d.rrowptr, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, st)) !=
+        cudaSuccess)
+        return e;
+    if (g.nnz == 0) return cudaSuccess;
+    unsigned long long* cur = (unsigned long long*)cnt;
+    const int64_t groups = (n - L.row_warp + 31) / 32;
+    if (g.off64) {
+        if (groups > 0)
+            transpose_rows_kernel<int64_t><<<grid_for(groups * 32, 256), 256, 0, st>>>(
+                (const int64_t*)g.rowptr, g.col, L.row_warp, n, cur, d.rcol);
+        if (L.chunks > 0)
+            transpose_chunks_kernel<int64_t><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
+                (const int64_t*)g.rowptr, g.col, g.chunk_row, g.chunk_first, L.chunks, cur, d.rcol);
+    } else {
+        if (groups > 0)
+            transpose_rows_kernel<int32_t><<<grid_for(groups * 32, 256), 256, 0, st>>>(
+                (const int32_t*)g.rowptr, g.col, L.row_warp, n, cur, d.rcol);
+        if (L.chunks > 0)
+            transpose_chunks_kernel<int32_t><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
+                (const int32_t*)g.rowptr, g.col, g.chunk_row, g.chunk_first, L.chunks, cur, d.rcol);
     }
     return cudaGetLastError();
 }
