@@ -253,6 +253,12 @@ def orient(g: Graph, seed: int, p_keep: float = 0.5) -> Graph:
     return directed_from_arcs(g.n, rows[keep], g.col[keep], g.name + f"_dir{seed}")
 
 
+def reverse(g: Graph) -> Graph:
+    """The reverse graph: arc v -> u for every arc u -> v of g."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.rowptr))
+    return directed_from_arcs(g.n, g.col.astype(np.int64), rows, g.name + "_rev")
+
+
 def directed_update_batch(g: Graph, m: int, seed: int, p_insert: float = 0.5, deg_bound: int | None = None):
     """Draw m directed updates against the directed graph g: inserts are
     uniform ordered non-arcs (out-degrees kept at or below deg_bound), deletes

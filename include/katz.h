@@ -78,7 +78,11 @@ typedef struct {
     void* cuda_stream;     /* cudaStream_t to run on; NULL: the library creates one */
     int32_t use_graph;     /* 1 (default): run the iteration as a CUDA graph with a
                               device-side while loop; 0: host-driven loop */
-    int32_t slack;         /* dynamic handles: spare arcs reserved per row (default 0) */
+    int32_t inbound;       /* directed handles: 1 ranks by inbound Katz (walks that end at
+                              v, Sec. 2.1), which is the outbound Katz of the reverse
+                              graph: the library reverses the CSR on the device at create.
+                              Update batches still name arcs src -> dst of the graph as
+                              given.  0 (default): outbound.  Ignored when undirected. */
     int32_t profile;       /* 1: time every walk-count SpMV launch with CUDA events on the
                               handle's stream (katz_info.spmv_ms); forces the host-driven loop */
     int32_t fp32_from;     /* KATZ_FP32_CERT: first walk level computed in FP32 (>= 2);

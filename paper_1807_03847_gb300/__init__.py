@@ -34,7 +34,7 @@ STATUS = ["KATZ_OK", "KATZ_EINVAL", "KATZ_EALPHA", "KATZ_ENOMEM", "KATZ_ECUDA", 
 class katz_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("undirected", ctypes.c_int32), ("keep_history", ctypes.c_int32),
                 ("r_max", ctypes.c_int32), ("deg_bound", ctypes.c_int64), ("frontier_abort_frac", ctypes.c_double),
-                ("cuda_stream", ctypes.c_void_p), ("use_graph", ctypes.c_int32), ("slack", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p), ("use_graph", ctypes.c_int32), ("inbound", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("fp32_from", ctypes.c_int32)]
 
 

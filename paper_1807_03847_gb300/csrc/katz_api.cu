@@ -452,6 +452,59 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
 
 }  // namespace katz
 
+namespace katz {
+
+// The reverse graph of the input CSR (host or device pointers) into
+// h->rp_new (n+1 int64) and h->col_spare (nnz), after checking the input in
+// full (offsets and column range), which the scatter needs.
+katz_status reverse_input(katz_handle* h, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col) {
+    cudaError_t e = cudaSuccess;
+    int64_t *rp_in = nullptr, *cnt = nullptr, *sums = nullptr, *d_degmax = nullptr;
+    int32_t* col_in = nullptr;
+    unsigned long long* d_bad = nullptr;
+    const bool copy_rp = !is_device_ptr(rowptr), copy_col = nnz > 0 && !is_device_ptr(col);
+    auto A = [&](auto** p, size_t count) {
+        if (e == cudaSuccess) e = dmalloc(h, p, count);
+    };
+    if (copy_rp) A(&rp_in, (size_t)n + 1);
+    if (copy_col) A(&col_in, (size_t)nnz);
+    A(&cnt, (size_t)n + 1);
+    A(&sums, (size_t)scan_blocks(n + 1));
+    A(&d_bad, 1);
+    A(&d_degmax, 1);
+    A(&h->rp_new, (size_t)n + 1);
+    A(&h->col_spare, (size_t)nnz);
+    katz_status st = KATZ_OK;
+    if (e == cudaSuccess) {
+        h->col_spare_cap = std::max<int64_t>(nnz, 1);
+        const int64_t* rp = copy_rp ? rp_in : rowptr;
+        const int32_t* cl = copy_col ? col_in : col;
+        if (copy_rp) e = cudaMemcpyAsync(rp_in, rowptr, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess && copy_col)
+            e = cudaMemcpyAsync(col_in, col, (size_t)nnz * sizeof(int32_t), cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_degmax, 0, sizeof(int64_t), h->stream);
+        DeviceGraph gin;
+        gin.n = n;
+        gin.nnz = nnz;
+        gin.off64 = true;
+        gin.rowptr = (void*)rp;
+        gin.col = (int32_t*)cl;
+        if (e == cudaSuccess) e = launch_validate_csr(gin, d_bad, d_degmax, h->stream);
+        unsigned long long* bad = (unsigned long long*)h->h_small;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bad, d_bad, sizeof(*bad), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess && *bad) st = KATZ_EINVAL;
+        if (e == cudaSuccess && st == KATZ_OK)
+            e = reverse_csr(rp, cl, n, nnz, cnt, sums, h->rp_new, h->col_spare, h->stream);
+    }
+    for (void* p : {(void*)rp_in, (void*)col_in, (void*)cnt, (void*)sums, (void*)d_bad, (void*)d_degmax}) dfree(h, p);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reverse graph");
+    return st;
+}
+
+}  // namespace katz
+
 extern "C" {
 
 void katz_default_opts(katz_opts* o) {
@@ -465,7 +518,7 @@ void katz_default_opts(katz_opts* o) {
     o->frontier_abort_frac = 0.05;
     o->cuda_stream = nullptr;
     o->use_graph = 1;
-    o->slack = 0;
+    o->inbound = 0;
     o->profile = 0;
     o->fp32_from = 0;
 }
@@ -550,6 +603,17 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     if ((st = init_handle_runtime(h)) != KATZ_OK) {
         katz_destroy(h);
         return st;
+    }
+    // inbound Katz of a directed graph is the outbound Katz of its reverse
+    // graph (Sec. 2.1): reverse the input on the device and take that as the
+    // input (held in rp_new / col_spare until the create has copied it)
+    if (h->opts.inbound && !h->opts.undirected) {
+        if ((st = reverse_input(h, n, nnz, rowptr, col)) != KATZ_OK) {
+            katz_destroy(h);
+            return st;
+        }
+        rowptr = h->rp_new;
+        col = h->col_spare;
     }
     DeviceGraph& g = h->g;
     g.n = n;
@@ -710,6 +774,11 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     dfree(h, rp_new);
     dfree(h, sums);
     drop_staging();
+    dfree(h, h->rp_new);  // the reverse graph of an inbound handle, now copied
+    dfree(h, h->col_spare);
+    h->rp_new = nullptr;
+    h->col_spare = nullptr;
+    h->col_spare_cap = 0;
     if (hv.bad_col) {  // a column entry outside [0, n)
         katz_destroy(h);
         return KATZ_EINVAL;
@@ -984,6 +1053,9 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
     if (!h->opts.keep_history) return fail(h, KATZ_ESTATE, "dynamic updates need keep_history = 1");
     if (h->fp32) return fail(h, KATZ_ESTATE, "dynamic updates run in FP64 mode");
     if (m < 0 || (m > 0 && (!src || !dst || !is_insert))) return fail(h, KATZ_EINVAL, "bad batch arguments");
+    // an inbound handle holds the reverse graph: the arc src -> dst of the
+    // given graph is dst -> src there
+    if (h->opts.inbound && !h->opts.undirected) std::swap(src, dst);
     cudaError_t e;
     DeviceGraph& g = h->g;
     DynBuffers& d = h->dyn;

@@ -232,6 +232,13 @@ int64_t scan_blocks(int64_t n);
 int degree_class_host(int64_t d);
 cudaError_t relabel_by_degree_class(const int64_t* rowptr64, int64_t n, uint32_t* counts_scratch, int nb,
                                     int32_t* perm, int32_t* inv, uint64_t* class_start_dev, cudaStream_t st);
+// in-degrees of a CSR's columns (cnt: n int64, zero on entry)
+cudaError_t launch_indegree(const int32_t* col, int64_t nnz, int64_t* cnt, cudaStream_t st);
+// the reverse graph of a validated CSR (int64 offsets): rowptr_rev[n+1],
+// col_rev[nnz]; the order inside a reverse row is unspecified; cnt: n+1
+// int64 of scratch, sums: scan_blocks(n+1)
+cudaError_t reverse_csr(const int64_t* rowptr, const int32_t* col, int64_t n, int64_t nnz, int64_t* cnt,
+                        int64_t* sums, int64_t* rowptr_rev, int32_t* col_rev, cudaStream_t st);
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* sums_scratch, cudaStream_t st);
 // new row offsets (int64, n+1) of the relabelled adjacency
 cudaError_t relabel_offsets(const int64_t* rowptr64, const int32_t* perm, int64_t n, int64_t* deg_new_scratch,

@@ -471,13 +471,6 @@ __global__ void expand_hubs_kernel(const Off* __restrict__ rowptr, const int32_t
 }
 
 // ---- directed graphs: the transposed CSR of the updated graph ----------------
-// in-degree of every node (cnt must be zero on entry)
-__global__ void indegree_kernel(const int32_t* __restrict__ col, int64_t nnz, unsigned long long* cnt) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += stride)
-        atomicAdd(&cnt[col[j]], 1ull);
-}
-
 // arcs of the rows from row_lo on into the transposed rows: one warp per 32
 // consecutive rows; cursor[x] starts at the first slot of x's in-arcs
 template <typename Off>
@@ -757,9 +750,7 @@ cudaError_t dyn_transpose(const DeviceGraph& g, const DynBuffers& d, int64_t* cn
     const SpmvLayout& L = g.layout;
     cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)(n + 1) * sizeof(int64_t), st);
     if (e != cudaSuccess) return e;
-    if (g.nnz > 0)
-        indegree_kernel<<<grid_for(g.nnz, 256), 256, 0, st>>>(g.col, g.nnz, (unsigned long long*)cnt);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_indegree(g.col, g.nnz, cnt, st)) != cudaSuccess) return e;
     if ((e = exclusive_scan_i64(cnt, n + 1, d.rrowptr, sums, st)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(cnt, d.rrowptr, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, st)) !=
         cudaSuccess)

@@ -269,6 +269,25 @@ __global__ void chunk_fill_kernel(const int64_t* __restrict__ chunk_first, int64
         for (int64_t q = chunk_first[u] + lane; q < chunk_first[u + 1]; q += 32) chunk_row[q] = (int32_t)u;
 }
 
+// ---- reverse graphs ----------------------------------------------------------
+// in-degree of every node (cnt zero on entry)
+__global__ void indegree_kernel(const int32_t* __restrict__ col, int64_t nnz, unsigned long long* cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += stride)
+        atomicAdd(&cnt[col[j]], 1ull);
+}
+
+// arc v -> x of the input becomes x -> v: one warp per row; cursor[x] starts
+// at the first slot of row x of the reverse graph
+__global__ void reverse_fill_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t n,
+                                    unsigned long long* cursor, int32_t* col_rev) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; v < n; v += warps)
+        for (int64_t j = rowptr[v] + lane; j < rowptr[v + 1]; j += 32)
+            col_rev[atomicAdd(&cursor[col[j]], 1ull)] = (int32_t)v;
+}
+
 int grid_for(int64_t n, int threads, int max_blocks = 152 * 16) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -340,6 +359,23 @@ cudaError_t build_chunk_table(const int64_t* rowptr_new, int64_t row_warp, int64
 }
 
 int64_t scan_blocks(int64_t n) { return (n + SCAN_THREADS - 1) / SCAN_THREADS; }
+
+cudaError_t launch_indegree(const int32_t* col, int64_t nnz, int64_t* cnt, cudaStream_t st) {
+    if (nnz > 0) indegree_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(col, nnz, (unsigned long long*)cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t reverse_csr(const int64_t* rowptr, const int32_t* col, int64_t n, int64_t nnz, int64_t* cnt,
+                        int64_t* sums, int64_t* rowptr_rev, int32_t* col_rev, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)(n + 1) * sizeof(int64_t), st);
+    if (e == cudaSuccess) e = launch_indegree(col, nnz, cnt, st);
+    if (e == cudaSuccess) e = exclusive_scan_i64(cnt, n + 1, rowptr_rev, sums, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cnt, rowptr_rev, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess || nnz == 0) return e;
+    reverse_fill_kernel<<<grid_for(n * 32, 256), 256, 0, st>>>(rowptr, col, n, (unsigned long long*)cnt, col_rev);
+    return cudaGetLastError();
+}
 int relabel_blocks(int64_t n) { return (int)((n + RL_THREADS - 1) / RL_THREADS); }
 
 }  // namespace katz

@@ -351,6 +351,36 @@ def test_alg2_literal_directed_equals_static_recompute(seed):
     assert new == [list(x) for x in _brute_walks(g2.rowptr, g2.col, r)]
 
 
+def _brute_inbound_walks(rowptr, col, r):
+    """Walks of length i that END at v, by enumerating every walk from every
+    start and crediting its last node (Sec. 2.1, inbound Katz)."""
+    n = len(rowptr) - 1
+    nbr = [list(col[rowptr[v]:rowptr[v + 1]]) for v in range(n)]
+    out = [[0] * n for _ in range(r)]
+    for v in range(n):
+        stack = [(v, 0)]
+        while stack:
+            x, length = stack.pop()
+            if length >= 1:
+                out[length - 1][x] += 1
+            if length < r:
+                for y in nbr[x]:
+                    stack.append((y, length + 1))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_inbound_walks_are_outbound_walks_of_the_reverse_graph(seed):
+    rng = np.random.default_rng(470 + seed)
+    n = int(rng.integers(5, 9))
+    rowptr, col = _random_graph(n, 0.35, rng, directed=True)
+    g = gg.Graph(rowptr, col)
+    rev = gg.reverse(g)
+    assert rev.nnz == g.nnz
+    assert oracle.walks_exact(rev.rowptr, rev.col, 5) == _brute_inbound_walks(rowptr, col, 5)
+    assert np.array_equal(gg.reverse(rev).rowptr, g.rowptr) and np.array_equal(gg.reverse(rev).col, g.col)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_dynamic_session_directed_equals_static_recompute(seed):
     g = gg.orient(gg.rmat(9, 8, seed=520 + seed), seed)
