@@ -116,6 +116,8 @@ void free_iter(katz_handle* h) {
     dfree(h, b.lb);
     dfree(h, b.ub);
     dfree(h, b.active);
+    dfree(h, b.alist[0]);
+    dfree(h, b.alist[1]);
     dfree(h, b.cand_l);
     dfree(h, b.cand_u);
     dfree(h, b.cand_id);
@@ -152,6 +154,8 @@ katz_status ensure_iter_buffers(katz_handle* h) {
     KALLOC(b.ub, n);
     if (h->fp32) KALLOC(b.c32, n);
     KALLOC(b.active, n);
+    KALLOC(b.alist[0], n);
+    KALLOC(b.alist[1], n);
     KALLOC(b.cand_l, n);
     KALLOC(b.cand_u, n);
     KALLOC(b.cand_id, n);
@@ -731,6 +735,8 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     }
     h->deg_max = hv.degmax;
     h->D = std::max<int64_t>(h->opts.deg_bound, hv.degmax);
+    for (int c = 0; c < NUM_CLASSES; ++c) h->cls_start[c] = hv.cs[c];
+    h->classes_exact = true;
     // rows of degree > 2048 / > 128 / > 16 come first: classes >= 13 / >= 9 / >= 6
     const int64_t row_warp = (int64_t)hv.cs[12], row_octet = (int64_t)hv.cs[8], row_thread = (int64_t)hv.cs[5];
     // chunk table of the CHUNK rows, on the device (every CHUNK row holds more
@@ -808,14 +814,28 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
     h->criterion = KATZ_CRIT_TOPK;
     h->b.use_cond = 0;
     h->ranked = false;
-    h->launches = 3;  // init_walk, deg_hist, kth_degree
+    h->launches = h->classes_exact ? 3 : 4;  // init_walk, cert_init, theta_0 (one or two kernels)
     h->big_paths = 0;
     cudaError_t e;
     if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
     if ((e = cudaMemsetAsync(h->b.ctrl, 0, sizeof(Ctrl), h->stream)) != cudaSuccess) return cuda_fail(h, e, "memset ctrl");
     if ((e = launch_init_walk(h->g, h->b, p, h->fp32, h->stream)) != cudaSuccess) return cuda_fail(h, e, "init");
     if ((e = launch_cert_init(h->b, p, h->stream)) != cudaSuccess) return cuda_fail(h, e, "init levels");
-    if ((e = launch_theta0(h->g, h->b, p, h->d_deghist, h->D, h->stream)) != cudaSuccess) return cuda_fail(h, e, "theta0");
+    if (h->classes_exact) {
+        // the degree class holding the k-th largest degree: classes are laid
+        // out from the highest down, class c (>= 1) ends where class c-1 starts
+        const int64_t n = h->g.n;
+        auto end_of = [&](int c) -> int64_t { return c >= 1 ? (int64_t)h->cls_start[c - 1] : n; };
+        int c = NUM_CLASSES - 1;
+        while (c > 0 && end_of(c) < k_eff) --c;
+        const int64_t a = (int64_t)h->cls_start[c];
+        const int64_t lo = c == 0 ? -1 : (c == 1 ? 0 : (int64_t)1 << (c - 2));
+        const int bits = c >= 2 ? c - 2 : 0;
+        if ((e = launch_theta0_class(h->g, h->b, p, a, end_of(c), lo, bits, k_eff - a, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "theta0");
+    } else if ((e = launch_theta0(h->g, h->b, p, h->d_deghist, h->D, h->stream)) != cudaSuccess) {
+        return cuda_fail(h, e, "theta0");
+    }
     st = run_loop(h);
     if (st != KATZ_OK) return st;
     if ((e = cudaEventRecord(h->ev1, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
@@ -1127,6 +1147,7 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
         std::swap(g.col, h->col_spare);
         std::swap(h->col_cap, h->col_spare_cap);
         g.nnz = nnz_new;
+        h->classes_exact = false;  // rows keep their place while their degrees change
         if ((e = dyn_clear(g, d, m, h->stream)) != cudaSuccess) return cuda_fail(h, e, "clear batch");
         h->launches += 1;
         // chunk table of the CHUNK rows from their new degrees

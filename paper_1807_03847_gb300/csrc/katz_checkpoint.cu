@@ -219,6 +219,8 @@ katz_status katz_restore(katz_h* out, const void* buf, uint64_t bytes, const kat
         katz_destroy(h);
         return st;
     }
+    hd.ctrl.list_ready = 0;  // the active list is not in the image: rebuilt from the flags
+    hd.ctrl.n_list_next = 0;
     Image im{Image::READ, h, (unsigned char*)buf, bytes};
     im.pos = sizeof(hd);
     h->trace.resize((size_t)hd.trace_len);

@@ -56,6 +56,10 @@ struct Ctrl {
     double los, his;     // same for the stored s_r of the current level
     unsigned long long smax_bits, smax_prev_bits;  // max s_r over M (this / previous level)
     unsigned long long tailw_bits, roundw_bits;    // max tail width / rounding width over M
+    // the active set M as a compact list, kept by the count kernel
+    int32_t list_ready;  // 1: alist[list_cur] holds exactly the active nodes (n_list of them)
+    int32_t list_cur;
+    unsigned long long n_list, n_list_next;
 };
 
 // Per-call constants.
@@ -151,6 +155,7 @@ struct IterBuffers {
     double* lb = nullptr;      // FP32-certified mode: stored bounds of active nodes, kept
     double* ub = nullptr;      //   monotone (l = max over levels, u = min over levels)
     uint8_t* active = nullptr;
+    int32_t* alist[2] = {nullptr, nullptr};  // [n] each: the active nodes (internal ids), double-buffered
     double* cand_l = nullptr;
     double* cand_u = nullptr;
     int32_t* cand_id = nullptr;
@@ -261,6 +266,10 @@ cudaError_t launch_validate_csr(const DeviceGraph& g, unsigned long long* d_bad,
                                 cudaStream_t st);
 cudaError_t launch_init_walk(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                              cudaStream_t st);
+// theta_0 from the kk-th largest degree among rows [a, bend) of one exact
+// degree class (degrees in (lo, lo + 2^bits])
+cudaError_t launch_theta0_class(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int64_t a,
+                                int64_t bend, int64_t lo, int bits, int64_t kk, cudaStream_t st);
 cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const IterParams& p,
                           uint32_t* d_deghist, int64_t D, cudaStream_t st);
 cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,

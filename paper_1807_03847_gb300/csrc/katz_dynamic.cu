@@ -563,6 +563,8 @@ __global__ void theta_lb_kernel(const int32_t* __restrict__ topk_id, const int32
         ctrl->stop = 0;
         ctrl->flags = 0;
         ctrl->converged = 0;
+        ctrl->list_ready = 0;  // every node is reactivated: the next count scans all of V
+        ctrl->n_list_next = 0;
     }
 }
 

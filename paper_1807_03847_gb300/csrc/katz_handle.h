@@ -19,6 +19,10 @@ struct katz_handle {
     int64_t deg_max = 0;
     int64_t D = 0;  // degree bound used for gamma
     int sum_depth = 1;   // longest addition chain of one SpMV row sum
+    // first internal id of each degree class of the relabelling; exact until
+    // an update batch changes degrees (theta_0 then falls back to a histogram)
+    uint64_t cls_start[katz::NUM_CLASSES] = {};
+    bool classes_exact = false;
     int f32_from = 0x7fffffff;  // first FP32 level of the last ranking
     katz::IterBuffers b;
     katz::IterParams p{};

@@ -95,6 +95,17 @@ __global__ void deg_hist_kernel(const Off* __restrict__ rowptr, int64_t n, uint3
     }
 }
 
+// theta_0 from the k-th largest degree: level 1 is always FP64, s_1 = alpha
+// * deg, c64 = 0 + s_1, c32 = 0, and l_1 grows with the degree
+template <typename T>
+__device__ __forceinline__ void set_theta0(long long found, const IterParams& p, Ctrl* ctrl) {
+    const T s1 = scale<T>(p.alpha, (T)found);
+    const double sd = (double)s1;
+    double l, u;
+    node_bounds(add<double>(0.0, sd), 0.0, sd, p, bstate(ctrl), l, u);
+    ctrl->theta_prev = l;
+}
+
 template <typename T>
 __global__ void kth_degree_kernel(const uint32_t* __restrict__ hist, int64_t D, IterParams p, Ctrl* ctrl) {
     __shared__ unsigned long long part[SELECT_THREADS];
@@ -124,14 +135,67 @@ __global__ void kth_degree_kernel(const uint32_t* __restrict__ hist, int64_t D, 
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        // level 1 is always FP64: s_1 = alpha * deg, c64 = 0 + s_1, c32 = 0
-        const T s1 = scale<T>(p.alpha, (T)found);
-        const double sd = (double)s1;
-        double l, u;
-        node_bounds(add<double>(0.0, sd), 0.0, sd, p, bstate(ctrl), l, u);
-        ctrl->theta_prev = l;
+    if (tid == 0) set_theta0<T>(found, p, ctrl);
+}
+
+// theta_0 while the degree classes of the relabelling are exact: the k-th
+// largest degree is the kk-th largest among the rows [a, b) of one class,
+// whose degrees lie in (lo, lo + 2^bits]; a radix select of the offset
+// d - lo - 1 over 11-bit digits from the top, each digit one shared-memory
+// histogram of those rows.
+template <typename Off, typename T>
+__global__ void __launch_bounds__(SELECT_THREADS)
+kth_degree_class_kernel(const Off* __restrict__ rowptr, int64_t a, int64_t b, int64_t lo, int bits, int64_t kk,
+                        IterParams p, Ctrl* ctrl) {
+    constexpr int DIGIT = 11;
+    __shared__ unsigned int hist[1 << DIGIT];
+    __shared__ int s_digit;
+    __shared__ long long s_k;
+    const int tid = threadIdx.x, lane = tid & 31;
+    long long prefix = 0, k = kk;
+    for (int hi = bits; hi > 0;) {
+        const int w = min(DIGIT, hi), sh = hi - w, nb = 1 << w;
+        for (int q = tid; q < nb; q += SELECT_THREADS) hist[q] = 0;
+        if (tid == 0) {  // a valid fallback (the smallest value the digit can take)
+            s_digit = 0;
+            s_k = 1;
+        }
+        __syncthreads();
+        for (int64_t u = a + tid; u < b; u += SELECT_THREADS) {
+            const long long o = (long long)rowptr[u + 1] - (long long)rowptr[u] - lo - 1;
+            if (o >= 0 && (o >> hi) == (prefix >> hi)) atomicAdd(&hist[(o >> sh) & (nb - 1)], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {  // lane l sums the bins [top - per, top), counted from the highest bin down
+            const int per = (nb + 31) / 32, top = nb - lane * per;
+            unsigned long long sum = 0;
+            for (int q = top - 1; q >= max(0, top - per); --q) sum += hist[q];
+            unsigned long long incl = sum;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long y = __shfl_up_sync(FULL, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const unsigned long long excl = incl - sum;
+            if (excl < (unsigned long long)k && incl >= (unsigned long long)k) {
+                unsigned long long cum = excl;
+                for (int q = top - 1; q >= max(0, top - per); --q) {
+                    if (cum + hist[q] >= (unsigned long long)k) {
+                        s_digit = q;
+                        s_k = k - (long long)cum;
+                        break;
+                    }
+                    cum += hist[q];
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (long long)s_digit << sh;
+        k = s_k;
+        hi = sh;
+        __syncthreads();  // hist, s_digit and s_k are rewritten by the next digit
     }
+    if (tid == 0) set_theta0<T>(lo + 1 + prefix, p, ctrl);
 }
 
 // ---------------------------------------------------------------------------
@@ -146,6 +210,101 @@ struct SelEntry {
 
 __device__ __forceinline__ bool sel_before(const SelEntry& a, const SelEntry& b) {
     return a.key > b.key || (a.key == b.key && a.id < b.id);
+}
+
+// A bitonic sort of E * SELECT_THREADS entries by sel_before, entry
+// e = j * SELECT_THREADS + tid held in register j of thread tid.  A compare
+// at distance d pairs e with e ^ d: for d < 32 the partner is in the same
+// warp (shuffles), for d >= SELECT_THREADS in the same thread, and only the
+// distances in between go through shared memory (one barrier on each side).
+// The first cnt entries of sel are sorted (the rest padding that sorts
+// last); the first kk go out as the top-k and entry kk-1 gives theta.
+__device__ __forceinline__ SelEntry shfl_entry(const SelEntry& a, int d) {
+    SelEntry b;
+    b.key = __shfl_xor_sync(FULL, a.key, d);
+    b.id = __shfl_xor_sync(FULL, a.id, d);
+    b.src = __shfl_xor_sync(FULL, a.src, d);
+    return b;
+}
+
+// entry e holding `own` meets its partner's `other` in a network block of
+// `size` (ascending when e & size == 0): it keeps the earlier of the two if
+// it is the lower position of an ascending pair or the upper of a
+// descending one, else the later.  Only padding entries compare equal, and
+// those are identical.
+__device__ __forceinline__ SelEntry pick(const SelEntry& own, const SelEntry& other, int e, int d, int size) {
+    const bool lower = (e & d) == 0, up = (e & size) == 0;
+    const bool own_first = sel_before(own, other);
+    return (lower == up) == own_first ? own : other;
+}
+
+// the compares at distance DJ * SELECT_THREADS, inside each thread
+template <int E, int DJ>
+__device__ __forceinline__ void step_in_thread(SelEntry (&x)[E], int size, int tid) {
+    if constexpr (DJ < E) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            if (j & DJ) continue;
+            const int e = j * SELECT_THREADS + tid;
+            const bool up = (e & size) == 0;
+            const SelEntry a = x[j], b = x[j | DJ];
+            const bool swap = up ? sel_before(b, a) : sel_before(a, b);
+            x[j] = swap ? b : a;
+            x[j | DJ] = swap ? a : b;
+        }
+    }
+}
+
+template <int E>
+__device__ void sort_and_emit(SelEntry* sel, unsigned int cnt, int kk, const double* __restrict__ cu,
+                              int32_t* topk_id, double* topk_l, double* topk_u, Ctrl* ctrl) {
+    constexpr int P = E * SELECT_THREADS;
+    const int tid = threadIdx.x;
+    SelEntry x[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int e = j * SELECT_THREADS + tid;
+        x[j] = e < (int)cnt ? sel[e] : SelEntry{0ULL, 0x7fffffff, -1};
+    }
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int d = size >> 1; d > 0; d >>= 1) {
+            if (d >= SELECT_THREADS) {
+                const int dj = d / SELECT_THREADS;  // 1, 2 or 4: register indices stay compile-time
+                if (dj == 1) step_in_thread<E, 1>(x, size, tid);
+                else if (dj == 2) step_in_thread<E, 2>(x, size, tid);
+                else step_in_thread<E, 4>(x, size, tid);
+            } else if (d >= 32) {
+                __syncthreads();  // earlier readers of sel are done
+#pragma unroll
+                for (int j = 0; j < E; ++j) sel[j * SELECT_THREADS + tid] = x[j];
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const int e = j * SELECT_THREADS + tid;
+                    x[j] = pick(x[j], sel[e ^ d], e, d, size);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const int e = j * SELECT_THREADS + tid;
+                    x[j] = pick(x[j], shfl_entry(x[j], d), e, d, size);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int e = j * SELECT_THREADS + tid;
+        if (e < kk) {
+            topk_id[e] = x[j].id;
+            topk_l[e] = __longlong_as_double((long long)x[j].key);
+            topk_u[e] = cu[x[j].src];
+        }
+        if (e == kk - 1) {
+            ctrl->theta = __longlong_as_double((long long)x[j].key);
+            ctrl->theta_id = x[j].id;
+        }
+    }
 }
 
 template <typename T>
@@ -202,11 +361,20 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
         return;
     }
     const double tau = s_tau;
-    for (unsigned long long q = tid; q < nc; q += SELECT_THREADS) {
-        const double l = cl[q];
-        if (l >= tau) {
-            const unsigned int pos = atomicAdd(&s_cnt, 1u);
-            if (pos < (unsigned int)SELECT_CAP) sel[pos] = SelEntry{(unsigned long long)__double_as_longlong(l), cid[q], (int32_t)q};
+    // the candidates with l >= tau, one shared-memory atomic per warp
+    const int lane = tid & 31;
+    for (unsigned long long base = 0; base < nc; base += SELECT_THREADS) {
+        const unsigned long long q = base + tid;
+        const double l = q < nc ? cl[q] : -1.0;
+        const bool take = q < nc && l >= tau;
+        const unsigned m = __ballot_sync(FULL, take);
+        unsigned int wpos = 0;
+        if (lane == 0 && m) wpos = atomicAdd(&s_cnt, (unsigned int)__popc(m));
+        wpos = __shfl_sync(FULL, wpos, 0);
+        if (take) {
+            const unsigned int pos = wpos + __popc(m & ((1u << lane) - 1u));
+            if (pos < (unsigned int)SELECT_CAP)
+                sel[pos] = SelEntry{(unsigned long long)__double_as_longlong(l), cid[q], (int32_t)q};
         }
     }
     __syncthreads();
@@ -215,105 +383,127 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
         if (tid == 0) atomicOr(&ctrl->flags, F_NEED_BIG);
         return;
     }
-    int P = 1;
-    while (P < (int)cnt) P <<= 1;
-    for (int q = (int)cnt + tid; q < P; q += SELECT_THREADS) sel[q] = SelEntry{0ULL, 0x7fffffff, -1};
-    __syncthreads();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int q = tid; q < (P >> 1); q += SELECT_THREADS) {
-                const int pos = 2 * q - (q & (stride - 1));
-                const int partner = pos + stride;
-                const SelEntry a = sel[pos], b = sel[partner];
-                const bool up = (pos & size) == 0;
-                const bool sw = up ? sel_before(b, a) : sel_before(a, b);
-                if (sw) {
-                    sel[pos] = b;
-                    sel[partner] = a;
-                }
-            }
-            __syncthreads();
-        }
-    }
     const int kk = (int)min((long long)p.k, (long long)cnt);
-    for (int q = tid; q < kk; q += SELECT_THREADS) {
-        const SelEntry a = sel[q];
-        topk_id[q] = a.id;
-        topk_l[q] = __longlong_as_double((long long)a.key);
-        topk_u[q] = cu[a.src];
-    }
+    if (cnt <= (unsigned int)SELECT_THREADS) sort_and_emit<1>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
+    else if (cnt <= 2u * SELECT_THREADS) sort_and_emit<2>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
+    else if (cnt <= 4u * SELECT_THREADS) sort_and_emit<4>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
+    else sort_and_emit<8>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
     if (tid == 0) {
         ctrl->k_eff = kk;
         ctrl->tau = tau;
-        if (kk > 0) {
-            ctrl->theta = __longlong_as_double((long long)sel[kk - 1].key);
-            ctrl->theta_id = sel[kk - 1].id;
-        }
     }
 }
 
 // ---------------------------------------------------------------------------
 // count: deactivate nodes of M outside the top-k with u_r - eps < theta_r and
 // count the ones that remain (converged() returns false if any remain).
+//
+// M is read from a compact list of its nodes: the first count after all
+// nodes became active scans the flags of all of V instead.  Either way the
+// survivors are written, in tiles, to the other list buffer (one atomic per
+// tile for its place), which finalize then makes current.  The order of a
+// list is arbitrary; nothing computed from it depends on the order.
 // ---------------------------------------------------------------------------
+constexpr int COUNT_THREADS = 256;
+constexpr int COUNT_U = 4;  // nodes per thread and tile, their loads issued together
+constexpr int COUNT_TILE = COUNT_THREADS * COUNT_U;
+
 template <typename T>
-__global__ void count_kernel(const T* walk, const double* __restrict__ c, const double* __restrict__ c32,
-                             const double* __restrict__ lb, const double* __restrict__ ub,
-                             const int32_t* __restrict__ perm, uint8_t* active, Ctrl* ctrl, IterParams p) {
+__global__ void __launch_bounds__(COUNT_THREADS)
+count_kernel(const T* walk, const double* __restrict__ c, const double* __restrict__ c32,
+             const double* __restrict__ lb, const double* __restrict__ ub, const int32_t* __restrict__ perm,
+             uint8_t* active, int32_t* alist0, int32_t* alist1, Ctrl* ctrl, IterParams p) {
+    __shared__ int s_wcnt[COUNT_THREADS / 32];
+    __shared__ unsigned long long s_base;
     if (ctrl->stop || (ctrl->flags & F_NEED_BIG)) return;
     const int r_cur = ctrl->r + 1;
     const int f32_from = ctrl->f32_from;
     const BState bs = bstate(ctrl);
     const double th = ctrl->theta;
     const int32_t thid = ctrl->theta_id;
+    const bool full = !ctrl->list_ready;
+    const int cur = ctrl->list_cur;
+    const int32_t* in = cur ? alist1 : alist0;
+    int32_t* out = cur ? alist0 : alist1;
+    const int64_t total = full ? p.n : (int64_t)ctrl->n_list;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     unsigned long long cross = 0, act = 0;
     double smax = 0.0, tailw = 0.0, roundw = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // l, th >= 0 (sums of non-negative terms): they order like their bit patterns
     const long long th_bits = __double_as_longlong(th);
-    // four nodes per thread and pass, their loads issued before any decision
-    constexpr int U = 4;
-    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v0 < p.n; v0 += U * stride) {
-        bool on[U];
-        double l[U], u[U];
-        int32_t ov[U];
+    // the trip count depends on the block only, so the barriers below are uniform
+    for (int64_t t0 = (int64_t)blockIdx.x * COUNT_TILE; t0 < total; t0 += (int64_t)gridDim.x * COUNT_TILE) {
+        bool on[COUNT_U], keep[COUNT_U];
+        int32_t v[COUNT_U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int64_t v = v0 + q * stride;
-            on[q] = v < p.n && active[v];
+        for (int q = 0; q < COUNT_U; ++q) {
+            const int64_t i = t0 + q * COUNT_THREADS + tid;
+            on[q] = i < total;
+            v[q] = on[q] ? (full ? (int32_t)i : in[i]) : 0;
         }
+        if (full) {
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int64_t v = v0 + q * stride;
-            l[q] = on[q] ? lb[v] : 0.0;  // stored by the SpMV epilogue of this level
-            u[q] = on[q] ? ub[v] : 0.0;
-            ov[q] = on[q] ? perm[v] : 0;  // ties are broken by the original id
+            for (int q = 0; q < COUNT_U; ++q) on[q] = on[q] && active[v[q]];
         }
+        double l[COUNT_U], u[COUNT_U];
+        int32_t ov[COUNT_U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
+        for (int q = 0; q < COUNT_U; ++q) {
+            l[q] = on[q] ? lb[v[q]] : 0.0;  // stored by the SpMV epilogue of this level
+            u[q] = on[q] ? ub[v[q]] : 0.0;
+            ov[q] = on[q] ? perm[v[q]] : 0;  // ties are broken by the original id
+        }
+        int mine = 0;
+#pragma unroll
+        for (int q = 0; q < COUNT_U; ++q) {
+            keep[q] = false;
             if (!on[q]) continue;
-            const int64_t v = v0 + q * stride;
             const long long l_bits = __double_as_longlong(l[q]);
             const bool top = l_bits > th_bits || (l_bits == th_bits && ov[q] <= thid);
             if (!top) {
                 if (__dsub_rn(u[q], p.eps) < th) {
-                    active[v] = 0;
+                    active[v[q]] = 0;
                     continue;
                 }
                 ++cross;
             }
-            ++act;
+            keep[q] = true;
+            ++mine;
             if (p.cert) {
-                const double sv = walk_value(walk, p, f32_from, r_cur, v);
-                const double c64v = c[v], c32v = c32 ? c32[v] : 0.0;
+                const double sv = walk_value(walk, p, f32_from, r_cur, v[q]);
+                const double c64v = c[v[q]], c32v = c32 ? c32[v[q]] : 0.0;
                 smax = fmax(smax, sv);
                 tailw = fmax(tailw, p.ag * sv);
                 roundw = fmax(roundw, c64v * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32));
             }
         }
+        act += (unsigned long long)mine;
+        // places of the survivors: scan within the warp, then over the warps
+        int incl = mine;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) s_wcnt[wid] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            int run = 0;
+            for (int w = 0; w < COUNT_THREADS / 32; ++w) {
+                const int x = s_wcnt[w];
+                s_wcnt[w] = run;
+                run += x;
+            }
+            s_base = run ? atomicAdd(&ctrl->n_list_next, (unsigned long long)run) : 0ull;
+        }
+        __syncthreads();
+        unsigned long long pos = s_base + (unsigned long long)(s_wcnt[wid] + incl - mine);
+#pragma unroll
+        for (int q = 0; q < COUNT_U; ++q)
+            if (keep[q]) out[pos++] = v[q];
+        __syncthreads();  // s_wcnt and s_base are rewritten by the next tile
     }
-    // block totals first: one atomic per block and counter (same-address
-    // atomics from every warp were the cost of this pass)
+    // block totals first: one atomic per block and counter
     __shared__ unsigned long long s_cross[32], s_act[32];
     __shared__ double s_smax[32], s_tailw[32], s_roundw[32];
     for (int off = 16; off; off >>= 1) {
@@ -323,7 +513,7 @@ __global__ void count_kernel(const T* walk, const double* __restrict__ c, const 
         tailw = fmax(tailw, __shfl_xor_sync(FULL, tailw, off));
         roundw = fmax(roundw, __shfl_xor_sync(FULL, roundw, off));
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nw = blockDim.x >> 5;
     if (lane == 0) {
         s_cross[wid] = cross;
         s_act[wid] = act;
@@ -430,6 +620,11 @@ __global__ void finalize_kernel(const double* __restrict__ topk_l, const double*
         ctrl->n_cand = 0;
         ctrl->cnt_cross = 0;
         ctrl->n_active = 0;
+        // the survivors of this count become the active list
+        ctrl->list_cur ^= 1;
+        ctrl->n_list = ctrl->n_list_next;
+        ctrl->n_list_next = 0;
+        ctrl->list_ready = 1;
         int stop = conv || r_cur >= p.r_max;
         if (p.cert) {
             const double smax = __longlong_as_double((long long)ctrl->smax_bits);
@@ -609,6 +804,17 @@ cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const Iter
     return cudaGetLastError();
 }
 
+cudaError_t launch_theta0_class(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int64_t a,
+                                int64_t bend, int64_t lo, int bits, int64_t kk, cudaStream_t st) {
+    if (g.off64)
+        kth_degree_class_kernel<int64_t, double><<<1, SELECT_THREADS, 0, st>>>((const int64_t*)g.rowptr, a, bend, lo,
+                                                                               bits, kk, p, b.ctrl);
+    else
+        kth_degree_class_kernel<int32_t, double><<<1, SELECT_THREADS, 0, st>>>((const int32_t*)g.rowptr, a, bend, lo,
+                                                                               bits, kk, p, b.ctrl);
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_kernels() {
     const int smem = SELECT_CAP * (int)sizeof(SelEntry);
     return cudaFuncSetAttribute(select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -626,8 +832,10 @@ cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const Iter
 cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                          cudaStream_t st) {
     (void)fp32;
-    count_kernel<double><<<grid_for(p.n, 256, 152 * 16), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, b.lb, b.ub,
-                                                                       g.perm, b.active, b.ctrl, p);
+    // a fixed grid (the launch may sit in a captured graph); the blocks stride
+    // over tiles of the list, or of V for the first count
+    count_kernel<double><<<grid_for(p.n, COUNT_TILE, 152 * 4), COUNT_THREADS, 0, st>>>(
+        (const double*)b.walk, b.c, b.c32, b.lb, b.ub, g.perm, b.active, b.alist[0], b.alist[1], b.ctrl, p);
     return cudaGetLastError();
 }
 
