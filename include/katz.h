@@ -102,9 +102,11 @@ typedef struct {
     int32_t fp32_levels;   /* FP32-certified mode: levels carried in FP32 */
     int32_t full_levels;   /* dynamic update: levels recomputed for every node */
     int64_t affected;      /* dynamic update: nodes whose walk counts were recomputed */
-    double spmv_ms;        /* profile = 1: summed device time of the SpMV launches */
+    double spmv_ms;        /* profile = 1: summed device time of the SpMV launches of
+                              levels 2..r (level 1 is the degree vector: A 1 = deg, no
+                              walk values are gathered) */
     int64_t launches;      /* kernels this call launched */
-    int32_t spmv_launches; /* SpMV launches this call made */
+    int32_t spmv_launches; /* SpMV launches of levels 2..r this call made */
     int32_t reserved;
 } katz_info;
 

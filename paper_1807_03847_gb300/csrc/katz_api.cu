@@ -185,6 +185,19 @@ cudaError_t launch_iteration(katz_handle* h, cudaEvent_t* ev_pair = nullptr) {
     return launch_finalize(h->b, h->p, h->stream);
 }
 
+// The first iteration of a ranking: level 1 is the degree vector (s_0 = 1,
+// A 1 = deg), one O(n) pass instead of a gather level; then the same check.
+cudaError_t launch_first_iteration(katz_handle* h, cudaEvent_t* ev_pair = nullptr) {
+    cudaError_t e;
+    if (ev_pair && (e = cudaEventRecord(ev_pair[0], h->stream)) != cudaSuccess) return e;
+    if ((e = launch_degree_level(h->g, h->b, h->p, h->stream)) != cudaSuccess) return e;
+    if (ev_pair && (e = cudaEventRecord(ev_pair[1], h->stream)) != cudaSuccess) return e;
+    if ((e = launch_select(h->g, h->b, h->p, h->b.cand_l, h->b.cand_u, h->b.cand_id, h->fp32, h->stream)) != cudaSuccess)
+        return e;
+    if ((e = launch_count(h->g, h->b, h->p, h->fp32, h->stream)) != cudaSuccess) return e;
+    return launch_finalize(h->b, h->p, h->stream);
+}
+
 bool same_params(const IterParams& a, const IterParams& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
 
 void drop_graph(katz_handle* h) {
@@ -299,23 +312,34 @@ katz_status big_select(katz_handle* h) {
 // Graph mode: one graph launch runs the whole loop on the device; the host
 // only steps in when the candidate set outgrows the one-CTA select.
 // Host mode: iterations are launched in batches and ctrl is read between
-// batches (launches after a stop return at once).
-katz_status run_loop(katz_handle* h) {
+// batches (launches after a stop return at once).  done: iterations already
+// enqueued by the caller (profile events of the loop's launches follow theirs).
+// one pair of timing events per iteration up to r_max (profile mode)
+katz_status ensure_prof_events(katz_handle* h) {
     cudaError_t e;
-    const bool graph_mode = h->opts.use_graph && !h->opts.profile;
-    const bool prof = h->opts.profile != 0;
-    const int batch = 4;
-    if (prof && h->sp_ev.size() < 2 * (size_t)(h->opts.r_max + 8)) {
+    if (h->sp_ev.size() < 2 * (size_t)(h->opts.r_max + 8)) {
         for (cudaEvent_t ev : h->sp_ev) cudaEventDestroy(ev);
         h->sp_ev.assign(2 * (size_t)(h->opts.r_max + 8), nullptr);
         for (auto& ev : h->sp_ev)
             if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
     }
+    return KATZ_OK;
+}
+
+katz_status run_loop(katz_handle* h, int done) {
+    cudaError_t e;
+    const bool graph_mode = h->opts.use_graph && !h->opts.profile;
+    const bool prof = h->opts.profile != 0;
+    const int batch = 4;
+    if (prof) {
+        const katz_status s = ensure_prof_events(h);
+        if (s != KATZ_OK) return s;
+    }
     if (graph_mode) {
         katz_status s = ensure_graph(h);
         if (s != KATZ_OK) return s;
     }
-    int launched_iters = 0;
+    int launched_iters = done;
     for (;;) {
         if (graph_mode) {
             if ((e = cudaGraphLaunch(h->graph_exec, h->stream)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
@@ -821,6 +845,7 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
     if ((e = cudaMemsetAsync(h->b.ctrl, 0, sizeof(Ctrl), h->stream)) != cudaSuccess) return cuda_fail(h, e, "memset ctrl");
     if ((e = launch_init_walk(h->g, h->b, p, h->fp32, h->stream)) != cudaSuccess) return cuda_fail(h, e, "init");
     if ((e = launch_cert_init(h->b, p, h->stream)) != cudaSuccess) return cuda_fail(h, e, "init levels");
+    const bool prof = h->opts.profile != 0;
     if (h->classes_exact) {
         // the degree class holding the k-th largest degree: classes are laid
         // out from the highest down, class c (>= 1) ends where class c-1 starts
@@ -836,7 +861,11 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
     } else if ((e = launch_theta0(h->g, h->b, p, h->d_deghist, h->D, h->stream)) != cudaSuccess) {
         return cuda_fail(h, e, "theta0");
     }
-    st = run_loop(h);
+    if (prof && (st = ensure_prof_events(h)) != KATZ_OK) return st;
+    if ((e = launch_first_iteration(h, prof ? &h->sp_ev[0] : nullptr)) != cudaSuccess)
+        return cuda_fail(h, e, "first iteration");
+    h->launches += 4;  // degree level, select, count, finalize
+    st = run_loop(h, 1);
     if (st != KATZ_OK) return st;
     if ((e = cudaEventRecord(h->ev1, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
     if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
@@ -860,10 +889,13 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
         return cuda_fail(h, e, "copy trace");
     h->trace.assign(tr.begin() + 1, tr.begin() + 1 + std::max(0, h->r));
     if (h->opts.use_graph && !h->opts.profile)
-        h->launches += (h->g.layout.row_warp > 0 ? 5 : 4) * ((int64_t)hc.body_runs - h->big_paths);
+        // loop bodies that did work: all finalize runs but the first iteration's
+        // and the big-select reruns
+        h->launches += (h->g.layout.row_warp > 0 ? 5 : 4) *
+                       std::max<int64_t>(0, (int64_t)hc.body_runs - 1 - h->big_paths);
     double spmv_ms = 0.0;
-    if (h->opts.profile) {
-        for (int q = 0; q < h->r && 2 * q + 1 < (int)h->sp_ev.size(); ++q) {
+    if (h->opts.profile) {  // levels 2..r: level 1 reads no walk values
+        for (int q = 1; q < h->r && 2 * q + 1 < (int)h->sp_ev.size(); ++q) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, h->sp_ev[2 * q], h->sp_ev[2 * q + 1]) == cudaSuccess) spmv_ms += t;
         }
@@ -874,7 +906,7 @@ katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz
         std::memset(info, 0, sizeof(*info));
         info->fp32_levels = fp32_levels;
         info->spmv_ms = spmv_ms;
-        info->spmv_launches = h->r;
+        info->spmv_launches = std::max(0, h->r - 1);
         info->launches = h->launches;
         info->r = h->r;
         info->converged = h->converged;
@@ -942,7 +974,9 @@ katz_status katz_rank(katz_h h, double alpha, int32_t criterion, int64_t k, cons
         return cuda_fail(h, e, "init");
     h->launches += 3;
     for (int it = 0; it < p.r_max; ++it) {
-        if ((e = launch_spmv(h->g, h->b, p, false, h->stream)) != cudaSuccess) return cuda_fail(h, e, "spmv");
+        // level 1 is the degree vector (A 1 = deg), one O(n) pass
+        e = it == 0 ? launch_degree_level(h->g, h->b, p, h->stream) : launch_spmv(h->g, h->b, p, false, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "spmv");
         if (criterion == KATZ_CRIT_RANKING)
             e = launch_ranking_check(h->g, h->b, p, h->rs, h->rank_ids, h->stream);
         else if (criterion == KATZ_CRIT_SCORE)
@@ -951,7 +985,7 @@ katz_status katz_rank(katz_h h, double alpha, int32_t criterion, int64_t k, cons
             e = launch_pair_check(h->g, h->b, p, oa, ob, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "criterion");
         if ((e = launch_finalize_crit(h->b, p, h->stream)) != cudaSuccess) return cuda_fail(h, e, "finalize");
-        h->launches += spmv_kernels + check_kernels + 1;
+        h->launches += (it == 0 ? 1 : spmv_kernels) + check_kernels + 1;
         if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "sync");
@@ -984,7 +1018,7 @@ katz_status katz_rank(katz_h h, double alpha, int32_t criterion, int64_t k, cons
         info->time_ms = ms;
         info->nnz = h->g.nnz;
         info->launches = h->launches;
-        info->spmv_launches = h->r;
+        info->spmv_launches = std::max(0, h->r - 1);
     }
     if (!h->converged) return fail(h, KATZ_ENOTCONV, "r_max reached before the criterion held");
     return KATZ_OK;
@@ -1263,7 +1297,7 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
             return cuda_fail(h, e, "re-check sync");
     }
     if (!h->h_ctrl->stop) {
-        st = run_loop(h);
+        st = run_loop(h, 0);
         if (st != KATZ_OK) return st;
     }
     if ((e = cudaEventRecord(h->ev1, h->stream)) != cudaSuccess ||

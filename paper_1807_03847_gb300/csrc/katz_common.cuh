@@ -272,6 +272,8 @@ cudaError_t launch_theta0_class(const DeviceGraph& g, const IterBuffers& b, cons
                                 int64_t bend, int64_t lo, int bits, int64_t kk, cudaStream_t st);
 cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const IterParams& p,
                           uint32_t* d_deghist, int64_t D, cudaStream_t st);
+// level 1 of a ranking (s_1 = alpha deg) in one pass over the rows, fixup included
+cudaError_t launch_degree_level(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, cudaStream_t st);
 cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,
                         cudaStream_t st);
 cudaError_t launch_spmv_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level,

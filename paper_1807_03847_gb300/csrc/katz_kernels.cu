@@ -594,7 +594,10 @@ __global__ void finalize_kernel(const double* __restrict__ topk_l, const double*
     const int tid = threadIdx.x;
     if (tid == 0) bad = 0;
     __syncthreads();
-    if (ctrl->stop) return;
+    if (ctrl->stop) {  // the loop was already over: leave the device-side while loop too
+        if (tid == 0 && use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0);
+        return;
+    }
     if (tid == 0) ctrl->body_runs += 1;
     if (ctrl->flags & F_NEED_BIG) {
         if (tid == 0) {

@@ -460,6 +460,57 @@ __device__ __forceinline__ Epi make_epi(void* y, double* c64, double* c32, doubl
                ctrl->theta_prev, bstate(ctrl), 0};
 }
 
+// Level 1: s_0 = 1, so the exact sum of a row is its length (A 1 = deg) and
+// no walk value is read; a CHUNK row's chunks store their arc counts, which
+// the hub fixup merges as it merges any partials.  Same lane partition and
+// epilogue as the other levels, so every result has the same bits.
+template <typename Off>
+__device__ __forceinline__ void spmv_rows_degree(const Off* __restrict__ rowptr, const SpmvLayout& L, const Epi& ep,
+                                                 const int32_t* __restrict__ chunk_row,
+                                                 const int64_t* __restrict__ chunk_first, double* chunk_part,
+                                                 const IterParams& p) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t b = blockIdx.x;
+    auto deg = [&](int64_t u) { return (double)((int64_t)rowptr[u + 1] - (int64_t)rowptr[u]); };
+    if (b >= L.blk_thread) {  // THREAD rows
+        const int64_t u = L.row_thread + (b - L.blk_thread) * BLOCK + tid;
+        if (u < L.n) finish_row<double>(u, deg(u), ep, p);
+    } else if (b >= L.blk_octet) {  // OCTET rows
+        const int64_t u = L.row_octet + (b - L.blk_octet) * (BLOCK / 8) + (tid >> 3);
+        if ((tid & 7) == 0 && u < L.row_thread) finish_row<double>(u, deg(u), ep, p);
+    } else if (b >= L.blk_warp) {  // WARP rows
+        const int64_t u = L.row_warp + (b - L.blk_warp) * WARPS + wid;
+        if (lane == 0 && u < L.row_octet) finish_row<double>(u, deg(u), ep, p);
+    } else {  // CHUNK rows
+        const int64_t ch = b * WARPS + wid;
+        if (lane == 0 && ch < L.chunks) {
+            const int64_t u = chunk_row[ch];
+            const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+            const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+            XAcc s = xacc_zero();
+            xacc_add(s, (double)(j1 - j0));
+            store_part(chunk_part, ch, s);
+        }
+    }
+}
+
+// Level 1 of a ranking as one pass over all rows, any row mode: s_1 = alpha
+// deg with the epilogue of every level (no chunk partials: no fixup follows).
+// The same sums and epilogue as spmv_rows_degree, in a grid sized for O(n)
+// work instead of the gather levels' one block per row group.
+template <typename Off>
+__global__ void degree_level_kernel(const Off* __restrict__ rowptr, int64_t n, double* walk, double* c64,
+                                    double* c32, double* lb, double* ub, uint8_t* active,
+                                    const int32_t* __restrict__ perm, double* cand_l, double* cand_u,
+                                    int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
+    if (ctrl->stop) return;
+    const Epi ep = make_epi(walk_slot(walk, p, 1), c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id,
+                            cand_cap, ctrl);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
+        finish_row<double>(u, (double)((int64_t)rowptr[u + 1] - (int64_t)rowptr[u]), ep, p);
+}
+
 // Six 256-thread blocks per SM (40 registers): the gathers need the warps in
 // flight more than the lanes need registers.
 template <typename Off>
@@ -477,7 +528,9 @@ spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col
     double* ys = walk_slot(walk, p, r_cur);
     Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
     ep.store_only = store_level > 0;
-    if (r_cur < f32_from)
+    if (r_cur == 1)  // always an FP64 level
+        spmv_rows_degree<Off>(rowptr, L, ep, chunk_row, chunk_first, chunk_part, p);
+    else if (r_cur < f32_from)
         spmv_rows<Off, double, double>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
     else if (r_cur == f32_from)
         spmv_rows<Off, double, float>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
@@ -564,6 +617,19 @@ cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterPa
                         cudaStream_t st) {
     (void)fp32;
     return spmv_launch(g, b, p, 0, st);
+}
+
+cudaError_t launch_degree_level(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>(std::max<int64_t>((g.n + BLOCK - 1) / BLOCK, 1), 152 * 8);
+    if (g.off64)
+        degree_level_kernel<int64_t><<<(unsigned)blocks, BLOCK, 0, st>>>(
+            (const int64_t*)g.rowptr, g.n, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, b.cand_l,
+            b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
+    else
+        degree_level_kernel<int32_t><<<(unsigned)blocks, BLOCK, 0, st>>>(
+            (const int32_t*)g.rowptr, g.n, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, b.cand_l,
+            b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_spmv_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level,
