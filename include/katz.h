@@ -223,6 +223,18 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
                                     const uint8_t* is_insert, int64_t m, katz_info* info);
 
 /*
+ * The number conversions of the FP32-certified levels, for tests and
+ * diagnostics: out[i] = in[i] rounded to binary32 (to nearest, ties to even;
+ * subnormal results kept, 0 below half the smallest subnormal) and
+ * back[i] = out[i] widened exactly to binary64, computed on the device with
+ * the integer routines the SpMV epilogue uses.  in holds n non-negative finite
+ * values; in, out and back are device pointers (n elements each).  Runs on
+ * the default stream and returns when done.
+ * Errors: KATZ_EINVAL (NULL or host pointer, n < 0), KATZ_ECUDA.
+ */
+katz_status katz_convert_f64_f32(const double* in, int64_t n, float* out, double* back);
+
+/*
  * Checkpoint and restore of a ranked handle (the state Sec. 4 keeps between
  * batches: the walk history s_1..s_r, c_r, the active set M and r, with the
  * graph and the last ranking).  katz_checkpoint_size gives the bytes of the

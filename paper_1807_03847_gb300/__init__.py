@@ -19,7 +19,7 @@ __all__ = [
     "KatzError", "katz_opts", "katz_info", "katz_default_opts", "katz_create_csr", "katz_destroy",
     "katz_rank_static", "katz_rank", "katz_checkpoint", "katz_restore", "KATZ_CRIT_TOPK", "KATZ_CRIT_RANKING", "KATZ_CRIT_SCORE", "KATZ_CRIT_PAIR",
     "katz_get_ranking", "katz_get_bounds", "katz_get_walk", "katz_get_trace",
-    "katz_apply_update_batch", "katz_certify_topk_noalloc", "katz_server_opts", "katz_request_result",
+    "katz_apply_update_batch", "katz_certify_topk_noalloc", "katz_convert_f64_f32", "katz_server_opts", "katz_request_result",
     "katz_server_default_opts", "Server", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT",
     "KATZ_MAX_K", "library_path",
 ]
@@ -100,6 +100,7 @@ def _load():
         "katz_get_trace": (ctypes.c_int, [P, P, i32]),
         "katz_apply_update_batch": (ctypes.c_int, [P, P, P, P, i64, ctypes.POINTER(katz_info)]),
         "katz_certify_topk_noalloc": (ctypes.c_int, [P, P, i64, i64, dbl, P, P, P]),
+        "katz_convert_f64_f32": (ctypes.c_int, [P, i64, P, P]),
         "katz_server_default_opts": (None, [ctypes.POINTER(katz_server_opts)]),
         "katz_server_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(katz_server_opts)]),
         "katz_server_attach": (ctypes.c_int, [P, P, i64]),
@@ -246,6 +247,19 @@ def katz_apply_update_batch(h, src, dst, is_insert, m: int | None = None, check:
         _check(h, st, "katz_apply_update_batch")
     info.status = st
     return info
+
+
+def katz_convert_f64_f32(x):
+    """The FP32-certified levels' rounding of the non-negative float64 device
+    tensor x to float32 and the exact widening back (katz_convert_f64_f32)."""
+    import torch
+    assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+    out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    back = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    st = _load().katz_convert_f64_f32(x.data_ptr(), x.numel(), out.data_ptr(), back.data_ptr())
+    if st != 0:
+        raise KatzError(st, "katz_convert_f64_f32")
+    return out, back
 
 
 def katz_certify_topk_noalloc(lower, upper, k: int, eps: float, ids_out, certified_out, stream=None) -> None:

@@ -116,6 +116,7 @@ void free_iter(katz_handle* h) {
     dfree(h, b.lb);
     dfree(h, b.ub);
     dfree(h, b.active);
+    dfree(h, b.s32);
     dfree(h, b.alist[0]);
     dfree(h, b.alist[1]);
     dfree(h, b.cand_l);
@@ -153,6 +154,7 @@ katz_status ensure_iter_buffers(katz_handle* h) {
     KALLOC(b.lb, n);  // bounds of the active nodes at the last level (cert mode: monotone)
     KALLOC(b.ub, n);
     if (h->fp32) KALLOC(b.c32, n);
+    if (h->fp32) KALLOC(b.s32, n);
     KALLOC(b.active, n);
     KALLOC(b.alist[0], n);
     KALLOC(b.alist[1], n);
@@ -534,6 +536,14 @@ katz_status reverse_input(katz_handle* h, int64_t n, int64_t nnz, const int64_t*
 }  // namespace katz
 
 extern "C" {
+
+katz_status katz_convert_f64_f32(const double* in, int64_t n, float* out, double* back) {
+    if (n < 0 || (n > 0 && (!in || !out || !back))) return KATZ_EINVAL;
+    if (n > 0 && (!is_device_ptr(in) || !is_device_ptr(out) || !is_device_ptr(back))) return KATZ_EINVAL;
+    cudaError_t e = launch_convert(in, n, out, back, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    return e == cudaSuccess ? KATZ_OK : KATZ_ECUDA;
+}
 
 void katz_default_opts(katz_opts* o) {
     if (!o) return;

@@ -91,10 +91,16 @@ struct IterParams {
 // the bounds gets bit-identical values (no contraction into FMA).
 struct BState {
     double lo64, hi64, lo32, hi32, los, his;
+    double a_lo, a_hi;  // cert mode: RD(alpha los) and RU(alpha gamma his), the tail factors of l and u
 };
 
-__device__ __forceinline__ BState bstate(const Ctrl* c) {
-    return BState{c->lo64, c->hi64, c->lo32, c->hi32, c->los, c->his};
+__device__ __forceinline__ BState bstate(const Ctrl* c, const IterParams& p) {
+    BState b{c->lo64, c->hi64, c->lo32, c->hi32, c->los, c->his, 0.0, 0.0};
+    if (p.cert) {
+        b.a_lo = __dmul_rd(p.alpha, b.los);
+        b.a_hi = __dmul_ru(p.ag_hi, b.his);
+    }
+    return b;
 }
 
 __device__ __forceinline__ void node_bounds(double c64, double c32, double s_r, const IterParams& p,
@@ -104,10 +110,20 @@ __device__ __forceinline__ void node_bounds(double c64, double c32, double s_r, 
         u = __dadd_rn(c64, __dmul_rn(p.ag, s_r));
         return;
     }
-    const double c_lo = __dadd_rd(__dmul_rd(c64, b.lo64), __dmul_rd(c32, b.lo32));
-    const double c_hi = __dadd_ru(__dmul_ru(c64, b.hi64), __dmul_ru(c32, b.hi32));
-    l = p.undirected ? __dadd_rd(c_lo, __dmul_rd(__dmul_rd(p.alpha, s_r), b.los)) : c_lo;
-    u = __dadd_ru(c_hi, __dmul_ru(__dmul_ru(p.ag_hi, s_r), b.his));
+    // c32 = +0 (every node before the switch to FP32 levels): its terms add
+    // exactly nothing, and the FP64 pipe (narrow on this GPU) is spared them
+    double c_lo, c_hi;
+    if (__double_as_longlong(c32) == 0) {
+        c_lo = __dmul_rd(c64, b.lo64);
+        c_hi = __dmul_ru(c64, b.hi64);
+    } else {
+        c_lo = __dadd_rd(__dmul_rd(c64, b.lo64), __dmul_rd(c32, b.lo32));
+        c_hi = __dadd_ru(__dmul_ru(c64, b.hi64), __dmul_ru(c32, b.hi32));
+    }
+    // s_r >= 0 and the exact level value lies in [s_r los, s_r his]: with the
+    // factors rounded outward, s_r a_lo <= alpha s_exact and s_r a_hi >= alpha gamma s_exact
+    l = p.undirected ? __dadd_rd(c_lo, __dmul_rd(s_r, b.a_lo)) : c_lo;
+    u = __dadd_ru(c_hi, __dmul_ru(s_r, b.a_hi));
 }
 
 template <typename T>
@@ -155,6 +171,8 @@ struct IterBuffers {
     double* lb = nullptr;      // FP32-certified mode: stored bounds of active nodes, kept
     double* ub = nullptr;      //   monotone (l = max over levels, u = min over levels)
     uint8_t* active = nullptr;
+    float* s32 = nullptr;      // FP32-certified mode: the latest FP64 level rounded to FP32 (the input of
+                               //   the first FP32 level, which would otherwise convert every gathered value)
     int32_t* alist[2] = {nullptr, nullptr};  // [n] each: the active nodes (internal ids), double-buffered
     double* cand_l = nullptr;
     double* cand_u = nullptr;
@@ -272,6 +290,8 @@ cudaError_t launch_theta0_class(const DeviceGraph& g, const IterBuffers& b, cons
                                 int64_t bend, int64_t lo, int bits, int64_t kk, cudaStream_t st);
 cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const IterParams& p,
                           uint32_t* d_deghist, int64_t D, cudaStream_t st);
+// the FP32-certified levels' binary64 -> binary32 rounding and exact widening
+cudaError_t launch_convert(const double* in, int64_t n, float* out, double* back, cudaStream_t st);
 // level 1 of a ranking (s_1 = alpha deg) in one pass over the rows, fixup included
 cudaError_t launch_degree_level(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, cudaStream_t st);
 cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,

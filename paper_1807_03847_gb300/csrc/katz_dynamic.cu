@@ -541,7 +541,7 @@ __global__ void theta_lb_kernel(const int32_t* __restrict__ topk_id, const int32
     __shared__ double wmin[32];
     const int kk = ctrl->k_eff;
     const double* s = walk_slot(walk, p, r);
-    const BState bs = bstate(ctrl);
+    const BState bs = bstate(ctrl, p);
     double m = 1.0 / 0.0;
     for (int q = threadIdx.x; q < kk; q += blockDim.x) {
         const int32_t v = inv[topk_id[q]];
@@ -577,7 +577,7 @@ __global__ void reactivate_kernel(const double* walk, const double* __restrict__
                                   int64_t cand_cap, Ctrl* ctrl) {
     const double* s = walk_slot(walk, p, r);
     const double th = ctrl->theta_prev;
-    const BState bs = bstate(ctrl);
+    const BState bs = bstate(ctrl, p);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
         active[v] = 1;

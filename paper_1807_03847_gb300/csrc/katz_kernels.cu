@@ -102,7 +102,7 @@ __device__ __forceinline__ void set_theta0(long long found, const IterParams& p,
     const T s1 = scale<T>(p.alpha, (T)found);
     const double sd = (double)s1;
     double l, u;
-    node_bounds(add<double>(0.0, sd), 0.0, sd, p, bstate(ctrl), l, u);
+    node_bounds(add<double>(0.0, sd), 0.0, sd, p, bstate(ctrl, p), l, u);
     ctrl->theta_prev = l;
 }
 
@@ -334,7 +334,7 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
         if (r_cur <= 1 || kprev < (int)p.k) {
             if (tid == 0 && nc > (unsigned long long)SELECT_CAP) s_big = 1;
         } else {
-            const BState bs = bstate(ctrl);
+            const BState bs = bstate(ctrl, p);
             const int f32_from = ctrl->f32_from;
             double m = 1.0 / 0.0;
             for (int q = tid; q < kprev; q += SELECT_THREADS) {
@@ -418,7 +418,7 @@ count_kernel(const T* walk, const double* __restrict__ c, const double* __restri
     if (ctrl->stop || (ctrl->flags & F_NEED_BIG)) return;
     const int r_cur = ctrl->r + 1;
     const int f32_from = ctrl->f32_from;
-    const BState bs = bstate(ctrl);
+    const BState bs = bstate(ctrl, p);
     const double th = ctrl->theta;
     const int32_t thid = ctrl->theta_id;
     const bool full = !ctrl->list_ready;
@@ -428,7 +428,13 @@ count_kernel(const T* walk, const double* __restrict__ c, const double* __restri
     const int64_t total = full ? p.n : (int64_t)ctrl->n_list;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     unsigned long long cross = 0, act = 0;
-    double smax = 0.0, tailw = 0.0, roundw = 0.0;
+    double roundw = 0.0;
+    // cert mode: the maxima of s_r and, over nodes with c32 = +0 (all of them
+    // before the switch to FP32 levels), of c64, taken on bit patterns (the
+    // values are non-negative); the tail and rounding widths follow from them
+    // below, because rounding a product with a non-negative factor is monotone
+    long long smax_b = 0, cmax_b = 0;
+    const double d64 = bs.hi64 - bs.lo64, d32 = bs.hi32 - bs.lo32;
     // l, th >= 0 (sums of non-negative terms): they order like their bit patterns
     const long long th_bits = __double_as_longlong(th);
     // the trip count depends on the block only, so the barriers below are uniform
@@ -472,9 +478,9 @@ count_kernel(const T* walk, const double* __restrict__ c, const double* __restri
             if (p.cert) {
                 const double sv = walk_value(walk, p, f32_from, r_cur, v[q]);
                 const double c64v = c[v[q]], c32v = c32 ? c32[v[q]] : 0.0;
-                smax = fmax(smax, sv);
-                tailw = fmax(tailw, p.ag * sv);
-                roundw = fmax(roundw, c64v * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32));
+                smax_b = max(smax_b, __double_as_longlong(sv));
+                if (__double_as_longlong(c32v) == 0) cmax_b = max(cmax_b, __double_as_longlong(c64v));
+                else roundw = fmax(roundw, __fma_rn(c64v, d64, __dmul_rn(c32v, d32)));
             }
         }
         act += (unsigned long long)mine;
@@ -502,6 +508,12 @@ count_kernel(const T* walk, const double* __restrict__ c, const double* __restri
         for (int q = 0; q < COUNT_U; ++q)
             if (keep[q]) out[pos++] = v[q];
         __syncthreads();  // s_wcnt and s_base are rewritten by the next tile
+    }
+    double smax = 0.0, tailw = 0.0;
+    if (p.cert) {
+        smax = __longlong_as_double(smax_b);
+        tailw = __dmul_rn(p.ag, smax);  // = the largest of ag s_r over this thread's nodes
+        roundw = fmax(roundw, __dmul_rn(__longlong_as_double(cmax_b), d64));
     }
     // block totals first: one atomic per block and counter
     __shared__ unsigned long long s_cross[32], s_act[32];
@@ -669,7 +681,7 @@ __global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, c
                                   const uint8_t* __restrict__ active, const int32_t* __restrict__ inv,
                                   const Ctrl* ctrl, IterParams p, int level, double* lower, double* upper,
                                   double* err) {
-    const BState bs = bstate(ctrl);
+    const BState bs = bstate(ctrl, p);
     const int f32_from = ctrl->f32_from;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {

@@ -68,7 +68,52 @@ struct Epi {
     double theta_prev;
     BState bs;
     int store_only;   // dynamic repair: write s_r only (c and bounds are rebuilt afterwards)
+    float* s32;       // FP32-certified mode, FP64 levels before the switch: s_r rounded to FP32 too
 };
+
+// Conversions between binary64 and binary32 for the non-negative finite walk
+// values, on the integer pipes (the FP64 pipe of this GPU is narrow and the
+// epilogue converts once per row).  Written from the IEEE 754 encodings:
+// f64_to_f32_rn rounds to nearest, ties to even, into normal or subnormal
+// binary32 (0 below half the smallest subnormal); f32_to_f64 is exact.  The
+// GPU tests compare both with the hardware conversions.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)(b >> 52);  // biased exponent (the sign bit is 0)
+    if (e == 0) return 0.0f;       // zero or a binary64 subnormal, far below binary32's range
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // 53-bit significand
+    const int fe = e - 896;        // binary32 biased exponent (1023 - 127)
+    if (fe >= 255) return __uint_as_float(0x7f800000u);
+    const int sh = fe >= 1 ? 29 : 30 - fe;  // significand bits dropped: normal, or subnormal result
+    if (sh > 60) return 0.0f;
+    const unsigned long long r = m >> sh, rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    const unsigned long long q = r + ((rem > half || (rem == half && (r & 1ull))) ? 1ull : 0ull);
+    // normal: q in [2^23, 2^24], a carry to 2^24 moves into the exponent field;
+    // subnormal: q in [0, 2^23], 2^23 being the smallest normal
+    const uint32_t bits = fe >= 1 ? (uint32_t)(((unsigned long long)fe << 23) + (q - (1ull << 23))) : (uint32_t)q;
+    return __uint_as_float(bits);
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = b >> 23, m = b & 0x7FFFFFu;
+    if (e == 0) {
+        if (m == 0) return 0.0;
+        const int hb = 31 - __clz(m);  // subnormal: m 2^-149 = 1.x 2^(hb - 149)
+        const unsigned long long frac = ((unsigned long long)m << (52 - hb)) & 0xFFFFFFFFFFFFFull;
+        return __longlong_as_double((long long)(((unsigned long long)(hb + 874) << 52) | frac));
+    }
+    const unsigned long long ed = e == 255 ? 0x7FFull : (unsigned long long)(e + 896);  // inf stays inf
+    return __longlong_as_double((long long)((ed << 52) | ((unsigned long long)m << 29)));
+}
+
+// bounds and thresholds are non-negative doubles: they order like their bit patterns
+__device__ __forceinline__ double nn_max(double a, double b) {
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ double nn_min(double a, double b) {
+    return __longlong_as_double(min(__double_as_longlong(a), __double_as_longlong(b)));
+}
 
 // Finish row u of an FP64 level: s = alpha * sum, c64 += s, bounds, candidate.
 // Finish row u of an FP32 level: s = fl32(alpha_f * sum), c32 += s, bounds, candidate.
@@ -85,13 +130,14 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
     if constexpr (sizeof(Acc) == 8) {
         sd = __dmul_rn(p.alpha, (double)sum);
         ((double*)e.y)[u] = sd;
+        if (e.s32) e.s32[u] = f64_to_f32_rn(sd);  // one rounding per row, not per gathered arc
         c64 = __dadd_rn(e.c64[u], sd);
         e.c64[u] = c64;
         if (e.c32) c32 = e.c32[u];
     } else {
         const float sf = __fmul_rn(p.alpha_f, (float)sum);
         ((float*)e.y)[u] = sf;
-        sd = (double)sf;
+        sd = f32_to_f64(sf);
         c32 = __dadd_rn(e.c32[u], sd);
         e.c32[u] = c32;
         c64 = e.c64[u];
@@ -100,12 +146,12 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
         double l, up;
         node_bounds(c64, c32, sd, p, e.bs, l, up);
         if (p.cert) {  // both the new and the stored bounds are valid: keep the tighter ones
-            l = fmax(l, e.lb[u]);
-            up = fmin(up, e.ub[u]);
+            l = nn_max(l, e.lb[u]);
+            up = nn_min(up, e.ub[u]);
         }
         e.lb[u] = l;  // read by the deactivation count of this level
         e.ub[u] = up;
-        if (l >= e.theta_prev) {
+        if (__double_as_longlong(l) >= __double_as_longlong(e.theta_prev)) {
             const unsigned long long pos = atomicAdd(&e.ctrl->n_cand, 1ULL);
             if (pos < (unsigned long long)e.cand_cap) {
                 e.cand_l[pos] = l;
@@ -455,9 +501,9 @@ __device__ __forceinline__ void spmv_rows(const Off* __restrict__ rowptr, const 
 
 __device__ __forceinline__ Epi make_epi(void* y, double* c64, double* c32, double* lb, double* ub, uint8_t* active,
                                         const int32_t* perm, double* cand_l, double* cand_u, int32_t* cand_id,
-                                        int64_t cand_cap, Ctrl* ctrl) {
-    return Epi{y,      c64,     c32,     lb,       ub,    active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl,
-               ctrl->theta_prev, bstate(ctrl), 0};
+                                        int64_t cand_cap, Ctrl* ctrl, const IterParams& p, float* s32 = nullptr) {
+    return Epi{y,    c64,     c32,      lb,   ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl,
+               ctrl->theta_prev, bstate(ctrl, p), 0, s32};
 }
 
 // Level 1: s_0 = 1, so the exact sum of a row is its length (A 1 = deg) and
@@ -502,10 +548,10 @@ template <typename Off>
 __global__ void degree_level_kernel(const Off* __restrict__ rowptr, int64_t n, double* walk, double* c64,
                                     double* c32, double* lb, double* ub, uint8_t* active,
                                     const int32_t* __restrict__ perm, double* cand_l, double* cand_u,
-                                    int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p) {
+                                    int32_t* cand_id, int64_t cand_cap, float* s32, Ctrl* ctrl, IterParams p) {
     if (ctrl->stop) return;
     const Epi ep = make_epi(walk_slot(walk, p, 1), c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id,
-                            cand_cap, ctrl);
+                            cand_cap, ctrl, p, (p.cert && 1 < ctrl->f32_from) ? s32 : nullptr);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
         finish_row<double>(u, (double)((int64_t)rowptr[u + 1] - (int64_t)rowptr[u]), ep, p);
@@ -518,38 +564,49 @@ __global__ void __launch_bounds__(BLOCK, 6)
 spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L, double* walk,
                  double* c64, double* c32, double* lb, double* ub, uint8_t* active, const int32_t* __restrict__ perm,
                  const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first, double* chunk_part,
-                 double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p,
-                 int store_level) {
+                 double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap, float* s32, Ctrl* ctrl,
+                 IterParams p, int store_level) {
     // store_level > 0: dynamic repair of one FP64 level, s only
     if (!store_level && ctrl->stop) return;
     const int r_cur = store_level ? store_level : ctrl->r + 1;
     const int f32_from = store_level ? 0x7fffffff : ctrl->f32_from;
     const double* xs = walk_slot(walk, p, r_cur - 1);
     double* ys = walk_slot(walk, p, r_cur);
-    Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
+    // FP32-certified mode: while the switch is ahead, an FP64 level leaves its
+    // s_r rounded to FP32 too, the input of a first FP32 level
+    Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl, p,
+                      (p.cert && !store_level && r_cur < f32_from) ? s32 : nullptr);
     ep.store_only = store_level > 0;
     if (r_cur == 1)  // always an FP64 level
         spmv_rows_degree<Off>(rowptr, L, ep, chunk_row, chunk_first, chunk_part, p);
     else if (r_cur < f32_from)
         spmv_rows<Off, double, double>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
     else if (r_cur == f32_from)
-        spmv_rows<Off, double, float>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
+        spmv_rows<Off, float, float>(rowptr, col, L, s32, ep, chunk_row, chunk_first, chunk_part, p);
     else
         spmv_rows<Off, float, float>(rowptr, col, L, (const float*)xs, ep, chunk_row, chunk_first, chunk_part, p);
 }
 
-// CHUNK rows of an FP32 level: add the chunk sums of each row as a pairwise
-// tree in FP32, then finish the row.
-template <typename Acc>
-__device__ __forceinline__ Acc chunk_tree(const double* __restrict__ part, int64_t first, int64_t count) {
-    Acc buf[64];
-    Acc total = (Acc)0;
+// CHUNK rows of an FP32 level: the chunk sums of a row, in groups of 64, each
+// group a pairwise tree in FP32 (level by level, entry q = entry 2q + entry
+// 2q+1), the group totals chained in order.  A warp per row: lane l holds
+// entry l of each tree level, partners come by shuffle.
+__device__ __forceinline__ float chunk_tree_warp(const double* __restrict__ part, int64_t first, int64_t count) {
+    const int lane = threadIdx.x & 31;
+    float total = 0.0f;
     for (int64_t base = 0; base < count; base += 64) {
-        const int m = (int)min((int64_t)64, count - base);
-        for (int q = 0; q < 64; ++q) buf[q] = q < m ? (Acc)part[3 * (first + base + q)] : (Acc)0;
-        for (int w = 32; w >= 1; w >>= 1)
-            for (int q = 0; q < w; ++q) buf[q] = addA<Acc>(buf[2 * q], buf[2 * q + 1]);
-        total = addA<Acc>(total, buf[0]);
+        const int64_t m = min((int64_t)64, count - base);
+        const int q0 = 2 * lane, q1 = 2 * lane + 1;
+        const float a = q0 < m ? (float)part[3 * (first + base + q0)] : 0.0f;  // FP32 sums, exact in FP64
+        const float b = q1 < m ? (float)part[3 * (first + base + q1)] : 0.0f;
+        float v = __fadd_rn(a, b);
+#pragma unroll
+        for (int w = 16; w >= 1; w >>= 1) {  // entries q >= w of a level are not used further
+            const float x = __shfl_sync(FULL, v, (2 * lane) & 31);
+            const float y = __shfl_sync(FULL, v, (2 * lane + 1) & 31);
+            v = __fadd_rn(x, y);
+        }
+        total = __fadd_rn(total, __shfl_sync(FULL, v, 0));
     }
     return total;
 }
@@ -560,11 +617,13 @@ __global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double
                                  uint8_t* active,
                                  const int32_t* __restrict__ perm, const int64_t* __restrict__ chunk_first,
                                  const double* __restrict__ chunk_part, double* cand_l, double* cand_u,
-                                 int32_t* cand_id, int64_t cand_cap, Ctrl* ctrl, IterParams p, int store_level) {
+                                 int32_t* cand_id, int64_t cand_cap, float* s32, Ctrl* ctrl, IterParams p,
+                                 int store_level) {
     if (!store_level && ctrl->stop) return;
     const int r_cur = store_level ? store_level : ctrl->r + 1;
     double* ys = walk_slot(walk, p, r_cur);
-    Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl);
+    Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl, p,
+                      (p.cert && !store_level && r_cur < ctrl->f32_from) ? s32 : nullptr);
     ep.store_only = store_level > 0;
     const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;  // one warp per CHUNK row
     if (u >= L.row_warp) return;
@@ -572,8 +631,9 @@ __global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double
     if (store_level || r_cur < ctrl->f32_from) {
         const XAcc t = merge_chunks_warp(chunk_part, first, count);
         if ((threadIdx.x & 31) == 0) finish_row<double>(u, xacc_to_double(t), ep, p);
-    } else if ((threadIdx.x & 31) == 0) {
-        finish_row<float>(u, chunk_tree<float>(chunk_part, first, count), ep, p);
+    } else {
+        const float t = chunk_tree_warp(chunk_part, first, count);
+        if ((threadIdx.x & 31) == 0) finish_row<float>(u, t, ep, p);
     }
 }
 
@@ -598,18 +658,18 @@ static cudaError_t spmv_launch(const DeviceGraph& g, const IterBuffers& b, const
         if (g.off64)
             spmv_rows_kernel<int64_t><<<(unsigned)L.blocks_total, BLOCK, 0, st>>>(
                 (const int64_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm,
-                g.chunk_row, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p,
+                g.chunk_row, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.s32, b.ctrl, p,
                 store_level);
         else
             spmv_rows_kernel<int32_t><<<(unsigned)L.blocks_total, BLOCK, 0, st>>>(
                 (const int32_t*)g.rowptr, g.col, L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm,
-                g.chunk_row, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p,
+                g.chunk_row, g.chunk_first, g.chunk_part, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.s32, b.ctrl, p,
                 store_level);
     }
     if (L.row_warp > 0)
         spmv_chunk_fixup<<<(unsigned)((L.row_warp * 32 + 127) / 128), 128, 0, st>>>(
             L, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, g.chunk_first, g.chunk_part, b.cand_l,
-            b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p, store_level);
+            b.cand_u, b.cand_id, b.cand_cap, b.s32, b.ctrl, p, store_level);
     return cudaGetLastError();
 }
 
@@ -619,16 +679,34 @@ cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterPa
     return spmv_launch(g, b, p, 0, st);
 }
 
+namespace {
+__global__ void convert_kernel(const double* __restrict__ in, int64_t n, float* out, double* back) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float f = f64_to_f32_rn(in[i]);
+        out[i] = f;
+        back[i] = f32_to_f64(f);
+    }
+}
+}  // namespace
+
+cudaError_t launch_convert(const double* in, int64_t n, float* out, double* back, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    convert_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, n, out, back);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_degree_level(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, cudaStream_t st) {
     const int64_t blocks = std::min<int64_t>(std::max<int64_t>((g.n + BLOCK - 1) / BLOCK, 1), 152 * 8);
     if (g.off64)
         degree_level_kernel<int64_t><<<(unsigned)blocks, BLOCK, 0, st>>>(
             (const int64_t*)g.rowptr, g.n, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, b.cand_l,
-            b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
+            b.cand_u, b.cand_id, b.cand_cap, b.s32, b.ctrl, p);
     else
         degree_level_kernel<int32_t><<<(unsigned)blocks, BLOCK, 0, st>>>(
             (const int32_t*)g.rowptr, g.n, (double*)b.walk, b.c, b.c32, b.lb, b.ub, b.active, g.perm, b.cand_l,
-            b.cand_u, b.cand_id, b.cand_cap, b.ctrl, p);
+            b.cand_u, b.cand_id, b.cand_cap, b.s32, b.ctrl, p);
     return cudaGetLastError();
 }
 
