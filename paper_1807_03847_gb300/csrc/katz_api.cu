@@ -600,7 +600,8 @@ void katz_destroy(katz_h h) {
         for (void* ptr : {(void*)d.src, (void*)d.dst, (void*)d.ins, (void*)d.hub_epoch, (void*)d.table,
                           (void*)d.err, (void*)d.delta, (void*)d.ins_cnt, (void*)d.cursor, (void*)d.touched,
                           (void*)d.ins_start, (void*)d.ins_rows, (void*)d.n_ins_rows, (void*)d.bucket,
-                          (void*)d.vbits, (void*)d.frontier, (void*)d.fsize, (void*)d.rrowptr, (void*)d.rcol})
+                          (void*)d.vbits, (void*)d.frontier, (void*)d.fsize, (void*)d.rrowptr, (void*)d.rcol,
+                          (void*)d.hub_keep})
             dfree(h, ptr);
         dfree(h, h->col_spare);
         dfree(h, h->rp_new);
@@ -1185,9 +1186,20 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
             }
             h->col_spare_cap = cap;
         }
+        if (hubs && g.layout.chunks > d.hub_keep_cap) {
+            dfree(h, d.hub_keep);
+            d.hub_keep = nullptr;
+            d.hub_keep_cap = 0;
+            const int64_t cap = g.layout.chunks + g.layout.chunks / 8 + 64;
+            if ((e = dmalloc(h, &d.hub_keep, (size_t)cap)) != cudaSuccess) {
+                dyn_clear(g, d, m, h->stream);
+                return cuda_fail(h, e, "cudaMalloc hub chunks");
+            }
+            d.hub_keep_cap = cap;
+        }
         if ((e = dyn_rebuild(g, d, m, h->rp_new, h->col_spare, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "rebuild rows");
-        h->launches += (g.n > g.layout.row_warp ? 1 : 0) + (g.layout.chunks > 0 ? 1 : 0) + (hubs ? 1 : 0) + 1;
+        h->launches += (g.n > g.layout.row_warp ? 1 : 0) + (g.layout.chunks > 0 ? 1 : 0) + (hubs ? 3 : 0) + 1;
         std::swap(g.col, h->col_spare);
         std::swap(h->col_cap, h->col_spare_cap);
         g.nnz = nnz_new;
@@ -1259,20 +1271,33 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
         auto too_big = [&](unsigned long long cnt, unsigned long long vol) {
             return (double)cnt > tau * (double)n || (double)vol > tau * (double)g.nnz;
         };
+        // Expanding the nodes that joined at a level reads their arcs.  Past
+        // tau/25 of all arcs (0.2% at the default tau) their neighbourhoods
+        // hold hubs on graphs with skewed degrees, and the next frontier goes
+        // full all the same; such an expansion is skipped and the remaining
+        // levels are full.  Either way the repaired values are the same.
+        const double expand_cap = tau / 25.0 * (double)g.nnz;
         int64_t lo = 0, hi = (int64_t)fs[0];
+        unsigned long long vol_lo = 0;  // arcs of frontier[0, lo)
         bool full = too_big(fs[0], fs[1]);
         for (int i = 1; i <= r; ++i) {
             if (full) {
-                if ((e = launch_spmv_store(g, h->b, h->p, i, h->stream)) != cudaSuccess)
-                    return cuda_fail(h, e, "full level");
+                e = i == 1 ? launch_degree_store(g, h->b, h->p, h->stream)
+                           : launch_spmv_store(g, h->b, h->p, i, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "full level");
                 ++full_levels;
-                h->launches += hubs ? 2 : 1;
+                h->launches += i == 1 ? 1 : (hubs ? 2 : 1);
                 continue;
             }
             if ((e = launch_rows_store(g, h->b, h->p, d.frontier, d.fsize, hi, d.vbits, i, h->stream)) != cudaSuccess)
                 return cuda_fail(h, e, "repair rows");
             h->launches += (hi > 0 ? 1 : 0) + (hi > 0 && g.layout.chunks > 0 ? 2 : 0);
             if (i < r) {
+                if ((double)(fs[1] - vol_lo) > expand_cap) {
+                    full = true;
+                    continue;
+                }
+                vol_lo = fs[1];
                 if ((e = dyn_expand(g, d, lo, hi, i, h->stream)) != cudaSuccess) return cuda_fail(h, e, "expand");
                 h->launches += hi > lo ? 1 + (d.undirected && g.layout.chunks > 0 ? 1 : 0) : 0;
                 if ((e = cudaMemcpyAsync(fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||

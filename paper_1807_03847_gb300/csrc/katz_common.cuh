@@ -210,6 +210,8 @@ struct DynBuffers {
     int32_t* frontier = nullptr;     // [n] affected nodes, in order of discovery
     unsigned long long* fsize = nullptr;  // [2] frontier size, sum of the frontier's degrees
     int32_t* hub_epoch = nullptr;    // [row_warp] level at which a CHUNK row joined the frontier
+    int64_t* hub_keep = nullptr;     // [hub_keep_cap >= chunks] kept arcs, then place, of each hub chunk
+    int64_t hub_keep_cap = 0;
     int64_t* rrowptr = nullptr;      // [n+1] directed: transposed CSR (in-arcs) of the current graph
     int32_t* rcol = nullptr;         // [rcap]
     int64_t rcap = 0;
@@ -292,6 +294,8 @@ cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const Iter
                           uint32_t* d_deghist, int64_t D, cudaStream_t st);
 // the FP32-certified levels' binary64 -> binary32 rounding and exact widening
 cudaError_t launch_convert(const double* in, int64_t n, float* out, double* back, cudaStream_t st);
+// s_1 = alpha deg into its walk slot, nothing else (a full level 1 of a repair)
+cudaError_t launch_degree_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, cudaStream_t st);
 // level 1 of a ranking (s_1 = alpha deg) in one pass over the rows, fixup included
 cudaError_t launch_degree_level(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, cudaStream_t st);
 cudaError_t launch_spmv(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, bool fp32,

@@ -77,6 +77,22 @@ __device__ __forceinline__ unsigned long long table_find(const unsigned long lon
     return 0ull;
 }
 
+// out[j - a] = col[j] for j in [a, b): one warp, eight loads in flight per
+// lane (one load at a time left the copy at a third of the bandwidth)
+__device__ __forceinline__ void warp_copy(const int32_t* __restrict__ col, int64_t a, int64_t b,
+                                          int32_t* __restrict__ out) {
+    constexpr int U = 8;
+    int64_t j = a + (threadIdx.x & 31);
+    for (; j + (U - 1) * 32 < b; j += U * 32) {
+        int32_t v[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) v[q] = col[j + q * 32];
+#pragma unroll
+        for (int q = 0; q < U; ++q) out[j + q * 32 - a] = v[q];
+    }
+    for (; j < b; j += 32) out[j - a] = col[j];
+}
+
 // One warp per update: range, self-loop, duplicate (the pair table, which
 // also records deletions for the rebuild), presence (I and E disjoint, D a
 // subset of E; an undirected graph is symmetric, so the shorter of the two
@@ -288,8 +304,7 @@ __global__ void rebuild_groups_kernel(const Off* __restrict__ rowptr, const int3
         const bool t = u0 + lane < u1 && touched[u0 + lane];
         const unsigned tb = __ballot_sync(FULL, t);
         if (!tb) {
-            const int64_t a = rowptr[u0], b = rowptr[u1], o = rowptr_new[u0];
-            for (int64_t j = a + lane; j < b; j += 32) col_new[o + (j - a)] = col[j];
+            warp_copy(col, rowptr[u0], rowptr[u1], col_new + rowptr_new[u0]);
             continue;
         }
         for (int64_t v = u0; v < u1; ++v) {
@@ -297,8 +312,7 @@ __global__ void rebuild_groups_kernel(const Off* __restrict__ rowptr, const int3
             if ((tb >> (v - u0)) & 1u) {
                 rebuild_touched_row(rowptr, col, v, o, ins_cnt, ins_start, bucket, table, mask, und, col_new);
             } else {
-                const int64_t a = rowptr[v], b = rowptr[v + 1];
-                for (int64_t j = a + lane; j < b; j += 32) col_new[o + (j - a)] = col[j];
+                warp_copy(col, rowptr[v], rowptr[v + 1], col_new + o);
             }
         }
     }
@@ -317,53 +331,95 @@ __global__ void rebuild_chunks_kernel(const Off* __restrict__ rowptr, const int3
         if (touched[u]) continue;
         const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
         const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
-        const int64_t o = rowptr_new[u] + (j0 - (int64_t)rowptr[u]);
-        for (int64_t j = j0 + lane; j < j1; j += 32) col_new[o + (j - j0)] = col[j];
+        warp_copy(col, j0, j1, col_new + rowptr_new[u] + (j0 - (int64_t)rowptr[u]));
     }
 }
 
-// touched CHUNK rows: one block of HUB_THREADS per row compacts it tile by tile
-constexpr int HUB_THREADS = 1024;
+// Touched CHUNK rows, compacted chunk by chunk: (A) one warp per chunk counts
+// the arcs it keeps, (B) one warp per row turns the counts into the chunks'
+// places in the new row and appends the inserted arcs after them, (C) one
+// warp per chunk writes its kept arcs, in order, at its place.
 template <typename Off>
-__global__ void __launch_bounds__(HUB_THREADS)
-rebuild_hub_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
-                        const int64_t* __restrict__ rowptr_new, const uint8_t* __restrict__ touched,
-                        const int32_t* __restrict__ ins_cnt, const int64_t* __restrict__ ins_start,
-                        const int32_t* __restrict__ bucket, const unsigned long long* __restrict__ table, int64_t mask,
-                        bool und, int64_t row_warp, int32_t* col_new) {
-    __shared__ int wsum[HUB_THREADS / 32];
-    __shared__ int total;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int64_t u = blockIdx.x; u < row_warp; u += gridDim.x) {
-        if (!touched[u]) continue;  // the same for the whole block
-        const int64_t a = rowptr[u], b = rowptr[u + 1];
-        int64_t o = rowptr_new[u];
-        for (int64_t base = a; base < b; base += HUB_THREADS) {
-            const int64_t j = base + tid;
-            const int32_t x = j < b ? col[j] : -1;
-            const bool keep = x >= 0 && !(table_find(table, mask, pair_key((int32_t)u, x, und)) & DEL_BIT);
-            const unsigned kb = __ballot_sync(FULL, keep);
-            if (lane == 0) wsum[wid] = __popc(kb);
-            __syncthreads();
-            if (wid == 0) {  // exclusive scan of the warp counts
-                const int c = wsum[lane];
-                int inc = c;
+__device__ __forceinline__ void hub_chunk_range(const Off* __restrict__ rowptr, const int32_t* __restrict__ chunk_row,
+                                                const int64_t* __restrict__ chunk_first, int64_t ch, int64_t& u,
+                                                int64_t& j0, int64_t& j1) {
+    u = chunk_row[ch];
+    j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+    j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+}
+
+template <typename Off>
+__global__ void hub_keep_count_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                      const uint8_t* __restrict__ touched, const int32_t* __restrict__ chunk_row,
+                                      const int64_t* __restrict__ chunk_first, int64_t chunks,
+                                      const unsigned long long* __restrict__ table, int64_t mask, bool und,
+                                      int64_t* keep) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < chunks; ch += warps) {
+        int64_t u, j0, j1;
+        hub_chunk_range(rowptr, chunk_row, chunk_first, ch, u, j0, j1);
+        if (!touched[u]) continue;
+        int64_t cnt = 0;
+        for (int64_t base = j0; base < j1; base += 32) {
+            const int64_t j = base + lane;
+            const int32_t x = j < j1 ? col[j] : -1;
+            const bool k = x >= 0 && !(table_find(table, mask, pair_key((int32_t)u, x, und)) & DEL_BIT);
+            cnt += __popc(__ballot_sync(FULL, k));
+        }
+        if (lane == 0) keep[ch] = cnt;
+    }
+}
+
+template <typename Off>
+__global__ void hub_keep_scan_kernel(const uint8_t* __restrict__ touched, const int64_t* __restrict__ chunk_first,
+                                     const int64_t* __restrict__ rowptr_new, const int32_t* __restrict__ ins_cnt,
+                                     const int64_t* __restrict__ ins_start, const int32_t* __restrict__ bucket,
+                                     int64_t row_warp, int64_t* keep, int32_t* col_new) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; u < row_warp; u += warps) {
+        if (!touched[u]) continue;
+        int64_t run = rowptr_new[u];
+        for (int64_t c0 = chunk_first[u]; c0 < chunk_first[u + 1]; c0 += 32) {
+            const int64_t ch = c0 + lane;
+            const int64_t k = ch < chunk_first[u + 1] ? keep[ch] : 0;
+            int64_t incl = k;
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int y = __shfl_up_sync(FULL, inc, off);
-                    if (lane >= off) inc += y;
-                }
-                wsum[lane] = inc - c;
-                if (lane == 31) total = inc;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int64_t y = __shfl_up_sync(FULL, incl, off);
+                if (lane >= off) incl += y;
             }
-            __syncthreads();
-            if (keep) col_new[o + wsum[wid] + __popc(kb & ((1u << lane) - 1u))] = x;
-            o += total;
-            __syncthreads();
+            if (ch < chunk_first[u + 1]) keep[ch] = run + incl - k;  // the chunk's first place
+            run += __shfl_sync(FULL, incl, 31);
         }
         const int c = ins_cnt[u];
         const int32_t* bkt = bucket + ins_start[u];
-        for (int q = tid; q < c; q += HUB_THREADS) col_new[o + q] = bkt[q];
+        for (int q = lane; q < c; q += 32) col_new[run + q] = bkt[q];
+    }
+}
+
+template <typename Off>
+__global__ void hub_keep_write_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                      const uint8_t* __restrict__ touched, const int32_t* __restrict__ chunk_row,
+                                      const int64_t* __restrict__ chunk_first, int64_t chunks,
+                                      const unsigned long long* __restrict__ table, int64_t mask, bool und,
+                                      const int64_t* __restrict__ place, int32_t* col_new) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < chunks; ch += warps) {
+        int64_t u, j0, j1;
+        hub_chunk_range(rowptr, chunk_row, chunk_first, ch, u, j0, j1);
+        if (!touched[u]) continue;
+        int64_t o = place[ch];
+        for (int64_t base = j0; base < j1; base += 32) {
+            const int64_t j = base + lane;
+            const int32_t x = j < j1 ? col[j] : -1;
+            const bool k = x >= 0 && !(table_find(table, mask, pair_key((int32_t)u, x, und)) & DEL_BIT);
+            const unsigned kb = __ballot_sync(FULL, k);
+            if (k) col_new[o + __popc(kb & ((1u << lane) - 1u))] = x;
+            o += __popc(kb);
+        }
     }
 }
 
@@ -671,10 +727,16 @@ static void rebuild_launch(DeviceGraph& g, const DynBuffers& d, const int64_t* r
     if (L.chunks > 0)
         rebuild_chunks_kernel<Off><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
             rp, g.col, rowptr_new, d.touched, g.chunk_row, g.chunk_first, L.chunks, col_new);
-    if (L.row_warp > 0)
-        rebuild_hub_rows_kernel<Off><<<(unsigned)std::min<int64_t>(L.row_warp, 152 * 2), HUB_THREADS, 0, st>>>(
-            rp, g.col, rowptr_new, d.touched, d.ins_cnt, d.ins_start, d.bucket, d.table, d.table_mask, d.undirected,
-            L.row_warp, col_new);
+    if (L.row_warp > 0) {
+        hub_keep_count_kernel<Off><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
+            rp, g.col, d.touched, g.chunk_row, g.chunk_first, L.chunks, d.table, d.table_mask, d.undirected,
+            d.hub_keep);
+        hub_keep_scan_kernel<Off><<<grid_for(L.row_warp * 32, 256), 256, 0, st>>>(
+            d.touched, g.chunk_first, rowptr_new, d.ins_cnt, d.ins_start, d.bucket, L.row_warp, d.hub_keep, col_new);
+        hub_keep_write_kernel<Off><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
+            rp, g.col, d.touched, g.chunk_row, g.chunk_first, L.chunks, d.table, d.table_mask, d.undirected,
+            d.hub_keep, col_new);
+    }
 }
 
 // rows into col_new (old layout and chunk table), then the new offsets over

@@ -697,6 +697,27 @@ cudaError_t launch_convert(const double* in, int64_t n, float* out, double* back
     return cudaGetLastError();
 }
 
+namespace {
+template <typename Off>
+__global__ void degree_store_kernel(const Off* __restrict__ rowptr, int64_t n, double* walk, IterParams p) {
+    double* y = walk_slot(walk, p, 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
+        y[u] = __dmul_rn(p.alpha, (double)((int64_t)rowptr[u + 1] - (int64_t)rowptr[u]));
+}
+}  // namespace
+
+cudaError_t launch_degree_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>(std::max<int64_t>((g.n + BLOCK - 1) / BLOCK, 1), 152 * 8);
+    if (g.off64)
+        degree_store_kernel<int64_t><<<(unsigned)blocks, BLOCK, 0, st>>>((const int64_t*)g.rowptr, g.n,
+                                                                         (double*)b.walk, p);
+    else
+        degree_store_kernel<int32_t><<<(unsigned)blocks, BLOCK, 0, st>>>((const int32_t*)g.rowptr, g.n,
+                                                                         (double*)b.walk, p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_degree_level(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, cudaStream_t st) {
     const int64_t blocks = std::min<int64_t>(std::max<int64_t>((g.n + BLOCK - 1) / BLOCK, 1), 152 * 8);
     if (g.off64)
