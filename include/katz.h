@@ -60,12 +60,15 @@ typedef enum {
 
 /* Arithmetic of the walk vectors. */
 enum {
-    KATZ_FP64 = 0,        /* s_i in FP64, as the paper (which implies FP64) */
-    KATZ_FP32_CERT = 1    /* s_i in FP32, bounds widened by a rigorous rounding term */
+    KATZ_FP64 = 0,          /* s_i in FP64, as the paper (which implies FP64) */
+    KATZ_FP32_CERT = 1,     /* s_i in FP32, bounds widened by a rigorous rounding term;
+                               KATZ_EPRECISION when the widening stalls the certificate */
+    KATZ_FP32_CERT_AUTO = 2 /* as KATZ_FP32_CERT, but a stalled ranking is recomputed with
+                               FP64 levels (katz_info.escalated = 1) instead of failing */
 };
 
 typedef struct {
-    int32_t precision;     /* KATZ_FP64 (default) or KATZ_FP32_CERT */
+    int32_t precision;     /* KATZ_FP64 (default), KATZ_FP32_CERT or KATZ_FP32_CERT_AUTO */
     int32_t undirected;    /* 1 (default): the CSR is symmetric; use the undirected lower
                               bound l_r = c_r + alpha^{r+1} omega_r (Sec. 3.1) */
     int32_t keep_history;  /* 1: keep s_1..s_r (needed by katz_apply_update_batch and
@@ -107,7 +110,8 @@ typedef struct {
                               walk values are gathered) */
     int64_t launches;      /* kernels this call launched */
     int32_t spmv_launches; /* SpMV launches of levels 2..r this call made */
-    int32_t reserved;
+    int32_t escalated;     /* KATZ_FP32_CERT_AUTO: 1 if the FP32-certified run stalled and the
+                              ranking was recomputed with FP64 levels */
 } katz_info;
 
 /* Fill *opts with the defaults listed above. */

@@ -20,11 +20,11 @@ __all__ = [
     "katz_rank_static", "katz_rank", "katz_checkpoint", "katz_restore", "KATZ_CRIT_TOPK", "KATZ_CRIT_RANKING", "KATZ_CRIT_SCORE", "KATZ_CRIT_PAIR",
     "katz_get_ranking", "katz_get_bounds", "katz_get_walk", "katz_get_trace",
     "katz_apply_update_batch", "katz_certify_topk_noalloc", "katz_convert_f64_f32", "katz_server_opts", "katz_request_result",
-    "katz_server_default_opts", "Server", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT",
+    "katz_server_default_opts", "Server", "katz_last_error", "katz_status_string", "KATZ_FP64", "KATZ_FP32_CERT", "KATZ_FP32_CERT_AUTO",
     "KATZ_MAX_K", "library_path",
 ]
 
-KATZ_FP64, KATZ_FP32_CERT = 0, 1
+KATZ_FP64, KATZ_FP32_CERT, KATZ_FP32_CERT_AUTO = 0, 1, 2
 KATZ_CRIT_TOPK, KATZ_CRIT_RANKING, KATZ_CRIT_SCORE, KATZ_CRIT_PAIR = 0, 1, 2, 3
 KATZ_MAX_K = 8192
 STATUS = ["KATZ_OK", "KATZ_EINVAL", "KATZ_EALPHA", "KATZ_ENOMEM", "KATZ_ECUDA", "KATZ_ENOTCONV",
@@ -43,7 +43,7 @@ class katz_info(ctypes.Structure):
                 ("k", ctypes.c_int64), ("alpha", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("time_ms", ctypes.c_double), ("nnz", ctypes.c_int64), ("fp32_levels", ctypes.c_int32),
                 ("full_levels", ctypes.c_int32), ("affected", ctypes.c_int64), ("spmv_ms", ctypes.c_double),
-                ("launches", ctypes.c_int64), ("spmv_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("launches", ctypes.c_int64), ("spmv_launches", ctypes.c_int32), ("escalated", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

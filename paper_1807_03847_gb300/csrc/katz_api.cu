@@ -626,11 +626,12 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     katz_default_opts(&h->opts);
     if (opts) h->opts = *opts;
     if (h->opts.r_max < 1) h->opts.r_max = 1;
-    if (h->opts.precision != KATZ_FP64 && h->opts.precision != KATZ_FP32_CERT) {
+    if (h->opts.precision != KATZ_FP64 && h->opts.precision != KATZ_FP32_CERT &&
+        h->opts.precision != KATZ_FP32_CERT_AUTO) {
         delete h;
         return KATZ_EINVAL;
     }
-    h->fp32 = h->opts.precision == KATZ_FP32_CERT;
+    h->fp32 = h->opts.precision != KATZ_FP64;
     cudaError_t e;
     katz_status st = KATZ_OK;
 #define KCHK(call, what)                       \
@@ -835,7 +836,28 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     return KATZ_OK;
 }
 
+static katz_status rank_static_once(katz_h h, double alpha, int64_t k, double eps, katz_info* info);
+
+// KATZ_FP32_CERT_AUTO: a ranking whose FP32 rounding widening stalls the
+// certificate is recomputed with FP64 levels on the same handle (the
+// buffers of an FP32 handle hold FP64 levels too).
 katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz_info* info) {
+    if (!h) return KATZ_EINVAL;
+    katz_status st = rank_static_once(h, alpha, k, eps, info);
+    if (st != KATZ_EPRECISION || h->opts.precision != KATZ_FP32_CERT_AUTO) return st;
+    const int64_t launches = h->launches;
+    h->fp32 = false;
+    st = rank_static_once(h, alpha, k, eps, info);
+    h->fp32 = true;
+    h->launches += launches;
+    if (info) {
+        info->escalated = 1;
+        info->launches = h->launches;
+    }
+    return st;
+}
+
+static katz_status rank_static_once(katz_h h, double alpha, int64_t k, double eps, katz_info* info) {
     if (!h) return KATZ_EINVAL;
     h->err.clear();
     if (!(eps > 0.0) || !std::isfinite(eps) || k < 1 || !std::isfinite(alpha))

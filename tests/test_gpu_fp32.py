@@ -14,7 +14,7 @@ import sympy
 
 import graphgen as gg
 import oracle
-from tests.parity import assert_same_ranking
+from tests.parity import assert_close, assert_same_ranking
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -122,3 +122,24 @@ def test_fp32_switch_keeps_k_candidates_on_a_larger_graph():
     g = gg.rmat(18, 16, seed=18)
     got = _cert(g, 1000, 1e-9)
     assert got["info"].converged == 1 and got["info"].k == 1000 and len(got["ranking"]) == 1000
+
+
+def test_auto_precision_escalates_a_stalled_ranking_to_fp64():
+    # the stall case above, under KATZ_FP32_CERT_AUTO: the ranking is
+    # recomputed with FP64 levels and matches the FP64 oracle
+    g = gg.rmat(12, 16, seed=3)
+    k, eps = 400, 1e-15
+    opts = K.katz_default_opts(precision=K.KATZ_FP32_CERT_AUTO, fp32_from=2, r_max=256)
+    h = K.Katz(_dev(g.rowptr), _dev(g.col), opts)
+    info = h.rank(0.0, k, eps)
+    assert info.escalated == 1 and info.converged == 1 and info.fp32_levels == 0
+    ref = oracle.katz_static(g.rowptr, g.col, 0.0, k, eps, r_max=256)
+    assert info.r == ref["r"]
+    lo, up, err = h.bounds()
+    assert_close(lo, ref["l"], what="lower")
+    assert_close(up, ref["u"], what="upper")
+    assert_same_ranking(h.ranking(k), ref["ranking"], ref["l"])
+    # a ranking that certifies in FP32 is not escalated
+    info2 = h.rank(0.0, 50, 1e-4)
+    assert info2.escalated == 0 and info2.converged == 1 and info2.fp32_levels > 0
+    h.close()
