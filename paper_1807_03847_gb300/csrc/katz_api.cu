@@ -422,7 +422,7 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
         DALLOC(d.delta, n);
         DALLOC(d.ins_cnt, n);
         DALLOC(d.cursor, n);
-        DALLOC(d.touched, n);
+        DALLOC(d.touched, (n + 3) / 4 * 4);  // whole words: rows are claimed with word atomics
         DALLOC(d.ins_start, n);
         DALLOC(d.vbits, (n + 31) / 32);
         DALLOC(d.frontier, n);
@@ -436,7 +436,7 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
         if ((e = cudaMemsetAsync(d.delta, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
             (e = cudaMemsetAsync(d.ins_cnt, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
             (e = cudaMemsetAsync(d.cursor, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(d.touched, 0, (size_t)n, h->stream)) != cudaSuccess)
+            (e = cudaMemsetAsync(d.touched, 0, (size_t)((n + 3) / 4 * 4), h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "memset dynamic scratch");
         h->col_cap = g.nnz;
     }
@@ -1221,7 +1221,7 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
         }
         if ((e = dyn_rebuild(g, d, m, h->rp_new, h->col_spare, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "rebuild rows");
-        h->launches += (g.n > g.layout.row_warp ? 1 : 0) + (g.layout.chunks > 0 ? 1 : 0) + (hubs ? 3 : 0) + 1;
+        h->launches += (g.n > g.layout.row_warp ? 2 : 0) + (g.layout.chunks > 0 ? 1 : 0) + (hubs ? 3 : 0) + 1;
         std::swap(g.col, h->col_spare);
         std::swap(h->col_cap, h->col_spare_cap);
         g.nnz = nnz_new;

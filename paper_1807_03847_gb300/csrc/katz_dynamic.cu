@@ -265,17 +265,21 @@ __global__ void new_degrees_kernel(const Off* __restrict__ rowptr, const int32_t
 }
 
 // a touched row: its arcs minus the deleted ones (in their order), then its
-// inserted arcs; one warp
+// inserted arcs; one warp.  A row without deletions is copied as it is.
 template <typename Off>
 __device__ __forceinline__ void rebuild_touched_row(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                     int64_t v, int64_t o, const int32_t* __restrict__ ins_cnt,
                                                     const int64_t* __restrict__ ins_start,
                                                     const int32_t* __restrict__ bucket,
                                                     const unsigned long long* __restrict__ table, int64_t mask,
-                                                    bool und, int32_t* col_new) {
+                                                    bool und, bool no_deletes, int32_t* col_new) {
     const int lane = threadIdx.x & 31;
     const int64_t a = rowptr[v], b = rowptr[v + 1];
-    for (int64_t base = a; base < b; base += 32) {
+    if (no_deletes) {
+        warp_copy(col, a, b, col_new + o);
+        o += b - a;
+    }
+    for (int64_t base = a; !no_deletes && base < b; base += 32) {
         const int64_t j = base + lane;
         const int32_t x = j < b ? col[j] : -1;
         const bool keep = x >= 0 && !(table_find(table, mask, pair_key((int32_t)v, x, und)) & DEL_BIT);
@@ -303,17 +307,48 @@ __global__ void rebuild_groups_kernel(const Off* __restrict__ rowptr, const int3
         const int64_t u0 = row_lo + gi * 32, u1 = min(u0 + 32, n);
         const bool t = u0 + lane < u1 && touched[u0 + lane];
         const unsigned tb = __ballot_sync(FULL, t);
-        if (!tb) {
-            warp_copy(col, rowptr[u0], rowptr[u1], col_new + rowptr_new[u0]);
-            continue;
+        // the runs of untouched rows between touched ones, each one copy
+        // (touched rows are rebuilt by rebuild_touched_kernel)
+        int64_t v = u0;
+        while (v < u1) {
+            while (v < u1 && ((tb >> (v - u0)) & 1u)) ++v;
+            int64_t w = v;
+            while (w < u1 && !((tb >> (w - u0)) & 1u)) ++w;
+            if (w > v) warp_copy(col, rowptr[v], rowptr[w], col_new + rowptr_new[v]);
+            v = w;
         }
-        for (int64_t v = u0; v < u1; ++v) {
-            const int64_t o = rowptr_new[v];
-            if ((tb >> (v - u0)) & 1u) {
-                rebuild_touched_row(rowptr, col, v, o, ins_cnt, ins_start, bucket, table, mask, und, col_new);
-            } else {
-                warp_copy(col, rowptr[v], rowptr[v + 1], col_new + o);
-            }
+    }
+}
+
+// the first caller for row u gets true (its touched byte gains bit 1; the
+// array is padded to whole words)
+__device__ __forceinline__ bool claim_row(uint8_t* touched, int64_t u) {
+    unsigned int* w = (unsigned int*)(touched + (u & ~(int64_t)3));
+    const unsigned int bit = 2u << (8u * (unsigned int)(u & 3));
+    return !(atomicOr(w, bit) & bit);
+}
+
+// touched rows from row_lo on: one warp per update claims each of its rows
+// once and rebuilds it, so the rows of a batch are rebuilt in parallel
+template <typename Off>
+__global__ void rebuild_touched_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                       const int64_t* __restrict__ rowptr_new, const int32_t* __restrict__ inv,
+                                       const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                                       bool und, int64_t row_lo, uint8_t* touched,
+                                       const int32_t* __restrict__ ins_cnt, const int32_t* __restrict__ delta,
+                                       const int64_t* __restrict__ ins_start, const int32_t* __restrict__ bucket,
+                                       const unsigned long long* __restrict__ table, int64_t mask,
+                                       int32_t* col_new) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; e < m; e += warps) {
+        for (int q = 0; q < (und ? 2 : 1); ++q) {
+            const int64_t u = inv[q ? dst[e] : src[e]];
+            if (u < row_lo) continue;  // CHUNK rows: the hub kernels
+            int mine = lane == 0 ? (int)claim_row(touched, u) : 0;
+            if (!__shfl_sync(FULL, mine, 0)) continue;
+            rebuild_touched_row(rowptr, col, u, rowptr_new[u], ins_cnt, ins_start, bucket, table, mask, und,
+                                ins_cnt[u] == delta[u], col_new);
         }
     }
 }
@@ -715,15 +750,19 @@ cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, in
 }
 
 template <typename Off>
-static void rebuild_launch(DeviceGraph& g, const DynBuffers& d, const int64_t* rowptr_new, int32_t* col_new,
-                           cudaStream_t st) {
+static void rebuild_launch(DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new,
+                           int32_t* col_new, cudaStream_t st) {
     const Off* rp = (const Off*)g.rowptr;
     const SpmvLayout& L = g.layout;
     const int64_t groups = (g.n - L.row_warp + 31) / 32;
-    if (groups > 0)
+    if (groups > 0) {
         rebuild_groups_kernel<Off><<<grid_for(groups * 32, 256), 256, 0, st>>>(
             rp, g.col, rowptr_new, d.touched, d.ins_cnt, d.ins_start, d.bucket, d.table, d.table_mask, d.undirected,
             L.row_warp, g.n, col_new);
+        rebuild_touched_kernel<Off><<<grid_for(m * 32, 256), 256, 0, st>>>(
+            rp, g.col, rowptr_new, g.inv, d.src, d.dst, m, d.undirected, L.row_warp, d.touched, d.ins_cnt, d.delta,
+            d.ins_start, d.bucket, d.table, d.table_mask, col_new);
+    }
     if (L.chunks > 0)
         rebuild_chunks_kernel<Off><<<grid_for(L.chunks * 32, 256), 256, 0, st>>>(
             rp, g.col, rowptr_new, d.touched, g.chunk_row, g.chunk_first, L.chunks, col_new);
@@ -743,11 +782,10 @@ static void rebuild_launch(DeviceGraph& g, const DynBuffers& d, const int64_t* r
 // the old ones
 cudaError_t dyn_rebuild(DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new, int32_t* col_new,
                         cudaStream_t st) {
-    (void)m;
     if (g.off64)
-        rebuild_launch<int64_t>(g, d, rowptr_new, col_new, st);
+        rebuild_launch<int64_t>(g, d, m, rowptr_new, col_new, st);
     else
-        rebuild_launch<int32_t>(g, d, rowptr_new, col_new, st);
+        rebuild_launch<int32_t>(g, d, m, rowptr_new, col_new, st);
     if (g.off64)
         narrow_kernel<int64_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int64_t*)g.rowptr, g.n + 1);
     else
