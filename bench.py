@@ -254,7 +254,10 @@ def run_serving(batches, workers=2, slots=8):
     submit -> certified top-k on the host.  First at the specified rate
     (200 batches/s), then at 70% of the capacity that run measured (so the
     queue is stable), then the static recomputation of the final graph
-    (katz_rank_static on the same handle) as the baseline."""
+    (katz_rank_static on the same handle) as the baseline.  The capacity is
+    the throughput of the first run when it saturates (batches of one handle
+    are pipelined: the prepare of a batch overlaps the repair of the one
+    before it, so one request's service time is not the rate)."""
     import torch
 
     import graphgen as gg
@@ -263,7 +266,8 @@ def run_serving(batches, workers=2, slots=8):
     g = gg.workload(cfg["graph"])
     D = g.deg_max() + 64
     spec = serve_once(g, D, batches, cfg["rate"], workers, slots, torch)
-    capacity = 1e3 / spec["service_p50_ms"]
+    saturated = spec["achieved_rate"] < 0.97 * spec["offered_rate"]
+    capacity = spec["achieved_rate"] if saturated else spec["offered_rate"]
     stable = serve_once(g, D, batches, round(0.7 * capacity, 1), workers, slots, torch)
     spec["capacity_batches_per_s"] = capacity
     spec["within_capacity"] = stable

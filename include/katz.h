@@ -266,7 +266,13 @@ katz_status katz_restore(katz_h* out, const void* buf, uint64_t bytes, const kat
  * of `slots` staging slots is free and the admitted updates stay within
  * `admit_updates`; admission copies the batch to the device on the slot's own
  * stream, overlapping the work in flight.  `workers` host threads drive the
- * admitted requests through katz_apply_update_batch and katz_get_ranking.
+ * admitted requests through the two phases of katz_apply_update_batch and
+ * katz_get_ranking.  The first phase validates a batch and builds the updated
+ * graph into the handle's spare buffers on a second stream of the handle;
+ * the second swaps that graph in and repairs the walk vectors on the
+ * handle's stream.  On one handle the first phase of a request overlaps the
+ * second phase of the one before it, so with two or more workers the batches
+ * of one graph are pipelined.
  * Attaching a handle reserves its device buffers for batches of up to
  * slot_updates updates (and adjacency headroom), so a request allocates
  * nothing on the device unless its graph grows past that headroom.
@@ -288,7 +294,8 @@ typedef struct {
     katz_info info;         /* katz_apply_update_batch's info */
     double queue_ms;        /* submit -> admitted into a slot */
     double wait_ms;         /* admitted -> a worker started it */
-    double service_ms;      /* started -> ranking copied to the host */
+    double service_ms;      /* started -> ranking copied to the host (with pipelined batches
+                               this includes waiting for the earlier request's repair) */
     double latency_ms;      /* submit -> ranking copied to the host */
 } katz_request_result;
 

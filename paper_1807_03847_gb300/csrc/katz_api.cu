@@ -411,13 +411,19 @@ katz_status setup_ranking(katz_handle* h, double alpha, int64_t k_eff, double ep
     return KATZ_OK;
 }
 
-katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
+katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap, cudaStream_t st) {
     cudaError_t e;
     DeviceGraph& g = h->g;
     DynBuffers& d = h->dyn;
     const int64_t n = g.n;
 #define DALLOC(ptr, cnt)                                                      \
-    if ((e = dmalloc(h, &(ptr), (size_t)(cnt))) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc " #ptr);
+    if ((e = dmalloc_on(h, &(ptr), (size_t)(cnt), st)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc " #ptr);
+    if (!h->stream_a) {
+        if ((e = cudaStreamCreateWithFlags(&h->stream_a, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_prepared, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_committed, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(h, e, "update stream");
+    }
     if (!d.delta) {
         DALLOC(d.delta, n);
         DALLOC(d.ins_cnt, n);
@@ -433,32 +439,53 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
         DALLOC(h->rp_new, n + 1);
         DALLOC(h->deg_tmp, n + 1);
         DALLOC(h->scan_sums, scan_blocks(n + 1));
-        if ((e = cudaMemsetAsync(d.delta, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(d.ins_cnt, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(d.cursor, 0, (size_t)n * sizeof(int32_t), h->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(d.touched, 0, (size_t)((n + 3) / 4 * 4), h->stream)) != cudaSuccess)
+        if (g.off64) {
+            int64_t* rp = nullptr;
+            DALLOC(rp, n + 1);
+            h->rowptr_spare = rp;
+        } else {
+            int32_t* rp = nullptr;
+            DALLOC(rp, n + 1);
+            h->rowptr_spare = rp;
+        }
+        DALLOC(h->chunk_first_spare, g.layout.row_warp + 1);
+        DALLOC(h->chunk_row_spare, std::max<int64_t>(h->chunk_row_cap, 1));
+        h->chunk_row_spare_cap = std::max<int64_t>(h->chunk_row_cap, 1);
+        if ((e = cudaMemsetAsync(d.delta, 0, (size_t)n * sizeof(int32_t), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.ins_cnt, 0, (size_t)n * sizeof(int32_t), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.cursor, 0, (size_t)n * sizeof(int32_t), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.touched, 0, (size_t)((n + 3) / 4 * 4), st)) != cudaSuccess)
             return cuda_fail(h, e, "memset dynamic scratch");
         h->col_cap = g.nnz;
     }
+    if (m > h->bcap) {  // both batch sets (called before any batch is in flight, or for the first one)
+        for (int q = 0; q < 2; ++q) {
+            dfree_on(h->bsrc[q], st);
+            dfree_on(h->bdst[q], st);
+            dfree_on(h->bins[q], st);
+            h->bsrc[q] = nullptr;
+            h->bdst[q] = nullptr;
+            h->bins[q] = nullptr;
+        }
+        h->bcap = 0;
+        const int64_t cap = std::max<int64_t>(m, 1024);
+        for (int q = 0; q < 2; ++q) {
+            DALLOC(h->bsrc[q], cap);
+            DALLOC(h->bdst[q], cap);
+            DALLOC(h->bins[q], cap);
+        }
+        h->bcap = cap;
+    }
     if (m > d.cap) {
-        dfree(h, d.src);
-        dfree(h, d.dst);
-        dfree(h, d.ins);
-        dfree(h, d.ins_rows);
-        dfree(h, d.bucket);
-        dfree(h, d.table);
-        d.src = nullptr;
-        d.dst = nullptr;
-        d.ins = nullptr;
+        dfree_on(d.ins_rows, st);
+        dfree_on(d.bucket, st);
+        dfree_on(d.table, st);
         d.ins_rows = nullptr;
         d.bucket = nullptr;
         d.table = nullptr;
         d.table_mask = 0;
         d.cap = 0;
         const int64_t cap = std::max<int64_t>(m, 1024);
-        DALLOC(d.src, cap);
-        DALLOC(d.dst, cap);
-        DALLOC(d.ins, cap);
         DALLOC(d.ins_rows, 2 * cap);
         DALLOC(d.bucket, 2 * cap);
         int64_t tsize = 1;
@@ -466,11 +493,11 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap) {
         DALLOC(d.table, tsize);
         d.table_mask = tsize - 1;
         d.cap = cap;
-        if ((e = cudaMemsetAsync(d.table, 0, (size_t)tsize * sizeof(unsigned long long), h->stream)) != cudaSuccess)
+        if ((e = cudaMemsetAsync(d.table, 0, (size_t)tsize * sizeof(unsigned long long), st)) != cudaSuccess)
             return cuda_fail(h, e, "memset table");
     }
     if (nnz_cap > h->col_spare_cap) {
-        dfree(h, h->col_spare);
+        dfree_on(h->col_spare, st);
         h->col_spare = nullptr;
         h->col_spare_cap = 0;
         DALLOC(h->col_spare, nnz_cap);
@@ -600,13 +627,21 @@ void katz_destroy(katz_h h) {
         for (void* ptr : {(void*)d.src, (void*)d.dst, (void*)d.ins, (void*)d.hub_epoch, (void*)d.table,
                           (void*)d.err, (void*)d.delta, (void*)d.ins_cnt, (void*)d.cursor, (void*)d.touched,
                           (void*)d.ins_start, (void*)d.ins_rows, (void*)d.n_ins_rows, (void*)d.bucket,
-                          (void*)d.vbits, (void*)d.frontier, (void*)d.fsize, (void*)d.rrowptr, (void*)d.rcol,
+                          (void*)d.vbits, (void*)d.frontier, (void*)d.fsize, (void*)h->rrowptr, (void*)h->rcol,
                           (void*)d.hub_keep})
             dfree(h, ptr);
         dfree(h, h->col_spare);
         dfree(h, h->rp_new);
         dfree(h, h->deg_tmp);
         dfree(h, h->scan_sums);
+        if (h->stream_a) cudaStreamSynchronize(h->stream_a);
+        for (void* ptr : {(void*)h->rowptr_spare, (void*)h->chunk_first_spare, (void*)h->chunk_row_spare,
+                          (void*)h->bsrc[0], (void*)h->bsrc[1], (void*)h->bdst[0], (void*)h->bdst[1],
+                          (void*)h->bins[0], (void*)h->bins[1], (void*)h->t_cnt, (void*)h->t_sums})
+            dfree(h, ptr);
+        if (h->ev_prepared) cudaEventDestroy(h->ev_prepared);
+        if (h->ev_committed) cudaEventDestroy(h->ev_committed);
+        if (h->stream_a) cudaStreamDestroy(h->stream_a);
     }
     cudaFreeHost(h->h_ctrl);
     drop_graph(h);
@@ -781,6 +816,8 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     KCHK2(dmalloc(h, &g.chunk_first, (size_t)row_warp + 1), "cudaMalloc");
     KCHK2(dmalloc(h, &g.chunk_row, (size_t)chunks_cap), "cudaMalloc");
     KCHK2(dmalloc(h, &g.chunk_part, 3 * (size_t)chunks_cap), "cudaMalloc");
+    h->chunk_row_cap = chunks_cap;
+    h->chunk_part_cap = chunks_cap;
     KCHK2(build_chunk_table(rp_new, row_warp, deg_new, sums, g.chunk_first, g.chunk_row, d_bad + 2, h->stream),
           "chunk table");
     // the column array, slice by slice as it arrives (entries range-checked);
@@ -1129,153 +1166,245 @@ katz_status katz_get_trace(katz_h h, int64_t* active_per_iter, int32_t cap) {
     return KATZ_OK;
 }
 
-// Algorithm 2 on the device: validate, apply, repair s_1..s_r, re-derive the
-// active set and continue iterating until converged() holds again.
-katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t* dst, const uint8_t* is_insert,
-                                    int64_t m, katz_info* info) {
-    if (!h) return KATZ_EINVAL;
-    h->err.clear();
-    if (!h->ranked) return fail(h, KATZ_ESTATE, "rank the graph before updating it");
-    if (h->criterion != KATZ_CRIT_TOPK) return fail(h, KATZ_ESTATE, "dynamic updates continue the top-k criterion");
-    if (!h->opts.keep_history) return fail(h, KATZ_ESTATE, "dynamic updates need keep_history = 1");
-    if (h->fp32) return fail(h, KATZ_ESTATE, "dynamic updates run in FP64 mode");
-    if (m < 0 || (m > 0 && (!src || !dst || !is_insert))) return fail(h, KATZ_EINVAL, "bad batch arguments");
-    // an inbound handle holds the reverse graph: the arc src -> dst of the
-    // given graph is dst -> src there
-    if (h->opts.inbound && !h->opts.undirected) std::swap(src, dst);
+}  // extern "C"
+
+namespace katz {
+
+// Phase 1 of Algorithm 2 for one batch, on stream_a: the preconditions
+// checked against the current graph, then the updated graph built into the
+// spare buffers (col, row offsets, chunk table).  The current graph and
+// everything the repair of an earlier batch reads stay untouched, so this can
+// run while that repair is on the device.  The result waits in h->pend.
+katz_status update_prepare(katz_handle* h, const int32_t* src, const int32_t* dst, const uint8_t* is_insert,
+                           int64_t m, cudaEvent_t ready) {
+    katz_handle::Pending& pd = h->pend;
+    pd = katz_handle::Pending();
+    pd.m = m;
+    cudaError_t e;
+    const DeviceGraph& g = h->g;
+    const int64_t n = g.n;
+    if (!h->stream_a) {  // the stream and events of the two phases, once
+        if ((e = cudaStreamCreateWithFlags(&h->stream_a, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_prepared, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_committed, cudaEventDisableTiming)) != cudaSuccess) {
+            pd.status = KATZ_ECUDA;
+            pd.err = "update stream";
+            pd.ready = true;
+            return pd.status;
+        }
+    }
+    cudaStream_t sa = h->stream_a;
+    // every way out records ev_prepared on stream_a: the commit waits for it
+    auto done = [&](katz_status st, const char* msg) {
+        pd.status = st;
+        if (msg) pd.err = msg;
+        cudaEventRecord(h->ev_prepared, sa);
+        pd.ready = true;
+        return st;
+    };
+    auto cuda_done = [&](cudaError_t ce, const char* what) {
+        return done(ce == cudaErrorMemoryAllocation ? KATZ_ENOMEM : KATZ_ECUDA,
+                    (std::string(what) + ": " + cudaGetErrorString(ce)).c_str());
+    };
+    // the spare buffers held the graph before the current one: the repair
+    // that read it is queued on the handle's stream before ev_committed
+    if ((e = cudaStreamWaitEvent(sa, h->ev_committed, 0)) != cudaSuccess) return cuda_done(e, "event");
+    if (ready && (e = cudaStreamWaitEvent(sa, ready, 0)) != cudaSuccess) return cuda_done(e, "event");  // the batch
+    {
+        const katz_status rs = dyn_reserve(h, m, 0, sa);
+        if (rs != KATZ_OK) return done(rs, "cudaMalloc update scratch");
+    }
+    const int bs = h->next_bset;
+    h->next_bset ^= 1;
+    pd.bset = bs;
+    DynBuffers d = h->dyn;  // this phase's view: its batch set
+    d.src = h->bsrc[bs];
+    d.dst = h->bdst[bs];
+    d.ins = h->bins[bs];
+    d.undirected = h->opts.undirected != 0;
+    if (m == 0) return done(KATZ_OK, nullptr);
+    if ((e = cudaMemcpyAsync(d.src, src, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, sa)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d.dst, dst, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, sa)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d.ins, is_insert, (size_t)m, cudaMemcpyDefault, sa)) != cudaSuccess)
+        return cuda_done(e, "copy batch");
+    // ---- validate (nothing changes unless the whole batch is valid) --------------
+    int32_t* herr = (int32_t*)(h->h_small + H_SMALL - 64);  // pinned words of this phase
+    if ((e = cudaMemsetAsync(d.err, 0, sizeof(int32_t), sa)) != cudaSuccess ||
+        (e = dyn_validate(g, d, m, h->D, sa)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(herr, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, sa)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(sa)) != cudaSuccess)
+        return cuda_done(e, "validate batch");
+    pd.launches += 2;
+    if (*herr) {
+        const int32_t err = *herr;
+        if ((e = dyn_clear(g, d, m, sa)) != cudaSuccess || (e = cudaStreamSynchronize(sa)) != cudaSuccess)
+            return cuda_done(e, "clear batch");
+        if (err & DYN_E_INVAL)
+            return done(KATZ_EINVAL, "batch violates the preconditions (range, self-loop, duplicate pair, "
+                                     "inserted edge present or deleted edge absent)");
+        return done(KATZ_EALPHA, "a row would exceed the degree bound D");
+    }
+    // ---- apply: new offsets, rows rebuilt into the spare buffers ------------------
+    if ((e = dyn_prepare(g, d, m, h->rp_new, h->deg_tmp, h->scan_sums, sa)) != cudaSuccess)
+        return cuda_done(e, "prepare rebuild");
+    pd.launches += 8;  // 5 bucket/degree kernels + 3 scan passes
+    int64_t* hnnz = (int64_t*)(h->h_small + H_SMALL - 56);
+    if ((e = cudaMemcpyAsync(hnnz, h->rp_new + n, sizeof(int64_t), cudaMemcpyDeviceToHost, sa)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(sa)) != cudaSuccess)
+        return cuda_done(e, "rebuild size");
+    const int64_t nnz_new = *hnnz;
+    if (!g.off64 && n + nnz_new >= 0x7fffffffLL) {
+        dyn_clear(g, d, m, sa);
+        cudaStreamSynchronize(sa);
+        return done(KATZ_EINVAL, "the graph would outgrow 32-bit offsets; create it with more headroom");
+    }
+    if (nnz_new > h->col_spare_cap) {
+        dfree_on(h->col_spare, sa);
+        h->col_spare = nullptr;
+        h->col_spare_cap = 0;
+        const int64_t cap = nnz_new + nnz_new / 16 + 1024;
+        if ((e = dmalloc_on(h, &h->col_spare, (size_t)cap, sa)) != cudaSuccess) {
+            dyn_clear(g, d, m, sa);
+            cudaStreamSynchronize(sa);
+            return cuda_done(e, "cudaMalloc col");
+        }
+        h->col_spare_cap = cap;
+    }
+    const bool hubs = g.layout.row_warp > 0;
+    if (hubs && g.layout.chunks > d.hub_keep_cap) {
+        dfree_on(h->dyn.hub_keep, sa);
+        h->dyn.hub_keep = nullptr;
+        h->dyn.hub_keep_cap = 0;
+        const int64_t cap = g.layout.chunks + g.layout.chunks / 8 + 64;
+        if ((e = dmalloc_on(h, &h->dyn.hub_keep, (size_t)cap, sa)) != cudaSuccess) {
+            dyn_clear(g, d, m, sa);
+            cudaStreamSynchronize(sa);
+            return cuda_done(e, "cudaMalloc hub chunks");
+        }
+        h->dyn.hub_keep_cap = cap;
+        d.hub_keep = h->dyn.hub_keep;
+        d.hub_keep_cap = cap;
+    }
+    if ((e = dyn_rebuild(g, d, m, h->rp_new, h->col_spare, h->rowptr_spare, sa)) != cudaSuccess)
+        return cuda_done(e, "rebuild rows");
+    pd.launches += (g.n > g.layout.row_warp ? 2 : 0) + (g.layout.chunks > 0 ? 1 : 0) + (hubs ? 3 : 0) + 1;
+    if ((e = dyn_clear(g, d, m, sa)) != cudaSuccess) return cuda_done(e, "clear batch");
+    pd.launches += 1;
+    // chunk table of the CHUNK rows from their new degrees, into the spares
+    const int64_t rw = g.layout.row_warp;
+    std::vector<int64_t> hrp((size_t)rw + 1);
+    if ((e = cudaMemcpyAsync(hrp.data(), h->rp_new, hrp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, sa)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(sa)) != cudaSuccess)
+        return cuda_done(e, "copy rowptr head");
+    std::vector<int64_t> first((size_t)rw + 1, 0);
+    for (int64_t u = 0; u < rw; ++u) first[u + 1] = first[u] + (hrp[u + 1] - hrp[u] + CHUNK_ARCS - 1) / CHUNK_ARCS;
+    const int64_t chunks = first[rw];
+    if (chunks > h->chunk_row_spare_cap) {
+        dfree_on(h->chunk_row_spare, sa);
+        h->chunk_row_spare = nullptr;
+        h->chunk_row_spare_cap = 0;
+        const int64_t cap = chunks + chunks / 8 + 16;
+        if ((e = dmalloc_on(h, &h->chunk_row_spare, (size_t)cap, sa)) != cudaSuccess)
+            return cuda_done(e, "cudaMalloc chunks");
+        h->chunk_row_spare_cap = cap;
+    }
+    std::vector<int32_t> crow((size_t)std::max<int64_t>(chunks, 1));
+    for (int64_t u = 0; u < rw; ++u)
+        for (int64_t q = first[u]; q < first[u + 1]; ++q) crow[q] = (int32_t)u;
+    if ((e = cudaMemcpyAsync(h->chunk_first_spare, first.data(), first.size() * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, sa)) != cudaSuccess ||
+        (chunks > 0 && (e = cudaMemcpyAsync(h->chunk_row_spare, crow.data(), (size_t)chunks * sizeof(int32_t),
+                                            cudaMemcpyHostToDevice, sa)) != cudaSuccess) ||
+        (e = cudaStreamSynchronize(sa)) != cudaSuccess)
+        return cuda_done(e, "copy chunks");
+    pd.nnz = nnz_new;
+    pd.chunks = chunks;
+    pd.applied = true;
+    return done(KATZ_OK, nullptr);
+}
+
+// Phase 2a on the handle's stream: the prepared graph becomes the current
+// one (host-side swaps; once this returns, the next batch may be prepared).
+katz_status update_swap(katz_handle* h) {
+    katz_handle::Pending& pd = h->pend;
     cudaError_t e;
     DeviceGraph& g = h->g;
-    DynBuffers& d = h->dyn;
     const int64_t n = g.n;
-    const int r = h->r;
-    if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
-    h->launches = 0;
+    h->err.clear();
+    h->launches = pd.launches;
     h->big_paths = 0;
-    const bool hubs = g.layout.row_warp > 0;
-    // ---- buffers --------------------------------------------------------------
+    if ((e = cudaStreamWaitEvent(h->stream, h->ev_prepared, 0)) != cudaSuccess) return cuda_fail(h, e, "event");
+    if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+    h->rep = pd;  // the next prepare may overwrite pend once this returns
+    if (pd.status != KATZ_OK || !pd.applied) {
+        if ((e = cudaEventRecord(h->ev_committed, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+        return pd.status != KATZ_OK ? fail(h, pd.status, pd.err) : KATZ_OK;
+    }
     {
-        const katz_status rs = katz::dyn_reserve(h, m, 0);
-        if (rs != KATZ_OK) return rs;
-    }
-    d.undirected = h->opts.undirected != 0;
-    if (m > 0) {
-        if ((e = cudaMemcpyAsync(d.src, src, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, h->stream)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(d.dst, dst, (size_t)m * sizeof(int32_t), cudaMemcpyDefault, h->stream)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(d.ins, is_insert, (size_t)m, cudaMemcpyDefault, h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "copy batch");
-    }
-    int64_t full_levels = 0, affected = 0;
-    if (m > 0) {
-        // ---- validate (nothing changes unless the whole batch is valid) ----------
-        if ((e = cudaMemsetAsync(d.err, 0, sizeof(int32_t), h->stream)) != cudaSuccess ||
-            (e = dyn_validate(g, d, m, h->D, h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "validate batch");
-        h->launches += 2;
-        int32_t err = 0;
-        if ((e = cudaMemcpyAsync(&err, d.err, sizeof(err), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "validate sync");
-        if (err) {
-            if ((e = dyn_clear(g, d, m, h->stream)) != cudaSuccess ||
-                (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-                return cuda_fail(h, e, "clear batch");
-            if (err & DYN_E_INVAL)
-                return fail(h, KATZ_EINVAL, "batch violates the preconditions (range, self-loop, duplicate pair, "
-                                            "inserted edge present or deleted edge absent)");
-            return fail(h, KATZ_EALPHA, "a row would exceed the degree bound D");
-        }
-        // ---- apply: new offsets, rows rebuilt into the spare col buffer -----------
-        if ((e = dyn_prepare(g, d, m, h->rp_new, h->deg_tmp, h->scan_sums, h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "prepare rebuild");
-        h->launches += 8;  // 5 bucket/degree kernels + 3 scan passes
-        int64_t nnz_new = 0;
-        if ((e = cudaMemcpyAsync(&nnz_new, h->rp_new + n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream)) !=
-                cudaSuccess ||
-            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "rebuild size");
-        if (!g.off64 && n + nnz_new >= 0x7fffffffLL) {
-            dyn_clear(g, d, m, h->stream);
-            return fail(h, KATZ_EINVAL, "the graph would outgrow 32-bit offsets; create it with more headroom");
-        }
-        if (nnz_new > h->col_spare_cap) {
-            dfree(h, h->col_spare);
-            h->col_spare = nullptr;
-            const int64_t cap = nnz_new + nnz_new / 16 + 1024;
-            if ((e = dmalloc(h, &h->col_spare, (size_t)cap)) != cudaSuccess) {
-                h->col_spare_cap = 0;
-                dyn_clear(g, d, m, h->stream);
-                return cuda_fail(h, e, "cudaMalloc col");
-            }
-            h->col_spare_cap = cap;
-        }
-        if (hubs && g.layout.chunks > d.hub_keep_cap) {
-            dfree(h, d.hub_keep);
-            d.hub_keep = nullptr;
-            d.hub_keep_cap = 0;
-            const int64_t cap = g.layout.chunks + g.layout.chunks / 8 + 64;
-            if ((e = dmalloc(h, &d.hub_keep, (size_t)cap)) != cudaSuccess) {
-                dyn_clear(g, d, m, h->stream);
-                return cuda_fail(h, e, "cudaMalloc hub chunks");
-            }
-            d.hub_keep_cap = cap;
-        }
-        if ((e = dyn_rebuild(g, d, m, h->rp_new, h->col_spare, h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "rebuild rows");
-        h->launches += (g.n > g.layout.row_warp ? 2 : 0) + (g.layout.chunks > 0 ? 1 : 0) + (hubs ? 3 : 0) + 1;
         std::swap(g.col, h->col_spare);
         std::swap(h->col_cap, h->col_spare_cap);
-        g.nnz = nnz_new;
-        h->classes_exact = false;  // rows keep their place while their degrees change
-        if ((e = dyn_clear(g, d, m, h->stream)) != cudaSuccess) return cuda_fail(h, e, "clear batch");
-        h->launches += 1;
-        // chunk table of the CHUNK rows from their new degrees
-        {
-            const int64_t rw = g.layout.row_warp;
-            std::vector<int64_t> hrp((size_t)rw + 1);
-            if ((e = cudaMemcpyAsync(hrp.data(), h->rp_new, hrp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                     h->stream)) != cudaSuccess ||
-                (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-                return cuda_fail(h, e, "copy rowptr head");
-            std::vector<int64_t> first((size_t)rw + 1, 0);
-            for (int64_t u = 0; u < rw; ++u)
-                first[u + 1] = first[u] + (hrp[u + 1] - hrp[u] + CHUNK_ARCS - 1) / CHUNK_ARCS;
-            const int64_t chunks = first[rw];
-            if (chunks > g.layout.chunks) {
-                dfree(h, g.chunk_row);
-                dfree(h, g.chunk_part);
-                g.chunk_row = nullptr;
-                g.chunk_part = nullptr;
-                if ((e = dmalloc(h, &g.chunk_row, (size_t)chunks)) != cudaSuccess ||
-                    (e = dmalloc(h, &g.chunk_part, 3 * (size_t)chunks)) != cudaSuccess)
-                    return cuda_fail(h, e, "cudaMalloc chunks");
-            }
-            std::vector<int32_t> crow((size_t)std::max<int64_t>(chunks, 1));
-            for (int64_t u = 0; u < rw; ++u)
-                for (int64_t q = first[u]; q < first[u + 1]; ++q) crow[q] = (int32_t)u;
-            if ((e = cudaMemcpyAsync(g.chunk_first, first.data(), first.size() * sizeof(int64_t),
-                                     cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
-                (chunks > 0 && (e = cudaMemcpyAsync(g.chunk_row, crow.data(), (size_t)chunks * sizeof(int32_t),
-                                                    cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) ||
-                (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-                return cuda_fail(h, e, "copy chunks");
-            g.layout = make_layout(n, g.layout.row_warp, g.layout.row_octet, g.layout.row_thread, chunks);
+        std::swap(g.rowptr, h->rowptr_spare);
+        std::swap(g.chunk_first, h->chunk_first_spare);
+        std::swap(g.chunk_row, h->chunk_row_spare);
+        std::swap(h->chunk_row_cap, h->chunk_row_spare_cap);
+        g.nnz = pd.nnz;
+        if (pd.chunks > h->chunk_part_cap) {
+            dfree(h, g.chunk_part);
+            g.chunk_part = nullptr;
+            h->chunk_part_cap = 0;
+            const int64_t cap = pd.chunks + pd.chunks / 8 + 16;
+            if ((e = dmalloc(h, &g.chunk_part, 3 * (size_t)cap)) != cudaSuccess)
+                return cuda_fail(h, e, "cudaMalloc chunk sums");
+            h->chunk_part_cap = cap;
         }
-        drop_graph(h);  // captured launches hold the old arrays and layout
+        g.layout = make_layout(n, g.layout.row_warp, g.layout.row_octet, g.layout.row_thread, pd.chunks);
+        h->classes_exact = false;  // rows keep their place while their degrees change
+        drop_graph(h);             // captured launches hold the old arrays and layout
+        // the next prepare may overwrite the old graph once the work on it,
+        // queued before this point, is done
+        if ((e = cudaEventRecord(h->ev_committed, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+    }
+    return KATZ_OK;
+}
+
+// Phase 2b on the handle's stream: s_1..s_r repaired (Sec. 4), the bounds and
+// the active set re-derived, and further iterations until converged() holds.
+katz_status update_repair(katz_handle* h, katz_info* info) {
+    const katz_handle::Pending& pd = h->rep;
+    cudaError_t e;
+    DeviceGraph& g = h->g;
+    const int64_t n = g.n, m = pd.m;
+    const int r = h->r;
+    DynBuffers d = h->dyn;  // the repair's view: the batch set its prepare used
+    d.src = h->bsrc[pd.bset];
+    d.dst = h->bdst[pd.bset];
+    d.ins = h->bins[pd.bset];
+    d.undirected = h->opts.undirected != 0;
+    const bool hubs = g.layout.row_warp > 0;
+    int64_t full_levels = 0, affected = 0;
+    if (pd.applied) {
         // directed: the reverse BFS walks in-arcs, from the transposed CSR of
         // the updated graph
         if (!d.undirected) {
-            if (!d.rrowptr && (e = dmalloc(h, &d.rrowptr, (size_t)n + 1)) != cudaSuccess)
+            if (!h->rrowptr && (e = dmalloc(h, &h->rrowptr, (size_t)n + 1)) != cudaSuccess)
                 return cuda_fail(h, e, "cudaMalloc transposed offsets");
-            if (g.nnz > d.rcap) {
-                dfree(h, d.rcol);
-                d.rcol = nullptr;
-                d.rcap = 0;
+            if (!h->t_cnt && ((e = dmalloc(h, &h->t_cnt, (size_t)n + 1)) != cudaSuccess ||
+                              (e = dmalloc(h, &h->t_sums, (size_t)scan_blocks(n + 1))) != cudaSuccess))
+                return cuda_fail(h, e, "cudaMalloc transposition scratch");
+            if (g.nnz > h->rcap) {
+                dfree(h, h->rcol);
+                h->rcol = nullptr;
+                h->rcap = 0;
                 const int64_t cap = g.nnz + g.nnz / 16 + 1024;
-                if ((e = dmalloc(h, &d.rcol, (size_t)cap)) != cudaSuccess)
+                if ((e = dmalloc(h, &h->rcol, (size_t)cap)) != cudaSuccess)
                     return cuda_fail(h, e, "cudaMalloc transposed arcs");
-                d.rcap = cap;
+                h->rcap = cap;
             }
-            if ((e = dyn_transpose(g, d, h->deg_tmp, h->scan_sums, h->stream)) != cudaSuccess)
+            d.rrowptr = h->rrowptr;
+            d.rcol = h->rcol;
+            d.rcap = h->rcap;
+            if ((e = dyn_transpose(g, d, h->t_cnt, h->t_sums, h->stream)) != cudaSuccess)
                 return cuda_fail(h, e, "transpose");
             h->launches += 3 + (g.nnz > 0 ? 1 + (g.n > g.layout.row_warp ? 1 : 0) + (g.layout.chunks > 0 ? 1 : 0) : 0);
         }
@@ -1283,8 +1412,9 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
         //      affected set is large (Sec. 4) ------------------------------------------
         if ((e = dyn_seed(g, d, m, h->stream)) != cudaSuccess) return cuda_fail(h, e, "seed frontier");
         h->launches += 1;
-        unsigned long long fs[2] = {0, 0};  // frontier size, sum of its degrees
-        if ((e = cudaMemcpyAsync(fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+        unsigned long long* fs = (unsigned long long*)(h->h_small + H_SMALL - 32);  // frontier size, its arcs
+        if ((e = cudaMemcpyAsync(fs, d.fsize, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream)) !=
+                cudaSuccess ||
             (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "frontier size");
         const double tau = h->opts.frontier_abort_frac > 0 ? h->opts.frontier_abort_frac : 0.05;
@@ -1322,7 +1452,8 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
                 vol_lo = fs[1];
                 if ((e = dyn_expand(g, d, lo, hi, i, h->stream)) != cudaSuccess) return cuda_fail(h, e, "expand");
                 h->launches += hi > lo ? 1 + (d.undirected && g.layout.chunks > 0 ? 1 : 0) : 0;
-                if ((e = cudaMemcpyAsync(fs, d.fsize, sizeof(fs), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+                if ((e = cudaMemcpyAsync(fs, d.fsize, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                         h->stream)) != cudaSuccess ||
                     (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
                     return cuda_fail(h, e, "frontier size");
                 lo = hi;
@@ -1390,6 +1521,41 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
     }
     if (!h->converged) return fail(h, KATZ_ENOTCONV, "r_max reached before the top-k criterion held");
     return KATZ_OK;
+}
+
+katz_status update_commit(katz_handle* h, katz_info* info) {
+    const katz_status st = update_swap(h);
+    return st != KATZ_OK ? st : update_repair(h, info);
+}
+
+// the checks a handle must pass before it takes update batches
+katz_status update_allowed(katz_handle* h) {
+    if (!h->ranked) return fail(h, KATZ_ESTATE, "rank the graph before updating it");
+    if (h->criterion != KATZ_CRIT_TOPK) return fail(h, KATZ_ESTATE, "dynamic updates continue the top-k criterion");
+    if (!h->opts.keep_history) return fail(h, KATZ_ESTATE, "dynamic updates need keep_history = 1");
+    if (h->fp32) return fail(h, KATZ_ESTATE, "dynamic updates run in FP64 mode");
+    return KATZ_OK;
+}
+
+}  // namespace katz
+
+extern "C" {
+
+// Algorithm 2 on the device: validate, apply, repair s_1..s_r, re-derive the
+// active set and continue iterating until converged() holds again (the two
+// phases back to back).
+katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t* dst, const uint8_t* is_insert,
+                                    int64_t m, katz_info* info) {
+    if (!h) return KATZ_EINVAL;
+    h->err.clear();
+    katz_status st = update_allowed(h);
+    if (st != KATZ_OK) return st;
+    if (m < 0 || (m > 0 && (!src || !dst || !is_insert))) return fail(h, KATZ_EINVAL, "bad batch arguments");
+    // an inbound handle holds the reverse graph: the arc src -> dst of the
+    // given graph is dst -> src there
+    if (h->opts.inbound && !h->opts.undirected) std::swap(src, dst);
+    update_prepare(h, src, dst, is_insert, m, nullptr);
+    return update_commit(h, info);
 }
 
 }  // extern "C"

@@ -199,6 +199,8 @@ katz_status katz_restore(katz_h* out, const void* buf, uint64_t bytes, const kat
     A(&g.chunk_first, (uint64_t)hd.row_warp + 1);
     A(&g.chunk_row, (uint64_t)hd.chunks + 1);
     A(&g.chunk_part, 3 * ((uint64_t)hd.chunks + 1));
+    h->chunk_row_cap = hd.chunks + 1;
+    h->chunk_part_cap = hd.chunks + 1;
     if (e != cudaSuccess) {
         st = cuda_fail(h, e, "cudaMalloc graph");
         katz_destroy(h);

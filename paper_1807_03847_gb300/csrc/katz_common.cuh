@@ -239,7 +239,8 @@ cudaError_t dyn_validate(const DeviceGraph& g, const DynBuffers& d, int64_t m, i
 cudaError_t dyn_clear(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st);
 cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, int64_t* rowptr_new, int64_t* deg,
                         int64_t* sums, cudaStream_t st);
-cudaError_t dyn_rebuild(DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new, int32_t* col_new,
+cudaError_t dyn_rebuild(const DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new,
+                        int32_t* col_new, void* rowptr_out,
                         cudaStream_t st);
 cudaError_t dyn_seed(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st);
 cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, int64_t hi, int level,

@@ -750,7 +750,7 @@ cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, in
 }
 
 template <typename Off>
-static void rebuild_launch(DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new,
+static void rebuild_launch(const DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new,
                            int32_t* col_new, cudaStream_t st) {
     const Off* rp = (const Off*)g.rowptr;
     const SpmvLayout& L = g.layout;
@@ -778,18 +778,18 @@ static void rebuild_launch(DeviceGraph& g, const DynBuffers& d, int64_t m, const
     }
 }
 
-// rows into col_new (old layout and chunk table), then the new offsets over
-// the old ones
-cudaError_t dyn_rebuild(DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new, int32_t* col_new,
-                        cudaStream_t st) {
+// rows into col_new (read through the old layout and chunk table), and the
+// new offsets, in the offset type of g, into rowptr_out (g itself unchanged)
+cudaError_t dyn_rebuild(const DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new,
+                        int32_t* col_new, void* rowptr_out, cudaStream_t st) {
     if (g.off64)
         rebuild_launch<int64_t>(g, d, m, rowptr_new, col_new, st);
     else
         rebuild_launch<int32_t>(g, d, m, rowptr_new, col_new, st);
     if (g.off64)
-        narrow_kernel<int64_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int64_t*)g.rowptr, g.n + 1);
+        narrow_kernel<int64_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int64_t*)rowptr_out, g.n + 1);
     else
-        narrow_kernel<int32_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int32_t*)g.rowptr, g.n + 1);
+        narrow_kernel<int32_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int32_t*)rowptr_out, g.n + 1);
     return cudaGetLastError();
 }
 

@@ -57,6 +57,36 @@ struct katz_handle {
     int64_t* rp_new = nullptr;        // [n+1]
     int64_t* deg_tmp = nullptr;       // [n+1]
     int64_t* scan_sums = nullptr;
+    // Updates in two phases (katz_api.cu): prepare validates a batch against
+    // the current graph and builds the next graph into the spare buffers on
+    // stream_a; commit swaps them in and repairs on stream.  The server runs
+    // the prepare of batch j+1 while batch j is repaired.
+    cudaStream_t stream_a = nullptr;
+    cudaEvent_t ev_prepared = nullptr;   // stream_a: the prepared graph is complete
+    cudaEvent_t ev_committed = nullptr;  // stream: work on the previous graph is queued before this
+    void* rowptr_spare = nullptr;        // [n+1], the offset type of g.rowptr
+    int64_t* chunk_first_spare = nullptr;  // [row_warp+1]
+    int32_t* chunk_row_spare = nullptr;
+    int64_t chunk_row_cap = 0, chunk_row_spare_cap = 0, chunk_part_cap = 0;  // in chunks
+    int32_t* bsrc[2] = {nullptr, nullptr};  // batch arrays, one set per phase in flight
+    int32_t* bdst[2] = {nullptr, nullptr};
+    uint8_t* bins[2] = {nullptr, nullptr};
+    int64_t bcap = 0;
+    int next_bset = 0;
+    int64_t* t_cnt = nullptr;   // [n+1] transposition scratch of the repair (directed)
+    int64_t* t_sums = nullptr;
+    struct Pending {
+        bool ready = false;
+        katz_status status = KATZ_OK;
+        std::string err;
+        int64_t m = 0, nnz = 0, chunks = 0, launches = 0;
+        int bset = 0;
+        bool applied = false;   // the batch changed the graph (m > 0 and valid)
+    } pend;                     // written by the prepare
+    Pending rep;                // the swapped-in batch, read by its repair
+    int64_t* rrowptr = nullptr; // [n+1] directed: transposed CSR of the current graph (the repair's)
+    int32_t* rcol = nullptr;
+    int64_t rcap = 0;
     // stopping criteria other than top-k
     int criterion = KATZ_CRIT_TOPK;
     int32_t* rank_ids = nullptr;      // [n] ranking criterion: the order, original ids
@@ -92,6 +122,20 @@ inline void dfree(katz_handle* h, void* p) {
     if (p) cudaFreeAsync(p, h->stream);
 }
 
+// the same, ordered on stream st instead of the handle's stream
+template <typename X>
+cudaError_t dmalloc_on(katz_handle* h, X** p, size_t count, cudaStream_t st) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaMemPool_t pool = library_pool(h->dev);
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync((void**)p, count * sizeof(X), pool, st);
+}
+
+inline void dfree_on(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
 katz_status init_handle_runtime(katz_handle* h);
 katz_status ensure_iter_buffers(katz_handle* h);
 katz_status alloc_rank_scratch(katz_handle* h);
@@ -100,5 +144,15 @@ katz_status cuda_fail(katz_handle* h, cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
 void drop_graph(katz_handle* h);
 cudaError_t launch_narrow_rowptr(const int64_t* in, int32_t* out, int64_t count, cudaStream_t st);
-katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap);
+katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap, cudaStream_t st);
+katz_status update_allowed(katz_handle* h);
+// Algorithm 2 in phases: prepare (stream_a; ready: an event the batch arrays
+// wait for, or nullptr), then swap and repair (the handle's stream).  At most
+// one prepared batch waits for its swap; a prepare reads the graph the
+// latest swap made current.
+katz_status update_prepare(katz_handle* h, const int32_t* src, const int32_t* dst, const uint8_t* is_insert,
+                           int64_t m, cudaEvent_t ready);
+katz_status update_swap(katz_handle* h);
+katz_status update_repair(katz_handle* h, katz_info* info);
+katz_status update_commit(katz_handle* h, katz_info* info);
 }  // namespace katz

@@ -11,10 +11,14 @@
 //     staging slots while a slot is free and the admitted updates stay within
 //     the update budget; admission starts the host-to-device copy of the batch
 //     on the slot's copy stream, so it overlaps whatever runs on the device;
-//   - `workers` threads take admitted requests, oldest first, skipping those
-//     whose handle is busy with an earlier request (requests on one handle run
-//     in arrival order, requests on different handles run at the same time,
-//     each on its handle's stream);
+//   - `workers` threads take admitted requests, oldest first.  A request runs
+//     in two phases (katz_api.cu): its prepare validates the batch and builds
+//     the updated graph into the handle's spare buffers on a second stream,
+//     its commit swaps that graph in and repairs the walk vectors on the
+//     handle's stream.  On one handle the phases follow arrival order, and the
+//     prepare of a request overlaps the repair of the one before it (it may
+//     start once that one has swapped its graph in); requests on different
+//     handles run at the same time;
 //   - a finished request releases its slot, which admits the next one, and
 //     its result (status, info, ranking, timestamps) waits for wait().
 // Every request sees exactly the graph that the requests on its handle before
@@ -47,6 +51,7 @@ enum RequestState { WAITING, ADMITTED, RUNNING, DONE };
 
 struct Request {
     uint64_t ticket = 0;
+    uint64_t seq = 0;  // arrival order on its handle
     katz_handle* h = nullptr;
     int64_t m = 0;
     std::vector<int32_t> src, dst;
@@ -73,7 +78,11 @@ struct Slot {
 
 struct Lane {
     int64_t k = 0;
-    bool busy = false;
+    uint64_t next_seq = 0;      // sequence number of the next submitted request
+    uint64_t prep_seq = 0;      // the next request to prepare
+    bool preparing = false;     // a prepare is running
+    bool swap_pending = false;  // a prepared request has not swapped its graph in yet
+    bool repairing = false;     // a swap or repair is running
 };
 
 }  // namespace
@@ -143,21 +152,41 @@ void admit_locked(katz_server* s) {
     }
 }
 
-void run_request(katz_server* s, Request* q, int64_t k) {
+// Phase 1 (the caller holds no lock): the batch, once on the device, is
+// validated and the next graph built into the handle's spare buffers.
+void prepare_request(katz_server* s, Request* q) {
     Slot& sl = s->slots[(size_t)q->slot];
     katz_handle* h = q->h;
-    cudaError_t e = cudaStreamWaitEvent(h->stream, sl.h2d_done, 0);
-    if (e != cudaSuccess) {
-        q->status = KATZ_ECUDA;
-        return;
-    }
-    q->status = katz_apply_update_batch(h, sl.d_src, sl.d_dst, sl.d_ins, q->m, &q->info);
+    const int32_t* src = sl.d_src;
+    const int32_t* dst = sl.d_dst;
+    if (h->opts.inbound && !h->opts.undirected) std::swap(src, dst);  // the handle holds the reverse graph
+    katz::update_prepare(h, src, dst, sl.d_ins, q->m, sl.h2d_done);
+}
+
+// Phase 2 (the caller holds mu, released while the device works): wait for
+// the earlier request's repair, swap the prepared graph in, let the next
+// prepare start, then repair and read the ranking.
+void commit_request(katz_server* s, Request* q, int64_t k, std::unique_lock<std::mutex>& lock) {
+    Lane& lane = s->lanes[q->h];
+    while (lane.repairing) s->cv_done.wait(lock);
+    lane.repairing = true;
+    lock.unlock();
+    katz_handle* h = q->h;
+    Slot& sl = s->slots[(size_t)q->slot];
+    const katz_status sw = katz::update_swap(h);
+    lock.lock();
+    lane.swap_pending = false;  // the next prepare reads the graph now current
+    s->cv_work.notify_all();
+    lock.unlock();
+    q->status = sw != KATZ_OK ? sw : katz::update_repair(h, &q->info);
     // the ranking of the graph the handle now holds (after a rejected batch
     // the graph is unchanged and so is the ranking)
     if (q->status == KATZ_OK || q->status == KATZ_EINVAL || q->status == KATZ_EALPHA) {
         const int64_t kk = std::min<int64_t>(k, h->k_eff);
         if (kk > 0 && katz_get_ranking(h, sl.h_ids, kk) == KATZ_OK) q->ids.assign(sl.h_ids, sl.h_ids + kk);
     }
+    lock.lock();
+    lane.repairing = false;
 }
 
 void worker_main(katz_server* s) {
@@ -167,8 +196,12 @@ void worker_main(katz_server* s) {
         Request* q = nullptr;
         for (;;) {
             if (s->stop) return;
+            // the oldest admitted request whose handle can start its prepare:
+            // its turn in arrival order, no prepare running, no prepared
+            // request still waiting to swap its graph in
             for (auto it = s->admitted.begin(); it != s->admitted.end(); ++it) {
-                if (!s->lanes[(*it)->h].busy) {
+                Lane& L = s->lanes[(*it)->h];
+                if ((*it)->seq == L.prep_seq && !L.preparing && !L.swap_pending) {
                     q = *it;
                     s->admitted.erase(it);
                     break;
@@ -178,16 +211,19 @@ void worker_main(katz_server* s) {
             s->cv_work.wait(lock);
         }
         Lane& lane = s->lanes[q->h];
-        lane.busy = true;
+        lane.preparing = true;
         q->state = RUNNING;
         q->t_start = Clock::now();
         const int64_t k = lane.k;
         lock.unlock();
-        run_request(s, q, k);
+        prepare_request(s, q);
         lock.lock();
+        lane.preparing = false;
+        lane.swap_pending = true;
+        lane.prep_seq += 1;
+        commit_request(s, q, k, lock);
         q->t_done = Clock::now();
         q->state = DONE;
-        s->lanes[q->h].busy = false;
         s->free_slots.push_back(q->slot);
         s->admitted_updates -= q->m;
         admit_locked(s);
@@ -260,11 +296,13 @@ katz_status katz_server_attach(katz_server_h s, katz_h h, int64_t k) {
     // device buffers for the largest batch and a rebuilt adjacency with headroom,
     // so that serving allocates nothing per request
     const int64_t nnz_cap = h->g.nnz + h->g.nnz / 16 + 2 * s->opts.slot_updates + 1024;
-    const katz_status st = katz::dyn_reserve(h, s->opts.slot_updates, nnz_cap);
+    const katz_status st = katz::dyn_reserve(h, s->opts.slot_updates, nnz_cap, h->stream);
     if (st != KATZ_OK) return st;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return katz::fail(h, KATZ_ECUDA, "attach sync");
     std::lock_guard<std::mutex> lock(s->mu);
-    s->lanes[h] = Lane{k, false};
+    Lane lane;
+    lane.k = k;
+    s->lanes[h] = lane;
     return KATZ_OK;
 }
 
@@ -285,6 +323,7 @@ katz_status katz_server_submit(katz_server_h s, katz_h h, const int32_t* src, co
         return KATZ_ESTATE;
     }
     q->ticket = s->next_ticket++;
+    q->seq = s->lanes[h].next_seq++;
     s->requests[q->ticket] = q;
     s->waiting.push_back(q);
     admit_locked(s);

@@ -124,3 +124,51 @@ def test_wait_times_out_and_one_slot_serialises_admission():
         assert res.latency_ms >= res.service_ms
     srv.close()
     h.close()
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_pipelined_batches_on_one_handle_match_sequential(directed):
+    # two workers on one handle: the prepare of each batch (validation and
+    # the rebuilt graph, on the handle's second stream) overlaps the repair
+    # of the batch before it; every answer must equal the batch-by-batch one
+    g = gg.rmat(13, 16, seed=61)
+    if directed:
+        g = gg.orient(g, seed=62)
+    D, k = g.deg_max() + 64, 40
+    batches, cur = [], g
+    for j in range(20):
+        m = [3, 800, 40, 2000, 1][j % 5]
+        if directed:
+            b = gg.directed_update_batch(cur, m, seed=700 + j, deg_bound=D)
+            cur = gg.apply_directed_batch(cur, *b)
+        else:
+            b = gg.update_batch(cur, m, seed=700 + j)
+            cur = gg.apply_batch(cur, *b)
+        batches.append(b)
+    opts = dict(keep_history=1, deg_bound=D, r_max=128, undirected=0 if directed else 1)
+    seq = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(**opts))
+    seq.rank(0.0, k, EPS)
+    ref = []
+    for b in batches:
+        info = seq.update(*b)
+        ref.append((info.r, seq.ranking(k).copy(), seq.bounds()[0].copy()))
+    h = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(**opts))
+    h.rank(0.0, k, EPS)
+    srv = K.Server(workers=2, slots=4, slot_updates=2000)
+    srv.attach(h, k)
+    tickets = [srv.submit(h, *b) for b in batches]
+    for j, t in enumerate(tickets):
+        status, ids, res = srv.wait(t, timeout_ms=120000)
+        assert status == 0, (j, status)
+        assert res.info.r == ref[j][0], j
+        np.testing.assert_array_equal(ids, ref[j][1], err_msg=f"batch {j}")
+    srv.close()
+    np.testing.assert_array_equal(h.bounds()[0], ref[-1][2])
+    s = oracle.Session(g.rowptr, g.col, not directed, D)
+    assert s.rank_static(0.0, k, EPS, 128) == oracle.OK
+    for b in batches:
+        assert s.apply_update(*b) == oracle.OK
+    c, l, u = s.bounds()
+    assert_same_ranking(h.ranking(k), s.ranking(), l)
+    seq.close()
+    h.close()
