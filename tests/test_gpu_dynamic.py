@@ -137,3 +137,47 @@ def test_empty_batch_keeps_the_ranking():
     r0 = h.ranking(10).copy()
     info = h.update(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint8))
     assert info.converged == 1 and np.array_equal(h.ranking(10), r0)
+
+
+def _star_on_rmat(n_leaves=5000, seed=17):
+    base = gg.rmat(13, 8, seed=seed)
+    rows = np.repeat(np.arange(base.n), np.diff(base.rowptr))
+    sel = rows < base.col
+    rng = np.random.default_rng(seed)
+    leaves = rng.choice(np.arange(1, base.n), n_leaves, replace=False)
+    u = np.concatenate([rows[sel], np.zeros(n_leaves, np.int64)])
+    v = np.concatenate([base.col[sel], leaves])
+    return gg.from_edges(base.n, u, v)
+
+
+@pytest.mark.parametrize("served", [False, True])
+def test_a_hub_row_emptied_and_refilled(served):
+    # node 0 is a CHUNK row (degree > 2048); one batch deletes every edge of
+    # it, so its row has no chunk left; the next batch gives it three edges
+    g = _star_on_rmat()
+    assert np.diff(g.rowptr)[0] > 4096
+    k, eps = 30, 1e-9
+    D = g.deg_max() + 8
+    h, s = _pair(g, k, eps, D)
+    nb = g.col[g.rowptr[0]:g.rowptr[1]]
+    b1 = (np.zeros(len(nb), np.int32), nb.astype(np.int32), np.zeros(len(nb), np.uint8))
+    b2 = (np.zeros(3, np.int32), nb[:3].astype(np.int32), np.ones(3, np.uint8))
+    if served:
+        srv = K.Server(workers=2, slots=2, slot_updates=len(nb))
+        srv.attach(h, k)
+        tickets = [srv.submit(h, *b) for b in (b1, b2)]
+        results = [srv.wait(t, timeout_ms=120000) for t in tickets]
+        srv.close()
+    for j, b in enumerate((b1, b2)):
+        assert s.apply_update(*b) == oracle.OK
+        if served:
+            status, ids, res = results[j]
+            assert status == 0
+            if j == 0:
+                c, l, u = s.bounds()
+                assert_same_ranking(ids, s.ranking(), l)
+        else:
+            h.update(*b)
+            _compare(h, s, k)
+    _compare(h, s, k)
+    assert h.walk(1)[0] == s.alpha_pow(1) * 3
