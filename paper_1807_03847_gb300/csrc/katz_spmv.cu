@@ -506,44 +506,11 @@ __device__ __forceinline__ Epi make_epi(void* y, double* c64, double* c32, doubl
                ctrl->theta_prev, bstate(ctrl, p), 0, s32};
 }
 
-// Level 1: s_0 = 1, so the exact sum of a row is its length (A 1 = deg) and
-// no walk value is read; a CHUNK row's chunks store their arc counts, which
-// the hub fixup merges as it merges any partials.  Same lane partition and
-// epilogue as the other levels, so every result has the same bits.
-template <typename Off>
-__device__ __forceinline__ void spmv_rows_degree(const Off* __restrict__ rowptr, const SpmvLayout& L, const Epi& ep,
-                                                 const int32_t* __restrict__ chunk_row,
-                                                 const int64_t* __restrict__ chunk_first, double* chunk_part,
-                                                 const IterParams& p) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t b = blockIdx.x;
-    auto deg = [&](int64_t u) { return (double)((int64_t)rowptr[u + 1] - (int64_t)rowptr[u]); };
-    if (b >= L.blk_thread) {  // THREAD rows
-        const int64_t u = L.row_thread + (b - L.blk_thread) * BLOCK + tid;
-        if (u < L.n) finish_row<double>(u, deg(u), ep, p);
-    } else if (b >= L.blk_octet) {  // OCTET rows
-        const int64_t u = L.row_octet + (b - L.blk_octet) * (BLOCK / 8) + (tid >> 3);
-        if ((tid & 7) == 0 && u < L.row_thread) finish_row<double>(u, deg(u), ep, p);
-    } else if (b >= L.blk_warp) {  // WARP rows
-        const int64_t u = L.row_warp + (b - L.blk_warp) * WARPS + wid;
-        if (lane == 0 && u < L.row_octet) finish_row<double>(u, deg(u), ep, p);
-    } else {  // CHUNK rows
-        const int64_t ch = b * WARPS + wid;
-        if (lane == 0 && ch < L.chunks) {
-            const int64_t u = chunk_row[ch];
-            const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
-            const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
-            XAcc s = xacc_zero();
-            xacc_add(s, (double)(j1 - j0));
-            store_part(chunk_part, ch, s);
-        }
-    }
-}
-
-// Level 1 of a ranking as one pass over all rows, any row mode: s_1 = alpha
-// deg with the epilogue of every level (no chunk partials: no fixup follows).
-// The same sums and epilogue as spmv_rows_degree, in a grid sized for O(n)
-// work instead of the gather levels' one block per row group.
+// Level 1 of a ranking as one pass over all rows, any row mode: s_0 = 1, so
+// the exact sum of a row is its length (A 1 = deg) and no walk value is read;
+// s_1 = alpha deg goes through the epilogue of every level, in a grid sized
+// for O(n) work (no chunk partials: no fixup follows).  The bits are those a
+// gather level would give: an exact sum of ones, rounded once.
 template <typename Off>
 __global__ void degree_level_kernel(const Off* __restrict__ rowptr, int64_t n, double* walk, double* c64,
                                     double* c32, double* lb, double* ub, uint8_t* active,
@@ -577,9 +544,7 @@ spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col
     Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl, p,
                       (p.cert && !store_level && r_cur < f32_from) ? s32 : nullptr);
     ep.store_only = store_level > 0;
-    if (r_cur == 1)  // always an FP64 level
-        spmv_rows_degree<Off>(rowptr, L, ep, chunk_row, chunk_first, chunk_part, p);
-    else if (r_cur < f32_from)
+    if (r_cur < f32_from)  // level 1, when it comes here, gathers s_0 = 1 (f32_from >= 2)
         spmv_rows<Off, double, double>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
     else if (r_cur == f32_from)
         spmv_rows<Off, float, float>(rowptr, col, L, s32, ep, chunk_row, chunk_first, chunk_part, p);
