@@ -209,9 +209,16 @@ katz_status katz_get_trace(katz_h h, int64_t* active_per_iter, int32_t cap);
 /*
  * Algorithm 2 (Sec. 4): apply a batch of m edge updates (insert if
  * is_insert[e] != 0, else delete) to the graph of a handle that has ranked
- * with keep_history = 1 under the top-k criterion in FP64 mode, repair the
- * stored walk vectors s_1..s_r, recompute the bounds, re-derive the active
- * set and continue iterating until the top-k criterion holds again.
+ * with keep_history = 1 under the top-k criterion, repair the stored walk
+ * vectors s_1..s_r, recompute the bounds, re-derive the active set and
+ * continue iterating until the top-k criterion holds again.
+ * FP32-certified handles repair each level in its own arithmetic (FP64 up
+ * to the switch level, FP32 from it on) and summation order; a batch that
+ * makes a row's sum longer than any before widens the rounding-error bound
+ * of every level.  If that widening stalls the certificate the call returns
+ * KATZ_EPRECISION (KATZ_FP32_CERT; the bounds stay valid) or, under
+ * KATZ_FP32_CERT_AUTO, ranks the updated graph again with FP64 levels
+ * (info->escalated = 1) and the handle continues in FP64.
  * On an undirected handle an update is the edge {src[e], dst[e]} (both arcs
  * change); on a directed one (opts.undirected = 0) it is the arc
  * src[e] -> dst[e] alone (Sec. 2.1), so a batch may name a -> b and b -> a.
@@ -221,7 +228,8 @@ katz_status katz_get_trace(katz_h h, int64_t* active_per_iter, int32_t cap);
  * exceeds the degree bound D afterwards (out-degrees when directed).
  * Arrays may be host or device pointers.
  * Errors: KATZ_EINVAL (precondition), KATZ_EALPHA (a row would exceed D),
- * KATZ_ESTATE (no ranking / no history), KATZ_ENOMEM, KATZ_ECUDA.
+ * KATZ_ESTATE (no ranking / no history), KATZ_EPRECISION, KATZ_ENOTCONV,
+ * KATZ_ENOMEM, KATZ_ECUDA.
  */
 katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t* dst,
                                     const uint8_t* is_insert, int64_t m, katz_info* info);
@@ -307,7 +315,7 @@ katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts)
 
 /*
  * Serve handle h, answering with its top k (1 <= k <= the ranked k).  h must
- * have ranked with keep_history = 1 in FP64 mode (directed or undirected) and
+ * have ranked with keep_history = 1 (any precision, directed or undirected) and
  * should own its stream (katz_opts.cuda_stream = NULL), so that its work can
  * overlap other handles'.  While attached, h belongs to the server: the caller
  * makes no other call on it until the server is destroyed.

@@ -436,6 +436,7 @@ katz_status dyn_reserve(katz_handle* h, int64_t m, int64_t nnz_cap, cudaStream_t
         DALLOC(d.hub_epoch, std::max<int64_t>(g.layout.row_warp, 1));
         DALLOC(d.n_ins_rows, 1);
         DALLOC(d.err, 1);
+        DALLOC(d.mode_dmax, 3);
         DALLOC(h->rp_new, n + 1);
         DALLOC(h->deg_tmp, n + 1);
         DALLOC(h->scan_sums, scan_blocks(n + 1));
@@ -875,6 +876,14 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
 
 static katz_status rank_static_once(katz_h h, double alpha, int64_t k, double eps, katz_info* info);
 
+namespace katz {
+// the handle's current top-k ranking recomputed from scratch with its alpha,
+// k and eps (the FP32 escalation of an update)
+katz_status rank_static_fp64(katz_handle* h, katz_info* info) {
+    return rank_static_once(h, h->alpha, h->k_eff, h->eps, info);
+}
+}  // namespace katz
+
 // KATZ_FP32_CERT_AUTO: a ranking whose FP32 rounding widening stalls the
 // certificate is recomputed with FP64 levels on the same handle (the
 // buffers of an FP32 handle hold FP64 levels too).
@@ -1248,10 +1257,21 @@ katz_status update_prepare(katz_handle* h, const int32_t* src, const int32_t* ds
     if ((e = dyn_prepare(g, d, m, h->rp_new, h->deg_tmp, h->scan_sums, sa)) != cudaSuccess)
         return cuda_done(e, "prepare rebuild");
     pd.launches += 8;  // 5 bucket/degree kernels + 3 scan passes
+    // FP32-certified levels: the rows the batch lengthens bound the chain of
+    // FP32 additions of their repaired sums (the precision option is fixed at
+    // creation; the repair reads the handle's current mode)
+    const bool cert = h->opts.precision != KATZ_FP64;
+    unsigned long long* hdmax = (unsigned long long*)(h->h_small + H_SMALL - 128);
+    if (cert && ((e = dyn_mode_degree_max(g, d, m, h->rp_new, sa)) != cudaSuccess ||
+                 (e = cudaMemcpyAsync(hdmax, d.mode_dmax, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                      sa)) != cudaSuccess))
+        return cuda_done(e, "degree maxima");
+    pd.launches += cert ? 1 : 0;
     int64_t* hnnz = (int64_t*)(h->h_small + H_SMALL - 56);
     if ((e = cudaMemcpyAsync(hnnz, h->rp_new + n, sizeof(int64_t), cudaMemcpyDeviceToHost, sa)) != cudaSuccess ||
         (e = cudaStreamSynchronize(sa)) != cudaSuccess)
         return cuda_done(e, "rebuild size");
+    const unsigned long long dmax[3] = {cert ? hdmax[0] : 0ull, cert ? hdmax[1] : 0ull, cert ? hdmax[2] : 0ull};
     const int64_t nnz_new = *hnnz;
     if (!g.off64 && n + nnz_new >= 0x7fffffffLL) {
         dyn_clear(g, d, m, sa);
@@ -1298,8 +1318,18 @@ katz_status update_prepare(katz_handle* h, const int32_t* src, const int32_t* ds
         (e = cudaStreamSynchronize(sa)) != cudaSuccess)
         return cuda_done(e, "copy rowptr head");
     std::vector<int64_t> first((size_t)rw + 1, 0);
-    for (int64_t u = 0; u < rw; ++u) first[u + 1] = first[u] + (hrp[u + 1] - hrp[u] + CHUNK_ARCS - 1) / CHUNK_ARCS;
+    int64_t max_chunks = 0;
+    for (int64_t u = 0; u < rw; ++u) {
+        const int64_t c = (hrp[u + 1] - hrp[u] + CHUNK_ARCS - 1) / CHUNK_ARCS;
+        first[u + 1] = first[u] + c;
+        max_chunks = std::max(max_chunks, c);
+    }
     const int64_t chunks = first[rw];
+    if (cert) {
+        const SpmvLayout& L = g.layout;
+        pd.depth = sum_depth_of((int64_t)dmax[0], (int64_t)dmax[1], (int64_t)dmax[2], L.row_thread > L.row_octet,
+                                L.row_octet > L.row_warp, rw > 0 ? std::max<int64_t>(max_chunks, 1) : 0);
+    }
     if (chunks > h->chunk_row_spare_cap) {
         dfree_on(h->chunk_row_spare, sa);
         h->chunk_row_spare = nullptr;
@@ -1465,6 +1495,15 @@ katz_status update_repair(katz_handle* h, katz_info* info) {
         if ((e = dyn_recompute_c(g, h->b, d, h->p, r, full, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "recompute c");
         h->launches += 1;
+        // FP32-certified: a row sum longer than any before widens every
+        // level's error bound; the bounds of level r are re-derived with it
+        if (h->p.cert && pd.depth > h->p.depth) {
+            h->p.depth = pd.depth;
+            h->sum_depth = pd.depth;
+            if ((e = launch_cert_replay(h->b, h->p, r, h->stream)) != cudaSuccess)
+                return cuda_fail(h, e, "error bounds");
+            h->launches += 1;
+        }
     }
     // ---- bounds, reactivation, converged() at level r, then more iterations ------
     h->launches += 5;  // theta_lb, reactivate, select, count, finalize
@@ -1499,14 +1538,32 @@ katz_status update_repair(katz_handle* h, katz_info* info) {
     h->converged = hc.converged;
     h->k_eff = hc.k_eff;
     h->last_ms = ms;
+    h->f32_from = hc.f32_from;
+    const bool stalled = !hc.converged && hc.stall;
     std::vector<int64_t> tr((size_t)h->opts.r_max + 2, 0);
     if ((e = cudaMemcpyAsync(tr.data(), h->b.trace, tr.size() * sizeof(int64_t), cudaMemcpyDeviceToHost,
                              h->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "copy trace");
     h->trace.assign(tr.begin() + 1, tr.begin() + 1 + std::max(0, h->r));
+    if (stalled && h->opts.precision == KATZ_FP32_CERT_AUTO) {
+        // the FP32 widening stalls the certificate on the updated graph: its
+        // levels are recomputed in FP64 (the handle continues in FP64)
+        const int64_t launches = h->launches;
+        h->fp32 = false;
+        const katz_status st2 = rank_static_fp64(h, info);
+        h->fp32 = true;
+        h->launches += launches;
+        if (info) {
+            info->escalated = 1;
+            info->launches = h->launches;
+            info->affected = n;
+        }
+        return st2;
+    }
     if (info) {
         std::memset(info, 0, sizeof(*info));
+        info->fp32_levels = (h->p.cert && hc.f32_from <= h->r) ? h->r - hc.f32_from + 1 : 0;
         info->r = h->r;
         info->converged = h->converged;
         info->active = h->trace.empty() ? n : h->trace.back();
@@ -1519,6 +1576,7 @@ katz_status update_repair(katz_handle* h, katz_info* info) {
         info->full_levels = (int32_t)full_levels;
         info->launches = h->launches;
     }
+    if (stalled) return fail(h, KATZ_EPRECISION, "FP32 rounding widening exceeds the remaining tail; rank in FP64");
     if (!h->converged) return fail(h, KATZ_ENOTCONV, "r_max reached before the top-k criterion held");
     return KATZ_OK;
 }
@@ -1533,7 +1591,6 @@ katz_status update_allowed(katz_handle* h) {
     if (!h->ranked) return fail(h, KATZ_ESTATE, "rank the graph before updating it");
     if (h->criterion != KATZ_CRIT_TOPK) return fail(h, KATZ_ESTATE, "dynamic updates continue the top-k criterion");
     if (!h->opts.keep_history) return fail(h, KATZ_ESTATE, "dynamic updates need keep_history = 1");
-    if (h->fp32) return fail(h, KATZ_ESTATE, "dynamic updates run in FP64 mode");
     return KATZ_OK;
 }
 

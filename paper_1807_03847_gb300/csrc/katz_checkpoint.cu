@@ -20,7 +20,7 @@ using namespace katz;
 namespace {
 
 constexpr uint64_t CKPT_MAGIC = 0x31504b435a54414bull;  // "KATZCKP1"
-constexpr uint32_t CKPT_VERSION = 1;
+constexpr uint32_t CKPT_VERSION = 2;
 
 struct CkptHeader {
     uint64_t magic;
@@ -75,6 +75,7 @@ void walk_arrays(Image& im, katz_handle* h, const CkptHeader& hd) {
     im.dev(b.walk, (uint64_t)hd.walk_slots * (uint64_t)hd.stride * 8);
     im.dev(b.c, n * 8);
     if (hd.fp32) im.dev(b.c32, n * 8);
+    if (hd.fp32) im.dev(b.s32, n * 4);  // the first FP32 level's input (an update may recompute that level)
     im.dev(b.lb, n * 8);
     im.dev(b.ub, n * 8);
     im.dev(b.active, n);

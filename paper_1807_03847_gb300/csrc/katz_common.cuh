@@ -215,6 +215,7 @@ struct DynBuffers {
     int64_t* rrowptr = nullptr;      // [n+1] directed: transposed CSR (in-arcs) of the current graph
     int32_t* rcol = nullptr;         // [rcap]
     int64_t rcap = 0;
+    unsigned long long* mode_dmax = nullptr;  // [3] FP32-certified: largest new degree per row mode in a batch
 };
 
 // ---- stopping criteria other than top-k (katz_criteria.cu) -------------------
@@ -249,6 +250,8 @@ cudaError_t dyn_transpose(const DeviceGraph& g, const DynBuffers& d, int64_t* cn
 cudaError_t dyn_recompute_c(const DeviceGraph& g, const IterBuffers& b, const DynBuffers& d, const IterParams& p,
                             int r, bool all, cudaStream_t st);
 cudaError_t dyn_reactivate(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int r, cudaStream_t st);
+cudaError_t dyn_mode_degree_max(const DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rp_new,
+                                cudaStream_t st);
 
 cudaError_t prepare_kernels();  // one-time function attributes (outside any capture)
 SpmvLayout make_layout(int64_t n, int64_t row_warp, int64_t row_octet, int64_t row_thread, int64_t chunks);
@@ -317,7 +320,10 @@ cudaError_t launch_finalize(const IterBuffers& b, const IterParams& p, cudaStrea
 cudaError_t launch_bounds_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
                               double* lower, double* upper, double* err, cudaStream_t st);
 cudaError_t launch_cert_init(const IterBuffers& b, const IterParams& p, cudaStream_t st);
+cudaError_t launch_cert_replay(const IterBuffers& b, const IterParams& p, int r, cudaStream_t st);
 int max_sum_depth(const SpmvLayout& L, int64_t max_chunks_per_row);
+int sum_depth_of(int64_t deg_thread, int64_t deg_octet, int64_t deg_warp, bool has_octet, bool has_warp,
+                 int64_t max_chunks_per_row);
 cudaError_t launch_walk_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
                             double* out, cudaStream_t st);
 // radix select over candidates (large candidate sets): one pass of 8-bit digits

@@ -612,32 +612,61 @@ __global__ void expand_in_kernel(const Off* __restrict__ rowptr, const int64_t* 
     add_warp_volume(vol, fsize);
 }
 
-// c_r = s_1 + ... + s_r in level order (the order the static iteration adds them)
+// FP32-certified handles: the largest new degree among the batch's rows in
+// each row mode (THREAD, OCTET, WARP), from which the host bounds the chain of
+// FP32 additions of a repaired row.  Directed: only the source rows change.
+__global__ void mode_degree_max_kernel(const int32_t* __restrict__ inv, const int32_t* __restrict__ src,
+                                       const int32_t* __restrict__ dst, int64_t m, int und,
+                                       const int64_t* __restrict__ rp_new, SpmvLayout L, unsigned long long* dmax) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += stride) {
+        for (int side = 0; side <= und; ++side) {
+            const int64_t u = inv[side ? dst[q] : src[q]];
+            if (u < L.row_warp) continue;  // CHUNK rows: the host counts their chunks
+            const unsigned long long deg = (unsigned long long)(rp_new[u + 1] - rp_new[u]);
+            const int slot = u >= L.row_thread ? 0 : (u >= L.row_octet ? 1 : 2);
+            atomicMax(dmax + slot, deg);
+        }
+    }
+}
+
+// c_r = s_1 + ... + s_r in level order (the order the static iteration adds
+// them).  FP32-certified mode: the FP64 levels into c, the FP32 levels
+// (exact in FP64) into c32, as the two partial sums of the ranking.
 __global__ void recompute_c_kernel(const double* walk, IterParams p, int r, const int32_t* __restrict__ rows,
-                                   const unsigned long long* nrows, int64_t n, double* c) {
+                                   const unsigned long long* nrows, int64_t n, double* c, double* c32,
+                                   const Ctrl* ctrl) {
     const int64_t cnt = rows ? (int64_t)*nrows : n;
+    const int f32_from = ctrl->f32_from;
+    const int r64 = min(r, f32_from - 1);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += stride) {
         const int64_t v = rows ? rows[q] : q;
         double acc = 0.0;
-        for (int i = 1; i <= r; ++i) acc = __dadd_rn(acc, walk_slot(walk, p, i)[v]);
+        for (int i = 1; i <= r64; ++i) acc = __dadd_rn(acc, walk_slot(walk, p, i)[v]);
         c[v] = acc;
+        if (p.cert && c32) {
+            double acc32 = 0.0;
+            for (int i = f32_from; i <= r; ++i) acc32 = __dadd_rn(acc32, walk_value(walk, p, f32_from, i, v));
+            c32[v] = acc32;
+        }
     }
 }
 
 // a valid candidate threshold after the update: min of the new l_r over the
 // previous top-k (at least k nodes reach it)
 __global__ void theta_lb_kernel(const int32_t* __restrict__ topk_id, const int32_t* __restrict__ inv,
-                                const double* walk, const double* __restrict__ c, IterParams p, int r, Ctrl* ctrl) {
+                                const double* walk, const double* __restrict__ c, const double* __restrict__ c32,
+                                IterParams p, int r, Ctrl* ctrl) {
     __shared__ double wmin[32];
     const int kk = ctrl->k_eff;
-    const double* s = walk_slot(walk, p, r);
+    const int f32_from = ctrl->f32_from;
     const BState bs = bstate(ctrl, p);
     double m = 1.0 / 0.0;
     for (int q = threadIdx.x; q < kk; q += blockDim.x) {
         const int32_t v = inv[topk_id[q]];
         double l, u;
-        node_bounds(c[v], 0.0, s[v], p, bs, l, u);
+        node_bounds(c[v], (p.cert && c32) ? c32[v] : 0.0, walk_value(walk, p, f32_from, r, v), p, bs, l, u);
         m = fmin(m, l);
     }
     for (int off = 16; off; off >>= 1) m = fmin(m, __shfl_xor_sync(FULL, m, off));
@@ -654,6 +683,7 @@ __global__ void theta_lb_kernel(const int32_t* __restrict__ topk_id, const int32
         ctrl->stop = 0;
         ctrl->flags = 0;
         ctrl->converged = 0;
+        ctrl->stall = 0;
         ctrl->list_ready = 0;  // every node is reactivated: the next count scans all of V
         ctrl->n_list_next = 0;
     }
@@ -662,18 +692,21 @@ __global__ void theta_lb_kernel(const int32_t* __restrict__ topk_id, const int32
 // Reactivation: the active set is re-derived from all of V (a node outside
 // it satisfies the paper's reactivation test exactly when converged() would
 // keep it), and the candidates of the check at level r are collected.
-__global__ void reactivate_kernel(const double* walk, const double* __restrict__ c,
+__global__ void reactivate_kernel(const double* walk, const double* __restrict__ c, const double* __restrict__ c32,
                                   const int32_t* __restrict__ perm, IterParams p, int r, uint8_t* active,
                                   double* lb, double* ub, double* cand_l, double* cand_u, int32_t* cand_id,
                                   int64_t cand_cap, Ctrl* ctrl) {
-    const double* s = walk_slot(walk, p, r);
     const double th = ctrl->theta_prev;
+    const int f32_from = ctrl->f32_from;
     const BState bs = bstate(ctrl, p);
+    const bool two = p.cert && c32;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
         active[v] = 1;
         double l, u;
-        node_bounds(c[v], 0.0, s[v], p, bs, l, u);
+        node_bounds(c[v], two ? c32[v] : 0.0, walk_value(walk, p, f32_from, r, v), p, bs, l, u);
+        // FP32-certified mode: fresh bounds of the updated graph (the stored
+        // ones, which later levels tighten monotonically, belong to the old one)
         lb[v] = l;  // the bounds the deactivation count reads
         ub[v] = u;
         if (l >= th) {
@@ -878,17 +911,27 @@ cudaError_t dyn_transpose(const DeviceGraph& g, const DynBuffers& d, int64_t* cn
     return cudaGetLastError();
 }
 
+cudaError_t dyn_mode_degree_max(const DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rp_new,
+                                cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(d.mode_dmax, 0, 3 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess || m <= 0) return e;
+    mode_degree_max_kernel<<<grid_for(m, 256), 256, 0, st>>>(g.inv, d.src, d.dst, m, d.undirected ? 1 : 0, rp_new,
+                                                             g.layout, d.mode_dmax);
+    return cudaGetLastError();
+}
+
 cudaError_t dyn_recompute_c(const DeviceGraph& g, const IterBuffers& b, const DynBuffers& d, const IterParams& p,
                             int r, bool all, cudaStream_t st) {
     recompute_c_kernel<<<grid_for(g.n, 256), 256, 0, st>>>((const double*)b.walk, p, r, all ? nullptr : d.frontier,
-                                                           d.fsize, g.n, b.c);
+                                                           d.fsize, g.n, b.c, b.c32, b.ctrl);
     return cudaGetLastError();
 }
 
 cudaError_t dyn_reactivate(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int r, cudaStream_t st) {
-    theta_lb_kernel<<<1, 1024, 0, st>>>(b.topk_id, g.inv, (const double*)b.walk, b.c, p, r, b.ctrl);
-    reactivate_kernel<<<grid_for(g.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, g.perm, p, r, b.active, b.lb,
-                                                          b.ub, b.cand_l, b.cand_u, b.cand_id, b.cand_cap, b.ctrl);
+    theta_lb_kernel<<<1, 1024, 0, st>>>(b.topk_id, g.inv, (const double*)b.walk, b.c, b.c32, p, r, b.ctrl);
+    reactivate_kernel<<<grid_for(g.n, 256), 256, 0, st>>>((const double*)b.walk, b.c, b.c32, g.perm, p, r, b.active,
+                                                          b.lb, b.ub, b.cand_l, b.cand_u, b.cand_id, b.cand_cap,
+                                                          b.ctrl);
     return cudaGetLastError();
 }
 

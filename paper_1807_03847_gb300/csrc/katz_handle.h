@@ -81,6 +81,7 @@ struct katz_handle {
         std::string err;
         int64_t m = 0, nnz = 0, chunks = 0, launches = 0;
         int bset = 0;
+        int depth = 0;          // FP32-certified: summation depth the updated rows need (0: not computed)
         bool applied = false;   // the batch changed the graph (m > 0 and valid)
     } pend;                     // written by the prepare
     Pending rep;                // the swapped-in batch, read by its repair

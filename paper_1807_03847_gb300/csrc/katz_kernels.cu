@@ -600,6 +600,22 @@ __global__ void cert_init_kernel(Ctrl* ctrl, IterParams p) {
     set_level_state(ctrl, p, 1, p.cert ? next_error(ctrl, p, 1, 0.0) : 0.0);
 }
 
+// FP32-certified handles whose summation depth grew (an update batch made a
+// row longer than its row mode's nominal limit): the error state of level r
+// replayed from level 1 with the new depth.  This is the recursion the
+// ranking ran level by level (cert_init, then finalize), with the switch
+// level it chose; the repaired levels satisfy the larger bounds, and so do
+// the levels left as they were.
+__global__ void cert_replay_kernel(Ctrl* ctrl, IterParams p, int r) {
+    if (!p.cert) return;
+    ctrl->e64 = 0.0;
+    double e = 0.0;
+    for (int lvl = 1; lvl <= r; ++lvl) {
+        e = next_error(ctrl, p, lvl, e);
+        set_level_state(ctrl, p, lvl, e);
+    }
+}
+
 __global__ void finalize_kernel(const double* __restrict__ topk_l, const double* __restrict__ topk_u,
                                 int64_t* trace, Ctrl* ctrl, IterParams p, unsigned long long cond, int use_cond) {
     __shared__ int bad;
@@ -803,6 +819,11 @@ cudaError_t launch_init_walk(const DeviceGraph& g, const IterBuffers& b, const I
 
 cudaError_t launch_cert_init(const IterBuffers& b, const IterParams& p, cudaStream_t st) {
     cert_init_kernel<<<1, 1, 0, st>>>(b.ctrl, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cert_replay(const IterBuffers& b, const IterParams& p, int r, cudaStream_t st) {
+    cert_replay_kernel<<<1, 1, 0, st>>>(b.ctrl, p, r);
     return cudaGetLastError();
 }
 

@@ -286,8 +286,7 @@ katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts)
 katz_status katz_server_attach(katz_server_h s, katz_h h, int64_t k) {
     if (!s || !h) return KATZ_EINVAL;
     if (!h->ranked) return katz::fail(h, KATZ_ESTATE, "rank the graph before attaching it");
-    if (!h->opts.keep_history || h->fp32)
-        return katz::fail(h, KATZ_ESTATE, "served handles need keep_history = 1 and FP64");
+    if (!h->opts.keep_history) return katz::fail(h, KATZ_ESTATE, "served handles need keep_history = 1");
     if (k < 1 || k > h->k_eff) return katz::fail(h, KATZ_EINVAL, "k must lie in [1, ranked k]");
     {
         std::lock_guard<std::mutex> lock(s->mu);

@@ -120,11 +120,15 @@ __device__ __forceinline__ double nn_min(double a, double b) {
 // Candidates carry the original id.
 template <typename Acc>
 __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, const IterParams& p) {
-    if constexpr (sizeof(Acc) == 8) {
-        if (e.store_only) {
-            ((double*)e.y)[u] = __dmul_rn(p.alpha, (double)sum);
-            return;
+    if (e.store_only) {  // dynamic repair: the level value only (and its FP32 rounding at a transition)
+        if constexpr (sizeof(Acc) == 8) {
+            const double sd = __dmul_rn(p.alpha, (double)sum);
+            ((double*)e.y)[u] = sd;
+            if (e.s32) e.s32[u] = f64_to_f32_rn(sd);
+        } else {
+            ((float*)e.y)[u] = __fmul_rn(p.alpha_f, (float)sum);
         }
+        return;
     }
     double sd, c64, c32 = 0.0;
     if constexpr (sizeof(Acc) == 8) {
@@ -499,6 +503,16 @@ __device__ __forceinline__ void spmv_rows(const Off* __restrict__ rowptr, const 
     }
 }
 
+// FP32-certified mode: s32 holds the last FP64 level rounded to FP32, the
+// input of the first FP32 level.  A ranking writes it at every FP64 level
+// while the switch is ahead; a repair (store_level > 0) rewrites it at that
+// last FP64 level, min(f32_from - 1, r) for the r levels held.
+__device__ __forceinline__ bool writes_s32(const Ctrl* ctrl, const IterParams& p, int r_cur, int store_level) {
+    if (!p.cert) return false;
+    if (!store_level) return r_cur < ctrl->f32_from;
+    return r_cur == min(ctrl->f32_from - 1, ctrl->r);
+}
+
 __device__ __forceinline__ Epi make_epi(void* y, double* c64, double* c32, double* lb, double* ub, uint8_t* active,
                                         const int32_t* perm, double* cand_l, double* cand_u, int32_t* cand_id,
                                         int64_t cand_cap, Ctrl* ctrl, const IterParams& p, float* s32 = nullptr) {
@@ -533,16 +547,14 @@ spmv_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col
                  const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first, double* chunk_part,
                  double* cand_l, double* cand_u, int32_t* cand_id, int64_t cand_cap, float* s32, Ctrl* ctrl,
                  IterParams p, int store_level) {
-    // store_level > 0: dynamic repair of one FP64 level, s only
+    // store_level > 0: dynamic repair of one level, s only
     if (!store_level && ctrl->stop) return;
     const int r_cur = store_level ? store_level : ctrl->r + 1;
-    const int f32_from = store_level ? 0x7fffffff : ctrl->f32_from;
+    const int f32_from = ctrl->f32_from;
     const double* xs = walk_slot(walk, p, r_cur - 1);
     double* ys = walk_slot(walk, p, r_cur);
-    // FP32-certified mode: while the switch is ahead, an FP64 level leaves its
-    // s_r rounded to FP32 too, the input of a first FP32 level
     Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl, p,
-                      (p.cert && !store_level && r_cur < f32_from) ? s32 : nullptr);
+                      writes_s32(ctrl, p, r_cur, store_level) ? s32 : nullptr);
     ep.store_only = store_level > 0;
     if (r_cur < f32_from)  // level 1, when it comes here, gathers s_0 = 1 (f32_from >= 2)
         spmv_rows<Off, double, double>(rowptr, col, L, xs, ep, chunk_row, chunk_first, chunk_part, p);
@@ -588,12 +600,12 @@ __global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double
     const int r_cur = store_level ? store_level : ctrl->r + 1;
     double* ys = walk_slot(walk, p, r_cur);
     Epi ep = make_epi(ys, c64, c32, lb, ub, active, perm, cand_l, cand_u, cand_id, cand_cap, ctrl, p,
-                      (p.cert && !store_level && r_cur < ctrl->f32_from) ? s32 : nullptr);
+                      writes_s32(ctrl, p, r_cur, store_level) ? s32 : nullptr);
     ep.store_only = store_level > 0;
     const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;  // one warp per CHUNK row
     if (u >= L.row_warp) return;
     const int64_t first = chunk_first[u], count = chunk_first[u + 1] - first;
-    if (store_level || r_cur < ctrl->f32_from) {
+    if (r_cur < ctrl->f32_from) {
         const XAcc t = merge_chunks_warp(chunk_part, first, count);
         if ((threadIdx.x & 31) == 0) finish_row<double>(u, xacc_to_double(t), ep, p);
     } else {
@@ -605,15 +617,24 @@ __global__ void spmv_chunk_fixup(SpmvLayout L, double* walk, double* c64, double
 }  // namespace
 
 // Longest chain of additions in one row sum: ceil(per-lane terms / 8) chained
-// groups + 3 (tree of 8) + shuffle levels + tree over chunks.
-int max_sum_depth(const SpmvLayout& L, int64_t max_chunks_per_row) {
-    auto lane_depth = [](int64_t terms) { return (int)((terms + 7) / 8) + 3; };
-    int d = lane_depth(16);                                   // THREAD
-    if (L.row_thread > L.row_octet) d = std::max(d, lane_depth(128 / 8) + 3);   // OCTET
-    if (L.row_octet > L.row_warp) d = std::max(d, lane_depth(2048 / 32) + 5);   // WARP
-    if (L.row_warp > 0)                                       // CHUNK: + tree of 64 + chained groups
+// groups + 3 (tree of 8) + shuffle levels + tree over chunks.  The row modes
+// are fixed by position; their nominal degree limits (16, 128, 2048) hold at
+// creation, and an update batch can push a row past its mode's limit
+// (sum_depth_of with the largest degrees seen in each mode).
+int sum_depth_of(int64_t deg_thread, int64_t deg_octet, int64_t deg_warp, bool has_octet, bool has_warp,
+                 int64_t max_chunks_per_row) {
+    auto lane_depth = [](int64_t terms) { return (int)std::min<int64_t>((terms + 7) / 8 + 3, 1 << 24); };
+    int d = lane_depth(std::max<int64_t>(deg_thread, 16));                               // THREAD
+    if (has_octet) d = std::max(d, lane_depth((std::max<int64_t>(deg_octet, 128) + 7) / 8) + 3);   // OCTET
+    if (has_warp) d = std::max(d, lane_depth((std::max<int64_t>(deg_warp, 2048) + 31) / 32) + 5);  // WARP
+    if (max_chunks_per_row > 0)  // CHUNK: + tree of 64 + chained groups
         d = std::max(d, lane_depth(CHUNK_ARCS / 32) + 5 + 6 + (int)((max_chunks_per_row + 63) / 64));
     return d;
+}
+
+int max_sum_depth(const SpmvLayout& L, int64_t max_chunks_per_row) {
+    return sum_depth_of(16, 128, 2048, L.row_thread > L.row_octet, L.row_octet > L.row_warp,
+                        L.row_warp > 0 ? std::max<int64_t>(max_chunks_per_row, 1) : 0);
 }
 
 static cudaError_t spmv_launch(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int store_level,
@@ -664,11 +685,16 @@ cudaError_t launch_convert(const double* in, int64_t n, float* out, double* back
 
 namespace {
 template <typename Off>
-__global__ void degree_store_kernel(const Off* __restrict__ rowptr, int64_t n, double* walk, IterParams p) {
+__global__ void degree_store_kernel(const Off* __restrict__ rowptr, int64_t n, double* walk, float* s32,
+                                    const Ctrl* ctrl, IterParams p) {
     double* y = walk_slot(walk, p, 1);
+    float* t = writes_s32(ctrl, p, 1, 1) ? s32 : nullptr;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
-        y[u] = __dmul_rn(p.alpha, (double)((int64_t)rowptr[u + 1] - (int64_t)rowptr[u]));
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const double sd = __dmul_rn(p.alpha, (double)((int64_t)rowptr[u + 1] - (int64_t)rowptr[u]));
+        y[u] = sd;
+        if (t) t[u] = f64_to_f32_rn(sd);
+    }
 }
 }  // namespace
 
@@ -676,10 +702,10 @@ cudaError_t launch_degree_store(const DeviceGraph& g, const IterBuffers& b, cons
     const int64_t blocks = std::min<int64_t>(std::max<int64_t>((g.n + BLOCK - 1) / BLOCK, 1), 152 * 8);
     if (g.off64)
         degree_store_kernel<int64_t><<<(unsigned)blocks, BLOCK, 0, st>>>((const int64_t*)g.rowptr, g.n,
-                                                                         (double*)b.walk, p);
+                                                                         (double*)b.walk, b.s32, b.ctrl, p);
     else
         degree_store_kernel<int32_t><<<(unsigned)blocks, BLOCK, 0, st>>>((const int32_t*)g.rowptr, g.n,
-                                                                         (double*)b.walk, p);
+                                                                         (double*)b.walk, b.s32, b.ctrl, p);
     return cudaGetLastError();
 }
 
@@ -709,12 +735,37 @@ cudaError_t launch_spmv_store(const DeviceGraph& g, const IterBuffers& b, const 
 template <typename Off>
 __global__ void rows_store_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L,
                                   const int32_t* __restrict__ rows, const unsigned long long* nrows_ptr,
-                                  double* walk, IterParams p, int level) {
+                                  double* walk, float* s32, const Ctrl* ctrl, IterParams p, int level) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     const int64_t nrows = (int64_t)*nrows_ptr;
+    const int f32_from = ctrl->f32_from;
+    if (level >= f32_from) {  // FP32 level: the FP32 order of spmv_rows
+        const float* __restrict__ x = level == f32_from ? s32 : (const float*)walk_slot(walk, p, level - 1);
+        float* y = (float*)walk_slot(walk, p, level);
+        for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < nrows; w += warps) {
+            const int64_t u = rows[w];
+            if (u < L.row_warp) continue;  // CHUNK row
+            const int64_t a = rowptr[u], e = rowptr[u + 1];
+            float s = 0.0f;
+            if (u >= L.row_thread) {
+                if (lane == 0) s = strided_sum<float, float>(col, x, a, e, 0, 1);
+            } else if (u >= L.row_octet) {
+                if (lane < 8) s = strided_sum<float, float>(col, x, a, e, lane, 8);
+#pragma unroll
+                for (int off = 4; off; off >>= 1) s = addA<float>(s, __shfl_down_sync(FULL, s, off, 8));
+            } else {
+                s = strided_sum<float, float>(col, x, a, e, lane, 32);
+#pragma unroll
+                for (int off = 16; off; off >>= 1) s = addA<float>(s, __shfl_down_sync(FULL, s, off));
+            }
+            if (lane == 0) y[u] = __fmul_rn(p.alpha_f, s);
+        }
+        return;
+    }
     const double* __restrict__ x = walk_slot(walk, p, level - 1);
     double* y = walk_slot(walk, p, level);
+    float* t = writes_s32(ctrl, p, level, level) ? s32 : nullptr;
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < nrows; w += warps) {
         const int64_t u = rows[w];
         if (u < L.row_warp) continue;     // CHUNK row
@@ -729,7 +780,11 @@ __global__ void rows_store_kernel(const Off* __restrict__ rowptr, const int32_t*
             s = strided_xsum<8>(col, x, a, e, lane, 32);
             s = xacc_group_sum<32>(s);
         }
-        if (lane == 0) y[u] = __dmul_rn(p.alpha, xacc_to_double(s));
+        if (lane == 0) {
+            const double sd = __dmul_rn(p.alpha, xacc_to_double(s));
+            y[u] = sd;
+            if (t) t[u] = f64_to_f32_rn(sd);
+        }
     }
 }
 
@@ -742,29 +797,48 @@ template <typename Off>
 __global__ void hub_chunks_store_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L,
                                         const int32_t* __restrict__ chunk_row,
                                         const int64_t* __restrict__ chunk_first, double* chunk_part,
-                                        const uint32_t* __restrict__ vbits, const double* walk, IterParams p,
-                                        int level) {
+                                        const uint32_t* __restrict__ vbits, const double* walk,
+                                        const float* __restrict__ s32, const Ctrl* ctrl, IterParams p, int level) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int f32_from = ctrl->f32_from;
     const double* __restrict__ x = walk_slot(walk, p, level - 1);
+    const float* __restrict__ xf = level == f32_from ? s32 : (const float*)x;
     for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < L.chunks; ch += warps) {
         const int64_t u = chunk_row[ch];
         if (!visited(vbits, u)) continue;
         const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
         const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
-        const XAcc t = xacc_group_sum<32>(strided_xsum<8>(col, x, j0, j1, lane, 32));
-        if (lane == 0) store_part(chunk_part, ch, t);
+        if (level >= f32_from) {  // FP32 level: the chunk sum of spmv_rows, exact in FP64
+            float s = strided_sum<float, float>(col, xf, j0, j1, lane, 32);
+#pragma unroll
+            for (int off = 16; off; off >>= 1) s = addA<float>(s, __shfl_down_sync(FULL, s, off));
+            if (lane == 0) chunk_part[3 * ch] = (double)s;
+        } else {
+            const XAcc t = xacc_group_sum<32>(strided_xsum<8>(col, x, j0, j1, lane, 32));
+            if (lane == 0) store_part(chunk_part, ch, t);
+        }
     }
 }
 
 // the CHUNK rows in the frontier: partials merged as spmv_chunk_fixup merges them
 __global__ void hub_rows_store_kernel(SpmvLayout L, const int64_t* __restrict__ chunk_first,
                                       const double* __restrict__ chunk_part, const uint32_t* __restrict__ vbits,
-                                      double* walk, IterParams p, int level) {
+                                      double* walk, float* s32, const Ctrl* ctrl, IterParams p, int level) {
     const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;  // one warp per CHUNK row
     if (u >= L.row_warp || !visited(vbits, u)) return;
-    const XAcc t = merge_chunks_warp(chunk_part, chunk_first[u], chunk_first[u + 1] - chunk_first[u]);
-    if ((threadIdx.x & 31) == 0) walk_slot(walk, p, level)[u] = __dmul_rn(p.alpha, xacc_to_double(t));
+    const int64_t first = chunk_first[u], count = chunk_first[u + 1] - first;
+    if (level >= ctrl->f32_from) {  // FP32 level: the chunk tree of spmv_chunk_fixup
+        const float t = chunk_tree_warp(chunk_part, first, count);
+        if ((threadIdx.x & 31) == 0) ((float*)walk_slot(walk, p, level))[u] = __fmul_rn(p.alpha_f, t);
+        return;
+    }
+    const XAcc t = merge_chunks_warp(chunk_part, first, count);
+    if ((threadIdx.x & 31) == 0) {
+        const double sd = __dmul_rn(p.alpha, xacc_to_double(t));
+        walk_slot(walk, p, level)[u] = sd;
+        if (writes_s32(ctrl, p, level, level)) s32[u] = f64_to_f32_rn(sd);
+    }
 }
 
 cudaError_t launch_rows_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const int32_t* rows,
@@ -775,23 +849,25 @@ cudaError_t launch_rows_store(const DeviceGraph& g, const IterBuffers& b, const 
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (g.off64)
         rows_store_kernel<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, g.layout, rows,
-                                                                    nrows_dev, (double*)b.walk, p, level);
+                                                                    nrows_dev, (double*)b.walk, b.s32, b.ctrl, p,
+                                                                    level);
     else
         rows_store_kernel<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, g.layout, rows,
-                                                                    nrows_dev, (double*)b.walk, p, level);
+                                                                    nrows_dev, (double*)b.walk, b.s32, b.ctrl, p,
+                                                                    level);
     const SpmvLayout& L = g.layout;
     if (L.chunks > 0) {
         const unsigned cb = (unsigned)std::min<int64_t>((L.chunks + 7) / 8, 152 * 32);
         if (g.off64)
             hub_chunks_store_kernel<int64_t><<<cb, 256, 0, st>>>((const int64_t*)g.rowptr, g.col, L, g.chunk_row,
                                                                 g.chunk_first, g.chunk_part, vbits,
-                                                                (const double*)b.walk, p, level);
+                                                                (const double*)b.walk, b.s32, b.ctrl, p, level);
         else
             hub_chunks_store_kernel<int32_t><<<cb, 256, 0, st>>>((const int32_t*)g.rowptr, g.col, L, g.chunk_row,
                                                                 g.chunk_first, g.chunk_part, vbits,
-                                                                (const double*)b.walk, p, level);
+                                                                (const double*)b.walk, b.s32, b.ctrl, p, level);
         hub_rows_store_kernel<<<(unsigned)((L.row_warp * 32 + 127) / 128), 128, 0, st>>>(
-            L, g.chunk_first, g.chunk_part, vbits, (double*)b.walk, p, level);
+            L, g.chunk_first, g.chunk_part, vbits, (double*)b.walk, b.s32, b.ctrl, p, level);
     }
     return cudaGetLastError();
 }

@@ -126,8 +126,8 @@ def test_wait_times_out_and_one_slot_serialises_admission():
     h.close()
 
 
-@pytest.mark.parametrize("directed", [False, True])
-def test_pipelined_batches_on_one_handle_match_sequential(directed):
+@pytest.mark.parametrize("directed,fp32", [(False, False), (True, False), (False, True), (True, True)])
+def test_pipelined_batches_on_one_handle_match_sequential(directed, fp32):
     # two workers on one handle: the prepare of each batch (validation and
     # the rebuilt graph, on the handle's second stream) overlaps the repair
     # of the batch before it; every answer must equal the batch-by-batch one
@@ -146,14 +146,18 @@ def test_pipelined_batches_on_one_handle_match_sequential(directed):
             cur = gg.apply_batch(cur, *b)
         batches.append(b)
     opts = dict(keep_history=1, deg_bound=D, r_max=128, undirected=0 if directed else 1)
+    eps = EPS
+    if fp32:  # FP32-certified levels from level 3 on
+        opts.update(precision=K.KATZ_FP32_CERT, fp32_from=3)
+        eps = 1e-4
     seq = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(**opts))
-    seq.rank(0.0, k, EPS)
+    seq.rank(0.0, k, eps)
     ref = []
     for b in batches:
         info = seq.update(*b)
         ref.append((info.r, seq.ranking(k).copy(), seq.bounds()[0].copy()))
     h = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(**opts))
-    h.rank(0.0, k, EPS)
+    h.rank(0.0, k, eps)
     srv = K.Server(workers=2, slots=4, slot_updates=2000)
     srv.attach(h, k)
     tickets = [srv.submit(h, *b) for b in batches]
@@ -165,10 +169,10 @@ def test_pipelined_batches_on_one_handle_match_sequential(directed):
     srv.close()
     np.testing.assert_array_equal(h.bounds()[0], ref[-1][2])
     s = oracle.Session(g.rowptr, g.col, not directed, D)
-    assert s.rank_static(0.0, k, EPS, 128) == oracle.OK
+    assert s.rank_static(0.0, k, eps, 128) == oracle.OK
     for b in batches:
         assert s.apply_update(*b) == oracle.OK
     c, l, u = s.bounds()
-    assert_same_ranking(h.ranking(k), s.ranking(), l)
+    assert_same_ranking(h.ranking(k), s.ranking(), l, atol=eps if fp32 else 0.0)
     seq.close()
     h.close()
