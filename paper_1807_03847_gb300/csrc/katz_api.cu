@@ -99,7 +99,7 @@ katz_status init_handle_runtime(katz_handle* h) {
 // Scratch of the ranking loop that does not depend on the ranking's size.
 katz_status alloc_rank_scratch(katz_handle* h) {
     cudaError_t e;
-    if ((e = dmalloc(h, &h->d_deghist, (size_t)h->D + 1)) != cudaSuccess ||
+    if ((e = dmalloc(h, &h->d_deghist, (size_t)deg_hist_top(h->D) + 1)) != cudaSuccess ||
         (e = dmalloc(h, &h->d_big_l, SELECT_CAP)) != cudaSuccess ||
         (e = dmalloc(h, &h->d_big_u, SELECT_CAP)) != cudaSuccess ||
         (e = dmalloc(h, &h->d_big_id, SELECT_CAP)) != cudaSuccess ||
@@ -937,7 +937,7 @@ static katz_status rank_static_once(katz_h h, double alpha, int64_t k, double ep
         const int bits = c >= 2 ? c - 2 : 0;
         if ((e = launch_theta0_class(h->g, h->b, p, a, end_of(c), lo, bits, k_eff - a, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "theta0");
-    } else if ((e = launch_theta0(h->g, h->b, p, h->d_deghist, h->D, h->stream)) != cudaSuccess) {
+    } else if ((e = launch_theta0(h->g, h->b, p, h->d_deghist, deg_hist_top(h->D), h->stream)) != cudaSuccess) {
         return cuda_fail(h, e, "theta0");
     }
     if (prof && (st = ensure_prof_events(h)) != KATZ_OK) return st;

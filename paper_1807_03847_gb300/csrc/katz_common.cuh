@@ -54,6 +54,12 @@ struct Ctrl {
     double lo64, hi64;   // c64 * lo64 <= exact FP64-level part <= c64 * hi64
     double lo32, hi32;   // same for c32, the FP32-level part
     double los, his;     // same for the stored s_r of the current level
+    double tail_lo, tail_hi;  // RD(alpha los), RU(alpha gamma his): the tail factors of l and u
+    // FP32 results that fall into the subnormal range carry an absolute error
+    // (at most 2^-150 per rounding) instead of a relative one: a_cur bounds it
+    // for the stored s_r, a_sum for the FP32 levels summed in c32 (both are
+    // folded into lo64 / hi64)
+    double a_cur, a_sum;
     unsigned long long smax_bits, smax_prev_bits;  // max s_r over M (this / previous level)
     unsigned long long tailw_bits, roundw_bits;    // max tail width / rounding width over M
     // the active set M as a compact list, kept by the count kernel
@@ -90,17 +96,14 @@ struct IterParams {
 // exact Katz score.  Explicit rounding intrinsics: every kernel that re-derives
 // the bounds gets bit-identical values (no contraction into FMA).
 struct BState {
-    double lo64, hi64, lo32, hi32, los, his;
+    double lo64, hi64, lo32, hi32;
     double a_lo, a_hi;  // cert mode: RD(alpha los) and RU(alpha gamma his), the tail factors of l and u
 };
 
+// the factors are derived once per level by the certification state machine
 __device__ __forceinline__ BState bstate(const Ctrl* c, const IterParams& p) {
-    BState b{c->lo64, c->hi64, c->lo32, c->hi32, c->los, c->his, 0.0, 0.0};
-    if (p.cert) {
-        b.a_lo = __dmul_rd(p.alpha, b.los);
-        b.a_hi = __dmul_ru(p.ag_hi, b.his);
-    }
-    return b;
+    (void)p;
+    return BState{c->lo64, c->hi64, c->lo32, c->hi32, c->tail_lo, c->tail_hi};
 }
 
 __device__ __forceinline__ void node_bounds(double c64, double c32, double s_r, const IterParams& p,
@@ -120,10 +123,12 @@ __device__ __forceinline__ void node_bounds(double c64, double c32, double s_r, 
         c_lo = __dadd_rd(__dmul_rd(c64, b.lo64), __dmul_rd(c32, b.lo32));
         c_hi = __dadd_ru(__dmul_ru(c64, b.hi64), __dmul_ru(c32, b.hi32));
     }
-    // s_r >= 0 and the exact level value lies in [s_r los, s_r his]: with the
-    // factors rounded outward, s_r a_lo <= alpha s_exact and s_r a_hi >= alpha gamma s_exact
-    l = p.undirected ? __dadd_rd(c_lo, __dmul_rd(s_r, b.a_lo)) : c_lo;
-    u = __dadd_ru(c_hi, __dmul_ru(s_r, b.a_hi));
+    // s_r >= 0 and the exact level value lies in [s_r los, s_r his] (up to the
+    // absolute terms folded into lo64 / hi64): with the factors rounded
+    // outward, s_r a_lo <= alpha s_exact and s_r a_hi >= alpha gamma s_exact.
+    // Each tail is one fused multiply-add, rounded once in the safe direction.
+    l = p.undirected ? __fma_rd(s_r, b.a_lo, c_lo) : c_lo;
+    u = __fma_ru(s_r, b.a_hi, c_hi);
 }
 
 template <typename T>
@@ -294,6 +299,10 @@ cudaError_t launch_init_walk(const DeviceGraph& g, const IterBuffers& b, const I
 // degree class (degrees in (lo, lo + 2^bits])
 cudaError_t launch_theta0_class(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int64_t a,
                                 int64_t bend, int64_t lo, int bits, int64_t kk, cudaStream_t st);
+// Top bin of the degree histogram of theta_0: degrees above it count in it,
+// which can only lower theta_0 (still a valid threshold), and the histogram
+// stays small whatever degree bound a handle is given.
+inline int64_t deg_hist_top(int64_t D) { return D < ((int64_t)1 << 24) ? D : ((int64_t)1 << 24); }
 cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const IterParams& p,
                           uint32_t* d_deghist, int64_t D, cudaStream_t st);
 // the FP32-certified levels' binary64 -> binary32 rounding and exact widening

@@ -84,12 +84,12 @@ __global__ void init_walk_kernel(T* walk, double* c, double* c32, double* lb, do
 // (s_1 = alpha deg), so it is l_1 evaluated at the k-th largest degree.
 // ---------------------------------------------------------------------------
 template <typename Off>
-__global__ void deg_hist_kernel(const Off* __restrict__ rowptr, int64_t n, uint32_t* hist) {
+__global__ void deg_hist_kernel(const Off* __restrict__ rowptr, int64_t n, int64_t top, uint32_t* hist) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t v = base + threadIdx.x;
-        const long long d = v < n ? (long long)(rowptr[v + 1] - rowptr[v]) : -1;
+        const long long d = v < n ? min((long long)(rowptr[v + 1] - rowptr[v]), (long long)top) : -1;
         const unsigned mask = __match_any_sync(FULL, d);
         if (d >= 0 && lane == __ffs(mask) - 1) atomicAdd(&hist[d], (uint32_t)__popc(mask));
     }
@@ -568,7 +568,7 @@ __device__ __forceinline__ double gamma_up(double m, double u) {
 // FP32-certified mode: error bounds and widening factors of level `lvl`
 // (relative error e_lvl of its stored s, the largest error e64 of the FP64
 // levels, and how many terms the FP64 accumulations of c64 / c32 hold).
-__device__ void set_level_state(Ctrl* ctrl, const IterParams& p, int lvl, double e_lvl) {
+__device__ void set_level_state(Ctrl* ctrl, const IterParams& p, int lvl, double e_lvl, double a_lvl) {
     const double u64 = 0x1p-53;
     const int f32_from = ctrl->f32_from;
     ctrl->e_cur = e_lvl;
@@ -585,6 +585,24 @@ __device__ void set_level_state(Ctrl* ctrl, const IterParams& p, int lvl, double
     ctrl->hi32 = n32 ? __dadd_ru(1.0, __dmul_ru(2.0, w32)) : 1.0;
     ctrl->los = __dsub_rd(1.0, e_lvl);
     ctrl->his = __dadd_ru(1.0, __dmul_ru(2.0, e_lvl));
+    ctrl->tail_lo = __dmul_rd(p.alpha, ctrl->los);
+    ctrl->tail_hi = __dmul_ru(p.ag_hi, ctrl->his);
+    // With stored s_i = s_i (1 + t) + h, |t| <= e_i, |h| <= a_i on the FP32
+    // levels: the exact FP32-level part of c lies in [c32 lo32 - a_sum,
+    // c32 hi32 + 2 a_sum] (hi32 >= 1 / (1 - e)), the tail alpha gamma s_r
+    // below s_r tail_hi + 2 alpha gamma a_r, and alpha s_r above
+    // s_r tail_lo - alpha a_r.  Every node with a walk has c64 >= s_1 =
+    // alpha deg >= alpha (level 1 is FP64), and a node without one has exact
+    // zeros everywhere; so the absolute terms A are covered by the c64
+    // factors: c64 (lo64 - A_lo / alpha) <= c64 lo64 - A_lo, likewise above.
+    ctrl->a_cur = lvl < f32_from ? 0.0 : a_lvl;
+    ctrl->a_sum = lvl < f32_from ? 0.0 : __dadd_ru(ctrl->a_sum, a_lvl);
+    if (ctrl->a_sum > 0.0) {
+        const double abs_hi = __dmul_ru(2.0, __fma_ru(p.ag_hi, ctrl->a_cur, ctrl->a_sum));
+        const double abs_lo = p.undirected ? __fma_ru(p.alpha, ctrl->a_cur, ctrl->a_sum) : ctrl->a_sum;
+        ctrl->hi64 = __dadd_ru(ctrl->hi64, __ddiv_ru(abs_hi, p.alpha));
+        ctrl->lo64 = fmax(__dsub_rd(ctrl->lo64, __ddiv_ru(abs_lo, p.alpha)), 0.0);
+    }
 }
 
 // error bound of level lvl from the bound of level lvl - 1
@@ -594,10 +612,25 @@ __device__ double next_error(const Ctrl* ctrl, const IterParams& p, int lvl, dou
     return __dsub_ru(__dmul_ru(__dadd_ru(1.0, e_prev), __dadd_ru(1.0, g)), 1.0);
 }
 
+// Absolute error bound of an FP32 level from that of level lvl - 1.  With
+// gradual underflow an FP32 addition has no absolute error (a sum in the
+// subnormal range is exact); a product or a conversion to FP32 may lose up to
+// half the smallest subnormal, 2^-150.  The row sum of level lvl carries its
+// inputs' absolute errors times alpha_f (1 + g) deg <= 1 + g (alpha D < 1),
+// plus its own product; the first FP32 level's inputs are conversions.
+__device__ double next_abs(const Ctrl* ctrl, const IterParams& p, int lvl, double a_prev) {
+    if (lvl < ctrl->f32_from) return 0.0;
+    const double half_sub = 0x1p-150;
+    const double g = gamma_up((double)(p.depth + 3), 0x1p-24);
+    const double in = lvl == ctrl->f32_from ? half_sub : a_prev;
+    return __fma_ru(__dadd_ru(1.0, g), in, half_sub);
+}
+
 __global__ void cert_init_kernel(Ctrl* ctrl, IterParams p) {
     ctrl->f32_from = (p.cert && p.fp32_from >= 2) ? p.fp32_from : 0x7fffffff;
     ctrl->e64 = 0.0;
-    set_level_state(ctrl, p, 1, p.cert ? next_error(ctrl, p, 1, 0.0) : 0.0);
+    ctrl->a_sum = 0.0;
+    set_level_state(ctrl, p, 1, p.cert ? next_error(ctrl, p, 1, 0.0) : 0.0, 0.0);
 }
 
 // FP32-certified handles whose summation depth grew (an update batch made a
@@ -609,10 +642,12 @@ __global__ void cert_init_kernel(Ctrl* ctrl, IterParams p) {
 __global__ void cert_replay_kernel(Ctrl* ctrl, IterParams p, int r) {
     if (!p.cert) return;
     ctrl->e64 = 0.0;
-    double e = 0.0;
+    ctrl->a_sum = 0.0;
+    double e = 0.0, a = 0.0;
     for (int lvl = 1; lvl <= r; ++lvl) {
         e = next_error(ctrl, p, lvl, e);
-        set_level_state(ctrl, p, lvl, e);
+        a = next_abs(ctrl, p, lvl, a);
+        set_level_state(ctrl, p, lvl, e, a);
     }
 }
 
@@ -679,7 +714,8 @@ __global__ void finalize_kernel(const double* __restrict__ topk_l, const double*
                     const double e32 = ctrl->e_cur + 64.0 * gamma_up((double)(p.depth + 3), 0x1p-24);
                     if (2.0 * tail_est * e32 <= p.eps / 16.0) ctrl->f32_from = next;
                 }
-                set_level_state(ctrl, p, next, next_error(ctrl, p, next, ctrl->e_cur));
+                set_level_state(ctrl, p, next, next_error(ctrl, p, next, ctrl->e_cur),
+                                next_abs(ctrl, p, next, ctrl->a_cur));
             }
             ctrl->smax_prev_bits = ctrl->smax_bits;
             ctrl->smax_bits = 0;
@@ -712,7 +748,7 @@ __global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, c
         }
         if (err) {  // widening added for rounding (zero in FP64 mode)
             err[v] = p.cert ? c[w] * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32) +
-                                  p.ag_hi * sv * (bs.his - 1.0) + p.alpha * sv * (1.0 - bs.los)
+                                  p.ag_hi * sv * (ctrl->his - 1.0) + p.alpha * sv * (1.0 - ctrl->los)
                             : 0.0;
         }
         if (lower) lower[v] = l;
@@ -828,15 +864,15 @@ cudaError_t launch_cert_replay(const IterBuffers& b, const IterParams& p, int r,
 }
 
 cudaError_t launch_theta0(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, uint32_t* d_deghist,
-                          int64_t D, cudaStream_t st) {
-    cudaError_t err = cudaMemsetAsync(d_deghist, 0, (size_t)(D + 1) * sizeof(uint32_t), st);
+                          int64_t top, cudaStream_t st) {
+    cudaError_t err = cudaMemsetAsync(d_deghist, 0, (size_t)(top + 1) * sizeof(uint32_t), st);
     if (err != cudaSuccess) return err;
     const int blocks = grid_for(g.n, 256);
     if (g.off64)
-        deg_hist_kernel<int64_t><<<blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.n, d_deghist);
+        deg_hist_kernel<int64_t><<<blocks, 256, 0, st>>>((const int64_t*)g.rowptr, g.n, top, d_deghist);
     else
-        deg_hist_kernel<int32_t><<<blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.n, d_deghist);
-    kth_degree_kernel<double><<<1, SELECT_THREADS, 0, st>>>(d_deghist, D, p, b.ctrl);
+        deg_hist_kernel<int32_t><<<blocks, 256, 0, st>>>((const int32_t*)g.rowptr, g.n, top, d_deghist);
+    kth_degree_kernel<double><<<1, SELECT_THREADS, 0, st>>>(d_deghist, top, p, b.ctrl);
     return cudaGetLastError();
 }
 

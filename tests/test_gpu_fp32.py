@@ -143,3 +143,51 @@ def test_auto_precision_escalates_a_stalled_ranking_to_fp64():
     info2 = h.rank(0.0, 50, 1e-4)
     assert info2.escalated == 0 and info2.converged == 1 and info2.fp32_levels > 0
     h.close()
+
+
+def test_subnormal_fp32_levels_stay_certified():
+    # alpha = 1e-13 (deg_bound 5 10^12, so alpha gamma = 1): level 2 is ~1e-26, level 3 lies around
+    # the smallest normal binary32 (1.2e-38), where a rounding loses up to
+    # 2^-150 absolutely instead of 2^-24 relatively.  Hubs a and b have equal
+    # degree and differ in omega_2 by 1, a gap of alpha^2 that level 3
+    # certifies; the bounds must bracket the exact Katz score.
+    leaves = iter(range(3, 40))
+    pairs = []
+    a, b, c = 0, 1, 2
+    for hub, extra_deg in ((a, 2), (b, 3)):  # 4 leaves + one node of degree extra_deg
+        for _ in range(4):
+            pairs.append((hub, next(leaves)))
+        x = next(leaves)
+        pairs.append((hub, x))
+        for _ in range(extra_deg - 1):
+            pairs.append((x, next(leaves)))
+    for _ in range(4):
+        pairs.append((c, next(leaves)))
+    u, v = zip(*pairs)
+    g = gg.from_edges(40, np.array(u), np.array(v))
+    alpha = 1e-13
+    opts = K.katz_default_opts(precision=K.KATZ_FP32_CERT, fp32_from=2, keep_history=1, deg_bound=5 * 10**12)
+    h = K.Katz(_dev(g.rowptr), _dev(g.col), opts)
+    info = h.rank(alpha, 1, 1e-40)
+    assert info.converged == 1 and info.r == 3 and info.fp32_levels == 2
+    assert list(h.ranking(1)) == [b]
+    s3 = h.walk(3)
+    assert np.any((s3 > 0) & (s3 < 2.0 ** -126))  # subnormal FP32 values at level 3
+    # exact Katz: sum over i <= 12 of alpha^i omega_i, the rest below
+    # 2 (alpha deg_max)^13
+    af = Fraction(alpha)
+    n = g.n
+    w = [1] * n
+    y = [Fraction(0)] * n
+    p = Fraction(1)
+    for _ in range(12):
+        w = [sum(w[int(x)] for x in g.col[g.rowptr[t]:g.rowptr[t + 1]]) for t in range(n)]
+        p *= af
+        y = [y[t] + p * w[t] for t in range(n)]
+    rest = 2 * (af * g.deg_max()) ** 13
+    lo, up, _ = h.bounds()
+    deg = np.diff(g.rowptr)
+    for t in range(n):  # an isolated node has Katz score 0 exactly
+        assert Fraction(float(lo[t])) <= y[t], t
+        assert Fraction(float(up[t])) >= y[t] + (rest if deg[t] else 0), t
+    h.close()
