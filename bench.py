@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve-rmat23"], default="rmat22")
     ap.add_argument("--precision", choices=["fp64", "fp32cert"], default=None)
+    ap.add_argument("--serve-precision", choices=["fp64", "fp32cert"], default="fp64",
+                    help="walk levels of the served handle (FP32-certified: FP32 from the level the ranking picks)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -248,7 +250,7 @@ def cpu_baseline(g, wl, seconds):
             "sample": f"{runs} complete certified rankings (r = {r}) of the full {wl['graph']} graph; {dt:.1f} s"}, dt
 
 
-def run_serving(batches, workers=2, slots=8):
+def run_serving(batches, workers=2, slots=8, precision="fp64"):
     """Open-loop serving runs on one R-MAT23 handle: the batches of the stream
     are submitted at their arrival times to a katz_server; latency is
     submit -> certified top-k on the host.  First at the specified rate
@@ -265,24 +267,25 @@ def run_serving(batches, workers=2, slots=8):
     cfg = SERVING
     g = gg.workload(cfg["graph"])
     D = g.deg_max() + 64
-    spec = serve_once(g, D, batches, cfg["rate"], workers, slots, torch)
+    spec = serve_once(g, D, batches, cfg["rate"], workers, slots, torch, precision)
     saturated = spec["achieved_rate"] < 0.97 * spec["offered_rate"]
     capacity = spec["achieved_rate"] if saturated else spec["offered_rate"]
-    stable = serve_once(g, D, batches, round(0.7 * capacity, 1), workers, slots, torch)
+    stable = serve_once(g, D, batches, round(0.7 * capacity, 1), workers, slots, torch, precision)
     spec["capacity_batches_per_s"] = capacity
     spec["within_capacity"] = stable
     return spec
 
 
-def serve_once(g, D, batches, rate, workers, slots, torch):
+def serve_once(g, D, batches, rate, workers, slots, torch, precision="fp64"):
     import graphgen as gg
     import paper_1807_03847_gb300 as K
 
     cfg = SERVING
     st = gg.stream(g, batches, seed=gg.SEED_BASE + 230, min_size=cfg["min_size"], max_size=cfg["max_size"],
                    p_insert=cfg["p_insert"], rate=rate, deg_bound=D)
+    prec = K.KATZ_FP32_CERT if precision == "fp32cert" else K.KATZ_FP64
     h = K.Katz(torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.col).cuda(),
-               K.katz_default_opts(keep_history=1, deg_bound=D))
+               K.katz_default_opts(keep_history=1, deg_bound=D, precision=prec))
     info0 = h.rank(0.0, cfg["k"], cfg["eps"])
     srv = K.Server(workers=workers, slots=slots, slot_updates=cfg["max_size"])
     srv.attach(h, cfg["k"])
@@ -306,6 +309,7 @@ def serve_once(g, D, batches, rate, workers, slots, torch):
     aff = np.array([r[2].info.affected for r in results], np.float64)
     full = np.array([r[2].info.full_levels for r in results], np.float64)
     launches = int(sum(r[2].info.launches for r in results))
+    fp32_levels = [r[2].info.fp32_levels for r in results]
     sizes = st.sizes()
     # full static recomputation of the final graph, same handle (graph resident)
     rec_dev, rec_wall = [], []
@@ -327,6 +331,8 @@ def serve_once(g, D, batches, rate, workers, slots, torch):
         "batches": int(len(st)), "updates": int(sizes.sum()), "rejected": len(bad),
         "affected_mean_frac": float(aff.mean() / g.n), "full_levels_mean": float(full.mean()),
         "r_initial": int(info0.r), "gpu_launches": launches, "workers": workers, "slots": slots,
+        "precision": precision, "fp32_levels_initial": int(info0.fp32_levels),
+        "fp32_levels_median": float(np.median(fp32_levels)),
         "clocks": clocks, "n": g.n, "nnz": g.nnz, "deg_bound": D, "desc": cfg["desc"],
         "latency": "submit (at the batch's arrival time) -> certified top-100 copied to the host",
     }
@@ -377,14 +383,14 @@ def main():
     if args.workload == "serve-rmat23":
         rank = int(os.environ.get("RANK", "0"))
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        sv = run_serving(args.serve_batches or 2000)
+        sv = run_serving(args.serve_batches or 2000, precision=args.serve_precision)
         if rank == 0:
             print(json.dumps({
                 "metric": "update-to-certified top-100 latency p99 (serving, dynamic R-MAT23)",
                 "value": sv["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": sv["batches"], "warmup": 0,
                 "ms_per_step": sv["p50_ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "serve-rmat23-top100-fp64", "graph": sv["desc"],
+                "dtype": "f32" if args.serve_precision == "fp32cert" else "f64", "data": "synthetic",
+                "config": {"workload": f"serve-rmat23-top100-{args.serve_precision}", "graph": sv["desc"],
                            "l2": "not flushed: requests run back to back as they arrive"},
                 "serving": sv, "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"],
                 "e2e": {"value": sv["p99_ms"], "unit": "ms",
@@ -496,7 +502,7 @@ def main():
         h.close()
         del rowptr_d, col_d, flush
         torch.cuda.empty_cache()
-        serving = run_serving(args.serve_batches)
+        serving = run_serving(args.serve_batches, precision=args.serve_precision)
         h = None
 
     cpu = None
