@@ -73,8 +73,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve-rmat23"], default="rmat22")
     ap.add_argument("--precision", choices=["fp64", "fp32cert"], default=None)
-    ap.add_argument("--serve-precision", choices=["fp64", "fp32cert"], default="fp64",
-                    help="walk levels of the served handle (FP32-certified: FP32 from the level the ranking picks)")
+    ap.add_argument("--serve-precision", choices=["fp64", "fp32cert", "both"], default="both",
+                    help="walk levels of the served handle (FP32-certified: FP32 from the level the ranking picks); "
+                         "both: the FP64 run in 'serving', the FP32-certified one in 'serving_fp32cert'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -383,6 +384,8 @@ def main():
     if args.workload == "serve-rmat23":
         rank = int(os.environ.get("RANK", "0"))
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        if args.serve_precision == "both":
+            args.serve_precision = "fp64"
         sv = run_serving(args.serve_batches or 2000, precision=args.serve_precision)
         if rank == 0:
             print(json.dumps({
@@ -495,14 +498,17 @@ def main():
                "ms_per_step": 1e3 * e2e_t / len(e2e_times),
                "api": "katz_create_csr(host pinned CSR) + katz_rank_static + katz_get_ranking(host) + katz_destroy"}
 
-    serving = None
+    serving = serving32 = None
     if args.serve_batches is None:
         args.serve_batches = 400
     if args.serve_batches > 0:
         h.close()
         del rowptr_d, col_d, flush
         torch.cuda.empty_cache()
-        serving = run_serving(args.serve_batches, precision=args.serve_precision)
+        if args.serve_precision in ("fp64", "both"):
+            serving = run_serving(args.serve_batches, precision="fp64")
+        if args.serve_precision in ("fp32cert", "both"):
+            serving32 = run_serving(args.serve_batches, precision="fp32cert")
         h = None
 
     cpu = None
@@ -525,6 +531,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "ranking_head": [int(x) for x in ranking[:5]],
             "serving": serving,
+            "serving_fp32cert": serving32,
         }
         print(json.dumps(line), flush=True)
     if h is not None:
