@@ -350,7 +350,7 @@ katz_status run_loop(katz_handle* h, int done) {
                 cudaEvent_t* ev = nullptr;
                 if (prof && 2 * launched_iters + 1 < (int)h->sp_ev.size()) ev = &h->sp_ev[2 * launched_iters];
                 if ((e = launch_iteration(h, ev)) != cudaSuccess) return cuda_fail(h, e, "launch iteration");
-                h->launches += (h->g.layout.row_warp > 0 ? 6 : 5);  // SpMV (+ fixup), select, count, sort, finalize
+                h->launches += (h->g.layout.row_warp > 0 ? 5 : 4);
                 ++launched_iters;
             }
         }
@@ -361,7 +361,7 @@ katz_status run_loop(katz_handle* h, int done) {
         if (hc.flags & F_NEED_BIG) {
             katz_status s = big_select(h);
             if (s != KATZ_OK) return s;
-            h->launches += 17;  // 12 histogram passes, filter, select, count, sort, finalize
+            h->launches += 16;  // 12 histogram passes, filter, select, count, finalize
             h->big_paths += 1;
             if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
                 return cuda_fail(h, e, "copy ctrl");
@@ -943,7 +943,7 @@ static katz_status rank_static_once(katz_h h, double alpha, int64_t k, double ep
     if (prof && (st = ensure_prof_events(h)) != KATZ_OK) return st;
     if ((e = launch_first_iteration(h, prof ? &h->sp_ev[0] : nullptr)) != cudaSuccess)
         return cuda_fail(h, e, "first iteration");
-    h->launches += 5;  // degree level, select, count, sort, finalize
+    h->launches += 4;  // degree level, select, count, finalize
     st = run_loop(h, 1);
     if (st != KATZ_OK) return st;
     if ((e = cudaEventRecord(h->ev1, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
@@ -970,7 +970,7 @@ static katz_status rank_static_once(katz_h h, double alpha, int64_t k, double ep
     if (h->opts.use_graph && !h->opts.profile)
         // loop bodies that did work: all finalize runs but the first iteration's
         // and the big-select reruns
-        h->launches += (h->g.layout.row_warp > 0 ? 6 : 5) *
+        h->launches += (h->g.layout.row_warp > 0 ? 5 : 4) *
                        std::max<int64_t>(0, (int64_t)hc.body_runs - 1 - h->big_paths);
     double spmv_ms = 0.0;
     if (h->opts.profile) {  // levels 2..r: level 1 reads no walk values
@@ -1506,7 +1506,7 @@ katz_status update_repair(katz_handle* h, katz_info* info) {
         }
     }
     // ---- bounds, reactivation, converged() at level r, then more iterations ------
-    h->launches += 6;  // theta_lb, reactivate, select, count, sort, finalize
+    h->launches += 5;  // theta_lb, reactivate, select, count, finalize
     if ((e = dyn_reactivate(g, h->b, h->p, r, h->stream)) != cudaSuccess ||
         (e = launch_select(g, h->b, h->p, h->b.cand_l, h->b.cand_u, h->b.cand_id, h->fp32, h->stream)) != cudaSuccess ||
         (e = launch_count(g, h->b, h->p, h->fp32, h->stream)) != cudaSuccess ||

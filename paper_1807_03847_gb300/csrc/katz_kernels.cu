@@ -199,10 +199,8 @@ kth_degree_class_kernel(const Off* __restrict__ rowptr, int64_t a, int64_t b, in
 }
 
 // ---------------------------------------------------------------------------
-// select: theta_r is the k-th candidate in (l desc, id asc) order, found by a
-// radix select in shared memory; the k candidates up to it are the current
-// top-k, written unsorted.  sort_topk orders them in the iterations whose
-// check needs the order (no crossing node left, or the loop's last).
+// select: sort the candidates by (l desc, id asc) in shared memory; the k-th
+// entry is theta_r and the first k entries are the current top-k.
 // ---------------------------------------------------------------------------
 struct SelEntry {
     unsigned long long key;  // bit pattern of l (monotone for l >= 0)
@@ -309,115 +307,6 @@ __device__ void sort_and_emit(SelEntry* sel, unsigned int cnt, int kk, const dou
     }
 }
 
-// The kk-th entry of sel[0..cnt) in (l desc, id asc) order: a radix select
-// over the composite key (bits of l, then the complemented id; larger is
-// earlier), 8-bit digits from the most significant, each digit one
-// shared-memory histogram of the entries that match the digits chosen so far.
-// It stops as soon as the chosen digits single out one entry (keys are
-// distinct: ids are).  The kk entries whose key is at least that entry's go
-// out unsorted as the top-k, and the entry itself as theta.
-__device__ void select_and_emit(const SelEntry* sel, unsigned int cnt, int kk, const double* __restrict__ cu,
-                                int32_t* topk_id, double* topk_l, double* topk_u, Ctrl* ctrl) {
-    __shared__ unsigned int hist[256];
-    __shared__ unsigned int s_bin, s_rem, s_nmatch, s_out;
-    __shared__ unsigned long long s_key;
-    __shared__ int32_t s_id;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (kk <= 0) return;
-    unsigned long long pre_hi = 0, mask_hi = 0;
-    unsigned int pre_lo = 0, mask_lo = 0;
-    unsigned int rem = (unsigned int)kk;  // rank of the wanted entry among the matching ones (from 1)
-    for (int t = 0; t < 12; ++t) {
-        for (int q = tid; q < 256; q += SELECT_THREADS) hist[q] = 0;
-        __syncthreads();
-        for (unsigned int e = tid; e < cnt; e += SELECT_THREADS) {
-            const unsigned long long hi = sel[e].key;
-            const unsigned int lo = ~(unsigned int)sel[e].id;
-            if ((hi & mask_hi) == pre_hi && (lo & mask_lo) == pre_lo) {
-                const unsigned int dg = t < 8 ? (unsigned int)(hi >> (56 - 8 * t)) & 255u : (lo >> (88 - 8 * t)) & 255u;
-                atomicAdd(&hist[dg], 1u);
-            }
-        }
-        __syncthreads();
-        if (wid == 0) {  // lane l scans bins 255 - 8l down to 248 - 8l: the largest digits first
-            unsigned int c[8], sum = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                c[j] = hist[255 - 8 * lane - j];
-                sum += c[j];
-            }
-            unsigned int incl = sum;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const unsigned int y = __shfl_up_sync(FULL, incl, off);
-                if (lane >= off) incl += y;
-            }
-            const unsigned int excl = incl - sum;
-            if (excl < rem && rem <= incl) {  // one lane holds the bin that reaches rank rem
-                unsigned int cum = excl;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (cum < rem && rem <= cum + c[j]) {
-                        s_bin = 255u - 8u * lane - j;
-                        s_rem = rem - cum;
-                        s_nmatch = c[j];
-                    }
-                    cum += c[j];
-                }
-            }
-        }
-        __syncthreads();
-        const unsigned int b = s_bin, nm = s_nmatch;
-        rem = s_rem;
-        if (t < 8) {
-            pre_hi |= (unsigned long long)b << (56 - 8 * t);
-            mask_hi |= 255ull << (56 - 8 * t);
-        } else {
-            pre_lo |= b << (88 - 8 * t);
-            mask_lo |= 255u << (88 - 8 * t);
-        }
-        if (nm == 1) break;  // uniform: every thread read the same s_nmatch
-    }
-    if (tid == 0) s_out = 0;
-    for (unsigned int e = tid; e < cnt; e += SELECT_THREADS) {
-        const unsigned long long hi = sel[e].key;
-        const unsigned int lo = ~(unsigned int)sel[e].id;
-        if ((hi & mask_hi) == pre_hi && (lo & mask_lo) == pre_lo) {  // the one entry left
-            s_key = hi;
-            s_id = sel[e].id;
-        }
-    }
-    __syncthreads();
-    const unsigned long long thk = s_key;
-    const int32_t thid = s_id;
-    // the kk entries with key >= theta's, unsorted, one shared-memory atomic per warp
-    for (unsigned int base = 0; base < cnt; base += SELECT_THREADS) {
-        const unsigned int e = base + tid;
-        bool take = false;
-        SelEntry x{0ULL, 0, 0};
-        if (e < cnt) {
-            x = sel[e];
-            take = x.key > thk || (x.key == thk && x.id <= thid);
-        }
-        const unsigned int m = __ballot_sync(FULL, take);
-        unsigned int wpos = 0;
-        if (lane == 0 && m) wpos = atomicAdd(&s_out, (unsigned int)__popc(m));
-        wpos = __shfl_sync(FULL, wpos, 0);
-        if (take) {
-            const unsigned int pos = wpos + __popc(m & ((1u << lane) - 1u));
-            if (pos < (unsigned int)kk) {
-                topk_id[pos] = x.id;
-                topk_l[pos] = __longlong_as_double((long long)x.key);
-                topk_u[pos] = cu[x.src];
-            }
-        }
-    }
-    if (tid == 0) {
-        ctrl->theta = __longlong_as_double((long long)thk);
-        ctrl->theta_id = thid;
-    }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(SELECT_THREADS)
 select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, const int32_t* __restrict__ cid,
@@ -495,42 +384,14 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
         return;
     }
     const int kk = (int)min((long long)p.k, (long long)cnt);
-    select_and_emit(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
+    if (cnt <= (unsigned int)SELECT_THREADS) sort_and_emit<1>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
+    else if (cnt <= 2u * SELECT_THREADS) sort_and_emit<2>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
+    else if (cnt <= 4u * SELECT_THREADS) sort_and_emit<4>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
+    else sort_and_emit<8>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
     if (tid == 0) {
         ctrl->k_eff = kk;
         ctrl->tau = tau;
     }
-}
-
-// FP32-certified mode: the rounding widening of the active set has outgrown
-// the tail term, so further iterations cannot separate it (finalize stops)
-__device__ __forceinline__ bool cert_stalls(const Ctrl* ctrl, const IterParams& p, int r_cur) {
-    if (!p.cert || r_cur < ctrl->f32_from) return false;
-    return __longlong_as_double((long long)ctrl->tailw_bits) < __longlong_as_double((long long)ctrl->roundw_bits);
-}
-
-// The top-k in (l desc, id asc) order, in place, when this iteration's check
-// reads the order (no node outside the top-k crosses theta) or the loop ends
-// here (r_max, or an FP32 stall) and the top-k is the result.
-__global__ void __launch_bounds__(SELECT_THREADS)
-sort_topk_kernel(int32_t* topk_id, double* topk_l, double* topk_u, Ctrl* ctrl, IterParams p) {
-    extern __shared__ unsigned char sort_smem[];
-    SelEntry* sel = (SelEntry*)sort_smem;
-    double* us = (double*)(sel + SELECT_CAP);
-    if (ctrl->stop || (ctrl->flags & F_NEED_BIG)) return;
-    const int r_cur = ctrl->r + 1;
-    if (!(ctrl->cnt_cross == 0 || r_cur >= p.r_max || cert_stalls(ctrl, p, r_cur))) return;
-    const int kk = ctrl->k_eff;
-    for (int e = threadIdx.x; e < kk; e += SELECT_THREADS) {
-        sel[e] = SelEntry{(unsigned long long)__double_as_longlong(topk_l[e]), topk_id[e], e};
-        us[e] = topk_u[e];
-    }
-    __syncthreads();
-    const unsigned int cnt = (unsigned int)kk;
-    if (cnt <= (unsigned int)SELECT_THREADS) sort_and_emit<1>(sel, cnt, kk, us, topk_id, topk_l, topk_u, ctrl);
-    else if (cnt <= 2u * SELECT_THREADS) sort_and_emit<2>(sel, cnt, kk, us, topk_id, topk_l, topk_u, ctrl);
-    else if (cnt <= 4u * SELECT_THREADS) sort_and_emit<4>(sel, cnt, kk, us, topk_id, topk_l, topk_u, ctrl);
-    else sort_and_emit<8>(sel, cnt, kk, us, topk_id, topk_l, topk_u, ctrl);
 }
 
 // ---------------------------------------------------------------------------
@@ -834,9 +695,11 @@ __global__ void finalize_kernel(const double* __restrict__ topk_l, const double*
         if (p.cert) {
             const double smax = __longlong_as_double((long long)ctrl->smax_bits);
             const double sprev = __longlong_as_double((long long)ctrl->smax_prev_bits);
+            const double tailw = __longlong_as_double((long long)ctrl->tailw_bits);
+            const double roundw = __longlong_as_double((long long)ctrl->roundw_bits);
             // stall: over the active set the rounding widening is wider than the
             // Theorem-1 tail term, so further iterations cannot separate it
-            if (!conv && cert_stalls(ctrl, p, r_cur)) {
+            if (!conv && r_cur >= ctrl->f32_from && tailw < roundw) {
                 ctrl->stall = 1;
                 stop = 1;
             }
@@ -1024,13 +887,9 @@ cudaError_t launch_theta0_class(const DeviceGraph& g, const IterBuffers& b, cons
     return cudaGetLastError();
 }
 
-constexpr int SORT_SMEM = SELECT_CAP * (int)(sizeof(SelEntry) + sizeof(double));
-
 cudaError_t prepare_kernels() {
     const int smem = SELECT_CAP * (int)sizeof(SelEntry);
-    cudaError_t e = cudaFuncSetAttribute(select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sort_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SORT_SMEM);
+    return cudaFuncSetAttribute(select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t launch_select(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const double* cl,
@@ -1049,8 +908,6 @@ cudaError_t launch_count(const DeviceGraph& g, const IterBuffers& b, const IterP
     // over tiles of the list, or of V for the first count
     count_kernel<double><<<grid_for(p.n, COUNT_TILE, 152 * 4), COUNT_THREADS, 0, st>>>(
         (const double*)b.walk, b.c, b.c32, b.lb, b.ub, g.perm, b.active, b.alist[0], b.alist[1], b.ctrl, p);
-    // the order of the top-k, where the check (finalize) or the result needs it
-    sort_topk_kernel<<<1, SELECT_THREADS, SORT_SMEM, st>>>(b.topk_id, b.topk_l, b.topk_u, b.ctrl, p);
     return cudaGetLastError();
 }
 
