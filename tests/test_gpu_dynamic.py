@@ -181,3 +181,24 @@ def test_a_hub_row_emptied_and_refilled(served):
             _compare(h, s, k)
     _compare(h, s, k)
     assert h.walk(1)[0] == s.alpha_pow(1) * 3
+
+
+def test_a_large_degree_bound_and_the_histogram_theta0():
+    # D = 2^30: alpha = 1/(D+1) is tiny, and after an update batch theta_0
+    # comes from the degree histogram (the relabelling's classes are no
+    # longer exact), which holds min(D, 2^24) + 1 bins, not D + 1
+    g = gg.rmat(12, 16, seed=95)
+    D = 1 << 30
+    k, eps = 50, 1e-20
+    h, s = _pair(g, k, eps, D)
+    src, dst, ins = gg.update_batch(g, 300, seed=96)
+    assert s.apply_update(src, dst, ins) == oracle.OK
+    info = h.update(src, dst, ins)
+    assert info.converged == 1 and info.r == s.info()["r"]
+    _compare(h, s, k)
+    cur = gg.apply_batch(g, src, dst, ins)
+    info = h.rank(0.0, k, eps)  # a static ranking of the updated graph
+    t = oracle.Session(cur.rowptr, cur.col, True, D)
+    assert t.rank_static(0.0, k, eps, 128) == oracle.OK
+    assert info.r == t.info()["r"]
+    _compare(h, t, k)
