@@ -131,12 +131,25 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
         return;
     }
     double sd, c64, c32 = 0.0;
+    bool zero = false;  // a node without walks so far: every value of the row is +0
     if constexpr (sizeof(Acc) == 8) {
-        sd = __dmul_rn(p.alpha, (double)sum);
-        ((double*)e.y)[u] = sd;
-        if (e.s32) e.s32[u] = f64_to_f32_rn(sd);  // one rounding per row, not per gathered arc
-        c64 = __dadd_rn(e.c64[u], sd);
-        e.c64[u] = c64;
+        const double c_prev = e.c64[u];
+        if (__double_as_longlong((double)sum) == 0 && __double_as_longlong(c_prev) == 0) {
+            // alpha * +0 and +0 + +0 are +0 in every rounding mode: the bits of
+            // the full computation below, without the FP64 pipe (narrow on this
+            // GPU; most rows of an R-MAT graph are isolated nodes)
+            sd = 0.0;
+            c64 = 0.0;
+            zero = true;
+            ((double*)e.y)[u] = 0.0;
+            if (e.s32) e.s32[u] = 0.0f;
+        } else {
+            sd = __dmul_rn(p.alpha, (double)sum);
+            ((double*)e.y)[u] = sd;
+            if (e.s32) e.s32[u] = f64_to_f32_rn(sd);  // one rounding per row, not per gathered arc
+            c64 = __dadd_rn(c_prev, sd);
+            e.c64[u] = c64;
+        }
         if (e.c32) c32 = e.c32[u];
     } else {
         const float sf = __fmul_rn(p.alpha_f, (float)sum);
@@ -147,8 +160,8 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
         c64 = e.c64[u];
     }
     if (e.active[u]) {
-        double l, up;
-        node_bounds(c64, c32, sd, p, e.bs, l, up);
+        double l = 0.0, up = 0.0;  // c = s = +0: both bounds are +0 in either mode
+        if (!zero || __double_as_longlong(c32) != 0) node_bounds(c64, c32, sd, p, e.bs, l, up);
         if (p.cert) {  // both the new and the stored bounds are valid: keep the tighter ones
             l = nn_max(l, e.lb[u]);
             up = nn_min(up, e.ub[u]);
