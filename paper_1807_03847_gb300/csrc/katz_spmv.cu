@@ -118,7 +118,13 @@ __device__ __forceinline__ double nn_min(double a, double b) {
 // Finish row u of an FP64 level: s = alpha * sum, c64 += s, bounds, candidate.
 // Finish row u of an FP32 level: s = fl32(alpha_f * sum), c32 += s, bounds, candidate.
 // Candidates carry the original id.
-template <typename Acc>
+// ZeroRows: rows without walks so far (sum and c both +0) skip the FP64
+// arithmetic; alpha * +0 and +0 + +0 are +0 in every rounding mode, so the
+// bits are those of the full computation.  Worth it where the FP64 pipe
+// (narrow on this GPU) bounds the pass, as in the degree pass over an R-MAT
+// graph whose rows are mostly isolated nodes; the gather levels, bound by
+// their loads, run the plain epilogue.
+template <typename Acc, bool ZeroRows = false>
 __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, const IterParams& p) {
     if (e.store_only) {  // dynamic repair: the level value only (and its FP32 rounding at a transition)
         if constexpr (sizeof(Acc) == 8) {
@@ -131,13 +137,10 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
         return;
     }
     double sd, c64, c32 = 0.0;
-    bool zero = false;  // a node without walks so far: every value of the row is +0
+    bool zero = false;  // ZeroRows: a node without walks so far, every value of the row is +0
     if constexpr (sizeof(Acc) == 8) {
         const double c_prev = e.c64[u];
-        if (__double_as_longlong((double)sum) == 0 && __double_as_longlong(c_prev) == 0) {
-            // alpha * +0 and +0 + +0 are +0 in every rounding mode: the bits of
-            // the full computation below, without the FP64 pipe (narrow on this
-            // GPU; most rows of an R-MAT graph are isolated nodes)
+        if (ZeroRows && __double_as_longlong((double)sum) == 0 && __double_as_longlong(c_prev) == 0) {
             sd = 0.0;
             c64 = 0.0;
             zero = true;
@@ -160,8 +163,8 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
         c64 = e.c64[u];
     }
     if (e.active[u]) {
-        double l = 0.0, up = 0.0;  // c = s = +0: both bounds are +0 in either mode
-        if (!zero || __double_as_longlong(c32) != 0) node_bounds(c64, c32, sd, p, e.bs, l, up);
+        double l = 0.0, up = 0.0;  // zero: c = s = +0, both bounds are +0 in either mode
+        if (!ZeroRows || !zero || __double_as_longlong(c32) != 0) node_bounds(c64, c32, sd, p, e.bs, l, up);
         if (p.cert) {  // both the new and the stored bounds are valid: keep the tighter ones
             l = nn_max(l, e.lb[u]);
             up = nn_min(up, e.ub[u]);
@@ -548,7 +551,7 @@ __global__ void degree_level_kernel(const Off* __restrict__ rowptr, int64_t n, d
                             cand_cap, ctrl, p, (p.cert && 1 < ctrl->f32_from) ? s32 : nullptr);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
-        finish_row<double>(u, (double)((int64_t)rowptr[u + 1] - (int64_t)rowptr[u]), ep, p);
+        finish_row<double, true>(u, (double)((int64_t)rowptr[u + 1] - (int64_t)rowptr[u]), ep, p);
 }
 
 // Six 256-thread blocks per SM (40 registers): the gathers need the warps in
