@@ -235,6 +235,36 @@ katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t*
                                     const uint8_t* is_insert, int64_t m, katz_info* info);
 
 /*
+ * Algorithm 2 without blocking the caller: queue a batch for h and return at
+ * once with *ticket.  Batches submitted to one handle are applied in
+ * submission order, each exactly as katz_apply_update_batch applies it (the
+ * graph after the batches before it, re-certified top-k); the validation and
+ * rebuild of one batch overlap the repair of the one before it.  src, dst and
+ * is_insert are host arrays, copied before the call returns.  The first
+ * submitted batch sets up a private serving queue for h (the serving loop
+ * below, two workers) whose slots take batches of up to max(m, 10^4)
+ * updates; a later batch above that size returns KATZ_EINVAL.
+ * katz_submit_update_batch and katz_poll may be called from any thread.
+ * Between a submit and the katz_poll that reports its batch finished, the
+ * caller makes no other call on h; katz_destroy finishes the batch that is
+ * running and drops the queued ones.
+ * Errors: KATZ_EINVAL (arguments, batch size), KATZ_ESTATE (as
+ * katz_apply_update_batch), KATZ_ENOMEM, KATZ_ECUDA.
+ */
+katz_status katz_submit_update_batch(katz_h h, const int32_t* src, const int32_t* dst,
+                                     const uint8_t* is_insert, int64_t m, uint64_t* ticket);
+
+/*
+ * The outcome of a submitted batch.  KATZ_EBUSY: still queued or running.
+ * Otherwise the batch has finished: *info (nullable) is what
+ * katz_apply_update_batch would have written, and the return value is its
+ * status (KATZ_EINVAL: the batch was rejected and changed nothing).  Each
+ * ticket is reported finished once; an unknown or already collected ticket
+ * gives KATZ_ESTATE.
+ */
+katz_status katz_poll(katz_h h, uint64_t ticket, katz_info* info);
+
+/*
  * The number conversions of the FP32-certified levels, for tests and
  * diagnostics: out[i] = in[i] rounded to binary32 (to nearest, ties to even;
  * subnormal results kept, 0 below half the smallest subnormal) and

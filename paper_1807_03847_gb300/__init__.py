@@ -99,6 +99,8 @@ def _load():
         "katz_get_walk": (ctypes.c_int, [P, i32, P]),
         "katz_get_trace": (ctypes.c_int, [P, P, i32]),
         "katz_apply_update_batch": (ctypes.c_int, [P, P, P, P, i64, ctypes.POINTER(katz_info)]),
+        "katz_submit_update_batch": (ctypes.c_int, [P, P, P, P, i64, ctypes.POINTER(ctypes.c_uint64)]),
+        "katz_poll": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(katz_info)]),
         "katz_certify_topk_noalloc": (ctypes.c_int, [P, P, i64, i64, dbl, P, P, P]),
         "katz_convert_f64_f32": (ctypes.c_int, [P, i64, P, P]),
         "katz_server_default_opts": (None, [ctypes.POINTER(katz_server_opts)]),
@@ -249,6 +251,31 @@ def katz_apply_update_batch(h, src, dst, is_insert, m: int | None = None, check:
     return info
 
 
+def katz_submit_update_batch(h, src, dst, is_insert) -> int:
+    """Queue a batch (host arrays) for asynchronous application; the ticket."""
+    src = np.ascontiguousarray(src, np.int32)
+    dst = np.ascontiguousarray(dst, np.int32)
+    ins = np.ascontiguousarray(is_insert, np.uint8)
+    t = ctypes.c_uint64()
+    st = _load().katz_submit_update_batch(h, _ptr(src), _ptr(dst), _ptr(ins), len(src), ctypes.byref(t))
+    if st != 0:
+        raise KatzError(st, "katz_submit_update_batch")
+    return t.value
+
+
+def katz_poll(h, ticket: int) -> katz_info | None:
+    """None while the batch is queued or running; else its katz_info, with
+    the batch's own outcome in .status."""
+    info = katz_info()
+    st = _load().katz_poll(h, int(ticket), ctypes.byref(info))
+    if st == 8:  # KATZ_EBUSY
+        return None
+    if st == 9:  # KATZ_ESTATE: unknown or collected ticket
+        raise KatzError(st, "katz_poll")
+    info.status = st
+    return info
+
+
 def katz_convert_f64_f32(x):
     """The FP32-certified levels' rounding of the non-negative float64 device
     tensor x to float32 and the exact widening back (katz_convert_f64_f32)."""
@@ -389,6 +416,12 @@ class Katz:
 
     def update(self, src, dst, is_insert, check=True) -> katz_info:
         return katz_apply_update_batch(self.h, src, dst, is_insert, check=check)
+
+    def submit(self, src, dst, is_insert) -> int:
+        return katz_submit_update_batch(self.h, src, dst, is_insert)
+
+    def poll(self, ticket: int) -> katz_info | None:
+        return katz_poll(self.h, ticket)
 
 
 _load()

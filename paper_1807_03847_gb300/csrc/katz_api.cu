@@ -598,6 +598,10 @@ const char* katz_last_error(katz_h h) { return h ? h->err.c_str() : "null handle
 
 void katz_destroy(katz_h h) {
     if (!h) return;
+    if (h->async) {  // the running batch finishes, queued ones are dropped
+        katz_server_destroy(h->async);
+        h->async = nullptr;
+    }
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_iter(h);
     dfree(h, h->g.rowptr);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -101,6 +102,10 @@ struct katz_handle {
     float last_ms = 0.f;
     std::vector<int64_t> trace;
     std::string err;
+    // katz_submit_update_batch / katz_poll: a private serving queue, made at
+    // the first submitted batch
+    std::mutex async_mu;
+    katz_server* async = nullptr;
 };
 
 namespace katz {

@@ -358,6 +358,48 @@ katz_status katz_server_wait(katz_server_h s, uint64_t ticket, int64_t timeout_m
     return KATZ_OK;
 }
 
+// Algorithm 2 without blocking the caller: the handle's private server (two
+// workers, so the prepare of a batch overlaps the repair of the one before it)
+katz_status katz_submit_update_batch(katz_h h, const int32_t* src, const int32_t* dst, const uint8_t* is_insert,
+                                     int64_t m, uint64_t* ticket) {
+    if (!h || !ticket || m < 0 || (m > 0 && (!src || !dst || !is_insert))) return KATZ_EINVAL;
+    std::lock_guard<std::mutex> lock(h->async_mu);
+    if (!h->async) {
+        katz_status st = katz::update_allowed(h);
+        if (st != KATZ_OK) return st;
+        katz_server_opts o;
+        katz_server_default_opts(&o);
+        o.workers = 2;
+        o.slots = 4;
+        o.slot_updates = std::max<int64_t>(m, o.slot_updates);
+        katz_server* s = nullptr;
+        if ((st = katz_server_create(&s, &o)) != KATZ_OK) return st;
+        if ((st = katz_server_attach(s, h, h->k_eff)) != KATZ_OK) {
+            katz_server_destroy(s);
+            return st;
+        }
+        h->async = s;
+    }
+    if (m > h->async->opts.slot_updates) return KATZ_EINVAL;
+    return katz_server_submit(h->async, h, src, dst, is_insert, m, ticket);
+}
+
+katz_status katz_poll(katz_h h, uint64_t ticket, katz_info* info) {
+    if (!h) return KATZ_EINVAL;
+    katz_server* s = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(h->async_mu);
+        s = h->async;
+    }
+    if (!s) return KATZ_ESTATE;  // nothing was submitted
+    katz_request_result res;
+    const katz_status st = katz_server_wait(s, ticket, 0, nullptr, &res);
+    if (st == KATZ_ETIMEOUT) return KATZ_EBUSY;
+    if (st != KATZ_OK) return KATZ_ESTATE;  // unknown or collected ticket
+    if (info) *info = res.info;
+    return (katz_status)res.status;
+}
+
 void katz_server_destroy(katz_server_h s) {
     if (!s) return;
     {

@@ -176,3 +176,74 @@ def test_pipelined_batches_on_one_handle_match_sequential(directed, fp32):
     assert_same_ranking(h.ranking(k), s.ranking(), l, atol=eps if fp32 else 0.0)
     seq.close()
     h.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_submit_and_poll_match_applying_the_batches_in_order(fp32):
+    # katz_submit_update_batch / katz_poll: the asynchronous form of
+    # katz_apply_update_batch on one handle (its private serving queue)
+    import time
+
+    g = gg.rmat(13, 16, seed=63)
+    D, k = g.deg_max() + 64, 40
+    opts = dict(keep_history=1, deg_bound=D, r_max=128)
+    eps = EPS
+    if fp32:
+        opts.update(precision=K.KATZ_FP32_CERT, fp32_from=3)
+        eps = 1e-4
+    batches, cur = [], g
+    for j in range(8):
+        b = gg.update_batch(cur, [5, 900, 30, 3000][j % 4], seed=800 + j)
+        cur = gg.apply_batch(cur, *b)
+        batches.append(b)
+    seq = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(**opts))
+    seq.rank(0.0, k, eps)
+    ref = [seq.update(*b) for b in batches]
+    h = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(**opts))
+    h.rank(0.0, k, eps)
+    tickets = [h.submit(*b) for b in batches]
+
+    def result(t):
+        deadline = time.time() + 120
+        while True:
+            info = h.poll(t)
+            if info is not None:
+                return info
+            assert time.time() < deadline, "batch did not finish"
+            time.sleep(0.001)
+
+    infos = [result(t) for t in tickets]
+    for j, (a, b) in enumerate(zip(infos, ref)):
+        assert a.status == 0 and a.r == b.r and a.nnz == b.nnz and a.converged == 1, j
+    np.testing.assert_array_equal(h.ranking(k), seq.ranking(k))
+    for x, y in zip(h.bounds(), seq.bounds()):
+        np.testing.assert_array_equal(x, y)
+    with pytest.raises(K.KatzError) as e:  # each ticket is reported once
+        h.poll(tickets[0])
+    assert e.value.name == "KATZ_ESTATE"
+    # a rejected batch (an edge that is already there) changes nothing
+    u = 0 if cur.rowptr[1] > cur.rowptr[0] else int(np.argmax(np.diff(cur.rowptr) > 0))
+    v = int(cur.col[cur.rowptr[u]])
+    before = h.ranking(k).copy()
+    t = h.submit(np.array([u], np.int32), np.array([v], np.int32), np.array([1], np.uint8))
+    info = result(t)
+    assert info.status == 1  # KATZ_EINVAL
+    np.testing.assert_array_equal(h.ranking(k), before)
+    # batches still queued when the handle is destroyed are dropped
+    for j in range(3):
+        h.submit(*gg.update_batch(cur, 50, seed=900 + j))
+    h.close()
+    seq.close()
+
+
+def test_submit_needs_a_ranked_handle_with_history():
+    g = gg.rmat(10, 8, seed=64)
+    h = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(keep_history=1))
+    src, dst, ins = gg.update_batch(g, 10, seed=1)
+    with pytest.raises(K.KatzError) as e:
+        h.submit(src, dst, ins)
+    assert e.value.name == "KATZ_ESTATE"
+    with pytest.raises(K.KatzError) as e:  # nothing submitted yet
+        h.poll(1)
+    assert e.value.name == "KATZ_ESTATE"
+    h.close()
