@@ -30,9 +30,10 @@
  *     n+1 entries, rowptr[0] = 0, non-decreasing) and col (int32, nnz =
  *     rowptr[n] entries).  An undirected graph is passed as its symmetric
  *     CSR (each edge as two arcs; Sec. 2.1).
- *   - A handle is used by one host thread at a time.  All device work is
- *     ordered on the handle's CUDA stream (katz_opts.cuda_stream, or a
- *     stream the library creates).
+ *   - A handle is used by one host thread at a time, except that
+ *     katz_submit_update_batch and katz_poll may be called from any thread.
+ *     All device work is ordered on the handle's CUDA stream
+ *     (katz_opts.cuda_stream, or a stream the library creates).
  */
 #ifndef KATZ_H_
 #define KATZ_H_
