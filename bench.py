@@ -13,6 +13,14 @@ traversed per second, summed over ranks).
 
 N > 1 runs N independent replicas (the method needs no exchange between
 GPUs at these sizes), launched by torch.distributed.run.
+
+Beside the static line the default run serves a stream of update batches on
+R-MAT23 (Algorithm 2 through the serving loop) and reports it under
+"serving" (FP64 levels) and "serving_fp32cert" (FP32-certified levels):
+capacity, p50/p99 latency at 200 batches/s and at 70% of capacity, device
+time per batch and the static recomputation it is compared with.
+--serve-batches 0 skips them; --workload serve-rmat23 makes the serving run
+the headline (p99 latency).
 """
 from __future__ import annotations
 
