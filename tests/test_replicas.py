@@ -57,3 +57,23 @@ def test_reference_arm_runs_on_rank_zero_only():
                           "er16k", "--steps", "1", "--warmup", "0"], env=env, cwd=ROOT, capture_output=True,
                          text=True, timeout=300)
     assert res.returncode == 0 and res.stdout.strip() == ""
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the oracle timed on the host cores, as bench.py --impl reference runs it
+    import json
+
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "er16k", "--steps", "2", "--warmup", "1"], env=env, cwd=ROOT, capture_output=True,
+                         text=True, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GTEPS" and d["value"] > 0
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "er16k-top100-fp64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
