@@ -77,6 +77,7 @@ def _load():
                 "oracle_session_active": (i64, [P, P, i64]),
                 "oracle_session_iterations": (ci, [P, dbl, i64, dbl, ci]),
                 "oracle_session_run_fixed": (ci, [P, dbl, ci]),
+                "oracle_converged_bounds": (ci, [i64, P, P, i64, dbl, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -137,6 +138,18 @@ def alg2_update_exact(rowptr, col, omega: list[list[int]], src, dst, ins) -> lis
     if st:
         raise OracleError(st, "alg2_update")
     return [[int(a_out[i, v, 1]) << 64 | int(a_out[i, v, 0]) for v in range(n)] for i in range(r)]
+
+
+def converged_bounds(lower, upper, k: int, eps: float):
+    """converged() of Algorithm 1 over all nodes (M = V) on the given bounds:
+    (certified, top) with top = the min(k, n) largest lower bounds in
+    decreasing order, ties by smaller id."""
+    lower = np.ascontiguousarray(lower, np.float64)
+    upper = np.ascontiguousarray(upper, np.float64)
+    n = lower.shape[0]
+    top = np.empty(max(min(k, n), 1), np.int32)
+    ok = _load().oracle_converged_bounds(n, _ptr(lower), _ptr(upper), int(k), float(eps), _ptr(top))
+    return bool(ok), top[:min(k, n)].copy()
 
 
 class Session:

@@ -521,6 +521,20 @@ int64_t oracle_session_active(void* p, int32_t* ids, int64_t cap) {
     return (int64_t)s->M.size();
 }
 
+// converged() of Algorithm 1 on given bounds l[v] <= c(v) <= u[v] with
+// M = V: writes the first min(k, n) entries of the sorted M to top (the
+// ranking when certified) and returns 1 if the top-k criterion holds, else 0.
+int oracle_converged_bounds(int64_t n, const double* l, const double* u, int64_t k, double eps, int32_t* top) {
+    std::vector<double> lv(l, l + n), uv(u, u + n);
+    std::vector<int32_t> M((size_t)n);
+    std::iota(M.begin(), M.end(), 0);
+    std::vector<int32_t> all(M);
+    const int64_t kk = std::min<int64_t>(k, n);
+    std::partial_sort(all.begin(), all.begin() + kk, all.end(), ByLowerDesc{lv.data()});
+    for (int64_t i = 0; i < kk; ++i) top[i] = all[(size_t)i];
+    return converged(M, k, lv, uv, eps) ? 1 : 0;
+}
+
 int oracle_session_run_fixed(void* p, double alpha, int R) {
     return ((Session*)p)->run_fixed(alpha, R);
 }

@@ -240,6 +240,43 @@ def test_converged_meets_topk_criterion_first_time(seed):
         assert not _criterion(l1, u1, k, eps)[0]
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_converged_on_given_bounds_is_the_pairwise_criterion(seed):
+    """converged() on caller-given bounds (M = V) against the all-pairs
+    criterion of Eq. 3; the bounds are drawn so that some arrays separate
+    and some fail either at an adjacent top-k pair or at a node outside the
+    top-k, and with many exact ties in l."""
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(5, 60))
+    k = int(rng.integers(1, n + 1))
+    eps = 1e-3
+    base = rng.integers(0, 6 if seed % 3 == 0 else 1000, n).astype(np.float64)  # seed % 3 == 0: heavy ties
+    width = rng.choice([0.0, 5e-4, 2e-3, 0.5], n, p=[0.4, 0.3, 0.2, 0.1]) * (seed % 2)
+    l = base.copy()
+    u = base + width
+    ok, top = oracle.converged_bounds(l, u, k, eps)
+    want_ok, order = _criterion(l, u, k, eps)
+    assert ok == want_ok
+    assert list(top) == order[:k]
+
+
+def test_converged_on_given_bounds_fails_at_each_test_alone():
+    """One array where only an adjacent top-k pair overlaps, one where only a
+    node outside the top-k crosses the k-th lower bound."""
+    eps = 0.25  # exact in binary: u - eps lands exactly on the compared lower bound
+    l = np.array([10.0, 9.0, 8.0, 1.0, 0.5])
+    u = l + 0.0
+    assert oracle.converged_bounds(l, u, 3, eps)[0]
+    u_pair = u.copy()
+    u_pair[1] = 10.0 + eps  # node 1 reaches node 0 within eps: adjacent pair not separated
+    assert not _criterion(l, u_pair, 3, eps)[0]
+    assert not oracle.converged_bounds(l, u_pair, 3, eps)[0]
+    u_cross = u.copy()
+    u_cross[3] = 8.0 + eps  # node 3 (rank 4) reaches the k-th lower bound
+    assert not _criterion(l, u_cross, 3, eps)[0]
+    assert not oracle.converged_bounds(l, u_cross, 3, eps)[0]
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_certified_ranking_matches_exact_katz(seed):
     rng = np.random.default_rng(300 + seed)
