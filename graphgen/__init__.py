@@ -51,6 +51,8 @@ def _load():
             lib.gg_rmat.argtypes = [ctypes.c_int, i64, dbl, dbl, dbl, u64]
             lib.gg_chung_lu.restype = P
             lib.gg_chung_lu.argtypes = [i64, i64, dbl, dbl, u64]
+            lib.gg_band_union.restype = P
+            lib.gg_band_union.argtypes = [i64, P, P, i64, i64, i64]
             lib.gg_from_pairs.restype = P
             lib.gg_from_pairs.argtypes = [i64, i64, P, P]
             lib.gg_n.restype = i64
@@ -133,6 +135,32 @@ def chung_lu(n: int, mean_degree: float = 16.0, exponent: float = 2.1, seed: int
     if pairs is None:
         pairs = int(n * mean_degree // 2)
     return _take(_load().gg_chung_lu(n, pairs, tail, x_m, seed), f"chunglu_n{n}_s{seed}")
+
+
+def band_union(g: Graph, n_band: int, d: int, n_pad: int = 0) -> Graph:
+    """g, then a band graph on n_band nodes (i ~ j iff 0 < |i - j| <= d), then
+    n_pad isolated nodes, as one undirected graph (disjoint union)."""
+    return _take(_load().gg_band_union(g.n, g.rowptr.ctypes.data, g.col.ctypes.data, n_band, d, n_pad),
+                 f"{g.name}+band{n_band}x{d}+{n_pad}")
+
+
+def padded_to(g: Graph, total: int, d: int = 128) -> Graph:
+    """g padded by a band of half-width d and isolated nodes so that n + nnz
+    of the result is exactly `total` (e.g. just below 2^31 - 1, the limit of
+    32-bit row offsets).  A band node adds 2d + 1 to n + nnz, less d(d+1) in all
+    for the band's two ends."""
+    rest = total - (g.n + g.nnz)
+    if rest < 0:
+        raise ValueError("graph already larger than the target")
+    n_band = (rest + d * (d + 1)) // (2 * d + 1)
+    while n_band > 0 and n_band * (2 * d + 1) - d * (d + 1) > rest:
+        n_band -= 1
+    if n_band <= d:
+        n_band = 0
+    band = 2 * d * n_band - d * (d + 1) + n_band if n_band else 0
+    out = band_union(g, n_band, d, rest - band)
+    assert out.n + out.nnz == total
+    return out
 
 
 def from_edges(n: int, u, v, name: str = "pairs") -> Graph:
@@ -316,6 +344,7 @@ def workload(name: str) -> Graph:
     if name.startswith("rmat"):
         scale = int(name[4:])
         return rmat(scale, 16, seed=SEED_BASE + scale)
-    if name == "chunglu27":
-        return chung_lu(1 << 27, 16.0, 2.1, SEED_BASE + 27)
+    if name.startswith("chunglu"):  # chunglu27: the large workload; smaller scales for profiling
+        scale = int(name[7:])
+        return chung_lu(1 << scale, 16.0, 2.1, SEED_BASE + scale)
     raise KeyError(name)

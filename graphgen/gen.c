@@ -153,6 +153,42 @@ int gg_max_threads(void) {
 #endif
 }
 
+/*
+ * Disjoint union of a given symmetric CSR (ids 0..n0-1), a band graph on
+ * n_band nodes (ids n0.., i ~ j iff 0 < |i - j| <= d) and n_pad isolated
+ * nodes (ids after the band).  The band's rows are sorted and duplicate-free
+ * by construction; it pads a graph to an exact size (n + nnz), e.g. just below
+ * the range of 32-bit row offsets.
+ */
+gg_csr *gg_band_union(int64_t n0, const int64_t *rowptr0, const int32_t *col0, int64_t n_band, int64_t d,
+                      int64_t n_pad) {
+    if (n0 < 0 || n_band < 0 || d < 0 || n_pad < 0) return NULL;
+    const int64_t n = n0 + n_band + n_pad;
+    gg_csr *g = (gg_csr *)malloc(sizeof(gg_csr));
+    if (!g) return NULL;
+    g->n = n;
+    g->rowptr = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    if (!g->rowptr) { free(g); return NULL; }
+    for (int64_t i = 0; i <= n0; ++i) g->rowptr[i] = rowptr0[i];
+    for (int64_t b = 0; b < n_band; ++b) {
+        const int64_t lo = b - d < 0 ? 0 : b - d, hi = b + d > n_band - 1 ? n_band - 1 : b + d;
+        g->rowptr[n0 + b + 1] = g->rowptr[n0 + b] + (hi - lo);
+    }
+    for (int64_t i = n0 + n_band; i < n; ++i) g->rowptr[i + 1] = g->rowptr[i];
+    g->nnz = g->rowptr[n];
+    g->col = (int32_t *)malloc((size_t)(g->nnz > 0 ? g->nnz : 1) * sizeof(int32_t));
+    if (!g->col) { free(g->rowptr); free(g); return NULL; }
+    if (rowptr0[n0]) memcpy(g->col, col0, (size_t)rowptr0[n0] * sizeof(int32_t));
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < n_band; ++b) {
+        const int64_t lo = b - d < 0 ? 0 : b - d, hi = b + d > n_band - 1 ? n_band - 1 : b + d;
+        int32_t *p = g->col + g->rowptr[n0 + b];
+        for (int64_t j = lo; j <= hi; ++j)
+            if (j != b) *p++ = (int32_t)(n0 + j);
+    }
+    return g;
+}
+
 /* CSR of an arbitrary pair list (used for hand-made graphs and update tests) */
 gg_csr *gg_from_pairs(int64_t n, int64_t m, const int32_t *u, const int32_t *v) {
     return assemble(n, m, u, v);

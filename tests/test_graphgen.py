@@ -121,3 +121,22 @@ def test_directed_helpers_make_valid_graphs_and_batches():
         assert nxt.nnz == cur.nnz + int(ins.sum()) - int((1 - ins).sum())
         assert nxt.deg_max() <= max(D, cur.deg_max())
         cur = nxt
+
+
+def test_band_union_pads_to_an_exact_size():
+    """The padding graph is symmetric, sorted, free of self-loops and
+    duplicates, leaves the base graph's rows unchanged, and lands n + nnz on
+    the requested total."""
+    base = gg.chung_lu(2000, 8.0, 2.1, seed=9)
+    for extra, d in ((7, 4), (5000, 4), (123457, 16)):
+        g = gg.padded_to(base, base.n + base.nnz + extra, d=d)
+        assert g.n + g.nnz == base.n + base.nnz + extra
+        assert np.array_equal(g.rowptr[:base.n + 1], base.rowptr)
+        assert np.array_equal(g.col[:base.nnz], base.col)
+        rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+        assert np.all(rows != g.col)
+        keys = rows.astype(np.int64) * g.n + g.col
+        assert np.all(np.diff(keys) > 0)  # rows sorted, no duplicates
+        rev = g.col.astype(np.int64) * g.n + rows
+        assert np.array_equal(np.sort(rev), keys)  # symmetric
+        assert int(np.diff(g.rowptr)[base.n:].max(initial=0)) <= 2 * d
