@@ -92,6 +92,11 @@ typedef struct {
     int32_t fp32_from;     /* KATZ_FP32_CERT: first walk level computed in FP32 (>= 2);
                               0 (default): chosen on the device once the FP32 rounding
                               widening is predicted to stay below eps/16 */
+    int32_t offsets64;     /* 1: keep the row offsets as int64 from the start.  0 (default):
+                              int32 while n + nnz < 2^31 - 1, int64 above; an update batch
+                              that takes a handle past that limit moves it to int64 offsets
+                              (one extra (n+1)-entry array during that batch) */
+    int32_t reserved;      /* set to 0 */
 } katz_opts;
 
 typedef struct {
@@ -193,8 +198,10 @@ katz_status katz_get_ranking(katz_h h, int32_t* ids, int64_t k);
 /*
  * Per-node bounds at the current r: lower[v] = l_r(v), upper[v] = u_r(v)
  * (Alg. 1), each n doubles, host or device.  err (nullable): in
- * KATZ_FP32_CERT mode the width added for rounding, per node; zeros in
- * FP64 mode.  Any pointer may be NULL to skip it.
+ * KATZ_FP32_CERT mode the width of the rounding interval per node: lower[v]
+ * and upper[v] each lie within err[v] of l_r(v) and u_r(v) evaluated in exact
+ * arithmetic (lower[v] below, upper[v] above them); zeros in FP64 mode.  Any
+ * pointer may be NULL to skip it.
  */
 katz_status katz_get_bounds(katz_h h, double* lower, double* upper, double* err);
 

@@ -35,7 +35,8 @@ class katz_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("undirected", ctypes.c_int32), ("keep_history", ctypes.c_int32),
                 ("r_max", ctypes.c_int32), ("deg_bound", ctypes.c_int64), ("frontier_abort_frac", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("use_graph", ctypes.c_int32), ("inbound", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("fp32_from", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("fp32_from", ctypes.c_int32),
+                ("offsets64", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class katz_info(ctypes.Structure):
@@ -289,11 +290,35 @@ def katz_convert_f64_f32(x):
     return out, back
 
 
+def _require_device_tensor(name, t, dtype_name, min_numel, exact=False):
+    """The library's kernels read and write this buffer directly: it must be a
+    contiguous CUDA tensor of the given dtype on the current device, with at
+    least (or, exact, exactly) min_numel elements."""
+    if not (hasattr(t, "is_cuda") and hasattr(t, "dtype")) or not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    import torch
+
+    if t.dtype != getattr(torch, dtype_name):
+        raise ValueError(f"{name}: expected dtype {dtype_name}, got {t.dtype}")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on cuda:{t.device.index}, the current device is cuda:{torch.cuda.current_device()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    if (t.numel() != min_numel) if exact else (t.numel() < min_numel):
+        raise ValueError(f"{name}: {t.numel()} elements, {'expected' if exact else 'need at least'} {min_numel}")
+
+
 def katz_certify_topk_noalloc(lower, upper, k: int, eps: float, ids_out, certified_out, stream=None) -> None:
     """Top-k ids and the separation verdict from device bounds, with no
-    allocation by the library; lower/upper/ids_out/certified_out are device
-    tensors the caller owns; stream: a torch.cuda.Stream or raw handle."""
-    n = lower.shape[0]
+    allocation by the library; lower/upper (float64, n each), ids_out (int32,
+    >= k) and certified_out (int32, >= 1) are CUDA tensors on the current
+    device that the caller owns; stream: a torch.cuda.Stream or raw handle.
+    Anything else raises ValueError before the library is called."""
+    _require_device_tensor("lower", lower, "float64", 1)
+    n = lower.numel()
+    _require_device_tensor("upper", upper, "float64", n, exact=True)
+    _require_device_tensor("ids_out", ids_out, "int32", max(int(k), 1))
+    _require_device_tensor("certified_out", certified_out, "int32", 1)
     handle = getattr(stream, "cuda_stream", stream)
     st = _load().katz_certify_topk_noalloc(_ptr(lower), _ptr(upper), int(n), int(k), float(eps), _ptr(ids_out),
                                            _ptr(certified_out), handle)

@@ -99,11 +99,7 @@ katz_status init_handle_runtime(katz_handle* h) {
 // Scratch of the ranking loop that does not depend on the ranking's size.
 katz_status alloc_rank_scratch(katz_handle* h) {
     cudaError_t e;
-    if ((e = dmalloc(h, &h->d_deghist, (size_t)deg_hist_top(h->D) + 1)) != cudaSuccess ||
-        (e = dmalloc(h, &h->d_big_l, SELECT_CAP)) != cudaSuccess ||
-        (e = dmalloc(h, &h->d_big_u, SELECT_CAP)) != cudaSuccess ||
-        (e = dmalloc(h, &h->d_big_id, SELECT_CAP)) != cudaSuccess ||
-        (e = dmalloc(h, &h->d_hist256, 256)) != cudaSuccess || (e = dmalloc(h, &h->d_count, 1)) != cudaSuccess)
+    if ((e = dmalloc(h, &h->d_deghist, (size_t)deg_hist_top(h->D) + 1)) != cudaSuccess)
         return cuda_fail(h, e, "cudaMalloc rank scratch");
     return KATZ_OK;
 }
@@ -256,60 +252,6 @@ katz_status ensure_graph(katz_handle* h) {
     return KATZ_OK;
 }
 
-// theta_r for a candidate set too large for the one-CTA select: radix select
-// of the k-th composite key (8-bit digits, most significant first), then the
-// k winners go through the one-CTA select for their order.
-katz_status big_select(katz_handle* h) {
-    cudaError_t e;
-    Ctrl& hc = *h->h_ctrl;
-    const unsigned long long nc = hc.n_cand;
-    unsigned long long krem = (unsigned long long)std::min<int64_t>(h->p.k, (int64_t)nc);
-    unsigned __int128 prefix = 0;
-    std::vector<unsigned long long> hist(256);
-    for (int pass = 0; pass < 12; ++pass) {
-        if ((e = cudaMemsetAsync(h->d_hist256, 0, 256 * sizeof(unsigned long long), h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "memset hist");
-        if ((e = launch_radix_hist(h->b, pass, (unsigned long long)(prefix >> 32), (unsigned int)prefix,
-                                   h->d_hist256, h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "radix_hist");
-        if ((e = cudaMemcpyAsync(hist.data(), h->d_hist256, 256 * sizeof(unsigned long long),
-                                 cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "copy hist");
-        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "sync");
-        unsigned long long cum = 0;
-        int bsel = -1;
-        for (int bkt = 255; bkt >= 0; --bkt) {
-            if (cum + hist[bkt] >= krem) {
-                bsel = bkt;
-                break;
-            }
-            cum += hist[bkt];
-        }
-        if (bsel < 0) return fail(h, KATZ_ECUDA, "radix select lost the k-th candidate");
-        prefix |= (unsigned __int128)bsel << (88 - 8 * pass);
-        krem -= cum;
-    }
-    if ((e = cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), h->stream)) != cudaSuccess)
-        return cuda_fail(h, e, "memset count");
-    if ((e = launch_radix_filter(h->b, (unsigned long long)(prefix >> 32), (unsigned int)prefix, h->d_big_l,
-                                 h->d_big_u, h->d_big_id, h->d_count, h->stream)) != cudaSuccess)
-        return cuda_fail(h, e, "radix_filter");
-    Ctrl* dc = h->b.ctrl;
-    if ((e = cudaMemcpyAsync(&dc->n_cand, h->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
-                             h->stream)) != cudaSuccess)
-        return cuda_fail(h, e, "copy count");
-    const int32_t zero = 0;
-    (void)zero;
-    if ((e = cudaMemsetAsync(&dc->flags, 0, sizeof(int32_t), h->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(&dc->stop, 0, sizeof(int32_t), h->stream)) != cudaSuccess)
-        return cuda_fail(h, e, "reset flags");
-    if ((e = launch_select(h->g, h->b, h->p, h->d_big_l, h->d_big_u, h->d_big_id, h->fp32, h->stream)) != cudaSuccess ||
-        (e = launch_count(h->g, h->b, h->p, h->fp32, h->stream)) != cudaSuccess ||
-        (e = launch_finalize(h->b, h->p, h->stream)) != cudaSuccess)
-        return cuda_fail(h, e, "iteration tail");
-    return KATZ_OK;
-}
-
 // Run iterations until the device sets ctrl.stop (converged or r_max).
 // Graph mode: one graph launch runs the whole loop on the device; the host
 // only steps in when the candidate set outgrows the one-CTA select.
@@ -357,19 +299,7 @@ katz_status run_loop(katz_handle* h, int done) {
         if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "copy ctrl");
         if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "iteration");
-        const Ctrl& hc = *h->h_ctrl;
-        if (hc.flags & F_NEED_BIG) {
-            katz_status s = big_select(h);
-            if (s != KATZ_OK) return s;
-            h->launches += 16;  // 12 histogram passes, filter, select, count, finalize
-            h->big_paths += 1;
-            if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
-                return cuda_fail(h, e, "copy ctrl");
-            if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "big select");
-            if (h->h_ctrl->stop) return KATZ_OK;
-            continue;
-        }
-        if (hc.stop) return KATZ_OK;
+        if (h->h_ctrl->stop) return KATZ_OK;
     }
 }
 
@@ -587,6 +517,7 @@ void katz_default_opts(katz_opts* o) {
     o->inbound = 0;
     o->profile = 0;
     o->fp32_from = 0;
+    o->offsets64 = 0;
 }
 
 const char* katz_status_string(katz_status s) {
@@ -612,11 +543,6 @@ void katz_destroy(katz_h h) {
     dfree(h, h->g.chunk_first);
     dfree(h, h->g.chunk_part);
     dfree(h, h->d_deghist);
-    dfree(h, h->d_big_l);
-    dfree(h, h->d_big_u);
-    dfree(h, h->d_big_id);
-    dfree(h, h->d_hist256);
-    dfree(h, h->d_count);
     dfree(h, h->d_scratch);
     dfree(h, h->rank_ids);
     for (int q = 0; q < 2; ++q) {
@@ -640,7 +566,8 @@ void katz_destroy(katz_h h) {
         dfree(h, h->deg_tmp);
         dfree(h, h->scan_sums);
         if (h->stream_a) cudaStreamSynchronize(h->stream_a);
-        for (void* ptr : {(void*)h->rowptr_spare, (void*)h->chunk_first_spare, (void*)h->chunk_row_spare,
+        for (void* ptr : {(void*)h->rowptr_spare, (void*)h->rp64_next, (void*)h->rp64_spare_next,
+                          (void*)h->chunk_first_spare, (void*)h->chunk_row_spare,
                           (void*)h->bsrc[0], (void*)h->bsrc[1], (void*)h->bdst[0], (void*)h->bdst[1],
                           (void*)h->bins[0], (void*)h->bins[1], (void*)h->t_cnt, (void*)h->t_sums})
             dfree(h, ptr);
@@ -698,7 +625,7 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     DeviceGraph& g = h->g;
     g.n = n;
     g.nnz = nnz;
-    g.off64 = (n + nnz) >= 0x7fffffffLL;
+    g.off64 = (n + nnz) >= 0x7fffffffLL || h->opts.offsets64 != 0;
     // Input: the row offsets are copied first and validated, and the
     // degree-class relabelling (which needs only them) runs while the column
     // array follows on a second stream in slices of rows; each slice is
@@ -922,7 +849,6 @@ static katz_status rank_static_once(katz_h h, double alpha, int64_t k, double ep
     h->b.use_cond = 0;
     h->ranked = false;
     h->launches = h->classes_exact ? 3 : 4;  // init_walk, cert_init, theta_0 (one or two kernels)
-    h->big_paths = 0;
     cudaError_t e;
     if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
     if ((e = cudaMemsetAsync(h->b.ctrl, 0, sizeof(Ctrl), h->stream)) != cudaSuccess) return cuda_fail(h, e, "memset ctrl");
@@ -973,9 +899,7 @@ static katz_status rank_static_once(katz_h h, double alpha, int64_t k, double ep
     h->trace.assign(tr.begin() + 1, tr.begin() + 1 + std::max(0, h->r));
     if (h->opts.use_graph && !h->opts.profile)
         // loop bodies that did work: all finalize runs but the first iteration's
-        // and the big-select reruns
-        h->launches += (h->g.layout.row_warp > 0 ? 5 : 4) *
-                       std::max<int64_t>(0, (int64_t)hc.body_runs - 1 - h->big_paths);
+        h->launches += (h->g.layout.row_warp > 0 ? 5 : 4) * std::max<int64_t>(0, (int64_t)hc.body_runs - 1);
     double spmv_ms = 0.0;
     if (h->opts.profile) {  // levels 2..r: level 1 reads no walk values
         for (int q = 1; q < h->r && 2 * q + 1 < (int)h->sp_ev.size(); ++q) {
@@ -1277,10 +1201,21 @@ katz_status update_prepare(katz_handle* h, const int32_t* src, const int32_t* ds
         return cuda_done(e, "rebuild size");
     const unsigned long long dmax[3] = {cert ? hdmax[0] : 0ull, cert ? hdmax[1] : 0ull, cert ? hdmax[2] : 0ull};
     const int64_t nnz_new = *hnnz;
-    if (!g.off64 && n + nnz_new >= 0x7fffffffLL) {
-        dyn_clear(g, d, m, sa);
-        cudaStreamSynchronize(sa);
-        return done(KATZ_EINVAL, "the graph would outgrow 32-bit offsets; create it with more headroom");
+    // the updated graph outgrows 32-bit offsets: its offsets go to a new
+    // int64 array, and a second one becomes the spare of later batches; the
+    // swap installs both and releases the two int32 arrays
+    const bool promote = !g.off64 && n + nnz_new >= 0x7fffffffLL;
+    if (promote && !h->rp64_next) {
+        if ((e = dmalloc_on(h, &h->rp64_next, (size_t)n + 1, sa)) != cudaSuccess ||
+            (e = dmalloc_on(h, &h->rp64_spare_next, (size_t)n + 1, sa)) != cudaSuccess) {
+            dfree_on(h->rp64_next, sa);
+            dfree_on(h->rp64_spare_next, sa);
+            h->rp64_next = nullptr;
+            h->rp64_spare_next = nullptr;
+            dyn_clear(g, d, m, sa);
+            cudaStreamSynchronize(sa);
+            return cuda_done(e, "cudaMalloc int64 rowptr");
+        }
     }
     if (nnz_new > h->col_spare_cap) {
         dfree_on(h->col_spare, sa);
@@ -1309,7 +1244,8 @@ katz_status update_prepare(katz_handle* h, const int32_t* src, const int32_t* ds
         d.hub_keep = h->dyn.hub_keep;
         d.hub_keep_cap = cap;
     }
-    if ((e = dyn_rebuild(g, d, m, h->rp_new, h->col_spare, h->rowptr_spare, sa)) != cudaSuccess)
+    if ((e = dyn_rebuild(g, d, m, h->rp_new, h->col_spare, promote ? (void*)h->rp64_next : h->rowptr_spare, promote,
+                         sa)) != cudaSuccess)
         return cuda_done(e, "rebuild rows");
     pd.launches += (g.n > g.layout.row_warp ? 2 : 0) + (g.layout.chunks > 0 ? 1 : 0) + (hubs ? 3 : 0) + 1;
     if ((e = dyn_clear(g, d, m, sa)) != cudaSuccess) return cuda_done(e, "clear batch");
@@ -1355,6 +1291,7 @@ katz_status update_prepare(katz_handle* h, const int32_t* src, const int32_t* ds
     pd.nnz = nnz_new;
     pd.chunks = chunks;
     pd.applied = true;
+    pd.promote = promote;
     return done(KATZ_OK, nullptr);
 }
 
@@ -1367,7 +1304,6 @@ katz_status update_swap(katz_handle* h) {
     const int64_t n = g.n;
     h->err.clear();
     h->launches = pd.launches;
-    h->big_paths = 0;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_prepared, 0)) != cudaSuccess) return cuda_fail(h, e, "event");
     if ((e = cudaEventRecord(h->ev0, h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
     h->rep = pd;  // the next prepare may overwrite pend once this returns
@@ -1378,7 +1314,17 @@ katz_status update_swap(katz_handle* h) {
     {
         std::swap(g.col, h->col_spare);
         std::swap(h->col_cap, h->col_spare_cap);
-        std::swap(g.rowptr, h->rowptr_spare);
+        if (pd.promote) {  // int32 -> int64 offsets; the old arrays are released after the work queued on them
+            dfree(h, g.rowptr);
+            dfree(h, h->rowptr_spare);
+            g.rowptr = h->rp64_next;
+            h->rowptr_spare = h->rp64_spare_next;
+            h->rp64_next = nullptr;
+            h->rp64_spare_next = nullptr;
+            g.off64 = true;
+        } else {
+            std::swap(g.rowptr, h->rowptr_spare);
+        }
         std::swap(g.chunk_first, h->chunk_first_spare);
         std::swap(g.chunk_row, h->chunk_row_spare);
         std::swap(h->chunk_row_cap, h->chunk_row_spare_cap);
@@ -1520,13 +1466,6 @@ katz_status update_repair(katz_handle* h, katz_info* info) {
         (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "re-check sync");
     katz_status st = KATZ_OK;
-    if (h->h_ctrl->flags & F_NEED_BIG) {
-        st = big_select(h);
-        if (st != KATZ_OK) return st;
-        if ((e = cudaMemcpyAsync(h->h_ctrl, h->b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-            return cuda_fail(h, e, "re-check sync");
-    }
     if (!h->h_ctrl->stop) {
         st = run_loop(h, 0);
         if (st != KATZ_OK) return st;

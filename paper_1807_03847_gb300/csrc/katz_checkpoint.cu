@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -20,7 +21,7 @@ using namespace katz;
 namespace {
 
 constexpr uint64_t CKPT_MAGIC = 0x31504b435a54414bull;  // "KATZCKP1"
-constexpr uint32_t CKPT_VERSION = 2;
+constexpr uint32_t CKPT_VERSION = 3;
 
 struct CkptHeader {
     uint64_t magic;
@@ -84,6 +85,62 @@ void walk_arrays(Image& im, katz_handle* h, const CkptHeader& hd) {
     im.dev(b.topk_u, (uint64_t)KATZ_MAX_K * 8);
     im.dev(b.trace, ((uint64_t)hd.opts.r_max + 2) * 8);
     if (hd.has_rank_ids) im.dev(h->rank_ids, n * 4);
+}
+
+// Consistency of the restored device arrays that the kernels index with
+// (the CSR itself is checked by launch_validate_csr):
+//   bad[0] perm / inv not inverse permutations of [0, n)
+//   bad[1] chunk table inconsistent (chunk_first monotone from 0 to `chunks`,
+//          every chunk inside the range of its row)
+//   bad[2] a top-k or ranking id outside [0, n)
+__global__ void image_check_kernel(const int32_t* __restrict__ perm, const int32_t* __restrict__ inv, int64_t n,
+                                   const int64_t* __restrict__ chunk_first, const int32_t* __restrict__ chunk_row,
+                                   int64_t row_warp, int64_t chunks, const int32_t* __restrict__ topk_id,
+                                   int64_t k_eff, const int32_t* __restrict__ rank_ids, unsigned long long* bad) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long b0 = 0, b1 = 0, b2 = 0;
+    for (int64_t i = tid; i < n; i += stride) {
+        const int32_t v = perm[i];
+        if (v < 0 || (int64_t)v >= n || (int64_t)inv[v] != i) ++b0;
+        if (rank_ids) {
+            const int32_t w = rank_ids[i];
+            if (w < 0 || (int64_t)w >= n) ++b2;
+        }
+    }
+    for (int64_t u = tid; u < row_warp; u += stride)
+        if (chunk_first[u + 1] < chunk_first[u]) ++b1;
+    if (tid == 0 && (chunk_first[0] != 0 || chunk_first[row_warp] != chunks)) ++b1;
+    for (int64_t q = tid; q < chunks; q += stride) {
+        const int32_t u = chunk_row[q];
+        if (u < 0 || (int64_t)u >= row_warp || chunk_first[u] > q || chunk_first[u + 1] <= q) ++b1;
+    }
+    for (int64_t q = tid; q < k_eff; q += stride)
+        if (topk_id[q] < 0 || (int64_t)topk_id[q] >= n) ++b2;
+    if (b0) atomicAdd(&bad[0], b0);
+    if (b1) atomicAdd(&bad[1], b1);
+    if (b2) atomicAdd(&bad[2], b2);
+}
+
+// The header fields a restored handle relies on, checked before any device
+// work: sizes, row-mode boundaries, the iteration state against the buffers.
+bool header_consistent(const CkptHeader& hd) {
+    const int64_t n = hd.n;
+    const bool f32_ok = hd.f32_from >= 2;  // INT32_MAX: no FP32 level
+    return hd.magic == CKPT_MAGIC && hd.version == CKPT_VERSION &&
+           hd.sizes == ((uint32_t)sizeof(Ctrl) | (uint32_t)sizeof(IterParams) << 16) && n >= 1 &&
+           n < 0x7fffffffLL && hd.nnz >= 0 && hd.ranked && hd.opts.r_max >= 1 && hd.opts.r_max <= (1 << 20) &&
+           hd.walk_slots >= 2 && hd.stride >= n + 1 && hd.row_warp >= 0 && hd.row_warp <= hd.row_octet &&
+           hd.row_octet <= hd.row_thread && hd.row_thread <= n && hd.chunks >= 0 && hd.trace_len >= 0 &&
+           hd.trace_len <= hd.opts.r_max + 2 && hd.r >= 0 && hd.r <= hd.opts.r_max && hd.k_eff >= 1 &&
+           hd.k_eff <= n && f32_ok && hd.sum_depth >= 1 && hd.deg_max >= 0 &&
+           hd.D >= hd.deg_max && hd.alpha > 0.0 && hd.alpha * (double)hd.D < 1.0 && hd.criterion >= KATZ_CRIT_TOPK &&
+           hd.criterion <= KATZ_CRIT_PAIR && (hd.off64 == 0 || hd.off64 == 1) && (hd.fp32 == 0 || hd.fp32 == 1) &&
+           (hd.off64 || n + hd.nnz < 0x7fffffffLL) && hd.ctrl.r == hd.r && hd.ctrl.k_eff >= 0 &&
+           hd.ctrl.k_eff <= std::min<int64_t>(n, KATZ_MAX_K) &&
+           (hd.ctrl.list_cur == 0 || hd.ctrl.list_cur == 1) && hd.ctrl.f32_from == hd.f32_from &&
+           hd.p.n == n && hd.p.stride == hd.stride && hd.p.slots == hd.walk_slots &&
+           hd.p.r_max == hd.opts.r_max;
 }
 
 void fill_header(katz_handle* h, CkptHeader& hd) {
@@ -164,11 +221,7 @@ katz_status katz_restore(katz_h* out, const void* buf, uint64_t bytes, const kat
     CkptHeader hd;
     if (bytes < sizeof(hd)) return KATZ_EINVAL;
     std::memcpy(&hd, buf, sizeof(hd));
-    if (hd.magic != CKPT_MAGIC || hd.version != CKPT_VERSION ||
-        hd.sizes != ((uint32_t)sizeof(Ctrl) | (uint32_t)sizeof(IterParams) << 16) || hd.n < 1 || hd.nnz < 0 ||
-        hd.walk_slots < 2 || hd.stride < hd.n + 1 || hd.row_warp < 0 || hd.row_warp > hd.n || hd.chunks < 0 ||
-        hd.trace_len < 0 || hd.trace_len > hd.opts.r_max + 2 || !hd.ranked)
-        return KATZ_EINVAL;
+    if (!header_consistent(hd)) return KATZ_EINVAL;
     katz_handle* h = new katz_handle();
     h->opts = hd.opts;
     h->opts.cuda_stream = opts ? opts->cuda_stream : nullptr;
@@ -233,6 +286,48 @@ katz_status katz_restore(katz_h* out, const void* buf, uint64_t bytes, const kat
     if (!im.ok || im.pos != bytes || cudaStreamSynchronize(h->stream) != cudaSuccess) {
         katz_destroy(h);
         return KATZ_EINVAL;
+    }
+    // the image's arrays are checked as create checks its input: a CSR with
+    // offsets and columns in range, degrees within D, consistent relabelling
+    // and chunk table, ids in range; anything else is refused before any
+    // kernel gathers through them
+    {
+        unsigned long long* d_bad = nullptr;
+        int64_t* d_degmax = nullptr;
+        struct Checks {
+            unsigned long long csr[3];
+            unsigned long long img[3];
+            int64_t degmax;
+        };
+        static_assert(sizeof(Checks) <= H_SMALL, "pinned scratch");
+        Checks& hc = *(Checks*)h->h_small;
+        const int64_t span = std::max<int64_t>(std::max<int64_t>(hd.n, hd.nnz), hd.chunks);
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((span + 255) / 256, 152 * 8));
+        if ((e = dmalloc(h, &d_bad, 6)) == cudaSuccess && (e = dmalloc(h, &d_degmax, 1)) == cudaSuccess &&
+            (e = cudaMemsetAsync(d_bad, 0, 6 * sizeof(unsigned long long), h->stream)) == cudaSuccess &&
+            (e = cudaMemsetAsync(d_degmax, 0, sizeof(int64_t), h->stream)) == cudaSuccess &&
+            (e = launch_validate_csr(g, d_bad, d_degmax, h->stream)) == cudaSuccess) {
+            image_check_kernel<<<blocks, 256, 0, h->stream>>>(g.perm, g.inv, g.n, g.chunk_first, g.chunk_row,
+                                                              hd.row_warp, hd.chunks, b.topk_id, hd.ctrl.k_eff,
+                                                              hd.has_rank_ids ? h->rank_ids : nullptr, d_bad + 3);
+            e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hc.csr, d_bad, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&hc.degmax, d_degmax, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        }
+        dfree(h, d_bad);
+        dfree(h, d_degmax);
+        if (e != cudaSuccess) {
+            st = cuda_fail(h, e, "check image");
+            katz_destroy(h);
+            return st;
+        }
+        if (hc.csr[0] || hc.csr[1] || hc.img[0] || hc.img[1] || hc.img[2] || hc.degmax > hd.D) {
+            katz_destroy(h);
+            return KATZ_EINVAL;
+        }
     }
     h->p = hd.p;
     h->k_eff = hd.k_eff;

@@ -27,7 +27,6 @@ constexpr int CHUNK_ARCS = 2048;  // arcs per warp for rows of degree > 2048
 constexpr int SELECT_CAP = KATZ_MAX_K;
 constexpr int SELECT_THREADS = 1024;
 
-enum : int32_t { F_NEED_BIG = 1 };
 enum : int32_t { DYN_E_INVAL = 1, DYN_E_ALPHA = 2 };  // batch validation failures
 
 // Iteration state kept on the device so that a captured graph can loop
@@ -36,7 +35,7 @@ struct Ctrl {
     int32_t r;           // iterations completed
     int32_t converged;   // result of the last converged() evaluation
     int32_t stop;        // 1: leave the loop
-    int32_t flags;       // F_NEED_BIG: candidate set too large for the one-CTA select
+    int32_t flags;       // reserved (0)
     unsigned long long n_cand;     // |{v in M : l_r(v) >= theta_{r-1}}|
     unsigned long long cnt_cross;  // active nodes outside the top-k with u_r - eps >= theta_r
     unsigned long long n_active;   // |M| after deactivation
@@ -246,8 +245,7 @@ cudaError_t dyn_clear(const DeviceGraph& g, const DynBuffers& d, int64_t m, cuda
 cudaError_t dyn_prepare(const DeviceGraph& g, const DynBuffers& d, int64_t m, int64_t* rowptr_new, int64_t* deg,
                         int64_t* sums, cudaStream_t st);
 cudaError_t dyn_rebuild(const DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new,
-                        int32_t* col_new, void* rowptr_out,
-                        cudaStream_t st);
+                        int32_t* col_new, void* rowptr_out, bool out64, cudaStream_t st);
 cudaError_t dyn_seed(const DeviceGraph& g, const DynBuffers& d, int64_t m, cudaStream_t st);
 cudaError_t dyn_expand(const DeviceGraph& g, const DynBuffers& d, int64_t lo, int64_t hi, int level,
                        cudaStream_t st);
@@ -336,10 +334,6 @@ int sum_depth_of(int64_t deg_thread, int64_t deg_octet, int64_t deg_warp, bool h
 cudaError_t launch_walk_out(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int level, bool fp32,
                             double* out, cudaStream_t st);
 // radix select over candidates (large candidate sets): one pass of 8-bit digits
-cudaError_t launch_radix_hist(const IterBuffers& b, int pass, unsigned long long key_hi, unsigned int key_lo,
-                              unsigned long long* d_hist, cudaStream_t st);
-cudaError_t launch_radix_filter(const IterBuffers& b, unsigned long long key_hi, unsigned int key_lo,
-                                double* out_l, double* out_u, int32_t* out_id, unsigned long long* d_count,
-                                cudaStream_t st);
+
 
 }  // namespace katz

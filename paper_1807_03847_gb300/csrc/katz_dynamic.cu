@@ -812,14 +812,15 @@ static void rebuild_launch(const DeviceGraph& g, const DynBuffers& d, int64_t m,
 }
 
 // rows into col_new (read through the old layout and chunk table), and the
-// new offsets, in the offset type of g, into rowptr_out (g itself unchanged)
+// new offsets into rowptr_out: int64 when g has int64 offsets or out64 is set
+// (a batch that outgrows int32 offsets), else int32 (g itself unchanged)
 cudaError_t dyn_rebuild(const DeviceGraph& g, const DynBuffers& d, int64_t m, const int64_t* rowptr_new,
-                        int32_t* col_new, void* rowptr_out, cudaStream_t st) {
+                        int32_t* col_new, void* rowptr_out, bool out64, cudaStream_t st) {
     if (g.off64)
         rebuild_launch<int64_t>(g, d, m, rowptr_new, col_new, st);
     else
         rebuild_launch<int32_t>(g, d, m, rowptr_new, col_new, st);
-    if (g.off64)
+    if (g.off64 || out64)
         narrow_kernel<int64_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int64_t*)rowptr_out, g.n + 1);
     else
         narrow_kernel<int32_t><<<grid_for(g.n + 1, 256), 256, 0, st>>>(rowptr_new, (int32_t*)rowptr_out, g.n + 1);

@@ -32,11 +32,6 @@ struct katz_handle {
     int64_t stride = 0;
     // scratch
     uint32_t* d_deghist = nullptr;
-    double* d_big_l = nullptr;
-    double* d_big_u = nullptr;
-    int32_t* d_big_id = nullptr;
-    unsigned long long* d_hist256 = nullptr;
-    unsigned long long* d_count = nullptr;
     double* d_scratch = nullptr;
     katz::Ctrl* h_ctrl = nullptr;  // pinned (one block with h_small)
     unsigned char* h_small = nullptr;  // pinned scratch of H_SMALL bytes for small device-to-host reads
@@ -44,7 +39,6 @@ struct katz_handle {
     // profiling: one event pair per SpMV launch
     std::vector<cudaEvent_t> sp_ev;
     int64_t launches = 0;   // kernels launched by the current call (host-counted part)
-    int64_t big_paths = 0;  // iterations whose select fell back to the radix path
     // CUDA graph of one iteration inside a device-side while loop
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -66,6 +60,10 @@ struct katz_handle {
     cudaEvent_t ev_prepared = nullptr;   // stream_a: the prepared graph is complete
     cudaEvent_t ev_committed = nullptr;  // stream: work on the previous graph is queued before this
     void* rowptr_spare = nullptr;        // [n+1], the offset type of g.rowptr
+    // a batch that takes n + nnz past the int32 offset range: the new int64
+    // offsets and the int64 spare that replace the two int32 arrays at its swap
+    int64_t* rp64_next = nullptr;
+    int64_t* rp64_spare_next = nullptr;
     int64_t* chunk_first_spare = nullptr;  // [row_warp+1]
     int32_t* chunk_row_spare = nullptr;
     int64_t chunk_row_cap = 0, chunk_row_spare_cap = 0, chunk_part_cap = 0;  // in chunks
@@ -84,6 +82,7 @@ struct katz_handle {
         int bset = 0;
         int depth = 0;          // FP32-certified: summation depth the updated rows need (0: not computed)
         bool applied = false;   // the batch changed the graph (m > 0 and valid)
+        bool promote = false;   // the updated graph needs int64 row offsets (rp64_next)
     } pend;                     // written by the prepare
     Pending rep;                // the swapped-in batch, read by its repair
     int64_t* rrowptr = nullptr; // [n+1] directed: transposed CSR of the current graph (the repair's)

@@ -307,6 +307,98 @@ __device__ void sort_and_emit(SelEntry* sel, unsigned int cnt, int kk, const dou
     }
 }
 
+// The candidate order as one 96-bit key: the bits of l (monotone for
+// l >= 0), then the complemented id, so that descending keys are
+// (l desc, id asc).
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 cand_key(double l, int32_t id) {
+    return ((u128)(unsigned long long)__double_as_longlong(l) << 32) | (u128)(0xffffffffu ^ (uint32_t)id);
+}
+
+// The min(k, |C|) largest keys of C = {candidates with l >= tau} gathered
+// into sel, for a C larger than the shared-memory sort holds: a radix select
+// of the k-th key inside this CTA (8-bit digits, most significant first,
+// with a 256-bin shared histogram per digit; the select ends at the first
+// digit whose bucket holds exactly the keys still missing), then one pass
+// that gathers every key at or above it.  Returns the number gathered.
+__device__ unsigned int select_large(const double* __restrict__ cl, const int32_t* __restrict__ cid,
+                                     unsigned long long nc, double tau, long long k, SelEntry* sel) {
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned long long s_pre_hi, s_krem;  // selected digits: key bits 95..32 ...
+    __shared__ unsigned int s_pre_lo, s_cnt;         // ... and 31..0
+    __shared__ int s_done;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        s_pre_hi = 0ull;
+        s_pre_lo = 0u;
+        s_krem = 0ull;
+        s_done = 0;
+        s_cnt = 0u;
+    }
+    for (int pass = 0; pass < 12; ++pass) {
+        for (int q = tid; q < 256; q += SELECT_THREADS) hist[q] = 0u;
+        __syncthreads();
+        const int shift = 88 - 8 * pass;
+        const u128 prefix = ((u128)s_pre_hi << 32) | s_pre_lo;
+        for (unsigned long long q = tid; q < nc; q += SELECT_THREADS) {
+            const double l = cl[q];
+            if (!(l >= tau)) continue;
+            const u128 key = cand_key(l, cid[q]);
+            if (pass == 0 || (key >> (shift + 8)) == (prefix >> (shift + 8)))
+                atomicAdd(&hist[(unsigned)(key >> shift) & 0xffu], 1u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long krem = s_krem;
+            if (pass == 0) {
+                unsigned long long total = 0;
+                for (int b = 0; b < 256; ++b) total += hist[b];
+                krem = min((unsigned long long)k, total);
+            }
+            if (krem == 0) {
+                s_done = 2;  // no candidate
+            } else {
+                unsigned long long cum = 0;
+                int bsel = 0;
+                for (int b = 255; b >= 0; --b) {
+                    if (cum + hist[b] >= krem) {
+                        bsel = b;
+                        break;
+                    }
+                    cum += hist[b];
+                }
+                const u128 pre = prefix | ((u128)bsel << shift);
+                s_pre_hi = (unsigned long long)(pre >> 32);
+                s_pre_lo = (unsigned int)pre;
+                krem -= cum;
+                if (hist[bsel] == krem) s_done = 1;  // the whole bucket is in: threshold = prefix, lower bits 0
+                s_krem = krem;
+            }
+        }
+        __syncthreads();
+        if (s_done) break;
+    }
+    if (s_done == 2) return 0u;
+    const u128 th = ((u128)s_pre_hi << 32) | s_pre_lo;
+    for (unsigned long long base = 0; base < nc; base += SELECT_THREADS) {
+        const unsigned long long q = base + tid;
+        const double l = q < nc ? cl[q] : -1.0;
+        const bool take = q < nc && l >= tau && cand_key(l, cid[q]) >= th;
+        const unsigned m = __ballot_sync(FULL, take);
+        unsigned int wpos = 0;
+        if (lane == 0 && m) wpos = atomicAdd(&s_cnt, (unsigned int)__popc(m));
+        wpos = __shfl_sync(FULL, wpos, 0);
+        if (take) {
+            const unsigned int pos = wpos + __popc(m & ((1u << lane) - 1u));
+            if (pos < (unsigned int)SELECT_CAP)
+                sel[pos] = SelEntry{(unsigned long long)__double_as_longlong(l), cid[q], (int32_t)q};
+        }
+    }
+    __syncthreads();
+    return min(s_cnt, (unsigned int)SELECT_CAP);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SELECT_THREADS)
 select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, const int32_t* __restrict__ cid,
@@ -356,33 +448,31 @@ select_kernel(const double* __restrict__ cl, const double* __restrict__ cu, cons
         }
         __syncthreads();
     }
-    if (s_big) {
-        if (tid == 0) atomicOr(&ctrl->flags, F_NEED_BIG);
-        return;
-    }
     const double tau = s_tau;
-    // the candidates with l >= tau, one shared-memory atomic per warp
-    const int lane = tid & 31;
-    for (unsigned long long base = 0; base < nc; base += SELECT_THREADS) {
-        const unsigned long long q = base + tid;
-        const double l = q < nc ? cl[q] : -1.0;
-        const bool take = q < nc && l >= tau;
-        const unsigned m = __ballot_sync(FULL, take);
-        unsigned int wpos = 0;
-        if (lane == 0 && m) wpos = atomicAdd(&s_cnt, (unsigned int)__popc(m));
-        wpos = __shfl_sync(FULL, wpos, 0);
-        if (take) {
-            const unsigned int pos = wpos + __popc(m & ((1u << lane) - 1u));
-            if (pos < (unsigned int)SELECT_CAP)
-                sel[pos] = SelEntry{(unsigned long long)__double_as_longlong(l), cid[q], (int32_t)q};
+    unsigned int cnt = 0;
+    if (!s_big) {
+        // the candidates with l >= tau, one shared-memory atomic per warp
+        const int lane = tid & 31;
+        for (unsigned long long base = 0; base < nc; base += SELECT_THREADS) {
+            const unsigned long long q = base + tid;
+            const double l = q < nc ? cl[q] : -1.0;
+            const bool take = q < nc && l >= tau;
+            const unsigned m = __ballot_sync(FULL, take);
+            unsigned int wpos = 0;
+            if (lane == 0 && m) wpos = atomicAdd(&s_cnt, (unsigned int)__popc(m));
+            wpos = __shfl_sync(FULL, wpos, 0);
+            if (take) {
+                const unsigned int pos = wpos + __popc(m & ((1u << lane) - 1u));
+                if (pos < (unsigned int)SELECT_CAP)
+                    sel[pos] = SelEntry{(unsigned long long)__double_as_longlong(l), cid[q], (int32_t)q};
+            }
         }
+        __syncthreads();
+        cnt = s_cnt;
     }
-    __syncthreads();
-    const unsigned int cnt = s_cnt;
-    if (cnt > (unsigned int)SELECT_CAP) {
-        if (tid == 0) atomicOr(&ctrl->flags, F_NEED_BIG);
-        return;
-    }
+    // more candidates than the sort holds: select the top k of them first,
+    // here on the device (the loop never waits for the host)
+    if (s_big || cnt > (unsigned int)SELECT_CAP) cnt = select_large(cl, cid, nc, tau, (long long)p.k, sel);
     const int kk = (int)min((long long)p.k, (long long)cnt);
     if (cnt <= (unsigned int)SELECT_THREADS) sort_and_emit<1>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
     else if (cnt <= 2u * SELECT_THREADS) sort_and_emit<2>(sel, cnt, kk, cu, topk_id, topk_l, topk_u, ctrl);
@@ -415,7 +505,7 @@ count_kernel(const T* walk, const double* __restrict__ c, const double* __restri
              uint8_t* active, int32_t* alist0, int32_t* alist1, Ctrl* ctrl, IterParams p) {
     __shared__ int s_wcnt[COUNT_THREADS / 32];
     __shared__ unsigned long long s_base;
-    if (ctrl->stop || (ctrl->flags & F_NEED_BIG)) return;
+    if (ctrl->stop) return;
     const int r_cur = ctrl->r + 1;
     const int f32_from = ctrl->f32_from;
     const BState bs = bstate(ctrl, p);
@@ -662,13 +752,6 @@ __global__ void finalize_kernel(const double* __restrict__ topk_l, const double*
         return;
     }
     if (tid == 0) ctrl->body_runs += 1;
-    if (ctrl->flags & F_NEED_BIG) {
-        if (tid == 0) {
-            ctrl->stop = 1;
-            if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0);
-        }
-        return;
-    }
     const int kk = ctrl->k_eff;
     const bool none_cross = ctrl->cnt_cross == 0;
     if (none_cross) {
@@ -746,9 +829,14 @@ __global__ void bounds_out_kernel(const T* walk, const double* __restrict__ c, c
             l = fmax(l, lb[w]);
             u = fmin(u, ub[w]);
         }
-        if (err) {  // widening added for rounding (zero in FP64 mode)
+        if (err) {
+            // the width of the rounding interval around each bound (zero in
+            // FP64 mode): the exact partial sum lies in [c lo, c hi] and the
+            // exact level value in [s los, s his], so l and u each lie within
+            // this of the bound of Theorem 1 evaluated exactly at r (alpha
+            // gamma >= alpha, so the upper tail's term covers the lower's)
             err[v] = p.cert ? c[w] * (bs.hi64 - bs.lo64) + c32v * (bs.hi32 - bs.lo32) +
-                                  p.ag_hi * sv * (ctrl->his - 1.0) + p.alpha * sv * (1.0 - ctrl->los)
+                                  p.ag_hi * sv * (ctrl->his - ctrl->los)
                             : 0.0;
         }
         if (lower) lower[v] = l;
@@ -765,54 +853,6 @@ __global__ void walk_out_kernel(const T* walk, const int32_t* __restrict__ inv, 
         out[v] = walk_value(walk, p, f32_from, level, inv[v]);
 }
 
-// ---------------------------------------------------------------------------
-// radix select over a large candidate set (composite key: l bits, then
-// bitwise-complemented id, 96 bits, most significant digit first)
-// ---------------------------------------------------------------------------
-typedef unsigned __int128 u128;
-
-__device__ __forceinline__ u128 cand_key(double l, int32_t id) {
-    return ((u128)(unsigned long long)__double_as_longlong(l) << 32) | (u128)(0xffffffffu ^ (uint32_t)id);
-}
-
-__global__ void radix_hist_kernel(const double* __restrict__ cl, const int32_t* __restrict__ cid,
-                                  const Ctrl* ctrl, int pass, unsigned long long phi, unsigned int plo,
-                                  unsigned long long* hist) {
-    __shared__ unsigned int h[256];
-    for (int q = threadIdx.x; q < 256; q += blockDim.x) h[q] = 0;
-    __syncthreads();
-    const unsigned long long nc = ctrl->n_cand;
-    const int shift = 88 - 8 * pass;
-    const u128 prefix = ((u128)phi << 32) | plo;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)nc; q += stride) {
-        const u128 key = cand_key(cl[q], cid[q]);
-        if (pass == 0 || (key >> (shift + 8)) == (prefix >> (shift + 8)))
-            atomicAdd(&h[(unsigned)(key >> shift) & 0xffu], 1u);
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < 256; q += blockDim.x)
-        if (h[q]) atomicAdd(&hist[q], (unsigned long long)h[q]);
-}
-
-__global__ void radix_filter_kernel(const double* __restrict__ cl, const double* __restrict__ cu,
-                                    const int32_t* __restrict__ cid, Ctrl* ctrl, unsigned long long phi,
-                                    unsigned int plo, double* out_l, double* out_u, int32_t* out_id,
-                                    unsigned long long* count) {
-    const unsigned long long nc = ctrl->n_cand;
-    const u128 th = ((u128)phi << 32) | plo;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)nc; q += stride) {
-        if (cand_key(cl[q], cid[q]) >= th) {
-            const unsigned long long pos = atomicAdd(count, 1ULL);
-            if (pos < (unsigned long long)SELECT_CAP) {
-                out_l[pos] = cl[q];
-                out_u[pos] = cu[q];
-                out_id[pos] = cid[q];
-            }
-        }
-    }
-}
 
 __global__ void narrow_kernel(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t count) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -931,18 +971,5 @@ cudaError_t launch_walk_out(const DeviceGraph& g, const IterBuffers& b, const It
     return cudaGetLastError();
 }
 
-cudaError_t launch_radix_hist(const IterBuffers& b, int pass, unsigned long long key_hi, unsigned int key_lo,
-                              unsigned long long* d_hist, cudaStream_t st) {
-    radix_hist_kernel<<<152 * 4, 256, 0, st>>>(b.cand_l, b.cand_id, b.ctrl, pass, key_hi, key_lo, d_hist);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_radix_filter(const IterBuffers& b, unsigned long long key_hi, unsigned int key_lo,
-                                double* out_l, double* out_u, int32_t* out_id, unsigned long long* d_count,
-                                cudaStream_t st) {
-    radix_filter_kernel<<<152 * 4, 256, 0, st>>>(b.cand_l, b.cand_u, b.cand_id, b.ctrl, key_hi, key_lo, out_l,
-                                                 out_u, out_id, d_count);
-    return cudaGetLastError();
-}
 
 }  // namespace katz

@@ -55,6 +55,7 @@ __device__ __align__(256) NoAllocScratch g_noalloc;
 
 std::mutex g_addr_mu;
 NoAllocScratch* g_addr[NA_MAX_DEVICES] = {};
+int g_sms[NA_MAX_DEVICES] = {};  // multiprocessors of each device (grid size of the O(n) passes)
 
 typedef unsigned __int128 u128;
 
@@ -234,20 +235,26 @@ __global__ void na_finish(NoAllocScratch* S, int32_t* certified_out) {
     *certified_out = (S->cross == 0 && !S->pairs_bad) ? 1 : 0;
 }
 
-// Address of the scratch array on the current device, resolved once per device.
-katz_status scratch_on_current_device(NoAllocScratch** out) {
+// Address of the scratch array on the current device and the device's
+// multiprocessor count, resolved once per device.
+katz_status scratch_on_current_device(NoAllocScratch** out, int* sms) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return KATZ_ECUDA;
     std::lock_guard<std::mutex> lock(g_addr_mu);
     if (!g_addr[dev]) {
         void* p = nullptr;
+        int count = 0;
         if (cudaGetSymbolAddress(&p, g_noalloc) != cudaSuccess) return KATZ_ECUDA;
+        if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || count < 1)
+            return KATZ_ECUDA;
         if (cudaFuncSetAttribute(na_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  NA_CAP * (int)sizeof(Ent)) != cudaSuccess)
             return KATZ_ECUDA;
+        g_sms[dev] = count;
         g_addr[dev] = (NoAllocScratch*)p;
     }
     *out = g_addr[dev];
+    *sms = g_sms[dev];
     return KATZ_OK;
 }
 
@@ -259,11 +266,16 @@ extern "C" katz_status katz_certify_topk_noalloc(const double* lower, const doub
     if (!lower || !upper || !ids_out || !certified_out) return KATZ_EINVAL;
     if (n < 1 || n > 0x7ffffffeLL || k < 1 || k > n || k > KATZ_MAX_K || !(eps > 0.0)) return KATZ_EINVAL;
     static_assert(sizeof(NoAllocScratch) <= 420 * 1024, "the stated size of the array");
+    // an error left by the caller's earlier work stays the caller's: it is
+    // neither cleared here nor reported as a failure of this call's launches
+    if (cudaPeekAtLastError() != cudaSuccess) return KATZ_ECUDA;
     NoAllocScratch* S = nullptr;
-    katz_status st = scratch_on_current_device(&S);
+    int sms = 0;
+    katz_status st = scratch_on_current_device(&S, &sms);
     if (st != KATZ_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const int grid = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
+    const long long cap = 8LL * sms;  // eight 256-thread blocks per multiprocessor, grid-stride beyond
+    const int grid = (int)((n + 255) / 256 < cap ? (n + 255) / 256 : cap);
     na_reset<<<64, 1024, 0, s>>>(S, (long long)k);
     for (int pass = 0; pass < 6; ++pass) {
         na_hist<<<grid, 256, 0, s>>>(S, lower, (long long)n, pass);

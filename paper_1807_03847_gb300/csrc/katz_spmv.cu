@@ -38,11 +38,14 @@
 // mode starts in FP64 and computes the levels from Ctrl::f32_from on in FP32
 // (FP32 storage, FP32 sums, FP32 multiply by alpha), adding them to the
 // separate partial sum c32.
+#include <cooperative_groups.h>
 #include <stdint.h>
 
 #include <algorithm>
 
 #include "katz_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace katz {
 
@@ -172,7 +175,11 @@ __device__ __forceinline__ void finish_row(int64_t u, Acc sum, const Epi& e, con
         e.lb[u] = l;  // read by the deactivation count of this level
         e.ub[u] = up;
         if (__double_as_longlong(l) >= __double_as_longlong(e.theta_prev)) {
-            const unsigned long long pos = atomicAdd(&e.ctrl->n_cand, 1ULL);
+            // one atomic per group of lanes that append together
+            cg::coalesced_group grp = cg::coalesced_threads();
+            unsigned long long base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(&e.ctrl->n_cand, (unsigned long long)grp.size());
+            const unsigned long long pos = grp.shfl(base, 0) + grp.thread_rank();
             if (pos < (unsigned long long)e.cand_cap) {
                 e.cand_l[pos] = l;
                 e.cand_u[pos] = up;

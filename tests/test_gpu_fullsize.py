@@ -2,10 +2,15 @@
 bench.py times (profiled host loop, two walk slots unless history is needed):
 
 - R-MAT24 (FP64 and FP32-certified) against a complete oracle run;
-- Chung-Lu n = 2^27 (int64 offsets) by checks that hold at any size: sampled
-  rows of s_r recomputed on the host from the device's own s_{r-1} (Eq. 5),
-  l <= u, and the top-k criterion re-checked on the host from the returned
-  bounds; FP32-certified against FP64 up to eps;
+- Chung-Lu n = 2^27 (int64 offsets) against a complete oracle run: the same
+  r, ranking and per-node bounds in FP64; the FP32-certified ranking up to
+  eps, each node's bounds within the reported widening of the oracle's at the
+  same r; plus checks that hold at any size (sampled rows of s_r recomputed
+  from the device's own s_{r-1}, Eq. 5; the top-k criterion re-checked on the
+  host from the returned bounds);
+- a graph just below the range of 32-bit row offsets and update batches that
+  take it past that range (the handle moves to int64 offsets) and back,
+  against the oracle session;
 - the R-MAT23 serving stream: a few batches through katz_server against the
   oracle session fed the same batches.
 """
@@ -81,23 +86,74 @@ def test_rmat24_top1000_against_the_oracle():
     h.close()
 
 
-def test_chunglu27_top100_by_properties():
+def test_chunglu27_top100_against_the_oracle():
     g = gg.workload("chunglu27")
     assert g.n + g.nnz >= 0x7fffffff  # int64 offsets
     k, eps = 100, 1e-9
     rng = np.random.default_rng(27)
+    oracle.set_threads(0)
+    s = oracle.Session(g.rowptr, g.col, True)
+    assert s.rank_static(0.0, k, eps, 256) == oracle.OK
+    ref = s.info()
+    _, l_ref, u_ref = s.bounds()
+    ranking_ref = s.ranking()
     h, info = _rank(g, k, eps)
-    assert info.converged == 1
+    assert info.converged == 1 and info.r == ref["r"] and info.alpha == ref["alpha"]
     lo, up, _ = h.bounds()
-    assert np.all(lo <= up)
     ranking = h.ranking(k)
+    assert_same_ranking(ranking, ranking_ref, l_ref)
+    assert_close(lo, l_ref, what="lower")
+    assert_close(up, u_ref, what="upper")
     _topk_certified(lo, up, ranking, eps)
     _sampled_rows_exact(g, h, info, rng)
     h.close()
     h32, info32 = _rank(g, k, eps, precision=1)
-    assert info32.converged == 1
-    assert_same_ranking(h32.ranking(k), ranking, lo, atol=eps)
+    assert info32.converged == 1 and info32.fp32_levels > 0
+    assert_same_ranking(h32.ranking(k), ranking_ref, l_ref, atol=eps)
+    lo32, up32, err = h32.bounds()
     h32.close()
+    if info32.r != ref["r"]:  # the oracle's bounds at the FP32 run's r
+        assert s.run_fixed(0.0, info32.r) == oracle.OK
+        _, l_ref, u_ref = s.bounds()
+    assert np.all(np.abs(lo32 - l_ref) <= err + 1e-12 * np.abs(l_ref) + 1e-300)
+    assert np.all(np.abs(up32 - u_ref) <= err + 1e-12 * np.abs(u_ref) + 1e-300)
+    s.close()
+
+
+def test_batches_across_the_int32_offset_limit():
+    """A graph with n + nnz 64 below 2^31 - 1 (the largest value 32-bit row
+    offsets reach): a Chung-Lu graph of 2^20 nodes padded by a band graph.
+    The first batch inserts 100 edges and takes the handle past the limit
+    (it moves to int64 offsets); the second deletes edges and inserts others
+    on the int64 handle.  After each batch: the oracle session's r, ranking
+    and bounds."""
+    base = gg.chung_lu(1 << 20, 16.0, 2.1, seed=gg.SEED_BASE + 31)
+    g = gg.padded_to(base, 0x7fffffff - 64)
+    assert g.n + g.nnz < 0x7fffffff  # created with int32 offsets
+    k, eps, r_max = 20, 1e-9, 64
+    D = g.deg_max() + 64
+    oracle.set_threads(0)
+    h, info = _rank(g, k, eps, keep_history=1, D=D)
+    s = oracle.Session(g.rowptr, g.col, True, D)
+    assert s.rank_static(0.0, k, eps, r_max) == oracle.OK
+    assert info.r == s.info()["r"]
+    ins1 = gg.update_batch(g, 100, seed=gg.SEED_BASE + 32, p_insert=1.0)
+    dels = gg.update_batch(g, 300, seed=gg.SEED_BASE + 33, p_insert=0.0)  # edges of g, kept by batch 1
+    more = gg.update_batch(g, 200, seed=gg.SEED_BASE + 34, p_insert=1.0)
+    taken = set(zip(np.minimum(ins1[0], ins1[1]).tolist(), np.maximum(ins1[0], ins1[1]).tolist()))
+    keep = np.array([(min(a, b), max(a, b)) not in taken for a, b in zip(more[0], more[1])], bool)
+    batch2 = tuple(np.concatenate([dels[q], more[q][keep]]) for q in range(3))
+    for j, batch in enumerate((ins1, batch2)):
+        inf = h.update(*batch)
+        assert s.apply_update(*batch) == oracle.OK
+        assert inf.r == s.info()["r"]
+        _, l_ref, u_ref = s.bounds()
+        assert_same_ranking(h.ranking(k), s.ranking(), l_ref)
+        lo, up, _ = h.bounds()
+        assert_close(lo, l_ref, what=f"lower after batch {j}")
+        assert_close(up, u_ref, what=f"upper after batch {j}")
+    h.close()
+    s.close()
 
 
 def test_rmat23_serving_stream_against_the_oracle_session():

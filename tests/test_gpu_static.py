@@ -97,9 +97,12 @@ def test_small_and_degenerate_graphs(graph):
     check_parity(g, 0.0, k, 1e-6)
 
 
-def test_many_ties_take_the_large_candidate_path():
-    g = gg.cycle(20000)  # every node has the same bounds: candidate set = V
-    check_parity(g, 0.0, 50, 1e-6, walks=False)
+@pytest.mark.parametrize("k,use_graph", [(50, 1), (50, 0), (3000, 1), (K.KATZ_MAX_K, 0)])
+def test_many_ties_take_the_large_candidate_path(k, use_graph):
+    # every node has the same bounds: the candidate set is V, larger than the
+    # one-CTA sort holds, and the select kernel narrows it on the device
+    g = gg.cycle(20000)
+    check_parity(g, 0.0, k, 1e-6, walks=False, use_graph=use_graph)
 
 
 def test_k_at_least_n():
