@@ -9,7 +9,16 @@ Inputs are resident in HBM when the timed region starts; L2 is flushed
 between steps.  value = GTEPS = r * nnz / time (walk-recurrence arcs
 traversed per second, summed over ranks).
 
+The default workload is the largest one: a Chung-Lu graph with 2^27
+vertices and about 2.13 G arcs (int64 row offsets), certified top-100.  The
+headline is the FP64 path (the paper's precision); the FP32-certified path is
+timed beside it on the same graph ("fp32cert", with the speedup and whether
+both certified the same ranking), and the FP32-certified bounds' per-node
+deviation from the FP64 oracle at the same r is reported against the
+rounding widening ("fp32cert_deviation_vs_oracle").
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision fp64|fp32cert] [--no-compare]
 
 N > 1 runs N independent replicas (the method needs no exchange between
 GPUs at these sizes), launched by torch.distributed.run.
@@ -58,6 +67,10 @@ WORKLOADS = {
                            "exponent 2.1 and mean 16 (about 2^30 endpoint pairs before symmetrising and "
                            "deduplicating), int64 rowptr / int32 col CSR; alpha=1/(deg_max+1); certified top-100; "
                            "eps=1e-9"),
+    "chunglu25": dict(graph="chunglu25", k=100, eps=1e-9, alpha=0.0, precision=0,
+                      desc="undirected Chung-Lu graph, n=2^25 vertices, expected degrees Pareto with exponent 2.1 "
+                           "and mean 16, int32 CSR; alpha=1/(deg_max+1); certified top-100; eps=1e-9 (profiling case "
+                           "of the n=2^27 workload: walk vector larger than L2, a few GB on the device)"),
     "er16k": dict(graph="er16k", k=100, eps=1e-9, alpha=0.0, precision=0,
                   desc="undirected Erdos-Renyi n=16384, m=131072, int32 CSR; alpha=1/(deg_max+1); certified top-100; "
                        "eps=1e-9"),
@@ -79,15 +92,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve-rmat23"], default="rmat22")
-    ap.add_argument("--precision", choices=["fp64", "fp32cert"], default=None)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve-rmat23"], default="chunglu27")
+    ap.add_argument("--precision", choices=["fp64", "fp32cert"], default=None,
+                    help="precision of the headline value (default: FP64, the paper's)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="time the headline precision only (default: the other one is timed beside it)")
     ap.add_argument("--serve-precision", choices=["fp64", "fp32cert", "both"], default="both",
                     help="walk levels of the served handle (FP32-certified: FP32 from the level the ranking picks); "
                          "both: the FP64 run in 'serving', the FP32-certified one in 'serving_fp32cert'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-iters", type=int, default=3, help="--impl reference: oracle iterations per step")
+    ap.add_argument("--cpu-iters", type=int, default=3,
+                    help="--impl reference on graphs above 2^30 arcs: oracle iterations per step")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU work of the cpu_baseline sample")
     ap.add_argument("--serve-batches", type=int, default=None,
                     help="batches of the serving stream (default: 400 beside the static line, 2000 for "
@@ -241,7 +258,9 @@ def replica_throughput(units_local, seconds_local, world):
 def cpu_baseline(g, wl, seconds):
     """The CPU oracle as it stands (Algorithm 1, OpenMP rows, sequential
     partial sort) on a bounded sample: complete certified rankings of the
-    full graph, repeated until `seconds` of CPU work have been done."""
+    full graph, repeated until `seconds` of CPU work have been done (at least
+    one).  Returns the baseline and the oracle session, which holds the last
+    ranking's bounds (the caller closes it)."""
     import oracle
 
     s = oracle.Session(g.rowptr, g.col, True)
@@ -254,9 +273,9 @@ def cpu_baseline(g, wl, seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    s.close()
     return {"value": arcs / dt / 1e9, "unit": "GTEPS", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{runs} complete certified rankings (r = {r}) of the full {wl['graph']} graph; {dt:.1f} s"}, dt
+            "sample": f"{runs} complete certified ranking(s) (r = {r}) of the full {wl['graph']} graph; "
+                      f"{dt:.1f} s"}, s
 
 
 def run_serving(batches, workers=2, slots=8, precision="fp64"):
@@ -347,29 +366,49 @@ def serve_once(g, D, batches, rate, workers, slots, torch, precision="fp64"):
     }
 
 
+# graphs above this many arcs are sampled by the reference arm: each step runs
+# the first --cpu-iters iterations of Algorithm 1 instead of a whole ranking
+REFERENCE_SAMPLE_ARCS = 1 << 30
+
+
 def run_reference(args):
-    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    """The reference arm: the CPU oracle as it stands, timed on the host cores
+    on the same workload, metric and unit.  Each step is one complete
+    certified ranking, or on graphs above 2^30 arcs a bounded sample of it
+    (the first --cpu-iters iterations: walk recurrence, bounds, converged())
+    so that the run stays within minutes."""
+    world, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import graphgen as gg
     import oracle
 
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
     g = gg.workload(wl["graph"])
+    if wl["alpha"] == "half":
+        wl["alpha"] = 0.5 / g.deg_max()
+    sampled = g.nnz > REFERENCE_SAMPLE_ARCS
+    iters = args.cpu_iters if sampled else 10000
     s = oracle.Session(g.rowptr, g.col, True)
     times, edges = [], []
     r = 0
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = s.iterations(wl["alpha"], wl["k"], wl["eps"], 10000)
+        r = s.iterations(wl["alpha"], wl["k"], wl["eps"], iters)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
             edges.append(r * g.nnz)
+    s.close()
     total = sum(times)
     value = sum(edges) / total / 1e9
-    sample = (f"each step: one complete certified ranking (r = {r} iterations of Algorithm 1) of the full "
-              f"{wl['graph']} graph (oracle, FP64, OpenMP rows + sequential partial sort)")
+    if sampled:
+        sample = (f"each step: the first {r} iterations of Algorithm 1 (walk recurrence, bounds, converged()) on "
+                  f"the full {wl['graph']} graph, a bounded sample of one certified ranking (oracle, FP64, "
+                  f"OpenMP rows + sequential partial sort)")
+    else:
+        sample = (f"each step: one complete certified ranking (r = {r} iterations of Algorithm 1) of the full "
+                  f"{wl['graph']} graph (oracle, FP64, OpenMP rows + sequential partial sort)")
     line = {"metric": METRIC, "value": value, "unit": "GTEPS",
             "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
@@ -380,6 +419,87 @@ def run_reference(args):
                              "sample": sample},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def time_static(K, torch, g, wl, precision, steps, warmup, stream, flush, world, rank):
+    """W untimed warm-up rankings, then exactly `steps` certified rankings
+    timed with CUDA events on the handle's stream, L2 flushed before each,
+    barrier + synchronize on both sides; clocks sampled during the timed
+    region.  Returns the handle (still open), the infos and the step times."""
+    rowptr_d = torch.from_numpy(g.rowptr).cuda()
+    col_d = torch.from_numpy(g.col).cuda()
+    opts = K.katz_default_opts(precision=precision, profile=1, cuda_stream=stream.cuda_stream)
+    h = K.Katz(rowptr_d, col_d, opts)
+    del rowptr_d, col_d  # the handle holds its own relabelled copy
+    for _ in range(warmup):
+        h.rank(wl["alpha"], wl["k"], wl["eps"])
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    infos = []
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        infos.append(h.rank(wl["alpha"], wl["k"], wl["eps"]))
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    return h, infos, [a.elapsed_time(b) for a, b in evs], clocks
+
+
+def spmv_roofline(infos, n, nnz, off64, fp32_run, hbm_peak, hbm_src, tr):
+    """Roofline of the walk-count SpMV (levels 2..r) from the launch times the
+    library measured with CUDA events on its stream.  Algorithmic bytes per
+    launch: col, row offsets, s_{r-1} read once, s_r written, c read and
+    written, the active flags; an FP32-certified ranking's levels before its
+    switch move FP64 values, the ones after it FP32 values (averaged over the
+    launches)."""
+    spmv_ms = sum(inf.spmv_ms for inf in infos)
+    launches = sum(inf.spmv_launches for inf in infos)
+    total_bytes = 0
+    for inf in infos:
+        levels = list(range(2, inf.r + 1))[:inf.spmv_launches]
+        f32_from = inf.r - inf.fp32_levels + 1 if (fp32_run and inf.fp32_levels) else 1 << 30
+        total_bytes += sum(spmv_algorithmic_bytes(n, nnz, lv >= f32_from, off64) for lv in levels)
+        total_bytes += spmv_algorithmic_bytes(n, nnz, fp32_run, off64) * max(0, inf.spmv_launches - len(levels))
+    t_launch = spmv_ms / 1e3 / max(launches, 1)
+    bytes_alg = total_bytes / max(launches, 1)
+    ach = bytes_alg / t_launch / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+            "traffic": tr["bytes_per_launch"] if tr else None,
+            "traffic_source": tr.get("command") if tr else None,
+            "peak_source": f"{hbm_src} hbm_gbs (burst copy)",
+            "algorithmic_bytes_per_launch": bytes_alg, "spmv_ms_per_launch": t_launch * 1e3,
+            "gathers_per_s": nnz / t_launch, "launches": launches,
+            "limiter": "random gathers of s_{r-1} (one L1 request per arc; beyond L2 one DRAM sector per "
+                       "missed gather) and, for FP64 levels, the integer adds of the exact row sums"}
+
+
+def deviation_stats(lo, up, err, l_ref, u_ref):
+    """Per-node deviation of FP32-certified bounds from the FP64 oracle's at
+    the same r, absolute and relative to the reported rounding widening."""
+    dl = np.abs(lo - l_ref)
+    du = np.abs(up - u_ref)
+    w = np.where(err > 0, err, np.inf)
+    out = {}
+    for name, d in (("lower", dl), ("upper", du)):
+        rel = d / w
+        out[name] = {"max_abs": float(d.max()), "p99_abs": float(np.percentile(d, 99)),
+                     "max_over_widening": float(rel[np.isfinite(rel)].max(initial=0.0)),
+                     "p99_over_widening": float(np.percentile(rel[np.isfinite(rel)], 99)) if np.isfinite(rel).any()
+                     else 0.0}
+    out["widening_max"] = float(err.max())
+    out["widening_p99"] = float(np.percentile(err, 99))
+    # each certified bound lies within err of the exact bound at r; the
+    # oracle's FP64 bounds carry their own rounding (1e-12 relative)
+    out["within_widening"] = bool(np.all(dl <= err + 1e-12 * np.abs(l_ref) + 1e-300) and
+                                  np.all(du <= err + 1e-12 * np.abs(u_ref) + 1e-300))
+    return out
 
 
 def main():
@@ -416,69 +536,41 @@ def main():
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     wl = dict(WORKLOADS[args.workload])
-    if args.precision:
-        wl["precision"] = 1 if args.precision == "fp32cert" else 0
-    fp32 = wl["precision"] == 1
+    # the headline precision, and the other one timed beside it (--precision
+    # picks the headline; --no-compare times it alone)
+    head_prec = args.precision or ("fp64" if wl["precision"] == 0 else "fp32cert")
+    other_prec = None if args.no_compare else ("fp32cert" if head_prec == "fp64" else "fp64")
     g = gg.workload(wl["graph"])
     n, nnz = g.n, g.nnz
     if wl["alpha"] == "half":
         wl["alpha"] = 0.5 / g.deg_max()
     stream = torch.cuda.current_stream()
-    rowptr_d = torch.from_numpy(g.rowptr).cuda()
-    col_d = torch.from_numpy(g.col).cuda()
-    opts = K.katz_default_opts(precision=wl["precision"], profile=1, cuda_stream=stream.cuda_stream)
-    h = K.Katz(rowptr_d, col_d, opts)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
-
-    for _ in range(args.warmup):
-        h.rank(wl["alpha"], wl["k"], wl["eps"])
-    torch.cuda.synchronize()
-
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    if sampler:
-        sampler.start()
-    barrier(world)
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    infos = []
-    for i in range(args.steps):
-        flush.zero_()
-        evs[i][0].record(stream)
-        infos.append(h.rank(wl["alpha"], wl["k"], wl["eps"]))
-        evs[i][1].record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    clocks = sampler.stop() if sampler else None
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(step_ms) / 1e3
-    edges_local = sum(inf.r * nnz for inf in infos)
-    total_s_max = allreduce_max(total_s, world)
-    value = replica_throughput(edges_local, total_s, world) / 1e9
-    spmv_ms = sum(inf.spmv_ms for inf in infos)
-    spmv_launches = sum(inf.spmv_launches for inf in infos)
-    launches = sum(inf.launches for inf in infos)
-    r = infos[-1].r
-    ranking = h.ranking(wl["k"])
-
-    # roofline of the dominant kernel (the fused walk-count SpMV)
     hbm_peak, hbm_src = peaks()
     off64 = (n + nnz) >= 0x7fffffff
-    bytes_alg = spmv_algorithmic_bytes(n, nnz, fp32, off64)
-    t_launch = spmv_ms / 1e3 / max(spmv_launches, 1)
-    hbm_ach = bytes_alg / t_launch / 1e9
-    tr = ncu_traffic(args.workload, "fp32cert" if fp32 else "fp64")
-    traffic = tr["bytes_per_launch"] if tr else None
-    # The walk-count SpMV moves its compulsory bytes from HBM and sums on the
-    # integer pipes (exact FP64 row sums), so DRAM bandwidth is the roofline
-    # it is measured against; what holds it below that roof is the rate of
-    # random gathers through L1/L2 (see profiles/).
-    roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
-            "traffic": traffic, "peak_source": f"{hbm_src} hbm_gbs (burst copy)",
-            "gathers_per_s": nnz / t_launch,
-            "limiter": "random gathers of s_{r-1} through L1/L2 (one request per arc) and the integer adds of the "
-                       "exact row sums; DRAM traffic equals the compulsory bytes"}
-    roof["algorithmic_bytes_per_launch"] = bytes_alg
-    roof["spmv_ms_per_launch"] = t_launch * 1e3
+
+    arms = {}
+    for prec in [head_prec] + ([other_prec] if other_prec else []):
+        code = K.KATZ_FP32_CERT if prec == "fp32cert" else K.KATZ_FP64
+        h, infos, step_ms, clocks = time_static(K, torch, g, wl, code, args.steps, args.warmup, stream, flush,
+                                                world, rank)
+        total_s = sum(step_ms) / 1e3
+        edges_local = sum(inf.r * nnz for inf in infos)
+        arm = {"precision": prec, "infos": infos, "clocks": clocks,
+               "total_s_max": allreduce_max(total_s, world),
+               "value": replica_throughput(edges_local, total_s, world) / 1e9,
+               "ranking": [int(x) for x in h.ranking(wl["k"])],
+               "roofline": spmv_roofline(infos, n, nnz, off64, prec == "fp32cert", hbm_peak, hbm_src,
+                                         ncu_traffic(args.workload, prec))}
+        if prec == "fp32cert" and rank == 0 and world == 1 and not args.no_cpu_baseline:
+            arm["bounds"] = h.bounds()  # compared with the oracle's below
+        h.close()
+        arms[prec] = arm
+    head = arms[head_prec]
+    infos = head["infos"]
+    r = infos[-1].r
+    launches = sum(inf.launches for inf in infos)
+    fp32_head = head_prec == "fp32cert"
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -486,7 +578,8 @@ def main():
         rp_pin = torch.from_numpy(g.rowptr).pin_memory()
         col_pin = torch.from_numpy(g.col).pin_memory()
         out_pin = torch.empty(wl["k"], dtype=torch.int32).pin_memory()
-        e2e_opts = K.katz_default_opts(precision=wl["precision"], cuda_stream=stream.cuda_stream)
+        e2e_opts = K.katz_default_opts(precision=K.KATZ_FP32_CERT if fp32_head else K.KATZ_FP64,
+                                       cuda_stream=stream.cuda_stream)
         e2e_times, e2e_edges = [], 0
         for i in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
@@ -505,45 +598,70 @@ def main():
                "h2d_bytes_per_step": int(g.rowptr.nbytes + g.col.nbytes), "d2h_bytes_per_step": int(4 * wl["k"]),
                "ms_per_step": 1e3 * e2e_t / len(e2e_times),
                "api": "katz_create_csr(host pinned CSR) + katz_rank_static + katz_get_ranking(host) + katz_destroy"}
+        del rp_pin, col_pin
 
     serving = serving32 = None
     if args.serve_batches is None:
         args.serve_batches = 400
     if args.serve_batches > 0:
-        h.close()
-        del rowptr_d, col_d, flush
+        del flush
         torch.cuda.empty_cache()
         if args.serve_precision in ("fp64", "both"):
             serving = run_serving(args.serve_batches, precision="fp64")
         if args.serve_precision in ("fp32cert", "both"):
             serving32 = run_serving(args.serve_batches, precision="fp32cert")
-        h = None
 
     cpu = None
+    deviation = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = cpu_baseline(g, wl, args.cpu_seconds)
+        cpu, sess = cpu_baseline(g, wl, args.cpu_seconds)
+        if "fp32cert" in arms and "bounds" in arms["fp32cert"]:
+            lo, up, err = arms["fp32cert"]["bounds"]
+            r32 = arms["fp32cert"]["infos"][-1].r
+            if sess.info()["r"] != r32:  # the oracle's bounds at the FP32-certified run's r
+                sess.run_fixed(wl["alpha"], r32)
+            _, l_ref, u_ref = sess.bounds()
+            deviation = deviation_stats(lo, up, err, l_ref, u_ref)
+            deviation["r"] = r32
+        sess.close()
+
+    def arm_summary(a):
+        inf = a["infos"][-1]
+        return {"value": a["value"], "unit": "GTEPS", "ms_per_step": 1e3 * a["total_s_max"] / args.steps,
+                "r": inf.r, "fp32_levels": int(inf.fp32_levels), "roofline": a["roofline"],
+                "spmv_gteps": nnz / (a["roofline"]["spmv_ms_per_launch"] / 1e3) / 1e9,
+                "gpu_launches": int(sum(i.launches for i in a["infos"])), "clocks": a["clocks"],
+                "ranking_head": a["ranking"][:5]}
 
     if rank == 0:
         line = {
             "metric": METRIC,
-            "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total_s_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}-top{wl['k']}-{'fp32cert' if fp32 else 'fp64'}",
+            "value": head["value"], "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * head["total_s_max"] / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if fp32_head else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}-top{wl['k']}-{head_prec}",
                        "graph": wl["desc"], "n": n, "nnz": nnz, "k": wl["k"], "eps": wl["eps"],
                        "alpha": infos[-1].alpha, "r": r, "parallelism": f"replicas{world}",
+                       "offsets": "int64" if off64 else "int32",
                        "l2": "flushed between steps (256 MB write); col array alone is larger than L2"},
-            "time_to_certified_ms": 1e3 * total_s_max / args.steps,
-            "spmv_gteps": nnz / t_launch / 1e9,
+            "time_to_certified_ms": 1e3 * head["total_s_max"] / args.steps,
+            "spmv_gteps": nnz / (head["roofline"]["spmv_ms_per_launch"] / 1e3) / 1e9,
             "fp32_levels": int(infos[-1].fp32_levels),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "ranking_head": [int(x) for x in ranking[:5]],
-            "serving": serving,
-            "serving_fp32cert": serving32,
+            "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": head["clocks"], "ranking_head": head["ranking"][:5],
         }
+        if other_prec:
+            other = arms[other_prec]
+            line[other_prec] = arm_summary(other)
+            t32 = arms["fp32cert"]["total_s_max"]
+            t64 = arms["fp64"]["total_s_max"]
+            line["fp32cert_speedup_over_fp64"] = t64 / t32
+            line["same_ranking_fp32cert_fp64"] = arms["fp32cert"]["ranking"] == arms["fp64"]["ranking"]
+        if deviation is not None:
+            line["fp32cert_deviation_vs_oracle"] = deviation
+        line["serving"] = serving
+        line["serving_fp32cert"] = serving32
         print(json.dumps(line), flush=True)
-    if h is not None:
-        h.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
