@@ -107,8 +107,7 @@ def parse():
                     help="--impl reference on graphs above 2^30 arcs: oracle iterations per step")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU work of the cpu_baseline sample")
     ap.add_argument("--serve-batches", type=int, default=None,
-                    help="batches of the serving stream (default: 400 beside the static line, 2000 for "
-                         "--workload serve-rmat23; 0 skips it beside the static line)")
+                    help="batches of the serving stream (default 2000; 0 skips it beside the static line)")
     return ap.parse_args()
 
 
@@ -602,7 +601,7 @@ def main():
 
     serving = serving32 = None
     if args.serve_batches is None:
-        args.serve_batches = 400
+        args.serve_batches = 2000
     if args.serve_batches > 0:
         del flush
         torch.cuda.empty_cache()

@@ -293,9 +293,14 @@ katz_status katz_convert_f64_f32(const double* in, int64_t n, float* out, double
  * (opts: only cuda_stream is read; NULL: a stream of its own).  The restored
  * handle continues where the original stood: the same ranking, bounds and
  * walks, and later calls give the same results.  The image is this library
- * version's internal layout (checked on restore), not an exchange format.
+ * version's internal layout, not an exchange format.  katz_restore checks it
+ * before any kernel reads it, as katz_create_csr checks its input: the header
+ * fields against each other, the CSR (offsets monotone from 0 to nnz, column
+ * ids in range, degrees within the degree bound), the relabelling (an inverse
+ * pair of permutations), the hub-row chunk table and the stored ids.
  * Errors: KATZ_EINVAL (NULL pointer, buffer too small, not an image of this
- * version), KATZ_ESTATE (handle not ranked), KATZ_ENOMEM, KATZ_ECUDA.
+ * version, or an inconsistent image), KATZ_ESTATE (handle not ranked),
+ * KATZ_ENOMEM, KATZ_ECUDA.
  */
 katz_status katz_checkpoint_size(katz_h h, uint64_t* bytes);
 katz_status katz_checkpoint(katz_h h, void* buf, uint64_t bytes);
@@ -309,8 +314,9 @@ katz_status katz_restore(katz_h* out, const void* buf, uint64_t bytes, const kat
  * batch.  Requests on one handle run in arrival order, each on the graph the
  * previous ones left; requests on different handles run at the same time on
  * their handles' streams.  Submitted batches wait in arrival order until one
- * of `slots` staging slots is free and the admitted updates stay within
- * `admit_updates`; admission copies the batch to the device on the slot's own
+ * of `slots` staging slots is free and the admitted requests stay within
+ * `admit_updates` updates and `admit_bytes` bytes of staging memory;
+ * admission copies the batch to the device on the slot's own
  * stream, overlapping the work in flight.  `workers` host threads drive the
  * admitted requests through the two phases of katz_apply_update_batch and
  * katz_get_ranking.  The first phase validates a batch and builds the updated
@@ -330,6 +336,10 @@ typedef struct {
     int32_t slots;          /* requests admitted at once (default 8) */
     int64_t slot_updates;   /* largest batch accepted, in updates (default 10000) */
     int64_t admit_updates;  /* admitted updates in total at most (0: slots * slot_updates) */
+    int64_t admit_bytes;    /* staging memory of the admitted requests in bytes at most: a
+                               request of m updates holds 18 m bytes (its batch in pinned host
+                               memory and on the device) from admission to completion
+                               (0: no limit beyond admit_updates) */
 } katz_server_opts;
 
 typedef struct {

@@ -52,7 +52,7 @@ class katz_info(ctypes.Structure):
 
 class katz_server_opts(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("slots", ctypes.c_int32), ("slot_updates", ctypes.c_int64),
-                ("admit_updates", ctypes.c_int64)]
+                ("admit_updates", ctypes.c_int64), ("admit_bytes", ctypes.c_int64)]
 
 
 class katz_request_result(ctypes.Structure):

@@ -43,6 +43,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// staging memory of one admitted update: src, dst (int32) and the insert flag,
+// in pinned host memory and on the device
+constexpr int64_t kStagingBytesPerUpdate = 2 * (2 * (int64_t)sizeof(int32_t) + 1);
+
 double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
@@ -124,6 +128,9 @@ void admit_locked(katz_server* s) {
     while (!s->waiting.empty() && !s->free_slots.empty()) {
         Request* q = s->waiting.front();
         if (s->admitted_updates > 0 && s->admitted_updates + q->m > s->opts.admit_updates) break;
+        if (s->opts.admit_bytes > 0 && s->admitted_updates > 0 &&
+            (s->admitted_updates + q->m) * kStagingBytesPerUpdate > s->opts.admit_bytes)
+            break;
         s->waiting.pop_front();
         const int si = s->free_slots.back();
         s->free_slots.pop_back();
@@ -243,6 +250,7 @@ void katz_server_default_opts(katz_server_opts* o) {
     o->slots = 8;
     o->slot_updates = 10000;
     o->admit_updates = 0;
+    o->admit_bytes = 0;
 }
 
 katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts) {
@@ -251,7 +259,7 @@ katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts)
     katz_server_opts o;
     katz_server_default_opts(&o);
     if (opts) o = *opts;
-    if (o.workers < 1 || o.workers > 64 || o.slots < 1 || o.slots > 1024 || o.slot_updates < 1)
+    if (o.workers < 1 || o.workers > 64 || o.slots < 1 || o.slots > 1024 || o.slot_updates < 1 || o.admit_bytes < 0)
         return KATZ_EINVAL;
     if (o.admit_updates <= 0) o.admit_updates = (int64_t)o.slots * o.slot_updates;
     katz_server* s = new katz_server();

@@ -66,3 +66,12 @@ def test_create_rejects_bad_arguments_without_touching_the_device():
     with pytest.raises(K.KatzError) as e:
         K.katz_create_csr(0, 0, np.zeros(1, np.int64), np.zeros(1, np.int32))
     assert e.value.name == "KATZ_EINVAL"
+
+
+def test_server_options_are_checked_on_the_host():
+    import paper_1807_03847_gb300 as K
+
+    for kw in ({"admit_bytes": -1}, {"workers": 0}, {"slots": 0}, {"slot_updates": 0}):
+        with pytest.raises(K.KatzError) as e:
+            K.Server(**kw)
+        assert e.value.name == "KATZ_EINVAL"

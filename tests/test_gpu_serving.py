@@ -126,6 +126,28 @@ def test_wait_times_out_and_one_slot_serialises_admission():
     h.close()
 
 
+def test_a_byte_budget_admits_one_batch_at_a_time():
+    """admit_bytes below the staging memory of two batches: each request is
+    admitted only after the one before it has finished, and the answers are
+    those of applying the batches one by one."""
+    g = gg.rmat(12, 16, seed=43)
+    D, k = g.deg_max() + 64, 10
+    st = gg.stream(g, 5, seed=44, min_size=300, max_size=300, deg_bound=D)
+    ref = _alone(g, k, D, st)
+    h = _handle(g, k, D)
+    srv = K.Server(workers=4, slots=8, slot_updates=300, admit_bytes=18 * 400)
+    srv.attach(h, k)
+    ts = [srv.submit(h, *st.batch(j)) for j in range(len(st))]
+    res = [srv.wait(t) for t in ts]
+    for j, (status, ids, r) in enumerate(res):
+        assert status == 0
+        np.testing.assert_array_equal(ids, ref[j][1])
+        if j > 0:  # admitted (queue_ms after submit) no earlier than the previous request finished
+            assert r.queue_ms >= res[j - 1][2].latency_ms - 1.0
+    srv.close()
+    h.close()
+
+
 @pytest.mark.parametrize("directed,fp32", [(False, False), (True, False), (False, True), (True, True)])
 def test_pipelined_batches_on_one_handle_match_sequential(directed, fp32):
     # two workers on one handle: the prepare of each batch (validation and
