@@ -340,12 +340,21 @@ typedef struct {
                                request of m updates holds 18 m bytes (its batch in pinned host
                                memory and on the device) from admission to completion
                                (0: no limit beyond admit_updates) */
+    int32_t pair_batches;   /* two queued batches of one undirected graph in one pass: the walk
+                               levels of both graph states are computed together (one gathered
+                               line serves both), and each batch is answered with its own
+                               certified ranking, bit for bit that of applying the batches one
+                               by one.  1 (default): when the graph's last repair recomputed
+                               whole levels (the case where one pass for two pays off);
+                               2: whenever two batches are queued; 0: never */
+    int32_t reserved;       /* set to 0 */
 } katz_server_opts;
 
 typedef struct {
     int32_t status;         /* katz_status of the request (KATZ_EINVAL: batch rejected,
                                graph and ranking unchanged) */
-    int32_t reserved;
+    int32_t paired;         /* 1: its walk levels came from one two-state pass with the
+                               request before or after it on the same handle */
     int64_t k;              /* ids written to ids_out */
     katz_info info;         /* katz_apply_update_batch's info */
     double queue_ms;        /* submit -> admitted into a slot */
