@@ -286,7 +286,8 @@ def run_serving(batches, workers=2, slots=8, precision="fp64"):
     (katz_rank_static on the same handle) as the baseline.  The capacity is
     the throughput of the first run when it saturates (batches of one handle
     are pipelined: the prepare of a batch overlaps the repair of the one
-    before it, so one request's service time is not the rate)."""
+    before it, and two queued batches share one two-state pass, so one
+    request's service time is not the rate)."""
     import torch
 
     import graphgen as gg
@@ -337,6 +338,7 @@ def serve_once(g, D, batches, rate, workers, slots, torch, precision="fp64"):
     full = np.array([r[2].info.full_levels for r in results], np.float64)
     launches = int(sum(r[2].info.launches for r in results))
     fp32_levels = [r[2].info.fp32_levels for r in results]
+    paired = np.array([r[2].paired for r in results], np.float64)
     sizes = st.sizes()
     # full static recomputation of the final graph, same handle (graph resident)
     rec_dev, rec_wall = [], []
@@ -359,6 +361,7 @@ def serve_once(g, D, batches, rate, workers, slots, torch, precision="fp64"):
         "affected_mean_frac": float(aff.mean() / g.n), "full_levels_mean": float(full.mean()),
         "r_initial": int(info0.r), "gpu_launches": launches, "workers": workers, "slots": slots,
         "precision": precision, "fp32_levels_initial": int(info0.fp32_levels),
+        "paired_frac": float(paired.mean()),
         "fp32_levels_median": float(np.median(fp32_levels)),
         "clocks": clocks, "n": g.n, "nnz": g.nnz, "deg_bound": D, "desc": cfg["desc"],
         "latency": "submit (at the batch's arrival time) -> certified top-100 copied to the host",

@@ -52,11 +52,12 @@ class katz_info(ctypes.Structure):
 
 class katz_server_opts(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("slots", ctypes.c_int32), ("slot_updates", ctypes.c_int64),
-                ("admit_updates", ctypes.c_int64), ("admit_bytes", ctypes.c_int64)]
+                ("admit_updates", ctypes.c_int64), ("admit_bytes", ctypes.c_int64),
+                ("pair_batches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class katz_request_result(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("k", ctypes.c_int64),
+    _fields_ = [("status", ctypes.c_int32), ("paired", ctypes.c_int32), ("k", ctypes.c_int64),
                 ("info", katz_info), ("queue_ms", ctypes.c_double), ("wait_ms", ctypes.c_double),
                 ("service_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
 

@@ -545,6 +545,9 @@ void katz_destroy(katz_h h) {
     dfree(h, h->d_deghist);
     dfree(h, h->d_scratch);
     dfree(h, h->rank_ids);
+    dfree(h, h->pair_P);
+    dfree(h, h->pair_t);
+    dfree(h, h->pair_part);
     for (int q = 0; q < 2; ++q) {
         dfree(h, h->rs.hi[q]);
         dfree(h, h->rs.lo[q]);
@@ -1350,7 +1353,21 @@ katz_status update_swap(katz_handle* h) {
 
 // Phase 2b on the handle's stream: s_1..s_r repaired (Sec. 4), the bounds and
 // the active set re-derived, and further iterations until converged() holds.
+// The levels (repair_levels) and the rest (repair_finish) are separate steps:
+// the two-state pass (update_pair_levels) computes the levels of two batches
+// at once and then runs repair_finish for each.
+static katz_status repair_levels(katz_handle* h, int64_t& full_levels, int64_t& affected, bool& all_rows);
+static katz_status repair_finish(katz_handle* h, katz_info* info, int64_t full_levels, int64_t affected,
+                                 bool all_rows);
+
 katz_status update_repair(katz_handle* h, katz_info* info) {
+    int64_t full_levels = 0, affected = 0;
+    bool all_rows = false;
+    const katz_status st = repair_levels(h, full_levels, affected, all_rows);
+    return st != KATZ_OK ? st : repair_finish(h, info, full_levels, affected, all_rows);
+}
+
+static katz_status repair_levels(katz_handle* h, int64_t& full_levels, int64_t& affected, bool& all_rows) {
     const katz_handle::Pending& pd = h->rep;
     cudaError_t e;
     DeviceGraph& g = h->g;
@@ -1362,7 +1379,9 @@ katz_status update_repair(katz_handle* h, katz_info* info) {
     d.ins = h->bins[pd.bset];
     d.undirected = h->opts.undirected != 0;
     const bool hubs = g.layout.row_warp > 0;
-    int64_t full_levels = 0, affected = 0;
+    full_levels = 0;
+    affected = 0;
+    all_rows = false;
     if (pd.applied) {
         // directed: the reverse BFS walks in-arcs, from the transposed CSR of
         // the updated graph
@@ -1442,7 +1461,21 @@ katz_status update_repair(katz_handle* h, katz_info* info) {
             }
         }
         affected = full ? n : hi;
-        if ((e = dyn_recompute_c(g, h->b, d, h->p, r, full, h->stream)) != cudaSuccess)
+        all_rows = full;
+    }
+    return KATZ_OK;
+}
+
+static katz_status repair_finish(katz_handle* h, katz_info* info, int64_t full_levels, int64_t affected,
+                                 bool all_rows) {
+    const katz_handle::Pending& pd = h->rep;
+    cudaError_t e;
+    DeviceGraph& g = h->g;
+    const int64_t n = g.n;
+    const int r = h->r;
+    DynBuffers d = h->dyn;
+    if (pd.applied) {
+        if ((e = dyn_recompute_c(g, h->b, d, h->p, r, all_rows, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "recompute c");
         h->launches += 1;
         // FP32-certified: a row sum longer than any before widens every
@@ -1519,6 +1552,7 @@ katz_status update_repair(katz_handle* h, katz_info* info) {
         info->full_levels = (int32_t)full_levels;
         info->launches = h->launches;
     }
+    h->last_repair_whole = all_rows;
     if (stalled) return fail(h, KATZ_EPRECISION, "FP32 rounding widening exceeds the remaining tail; rank in FP64");
     if (!h->converged) return fail(h, KATZ_ENOTCONV, "r_max reached before the top-k criterion held");
     return KATZ_OK;
@@ -1527,6 +1561,84 @@ katz_status update_repair(katz_handle* h, katz_info* info) {
 katz_status update_commit(katz_handle* h, katz_info* info) {
     const katz_status st = update_swap(h);
     return st != KATZ_OK ? st : update_repair(h, info);
+}
+
+// ---- two batches in one pass (katz_spmv.cu, "Two graph states in one pass") ----
+bool pair_possible(katz_handle* h) {
+    const katz_handle::Pending& a = h->rep;   // swapped in, not yet repaired
+    const katz_handle::Pending& b = h->pend;  // prepared on top of it
+    return h->opts.undirected && a.status == KATZ_OK && a.applied && b.ready && b.status == KATZ_OK && b.applied &&
+           !b.promote && h->r >= 1 && h->ranked && h->criterion == KATZ_CRIT_TOPK;
+}
+
+katz_status update_pair_first(katz_handle* h, katz_info* info) {
+    const katz_handle::Pending& pb = h->pend;
+    DeviceGraph& g = h->g;
+    const int64_t n = g.n;
+    const int r = h->r;
+    cudaError_t e;
+    h->pair_r = -1;
+    // the second state's graph: the spare buffers its prepare built
+    DeviceGraph gb = g;
+    gb.nnz = pb.nnz;
+    gb.col = h->col_spare;
+    gb.rowptr = h->rowptr_spare;
+    gb.chunk_first = h->chunk_first_spare;
+    gb.chunk_row = h->chunk_row_spare;
+    gb.chunk_part = nullptr;
+    gb.layout = make_layout(n, g.layout.row_warp, g.layout.row_octet, g.layout.row_thread, pb.chunks);
+    const int64_t pstride = 2 * h->stride;
+    const size_t need = (size_t)(r + 1) * (size_t)pstride;
+    if (need > h->pair_P_cap) {
+        dfree(h, h->pair_P);
+        h->pair_P = nullptr;
+        h->pair_P_cap = 0;
+        if ((e = dmalloc(h, &h->pair_P, need)) != cudaSuccess) return cuda_fail(h, e, "cudaMalloc pair levels");
+        h->pair_P_cap = need;
+    }
+    if (h->p.cert && !h->pair_t && (e = dmalloc(h, &h->pair_t, 2 * (size_t)n)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaMalloc pair roundings");
+    const int64_t part_need = 6 * std::max<int64_t>(pb.chunks, 1);
+    if (part_need > h->pair_part_cap) {
+        dfree(h, h->pair_part);
+        h->pair_part = nullptr;
+        h->pair_part_cap = 0;
+        if ((e = dmalloc(h, &h->pair_part, (size_t)part_need)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaMalloc pair chunk sums");
+        h->pair_part_cap = part_need;
+    }
+    if ((e = cudaStreamWaitEvent(h->stream, h->ev_prepared, 0)) != cudaSuccess) return cuda_fail(h, e, "event");
+    const int f32_from = h->f32_from;
+    const int t_level = h->p.cert ? std::min(f32_from - 1, r) : 0;
+    if ((e = launch_pair_levels(g, gb, h->bsrc[pb.bset], h->bdst[pb.bset], pb.m, h->p, r, f32_from, t_level,
+                                h->pair_P, pstride, h->pair_t, h->pair_part, h->dyn.vbits, h->dyn.frontier,
+                                h->dyn.fsize, h->stream)) != cudaSuccess ||
+        (e = launch_pair_split(g, h->b, h->p, r, f32_from, 0, h->pair_P, pstride, h->pair_t, h->stream)) !=
+            cudaSuccess)
+        return cuda_fail(h, e, "pair levels");
+    {  // launches: mark, degrees, per level SpMV (+ hub merge) and the fixes, split
+        const int per_level = 1 + (gb.layout.row_warp > 0 ? 1 : 0) + (pb.m > 0 ? 1 + (g.layout.chunks > 0 ? 2 : 0) : 0);
+        h->launches += (pb.m > 0 ? 1 : 0) + 1 + (int64_t)std::max(0, r - 1) * per_level + 1;
+    }
+    h->pair_r = r;
+    h->pair_f32_from = f32_from;
+    return repair_finish(h, info, r, n, true);
+}
+
+katz_status update_pair_second(katz_handle* h, katz_info* info) {
+    const int r_pair = h->pair_r, f32_pair = h->pair_f32_from;
+    h->pair_r = -1;
+    h->pair_second_used = false;
+    // the first batch's finish kept r and the precision: the second state's
+    // levels of the same pass hold (else it is repaired alone)
+    if (r_pair < 0 || !h->rep.applied || h->r != r_pair || h->f32_from != f32_pair) return update_repair(h, info);
+    cudaError_t e;
+    if ((e = launch_pair_split(h->g, h->b, h->p, r_pair, f32_pair, 1, h->pair_P, 2 * h->stride, h->pair_t,
+                               h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "pair split");
+    h->launches += 1;
+    h->pair_second_used = true;
+    return repair_finish(h, info, r_pair, h->g.n, true);
 }
 
 // the checks a handle must pass before it takes update batches

@@ -315,6 +315,12 @@ cudaError_t launch_spmv_store(const DeviceGraph& g, const IterBuffers& b, const 
                               cudaStream_t st);
 // s_level recomputed for the listed rows (CHUNK rows excepted) and for the
 // CHUNK rows whose visit bit is set, with the lane partition of the SpMV
+cudaError_t launch_pair_levels(const DeviceGraph& ga, const DeviceGraph& gb, const int32_t* bsrc,
+                               const int32_t* bdst, int64_t m, const IterParams& p, int r, int f32_from,
+                               int t_level, double* P, int64_t pstride, float* t_pair, double* part,
+                               uint32_t* vbits, int32_t* rows, unsigned long long* nrows, cudaStream_t st);
+cudaError_t launch_pair_split(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int r, int f32_from,
+                              int state, const double* P, int64_t pstride, const float* t_pair, cudaStream_t st);
 cudaError_t launch_rows_store(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, const int32_t* rows,
                               const unsigned long long* nrows_dev, int64_t nrows_max, const uint32_t* vbits,
                               int level, cudaStream_t st);

@@ -85,6 +85,17 @@ struct katz_handle {
         bool promote = false;   // the updated graph needs int64 row offsets (rp64_next)
     } pend;                     // written by the prepare
     Pending rep;                // the swapped-in batch, read by its repair
+    // two-state pass (update_pair_levels): interleaved levels of the two
+    // graph states, their FP32 roundings and the chunk partials of both
+    double* pair_P = nullptr;
+    size_t pair_P_cap = 0;      // doubles
+    float* pair_t = nullptr;    // [2n]
+    double* pair_part = nullptr;
+    int64_t pair_part_cap = 0;  // doubles
+    int pair_r = -1;            // r of the levels in pair_P (-1: none pending for the second state)
+    int pair_f32_from = 0;      // the first FP32 level those levels used
+    bool last_repair_whole = false;  // the last repair recomputed whole levels
+    bool pair_second_used = false;   // update_pair_second finished from the two-state pass
     int64_t* rrowptr = nullptr; // [n+1] directed: transposed CSR of the current graph (the repair's)
     int32_t* rcol = nullptr;
     int64_t rcap = 0;
@@ -160,4 +171,13 @@ katz_status update_prepare(katz_handle* h, const int32_t* src, const int32_t* ds
 katz_status update_swap(katz_handle* h);
 katz_status update_repair(katz_handle* h, katz_info* info);
 katz_status update_commit(katz_handle* h, katz_info* info);
+// Two batches in one pass: after the first batch's swap (h->rep) and the
+// second batch's prepare on top of it (h->pend), pair_possible says whether
+// the pass applies; update_pair_first computes the levels of both graph
+// states and finishes the first batch (its ranking is then current);
+// update_pair_second swaps the second batch in and finishes it from the same
+// pass, or repairs it alone when the first one changed r or the precision.
+bool pair_possible(katz_handle* h);
+katz_status update_pair_first(katz_handle* h, katz_info* info);
+katz_status update_pair_second(katz_handle* h, katz_info* info);
 }  // namespace katz

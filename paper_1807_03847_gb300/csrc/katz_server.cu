@@ -64,6 +64,7 @@ struct Request {
     int slot = -1;
     Clock::time_point t_submit, t_admit, t_start, t_done;
     katz_status status = KATZ_OK;
+    bool paired = false;  // levels from a two-state pass with the neighbouring request
     katz_info info{};
     std::vector<int32_t> ids;
 };
@@ -170,30 +171,97 @@ void prepare_request(katz_server* s, Request* q) {
     katz::update_prepare(h, src, dst, sl.d_ins, q->m, sl.h2d_done);
 }
 
-// Phase 2 (the caller holds mu, released while the device works): wait for
-// the earlier request's repair, swap the prepared graph in, let the next
-// prepare start, then repair and read the ranking.
-void commit_request(katz_server* s, Request* q, int64_t k, std::unique_lock<std::mutex>& lock) {
-    Lane& lane = s->lanes[q->h];
-    while (lane.repairing) s->cv_done.wait(lock);
-    lane.repairing = true;
-    lock.unlock();
+// The ranking of the graph the handle now holds (after a rejected batch the
+// graph is unchanged and so is the ranking).
+void read_ranking(katz_server* s, Request* q, int64_t k) {
     katz_handle* h = q->h;
     Slot& sl = s->slots[(size_t)q->slot];
-    const katz_status sw = katz::update_swap(h);
-    lock.lock();
-    lane.swap_pending = false;  // the next prepare reads the graph now current
-    s->cv_work.notify_all();
-    lock.unlock();
-    q->status = sw != KATZ_OK ? sw : katz::update_repair(h, &q->info);
-    // the ranking of the graph the handle now holds (after a rejected batch
-    // the graph is unchanged and so is the ranking)
     if (q->status == KATZ_OK || q->status == KATZ_EINVAL || q->status == KATZ_EALPHA) {
         const int64_t kk = std::min<int64_t>(k, h->k_eff);
         if (kk > 0 && katz_get_ranking(h, sl.h_ids, kk) == KATZ_OK) q->ids.assign(sl.h_ids, sl.h_ids + kk);
     }
+}
+
+// A finished request releases its slot and admits the next (caller holds mu).
+void complete_locked(katz_server* s, Request* q) {
+    q->t_done = Clock::now();
+    q->state = DONE;
+    s->free_slots.push_back(q->slot);
+    s->admitted_updates -= q->m;
+    admit_locked(s);
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+}
+
+// Phase 2 (the caller holds mu, released while the device works): wait for
+// the earlier request's repair, swap the prepared graph in, let the next
+// prepare start, then repair and read the ranking.  With pairing, the next
+// request of the handle, when it is already admitted, is prepared here on top
+// of this one and both are repaired in one two-state pass; this request's
+// answer is ready before the second one's graph is swapped in.  Completes the
+// request(s) it ran.
+void commit_request(katz_server* s, Request* q, int64_t k, std::unique_lock<std::mutex>& lock) {
+    Lane& lane = s->lanes[q->h];
+    while (lane.repairing) s->cv_done.wait(lock);
+    lane.repairing = true;
+    katz_handle* h = q->h;
+    const bool want_pair = s->opts.pair_batches == 2 || (s->opts.pair_batches == 1 && h->last_repair_whole);
+    lock.unlock();
+    const katz_status sw = katz::update_swap(h);
     lock.lock();
+    lane.swap_pending = false;  // the next prepare reads the graph now current
+    Request* q2 = nullptr;
+    if (sw == KATZ_OK && want_pair && h->rep.applied && h->opts.undirected && !lane.preparing) {
+        for (auto it = s->admitted.begin(); it != s->admitted.end(); ++it)
+            if ((*it)->h == h && (*it)->seq == lane.prep_seq) {
+                q2 = *it;
+                s->admitted.erase(it);
+                break;
+            }
+    }
+    if (q2) {  // its prepare runs here; no other worker prepares for this handle meanwhile
+        lane.preparing = true;
+        q2->state = RUNNING;
+        q2->t_start = Clock::now();
+    }
+    s->cv_work.notify_all();
+    lock.unlock();
+    bool paired = false;
+    if (q2) {
+        prepare_request(s, q2);
+        lock.lock();
+        lane.preparing = false;
+        lane.swap_pending = true;
+        lane.prep_seq += 1;
+        lock.unlock();
+        if (katz::pair_possible(h)) {
+            paired = true;
+            q->paired = true;
+            q->status = katz::update_pair_first(h, &q->info);
+        }
+    }
+    if (!paired) q->status = sw != KATZ_OK ? sw : katz::update_repair(h, &q->info);
+    read_ranking(s, q, k);
+    lock.lock();
+    complete_locked(s, q);
+    if (!q2) {
+        lane.repairing = false;
+        s->cv_done.notify_all();
+        return;
+    }
+    lock.unlock();
+    const katz_status sw2 = katz::update_swap(h);
+    lock.lock();
+    lane.swap_pending = false;
+    s->cv_work.notify_all();
+    lock.unlock();
+    q2->status = sw2 != KATZ_OK ? sw2 : (paired ? katz::update_pair_second(h, &q2->info) : katz::update_repair(h, &q2->info));
+    q2->paired = paired && h->pair_second_used;
+    read_ranking(s, q2, k);
+    lock.lock();
+    complete_locked(s, q2);
     lane.repairing = false;
+    s->cv_done.notify_all();
 }
 
 void worker_main(katz_server* s) {
@@ -229,13 +297,6 @@ void worker_main(katz_server* s) {
         lane.swap_pending = true;
         lane.prep_seq += 1;
         commit_request(s, q, k, lock);
-        q->t_done = Clock::now();
-        q->state = DONE;
-        s->free_slots.push_back(q->slot);
-        s->admitted_updates -= q->m;
-        admit_locked(s);
-        s->cv_done.notify_all();
-        s->cv_work.notify_all();
     }
 }
 
@@ -251,6 +312,8 @@ void katz_server_default_opts(katz_server_opts* o) {
     o->slot_updates = 10000;
     o->admit_updates = 0;
     o->admit_bytes = 0;
+    o->pair_batches = 1;
+    o->reserved = 0;
 }
 
 katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts) {
@@ -259,7 +322,8 @@ katz_status katz_server_create(katz_server_h* out, const katz_server_opts* opts)
     katz_server_opts o;
     katz_server_default_opts(&o);
     if (opts) o = *opts;
-    if (o.workers < 1 || o.workers > 64 || o.slots < 1 || o.slots > 1024 || o.slot_updates < 1 || o.admit_bytes < 0)
+    if (o.workers < 1 || o.workers > 64 || o.slots < 1 || o.slots > 1024 || o.slot_updates < 1 || o.admit_bytes < 0 ||
+        o.pair_batches < 0 || o.pair_batches > 2)
         return KATZ_EINVAL;
     if (o.admit_updates <= 0) o.admit_updates = (int64_t)o.slots * o.slot_updates;
     katz_server* s = new katz_server();
@@ -353,6 +417,7 @@ katz_status katz_server_wait(katz_server_h s, uint64_t ticket, int64_t timeout_m
     if (res) {
         std::memset(res, 0, sizeof(*res));
         res->status = q->status;
+        res->paired = q->paired ? 1 : 0;
         res->k = (int64_t)q->ids.size();
         res->info = q->info;
         res->queue_ms = ms_between(q->t_submit, q->t_admit);

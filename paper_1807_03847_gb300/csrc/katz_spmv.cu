@@ -379,7 +379,9 @@ __device__ __forceinline__ double xacc_to_double(const XAcc& a) {
 // as nothing).  G = 8 for rows whose lanes see many terms, G = 4 for short
 // rows (fewer padded slots).  An empty accumulator starts at the largest
 // exponent of its first group, so it rarely has to rescale.
-template <int G>
+// S: entries of x are S apart (S = 2: one state of the interleaved pairs of
+// the two-state pass below).
+template <int G, int S = 1>
 __device__ __forceinline__ XAcc strided_xsum(const int32_t* __restrict__ col, const double* __restrict__ x,
                                              int64_t a, int64_t b, int first, int step) {
     XAcc s = xacc_zero();
@@ -388,7 +390,7 @@ __device__ __forceinline__ XAcc strided_xsum(const int32_t* __restrict__ col, co
 #pragma unroll
         for (int q = 0; q < G; ++q) {
             const int64_t jj = j + (int64_t)q * step;
-            v[q] = jj < b ? __ldg(x + col[jj]) : 0.0;
+            v[q] = jj < b ? __ldg(x + (int64_t)S * col[jj]) : 0.0;
         }
         if (s.E == 0) {
             int em = exp_of(v[0]);
@@ -432,7 +434,7 @@ __device__ __forceinline__ XAcc merge_chunks_warp(const double* __restrict__ par
 // Sum of x[col[j]] for j in [a, b) with stride `step` from a + first: eight
 // loads in flight, each group of eight added as a pairwise tree (depth 3),
 // groups chained in index order.
-template <typename Tin, typename Acc>
+template <typename Tin, typename Acc, int S = 1>
 __device__ __forceinline__ Acc strided_sum(const int32_t* __restrict__ col, const Tin* __restrict__ x, int64_t a,
                                            int64_t b, int first, int step) {
     Acc s = (Acc)0;
@@ -441,7 +443,7 @@ __device__ __forceinline__ Acc strided_sum(const int32_t* __restrict__ col, cons
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int64_t jj = j + (int64_t)q * step;
-            v[q] = jj < b ? (Acc)__ldg(x + col[jj]) : (Acc)0;
+            v[q] = jj < b ? (Acc)__ldg(x + (int64_t)S * col[jj]) : (Acc)0;
         }
         const Acc t = addA<Acc>(addA<Acc>(addA<Acc>(v[0], v[1]), addA<Acc>(v[2], v[3])),
                                 addA<Acc>(addA<Acc>(v[4], v[5]), addA<Acc>(v[6], v[7])));
@@ -892,6 +894,437 @@ cudaError_t launch_rows_store(const DeviceGraph& g, const IterBuffers& b, const 
         hub_rows_store_kernel<<<(unsigned)((L.row_warp * 32 + 127) / 128), 128, 0, st>>>(
             L, g.chunk_first, g.chunk_part, vbits, (double*)b.walk, b.s32, b.ctrl, p, level);
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Two graph states in one pass.
+//
+// A server with two batches of one graph queued answers both: A is the graph
+// after the first batch, B the graph after the second.  On graphs whose
+// repairs are whole levels (a batch reaches a hub within a level or two),
+// the walk levels of A and B are computed together, over B's adjacency, with
+// the level vectors of the two states stored interleaved: entry 2v is A's
+// s_i(v), entry 2v + 1 is B's (16 bytes per node for FP64 levels, 8 for FP32
+// ones).  One gathered line then serves both states, and the gathers, not
+// the arithmetic, bound the level.  The rows the second batch changed have
+// A's adjacency in A's graph: their A entries are recomputed afterwards from
+// A's rows (pair_fix_*).  Each state's row sums use the lane partition, the
+// grouping and the order of the one-state kernel, so every entry has the bits
+// that a repair of that state alone gives.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int G>
+__device__ __forceinline__ void strided_xsum2(const int32_t* __restrict__ col, const double2* __restrict__ x,
+                                              int64_t a, int64_t b, int first, int step, XAcc& sa, XAcc& sb) {
+    sa = xacc_zero();
+    sb = xacc_zero();
+    for (int64_t j = a + first; j < b; j += G * (int64_t)step) {
+        double2 v[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int64_t jj = j + (int64_t)q * step;
+            v[q] = jj < b ? __ldg(x + col[jj]) : make_double2(0.0, 0.0);
+        }
+        if (sa.E == 0) {
+            int em = exp_of(v[0].x);
+#pragma unroll
+            for (int q = 1; q < G; ++q) em = max(em, exp_of(v[q].x));
+            sa.E = em;
+        }
+        if (sb.E == 0) {
+            int em = exp_of(v[0].y);
+#pragma unroll
+            for (int q = 1; q < G; ++q) em = max(em, exp_of(v[q].y));
+            sb.E = em;
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) xacc_add(sa, v[q].x);
+#pragma unroll
+        for (int q = 0; q < G; ++q) xacc_add(sb, v[q].y);
+    }
+}
+
+__device__ __forceinline__ void strided_sum2(const int32_t* __restrict__ col, const float2* __restrict__ x, int64_t a,
+                                             int64_t b, int first, int step, float& sa, float& sb) {
+    sa = 0.0f;
+    sb = 0.0f;
+    for (int64_t j = a + first; j < b; j += 8 * (int64_t)step) {
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t jj = j + (int64_t)q * step;
+            v[q] = jj < b ? __ldg(x + col[jj]) : make_float2(0.0f, 0.0f);
+        }
+        const float ta = __fadd_rn(__fadd_rn(__fadd_rn(v[0].x, v[1].x), __fadd_rn(v[2].x, v[3].x)),
+                                   __fadd_rn(__fadd_rn(v[4].x, v[5].x), __fadd_rn(v[6].x, v[7].x)));
+        const float tb = __fadd_rn(__fadd_rn(__fadd_rn(v[0].y, v[1].y), __fadd_rn(v[2].y, v[3].y)),
+                                   __fadd_rn(__fadd_rn(v[4].y, v[5].y), __fadd_rn(v[6].y, v[7].y)));
+        sa = __fadd_rn(sa, ta);
+        sb = __fadd_rn(sb, tb);
+    }
+}
+
+template <int width>
+__device__ __forceinline__ float fsum_group(float s) {
+#pragma unroll
+    for (int off = width / 2; off; off >>= 1) s = __fadd_rn(s, __shfl_down_sync(FULL, s, off, width));
+    return s;
+}
+
+// s_i of both states from their exact row sums; at the level whose FP32
+// rounding feeds the first FP32 level, that rounding too
+__device__ __forceinline__ void store_pair64(double2* y, float2* t, int64_t u, const XAcc& sa, const XAcc& sb,
+                                             double alpha) {
+    const double a = __dmul_rn(alpha, xacc_to_double(sa)), b = __dmul_rn(alpha, xacc_to_double(sb));
+    y[u] = make_double2(a, b);
+    if (t) t[u] = make_float2(f64_to_f32_rn(a), f64_to_f32_rn(b));
+}
+
+// Level `level` >= 2 of both states over B's adjacency (store only).  Levels
+// below f32_from are FP64 (x and y double2), the others FP32 (float2; level
+// f32_from reads the FP32 roundings t_in of the level before).  Four 256-thread
+// blocks per SM: two accumulators per lane take the registers of the wider
+// gathers.
+template <typename Off>
+__global__ void __launch_bounds__(BLOCK, 4)
+spmv_pair_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L,
+                 const int32_t* __restrict__ chunk_row, const int64_t* __restrict__ chunk_first, double* P,
+                 int64_t pstride, int level, int f32_from, const float2* __restrict__ t_in, float2* t_out,
+                 double* part_a, double* part_b, double alpha, float alpha_f) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t b = blockIdx.x;
+    if (level < f32_from) {
+        const double2* __restrict__ x = (const double2*)(P + (size_t)(level - 1) * pstride);
+        double2* y = (double2*)(P + (size_t)level * pstride);
+        XAcc sa, sb;
+        if (b >= L.blk_thread) {
+            const int64_t u = L.row_thread + (b - L.blk_thread) * BLOCK + tid;
+            if (u < L.n) {
+                strided_xsum2<4>(col, x, rowptr[u], rowptr[u + 1], 0, 1, sa, sb);
+                store_pair64(y, t_out, u, sa, sb, alpha);
+            }
+        } else if (b >= L.blk_octet) {
+            const int64_t u = L.row_octet + (b - L.blk_octet) * (BLOCK / 8) + (tid >> 3);
+            const int sub = tid & 7;
+            sa = xacc_zero();
+            sb = xacc_zero();
+            if (u < L.row_thread) strided_xsum2<4>(col, x, rowptr[u], rowptr[u + 1], sub, 8, sa, sb);
+            sa = xacc_group_sum<8>(sa);
+            sb = xacc_group_sum<8>(sb);
+            if (sub == 0 && u < L.row_thread) store_pair64(y, t_out, u, sa, sb, alpha);
+        } else if (b >= L.blk_warp) {
+            const int64_t u = L.row_warp + (b - L.blk_warp) * WARPS + wid;
+            sa = xacc_zero();
+            sb = xacc_zero();
+            if (u < L.row_octet) strided_xsum2<8>(col, x, rowptr[u], rowptr[u + 1], lane, 32, sa, sb);
+            sa = xacc_group_sum<32>(sa);
+            sb = xacc_group_sum<32>(sb);
+            if (lane == 0 && u < L.row_octet) store_pair64(y, t_out, u, sa, sb, alpha);
+        } else {
+            const int64_t ch = b * WARPS + wid;
+            sa = xacc_zero();
+            sb = xacc_zero();
+            if (ch < L.chunks) {
+                const int64_t u = chunk_row[ch];
+                const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+                const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+                strided_xsum2<8>(col, x, j0, j1, lane, 32, sa, sb);
+            }
+            sa = xacc_group_sum<32>(sa);
+            sb = xacc_group_sum<32>(sb);
+            if (lane == 0 && ch < L.chunks) {
+                store_part(part_a, ch, sa);
+                store_part(part_b, ch, sb);
+            }
+        }
+    } else {
+        const float2* __restrict__ x = level == f32_from ? t_in : (const float2*)(P + (size_t)(level - 1) * pstride);
+        float2* y = (float2*)(P + (size_t)level * pstride);
+        float sa = 0.0f, sb = 0.0f;
+        if (b >= L.blk_thread) {
+            const int64_t u = L.row_thread + (b - L.blk_thread) * BLOCK + tid;
+            if (u < L.n) {
+                strided_sum2(col, x, rowptr[u], rowptr[u + 1], 0, 1, sa, sb);
+                y[u] = make_float2(__fmul_rn(alpha_f, sa), __fmul_rn(alpha_f, sb));
+            }
+        } else if (b >= L.blk_octet) {
+            const int64_t u = L.row_octet + (b - L.blk_octet) * (BLOCK / 8) + (tid >> 3);
+            const int sub = tid & 7;
+            if (u < L.row_thread) strided_sum2(col, x, rowptr[u], rowptr[u + 1], sub, 8, sa, sb);
+            sa = fsum_group<8>(sa);
+            sb = fsum_group<8>(sb);
+            if (sub == 0 && u < L.row_thread) y[u] = make_float2(__fmul_rn(alpha_f, sa), __fmul_rn(alpha_f, sb));
+        } else if (b >= L.blk_warp) {
+            const int64_t u = L.row_warp + (b - L.blk_warp) * WARPS + wid;
+            if (u < L.row_octet) strided_sum2(col, x, rowptr[u], rowptr[u + 1], lane, 32, sa, sb);
+            sa = fsum_group<32>(sa);
+            sb = fsum_group<32>(sb);
+            if (lane == 0 && u < L.row_octet) y[u] = make_float2(__fmul_rn(alpha_f, sa), __fmul_rn(alpha_f, sb));
+        } else {
+            const int64_t ch = b * WARPS + wid;
+            if (ch < L.chunks) {
+                const int64_t u = chunk_row[ch];
+                const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+                const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+                strided_sum2(col, x, j0, j1, lane, 32, sa, sb);
+            }
+            sa = fsum_group<32>(sa);
+            sb = fsum_group<32>(sb);
+            if (lane == 0 && ch < L.chunks) {
+                part_a[3 * ch] = (double)sa;  // exact for FP32 sums
+                part_b[3 * ch] = (double)sb;
+            }
+        }
+    }
+}
+
+// CHUNK rows of B's graph: each state's chunk partials merged as the
+// one-state fixup merges them
+__global__ void spmv_pair_fixup(SpmvLayout L, const int64_t* __restrict__ chunk_first,
+                                const double* __restrict__ part_a, const double* __restrict__ part_b, double* P,
+                                int64_t pstride, int level, int f32_from, float2* t_out, double alpha,
+                                float alpha_f) {
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (u >= L.row_warp) return;
+    const int64_t first = chunk_first[u], count = chunk_first[u + 1] - first;
+    if (level < f32_from) {
+        const XAcc ta = merge_chunks_warp(part_a, first, count);
+        const XAcc tb = merge_chunks_warp(part_b, first, count);
+        if ((threadIdx.x & 31) == 0) store_pair64((double2*)(P + (size_t)level * pstride), t_out, u, ta, tb, alpha);
+    } else {
+        const float ta = chunk_tree_warp(part_a, first, count);
+        const float tb = chunk_tree_warp(part_b, first, count);
+        if ((threadIdx.x & 31) == 0)
+            ((float2*)(P + (size_t)level * pstride))[u] = make_float2(__fmul_rn(alpha_f, ta), __fmul_rn(alpha_f, tb));
+    }
+}
+
+// Level 1 of both states: the degrees (A 1 = deg) in A's and in B's graph
+template <typename OffA, typename OffB>
+__global__ void pair_degree_kernel(const OffA* __restrict__ rp_a, const OffB* __restrict__ rp_b, int64_t n,
+                                   double* P, int64_t pstride, float2* t_out, double alpha) {
+    double2* y = (double2*)(P + (size_t)pstride);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const double a = __dmul_rn(alpha, (double)((int64_t)rp_a[u + 1] - (int64_t)rp_a[u]));
+        const double b = __dmul_rn(alpha, (double)((int64_t)rp_b[u + 1] - (int64_t)rp_b[u]));
+        y[u] = make_double2(a, b);
+        if (t_out) t_out[u] = make_float2(f64_to_f32_rn(a), f64_to_f32_rn(b));
+    }
+}
+
+// The rows the second batch changed (both endpoints of each update, internal
+// ids): marked in vbits; the non-CHUNK ones listed (each once)
+__global__ void pair_mark_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                                 const int32_t* __restrict__ inv, int64_t row_warp, uint32_t* vbits,
+                                 int32_t* rows, unsigned long long* nrows) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * m; e += stride) {
+        const int32_t u = inv[(e & 1) ? dst[e >> 1] : src[e >> 1]];
+        const uint32_t bit = 1u << (u & 31);
+        const uint32_t old = atomicOr(&vbits[u >> 5], bit);
+        if (!(old & bit) && (int64_t)u >= row_warp) rows[atomicAdd(nrows, 1ull)] = u;
+    }
+}
+
+// A's entries of the listed non-CHUNK rows from A's adjacency: the lane
+// partition of the one-state kernel for the row's mode, over the A entries
+// (stride 2) of the interleaved level below
+template <typename Off>
+__global__ void pair_fix_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col, SpmvLayout L,
+                                     const int32_t* __restrict__ rows, const unsigned long long* nrows_ptr,
+                                     double* P, int64_t pstride, int level, int f32_from,
+                                     const float2* __restrict__ t_in, float2* t_out, double alpha, float alpha_f) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t nrows = (int64_t)*nrows_ptr;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < nrows; w += warps) {
+        const int64_t u = rows[w];
+        const int64_t a = rowptr[u], e = rowptr[u + 1];
+        if (level >= f32_from) {
+            const float* __restrict__ x = level == f32_from ? (const float*)t_in
+                                                            : (const float*)(P + (size_t)(level - 1) * pstride);
+            float s = 0.0f;
+            if (u >= L.row_thread) {
+                if (lane == 0) s = strided_sum<float, float, 2>(col, x, a, e, 0, 1);
+            } else if (u >= L.row_octet) {
+                if (lane < 8) s = strided_sum<float, float, 2>(col, x, a, e, lane, 8);
+                s = fsum_group<8>(s);
+            } else {
+                s = strided_sum<float, float, 2>(col, x, a, e, lane, 32);
+                s = fsum_group<32>(s);
+            }
+            if (lane == 0) ((float*)(P + (size_t)level * pstride))[2 * u] = __fmul_rn(alpha_f, s);
+            continue;
+        }
+        const double* __restrict__ x = P + (size_t)(level - 1) * pstride;
+        XAcc s = xacc_zero();
+        if (u >= L.row_thread) {
+            if (lane == 0) s = strided_xsum<4, 2>(col, x, a, e, 0, 1);
+        } else if (u >= L.row_octet) {
+            if (lane < 8) s = strided_xsum<4, 2>(col, x, a, e, lane, 8);
+            s = xacc_group_sum<8>(s);
+        } else {
+            s = strided_xsum<8, 2>(col, x, a, e, lane, 32);
+            s = xacc_group_sum<32>(s);
+        }
+        if (lane == 0) {
+            const double sd = __dmul_rn(alpha, xacc_to_double(s));
+            (P + (size_t)level * pstride)[2 * u] = sd;
+            if (t_out) ((float*)t_out)[2 * u] = f64_to_f32_rn(sd);
+        }
+    }
+}
+
+// A's chunk partials of the marked CHUNK rows, with A's chunk table
+template <typename Off>
+__global__ void pair_fix_hub_chunks_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                           SpmvLayout L, const int32_t* __restrict__ chunk_row,
+                                           const int64_t* __restrict__ chunk_first, double* part,
+                                           const uint32_t* __restrict__ vbits, const double* P, int64_t pstride,
+                                           int level, int f32_from, const float2* __restrict__ t_in) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < L.chunks; ch += warps) {
+        const int64_t u = chunk_row[ch];
+        if (!visited(vbits, u)) continue;
+        const int64_t j0 = (int64_t)rowptr[u] + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
+        const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, (int64_t)rowptr[u + 1]);
+        if (level >= f32_from) {
+            const float* __restrict__ x = level == f32_from ? (const float*)t_in
+                                                            : (const float*)(P + (size_t)(level - 1) * pstride);
+            const float s = fsum_group<32>(strided_sum<float, float, 2>(col, x, j0, j1, lane, 32));
+            if (lane == 0) part[3 * ch] = (double)s;
+        } else {
+            const XAcc t = xacc_group_sum<32>(strided_xsum<8, 2>(col, P + (size_t)(level - 1) * pstride, j0, j1, lane, 32));
+            if (lane == 0) store_part(part, ch, t);
+        }
+    }
+}
+
+// A's entries of the marked CHUNK rows: A's partials merged
+__global__ void pair_fix_hub_rows_kernel(SpmvLayout L, const int64_t* __restrict__ chunk_first,
+                                         const double* __restrict__ part, const uint32_t* __restrict__ vbits,
+                                         double* P, int64_t pstride, int level, int f32_from, float2* t_out,
+                                         double alpha, float alpha_f) {
+    const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (u >= L.row_warp || !visited(vbits, u)) return;
+    const int64_t first = chunk_first[u], count = chunk_first[u + 1] - first;
+    if (level >= f32_from) {
+        const float t = chunk_tree_warp(part, first, count);
+        if ((threadIdx.x & 31) == 0) ((float*)(P + (size_t)level * pstride))[2 * u] = __fmul_rn(alpha_f, t);
+        return;
+    }
+    const XAcc t = merge_chunks_warp(part, first, count);
+    if ((threadIdx.x & 31) == 0) {
+        const double sd = __dmul_rn(alpha, xacc_to_double(t));
+        (P + (size_t)level * pstride)[2 * u] = sd;
+        if (t_out) ((float*)t_out)[2 * u] = f64_to_f32_rn(sd);
+    }
+}
+
+// state `st` (0: A, 1: B) of levels 1..r into the handle's walk slots, and of
+// the FP32 roundings into s32
+__global__ void pair_split_kernel(const double* __restrict__ P, int64_t pstride, int r, int f32_from, int st,
+                                  double* walk, IterParams p, const float* __restrict__ t_pair, float* s32) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < p.n; u += stride) {
+        for (int level = 1; level <= r; ++level) {
+            const double* lv = P + (size_t)level * pstride;
+            if (level < f32_from) walk_slot(walk, p, level)[u] = lv[2 * u + st];
+            else ((float*)walk_slot(walk, p, level))[u] = ((const float*)lv)[2 * u + st];
+        }
+        if (s32) s32[u] = t_pair[2 * u + st];
+    }
+}
+
+}  // namespace
+
+// Levels 1..r of both states (see above).  ga: A's graph (current), gb: B's
+// graph (the prepared spares, its own layout and chunk table); bsrc/bdst: the
+// second batch (original ids), m of them; P: (r + 1) interleaved slots of
+// pstride doubles; t_pair: n pairs of FP32 roundings (cert mode); part: 6 words
+// per chunk of B's graph (A's partials, then B's); vbits/rows/nrows: scratch of
+// the dynamic path (vbits and nrows cleared here).
+cudaError_t launch_pair_levels(const DeviceGraph& ga, const DeviceGraph& gb, const int32_t* bsrc,
+                               const int32_t* bdst, int64_t m, const IterParams& p, int r, int f32_from,
+                               int t_level, double* P, int64_t pstride, float* t_pair, double* part,
+                               uint32_t* vbits, int32_t* rows, unsigned long long* nrows, cudaStream_t st) {
+    const int64_t n = ga.n;
+    cudaError_t e = cudaMemsetAsync(vbits, 0, (size_t)((n + 31) / 32) * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nrows, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if (m > 0)
+        pair_mark_kernel<<<(unsigned)std::min<int64_t>((2 * m + 255) / 256, 152 * 8), 256, 0, st>>>(
+            bsrc, bdst, m, ga.inv, ga.layout.row_warp, vbits, rows, nrows);
+    const int64_t blocks_n = std::min<int64_t>(std::max<int64_t>((n + BLOCK - 1) / BLOCK, 1), 152 * 8);
+    float2* t2 = (float2*)t_pair;
+    {
+        float2* t_out = (p.cert && t_level == 1) ? t2 : nullptr;
+#define KATZ_PAIR_DEG(OA, OB)                                                                          \
+    pair_degree_kernel<OA, OB><<<(unsigned)blocks_n, BLOCK, 0, st>>>((const OA*)ga.rowptr, (const OB*)gb.rowptr, n, \
+                                                                      P, pstride, t_out, p.alpha)
+        if (ga.off64 && gb.off64) KATZ_PAIR_DEG(int64_t, int64_t);
+        else if (ga.off64) KATZ_PAIR_DEG(int64_t, int32_t);
+        else if (gb.off64) KATZ_PAIR_DEG(int32_t, int64_t);
+        else KATZ_PAIR_DEG(int32_t, int32_t);
+#undef KATZ_PAIR_DEG
+    }
+    const SpmvLayout& LB = gb.layout;
+    const SpmvLayout& LA = ga.layout;
+    double* part_a = part;
+    double* part_b = part + 3 * std::max<int64_t>(LB.chunks, 1);
+    for (int level = 2; level <= r; ++level) {
+        float2* t_out = (p.cert && level == t_level) ? t2 : nullptr;
+        if (LB.blocks_total > 0) {
+            if (gb.off64)
+                spmv_pair_kernel<int64_t><<<(unsigned)LB.blocks_total, BLOCK, 0, st>>>(
+                    (const int64_t*)gb.rowptr, gb.col, LB, gb.chunk_row, gb.chunk_first, P, pstride, level, f32_from,
+                    t2, t_out, part_a, part_b, p.alpha, p.alpha_f);
+            else
+                spmv_pair_kernel<int32_t><<<(unsigned)LB.blocks_total, BLOCK, 0, st>>>(
+                    (const int32_t*)gb.rowptr, gb.col, LB, gb.chunk_row, gb.chunk_first, P, pstride, level, f32_from,
+                    t2, t_out, part_a, part_b, p.alpha, p.alpha_f);
+        }
+        if (LB.row_warp > 0)
+            spmv_pair_fixup<<<(unsigned)((LB.row_warp * 32 + 127) / 128), 128, 0, st>>>(
+                LB, gb.chunk_first, part_a, part_b, P, pstride, level, f32_from, t_out, p.alpha, p.alpha_f);
+        // A's entries of the rows the second batch changed, from A's rows
+        if (m > 0) {
+            const unsigned fb = (unsigned)std::min<int64_t>((2 * m + 7) / 8, 152 * 32);
+            if (ga.off64)
+                pair_fix_rows_kernel<int64_t><<<fb, 256, 0, st>>>((const int64_t*)ga.rowptr, ga.col, LA, rows, nrows,
+                                                                 P, pstride, level, f32_from, t2, t_out, p.alpha,
+                                                                 p.alpha_f);
+            else
+                pair_fix_rows_kernel<int32_t><<<fb, 256, 0, st>>>((const int32_t*)ga.rowptr, ga.col, LA, rows, nrows,
+                                                                 P, pstride, level, f32_from, t2, t_out, p.alpha,
+                                                                 p.alpha_f);
+            if (LA.chunks > 0) {
+                const unsigned cb = (unsigned)std::min<int64_t>((LA.chunks + 7) / 8, 152 * 32);
+                if (ga.off64)
+                    pair_fix_hub_chunks_kernel<int64_t><<<cb, 256, 0, st>>>(
+                        (const int64_t*)ga.rowptr, ga.col, LA, ga.chunk_row, ga.chunk_first, ga.chunk_part, vbits, P,
+                        pstride, level, f32_from, t2);
+                else
+                    pair_fix_hub_chunks_kernel<int32_t><<<cb, 256, 0, st>>>(
+                        (const int32_t*)ga.rowptr, ga.col, LA, ga.chunk_row, ga.chunk_first, ga.chunk_part, vbits, P,
+                        pstride, level, f32_from, t2);
+                pair_fix_hub_rows_kernel<<<(unsigned)((LA.row_warp * 32 + 127) / 128), 128, 0, st>>>(
+                    LA, ga.chunk_first, ga.chunk_part, vbits, P, pstride, level, f32_from, t_out, p.alpha, p.alpha_f);
+            }
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_split(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int r, int f32_from,
+                              int state, const double* P, int64_t pstride, const float* t_pair, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>(std::max<int64_t>((g.n + 255) / 256, 1), 152 * 8);
+    pair_split_kernel<<<(unsigned)blocks, 256, 0, st>>>(P, pstride, r, f32_from, state, (double*)b.walk, p, t_pair,
+                                                        p.cert ? b.s32 : nullptr);
     return cudaGetLastError();
 }
 

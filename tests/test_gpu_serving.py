@@ -201,6 +201,74 @@ def test_pipelined_batches_on_one_handle_match_sequential(directed, fp32):
 
 
 @pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("graph", ["rmat", "hubs"])
+def test_two_state_pass_gives_the_bits_of_batch_by_batch_repairs(fp32, graph):
+    """pair_batches = 2: queued batches of one graph go through the two-state
+    pass (both graph states' levels in one pass, the rows the second batch
+    changed recomputed from the first state's graph).  Each answer equals the
+    batch-by-batch one, and the final walk levels and bounds are the same
+    bits.  The 'hubs' graph has rows of several 2048-arc chunks whose chunk
+    count the batches change."""
+    if graph == "rmat":
+        g = gg.rmat(13, 16, seed=81)
+    else:  # stars of 3000 to 7000 leaves joined by a sparse random graph
+        rng = np.random.default_rng(82)
+        n = 40000
+        u, v = [], []
+        for c, leaves in enumerate((7000, 5000, 4100, 3000)):
+            ls = rng.choice(np.arange(10, n), leaves, replace=False)
+            u.append(np.full(leaves, c))
+            v.append(ls)
+        u.append(rng.integers(0, n, 60000))
+        v.append(rng.integers(0, n, 60000))
+        g = gg.from_edges(n, np.concatenate(u), np.concatenate(v))
+    D, k = g.deg_max() + 2500, 40
+    batches, cur = [], g
+    for j in range(12):
+        m = [3, 800, 40, 2000][j % 4]
+        if graph == "hubs" and j % 3 == 0:  # grow and shrink the hubs across chunk boundaries
+            hub = j % 4
+            nb = set(cur.col[cur.rowptr[hub]:cur.rowptr[hub + 1]].tolist())
+            cand = [x for x in range(10, g.n) if x not in nb and x != hub][: m]
+            b = (np.full(len(cand), hub, np.int32), np.array(cand, np.int32), np.ones(len(cand), np.uint8))
+        else:
+            b = gg.update_batch(cur, m, seed=900 + j)
+        cur = gg.apply_batch(cur, *b)
+        batches.append(b)
+    opts = dict(keep_history=1, deg_bound=D, r_max=128)
+    eps = EPS
+    if fp32:
+        opts.update(precision=K.KATZ_FP32_CERT, fp32_from=3)
+        eps = 1e-4
+    seq = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(**opts))
+    seq.rank(0.0, k, eps)
+    ref = []
+    for b in batches:
+        info = seq.update(*b)
+        ref.append((info.r, seq.ranking(k).copy()))
+    h = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(**opts))
+    h.rank(0.0, k, eps)
+    srv = K.Server(workers=2, slots=8, slot_updates=4000, pair_batches=2)
+    srv.attach(h, k)
+    tickets = [srv.submit(h, *b) for b in batches]
+    paired = 0
+    for j, t in enumerate(tickets):
+        status, ids, res = srv.wait(t, timeout_ms=120000)
+        assert status == 0, (j, status)
+        assert res.info.r == ref[j][0], j
+        np.testing.assert_array_equal(ids, ref[j][1], err_msg=f"batch {j}")
+        paired += res.paired
+    srv.close()
+    assert paired >= 4  # the pass really ran
+    for a, b in zip(h.bounds(), seq.bounds()):
+        np.testing.assert_array_equal(a, b)
+    for i in range(1, ref[-1][0] + 1):
+        np.testing.assert_array_equal(h.walk(i), seq.walk(i), err_msg=f"s_{i}")
+    seq.close()
+    h.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
 def test_submit_and_poll_match_applying_the_batches_in_order(fp32):
     # katz_submit_update_batch / katz_poll: the asynchronous form of
     # katz_apply_update_batch on one handle (its private serving queue)
