@@ -96,6 +96,24 @@ typedef struct {
                               int32 while n + nnz < 2^31 - 1, int64 above; an update batch
                               that takes a handle past that limit moves it to int64 offsets
                               (one extra (n+1)-entry array during that batch) */
+    int32_t l2_fetch_bytes; /* > 0 (32, 64 or 128): during each katz_rank_static, katz_rank and
+                              katz_apply_update_batch call on the handle, the current context's
+                              maximum L2 fetch granularity (cudaLimitMaxL2FetchGranularity) is
+                              set to this many bytes, and set back to the value
+                              cudaDeviceGetLimit reported before the call when the call
+                              returns.  The limit is context-wide: other work of the process
+                              that runs during the call sees it too.  0 (default): the
+                              library leaves the limit alone.  On two GB300 machines, 64 changed
+                              a gather level with a 1 GB walk vector by -12% and by +4%;
+                              walk vectors within a few times L2 ran fastest at the default */
+    int32_t locality;      /* internal order of the rows of degree <= 16 (the low end of the
+                              degree-class order): 1 orders them inside each degree class by
+                              their anchor, the smallest internal id among their neighbours,
+                              so that the walk values one hub row gathers from them sit
+                              together and a line fetched from DRAM serves several gathers;
+                              -1 keeps them in original-id order; 0 (default): 1 when
+                              n >= 2^25 (walk vectors several times larger than L2), else -1.
+                              Results are the same bits either way. */
     int32_t reserved;      /* set to 0 */
 } katz_opts;
 

@@ -36,7 +36,8 @@ class katz_opts(ctypes.Structure):
                 ("r_max", ctypes.c_int32), ("deg_bound", ctypes.c_int64), ("frontier_abort_frac", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("use_graph", ctypes.c_int32), ("inbound", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("fp32_from", ctypes.c_int32),
-                ("offsets64", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("offsets64", ctypes.c_int32), ("l2_fetch_bytes", ctypes.c_int32),
+                ("locality", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class katz_info(ctypes.Structure):

@@ -312,6 +312,25 @@ namespace katz {
 // batch within these sizes allocates and frees nothing.
 // alpha (Sec. 3.1: 1 / (D + 1) when not given), gamma of Theorem 1 and the
 // iteration parameters of a ranking; the iteration buffers
+// katz_opts.l2_fetch_bytes: the context's maximum L2 fetch granularity for
+// the duration of one call, set back to the reported value afterwards.  A
+// random gather that misses L2 moves a whole fetch unit from DRAM; with a
+// walk vector far larger than L2 most of each unit is not used.
+L2FetchScope::L2FetchScope(const katz_handle* h) {
+    const int want = h->opts.l2_fetch_bytes;
+    if (want <= 0) return;
+    if (cudaDeviceGetLimit(&prev_, cudaLimitMaxL2FetchGranularity) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)want) == cudaSuccess) set_ = true;
+    else cudaGetLastError();
+}
+
+L2FetchScope::~L2FetchScope() {
+    if (set_ && cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, prev_) != cudaSuccess) cudaGetLastError();
+}
+
 katz_status setup_ranking(katz_handle* h, double alpha, int64_t k_eff, double eps, double& a, double& gamma) {
     const double D = (double)h->D;
     a = alpha > 0.0 ? alpha : 1.0 / (D + 1.0);
@@ -518,6 +537,8 @@ void katz_default_opts(katz_opts* o) {
     o->profile = 0;
     o->fp32_from = 0;
     o->offsets64 = 0;
+    o->l2_fetch_bytes = 0;
+    o->locality = 0;
 }
 
 const char* katz_status_string(katz_status s) {
@@ -745,6 +766,38 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     h->classes_exact = true;
     // rows of degree > 2048 / > 128 / > 16 come first: classes >= 13 / >= 9 / >= 6
     const int64_t row_warp = (int64_t)hv.cs[12], row_octet = (int64_t)hv.cs[8], row_thread = (int64_t)hv.cs[5];
+    // the low-degree rows reordered inside their classes by anchor (katz_opts.locality), once the
+    // whole column array is on the device; the new offsets follow the new order
+    const bool locality = h->opts.locality > 0 || (h->opts.locality == 0 && n >= ((int64_t)1 << 25));
+    if (locality && n - row_thread > 1) {
+        const int64_t m = n - row_thread, cnt = 256 * radix_tiles(m);
+        RadixBuffers rs;
+        auto drop_rs = [&]() {
+            for (int q = 0; q < 2; ++q) {
+                dfree(h, rs.hi[q]);
+                dfree(h, rs.lo[q]);
+                dfree(h, rs.val[q]);
+            }
+            dfree(h, rs.counts);
+            dfree(h, rs.offs);
+            dfree(h, rs.sums);
+        };
+        if ((e = dmalloc(h, &rs.hi[0], (size_t)m)) != cudaSuccess || (e = dmalloc(h, &rs.hi[1], (size_t)m)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.lo[0], (size_t)m)) != cudaSuccess || (e = dmalloc(h, &rs.lo[1], (size_t)m)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.val[0], (size_t)m)) != cudaSuccess || (e = dmalloc(h, &rs.val[1], (size_t)m)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.counts, (size_t)cnt)) != cudaSuccess || (e = dmalloc(h, &rs.offs, (size_t)cnt)) != cudaSuccess ||
+            (e = dmalloc(h, &rs.sums, (size_t)scan_blocks(cnt))) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(h->stream, ev[slices - 1], 0)) != cudaSuccess ||
+            (e = locality_order(rp64, col0, n, row_thread, g.perm, g.inv, rs, h->stream)) != cudaSuccess ||
+            (e = relabel_offsets(rp64, g.perm, n, deg_new, rp_new, sums, h->stream)) != cudaSuccess) {
+            drop_rs();
+            drop_staging();
+            st = cuda_fail(h, e, "locality order");
+            katz_destroy(h);
+            return st;
+        }
+        drop_rs();
+    }
     // chunk table of the CHUNK rows, on the device (every CHUNK row holds more
     // than CHUNK_ARCS arcs, so the count stays below nnz / CHUNK_ARCS + row_warp)
     const int64_t chunks_cap = nnz / CHUNK_ARCS + row_warp + 1;
@@ -823,6 +876,7 @@ katz_status rank_static_fp64(katz_handle* h, katz_info* info) {
 // buffers of an FP32 handle hold FP64 levels too).
 katz_status katz_rank_static(katz_h h, double alpha, int64_t k, double eps, katz_info* info) {
     if (!h) return KATZ_EINVAL;
+    const L2FetchScope fetch(h);
     katz_status st = rank_static_once(h, alpha, k, eps, info);
     if (st != KATZ_EPRECISION || h->opts.precision != KATZ_FP32_CERT_AUTO) return st;
     const int64_t launches = h->launches;
@@ -937,6 +991,7 @@ katz_status katz_rank(katz_h h, double alpha, int32_t criterion, int64_t k, cons
                       katz_info* info) {
     if (!h) return KATZ_EINVAL;
     if (criterion == KATZ_CRIT_TOPK) return katz_rank_static(h, alpha, k, eps, info);
+    const L2FetchScope fetch(h);
     h->err.clear();
     if (criterion != KATZ_CRIT_RANKING && criterion != KATZ_CRIT_SCORE && criterion != KATZ_CRIT_PAIR)
         return fail(h, KATZ_EINVAL, "unknown criterion");
@@ -1659,6 +1714,7 @@ extern "C" {
 katz_status katz_apply_update_batch(katz_h h, const int32_t* src, const int32_t* dst, const uint8_t* is_insert,
                                     int64_t m, katz_info* info) {
     if (!h) return KATZ_EINVAL;
+    const L2FetchScope fetch(h);
     h->err.clear();
     katz_status st = update_allowed(h);
     if (st != KATZ_OK) return st;

@@ -232,6 +232,9 @@ struct RadixBuffers {
     int64_t* sums = nullptr;    // scan scratch
 };
 int64_t radix_tiles(int64_t n);
+cudaError_t radix_sort_passes(RadixBuffers& rs, int64_t n, int first, int last, int& cur, cudaStream_t st);
+cudaError_t locality_order(const int64_t* rowptr, const int32_t* col, int64_t n, int64_t start, int32_t* perm,
+                           int32_t* inv, RadixBuffers& rs, cudaStream_t st);
 cudaError_t launch_crit_init(const IterBuffers& b, cudaStream_t st);
 cudaError_t launch_score_check(const IterBuffers& b, const IterParams& p, cudaStream_t st);
 cudaError_t launch_pair_check(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int32_t oa, int32_t ob,

@@ -214,6 +214,23 @@ cudaError_t launch_ranking_check(const DeviceGraph& g, const IterBuffers& b, con
     return cudaGetLastError();
 }
 
+// Stable LSD passes first..last (8-bit digits; 0-3 over lo, 4-11 over hi) of
+// the (hi, lo, val) triples in rs buffer `cur`, n of them; cur ends on the
+// buffer that holds the result.
+cudaError_t radix_sort_passes(RadixBuffers& rs, int64_t n, int first, int last, int& cur, cudaStream_t st) {
+    const int64_t tiles = radix_tiles(n);
+    for (int pass = first; pass <= last; ++pass) {
+        rs_hist_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(rs.hi[cur], rs.lo[cur], n, pass, rs.counts, tiles);
+        cudaError_t e = exclusive_scan_i64(rs.counts, 256 * tiles, rs.offs, rs.sums, st);
+        if (e != cudaSuccess) return e;
+        rs_scatter_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(rs.hi[cur], rs.lo[cur], rs.val[cur], n, pass, rs.offs,
+                                                                  tiles, rs.hi[1 - cur], rs.lo[1 - cur],
+                                                                  rs.val[1 - cur]);
+        cur = 1 - cur;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize_crit(const IterBuffers& b, const IterParams& p, cudaStream_t st) {
     finalize_crit_kernel<<<1, 1, 0, st>>>(b.trace, b.ctrl, p);
     return cudaGetLastError();

@@ -119,6 +119,20 @@ struct katz_handle {
 };
 
 namespace katz {
+// the context's maximum L2 fetch granularity for the duration of one call
+// (katz_opts.l2_fetch_bytes > 0), set back to the reported value afterwards
+class L2FetchScope {
+  public:
+    explicit L2FetchScope(const katz_handle* h);
+    ~L2FetchScope();
+    L2FetchScope(const L2FetchScope&) = delete;
+    L2FetchScope& operator=(const L2FetchScope&) = delete;
+
+  private:
+    size_t prev_ = 0;
+    bool set_ = false;
+};
+
 constexpr size_t CTRL_BYTES = (sizeof(Ctrl) + 255) / 256 * 256;
 constexpr size_t H_SMALL = 4096;
 

@@ -312,6 +312,72 @@ cudaError_t relabel_by_degree_class(const int64_t* rowptr64, int64_t n, uint32_t
     return cudaGetLastError();
 }
 
+namespace {
+
+// Locality order of the low-degree end (internal ids >= start): the key of
+// each vertex is its degree class (in the class order) and its anchor, the
+// smallest internal id among its neighbours (the neighbour whose row the SpMV
+// reaches first; n if none); val is its internal id so far.  Column ids
+// outside [0, n) are skipped here and refused by the remap that follows.
+__global__ void anchor_key_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  const int32_t* __restrict__ perm, const int32_t* __restrict__ inv, int64_t n,
+                                  int64_t start, uint64_t* hi, uint32_t* lo, int32_t* val) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n - start; i += stride) {
+        const int64_t u = start + i;
+        const int32_t v = perm[u];
+        const int64_t a = rowptr[v], b = rowptr[v + 1];
+        uint32_t m = (uint32_t)n;
+        for (int64_t j = a; j < b; ++j) {
+            const int32_t c = col[j];
+            if (c >= 0 && (int64_t)c < n) m = min(m, (uint32_t)inv[c]);
+        }
+        hi[i] = (uint64_t)(NUM_CLASSES - 1 - degree_class(b - a));
+        lo[i] = m;
+        val[i] = (int32_t)u;
+    }
+}
+
+// perm_new[start + i] = perm[sorted[i]], and inv of those vertices
+__global__ void locality_compose_kernel(const int32_t* __restrict__ sorted, int64_t n, int64_t start,
+                                        const int32_t* __restrict__ perm, int32_t* perm_tail) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n - start; i += stride)
+        perm_tail[i] = perm[sorted[i]];
+}
+
+__global__ void locality_install_kernel(const int32_t* __restrict__ perm_tail, int64_t n, int64_t start, int32_t* perm,
+                                        int32_t* inv) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n - start; i += stride) {
+        const int32_t v = perm_tail[i];
+        perm[start + i] = v;
+        inv[v] = (int32_t)(start + i);
+    }
+}
+
+}  // namespace
+
+// Reorder the vertices from internal id `start` on (the rows of degree <= 16,
+// already grouped by degree class) within their classes by anchor, ties kept
+// in their current order (a stable sort): the walk values that one hub row
+// gathers from low-degree rows then sit together, so a line fetched from DRAM
+// serves several of its gathers.  perm/inv are updated in place.  rs: radix
+// buffers for n - start entries.  rowptr/col: the input CSR (original ids).
+cudaError_t locality_order(const int64_t* rowptr, const int32_t* col, int64_t n, int64_t start, int32_t* perm,
+                           int32_t* inv, RadixBuffers& rs, cudaStream_t st) {
+    const int64_t m = n - start;
+    if (m <= 1) return cudaSuccess;
+    anchor_key_kernel<<<grid_for(m, 256), 256, 0, st>>>(rowptr, col, perm, inv, n, start, rs.hi[0], rs.lo[0],
+                                                         rs.val[0]);
+    int cur = 0;
+    cudaError_t e = radix_sort_passes(rs, m, 0, 4, cur, st);  // the anchor (4 digits), then the class
+    if (e != cudaSuccess) return e;
+    locality_compose_kernel<<<grid_for(m, 256), 256, 0, st>>>(rs.val[cur], n, start, perm, rs.val[1 - cur]);
+    locality_install_kernel<<<grid_for(m, 256), 256, 0, st>>>(rs.val[1 - cur], n, start, perm, inv);
+    return cudaGetLastError();
+}
+
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* sums_scratch,
                                cudaStream_t st) {
     const int64_t nb = (n + SCAN_THREADS - 1) / SCAN_THREADS;

@@ -21,9 +21,10 @@ def _dev(a):
 
 
 def run_gpu(g, alpha, k, eps, *, undirected=True, keep_history=True, r_max=256, on_device=True, use_graph=1,
-            precision=0, profile=0):
+            precision=0, profile=0, locality=0):
     opts = K.katz_default_opts(undirected=1 if undirected else 0, keep_history=1 if keep_history else 0,
-                               r_max=r_max, use_graph=use_graph, precision=precision, profile=profile)
+                               r_max=r_max, use_graph=use_graph, precision=precision, profile=profile,
+                               locality=locality)
     rp, cl = (_dev(g.rowptr), _dev(g.col)) if on_device else (g.rowptr, g.col)
     h = K.Katz(rp, cl, opts)
     info = h.rank(alpha, k, eps)
@@ -213,3 +214,58 @@ def test_large_host_csr_with_a_bad_column_entry_in_a_late_slice_is_rejected():
     with pytest.raises(K.KatzError) as e:
         K.Katz(rp, g.col)
     assert e.value.name == "KATZ_EINVAL"
+
+
+def test_l2_fetch_option_keeps_the_bits_and_restores_the_limit():
+    """katz_opts.l2_fetch_bytes changes the context's maximum L2 fetch
+    granularity only during the call: the ranking and bounds are the same
+    bits, and the limit reads as before afterwards."""
+    import ctypes
+
+    cu = ctypes.CDLL("libcuda.so.1")
+
+    def limit():
+        out = ctypes.c_size_t(0)
+        assert cu.cuCtxGetLimit(ctypes.byref(out), ctypes.c_int(5)) == 0  # CU_LIMIT_MAX_L2_FETCH_GRANULARITY
+        return int(out.value)
+
+    g = gg.rmat(14, 16, seed=9)
+    torch.zeros(1, device="cuda")
+    before = limit()
+    out = []
+    for fetch in (0, 64, 32):
+        h = K.Katz(_dev(g.rowptr), _dev(g.col), K.katz_default_opts(l2_fetch_bytes=fetch))
+        h.rank(0.0, 200, 1e-9)
+        out.append((h.ranking(200), *h.bounds()[:2]))
+        h.close()
+        assert limit() == before
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_locality_order_gives_the_same_bits(precision):
+    """katz_opts.locality = 1 reorders the low-degree rows by anchor (the
+    internal order only): ranking, bounds and every walk level are the same
+    bits as in the plain degree-class order, also after update batches, and
+    the FP64 path still matches the oracle."""
+    g = gg.chung_lu(1 << 15, 16.0, 2.1, seed=95)
+    D, k, eps = g.deg_max() + 32, 100, 1e-9
+    st = gg.stream(g, 3, seed=96, max_size=400, deg_bound=D)
+    res = []
+    for loc in (-1, 1):
+        h = K.Katz(_dev(g.rowptr), _dev(g.col),
+                   K.katz_default_opts(locality=loc, precision=precision, keep_history=1, deg_bound=D))
+        info = h.rank(0.0, k, eps)
+        out = [h.ranking(k), *h.bounds()[:2], *[h.walk(i) for i in range(1, info.r + 1)]]
+        for j in range(len(st)):
+            h.update(*st.batch(j))
+            out += [h.ranking(k), *h.bounds()[:2]]
+        res.append(out)
+        h.close()
+    assert len(res[0]) == len(res[1])
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+    if precision == 0:
+        check_parity(g, 0.0, k, eps, locality=1)
