@@ -726,13 +726,12 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
         KCHK2(launch_validate_csr(g64, d_bad, d_degmax, h->stream), "validate");
     }
     // relabel: stable counting sort by degree class, then the new offsets
-    const int nb = relabel_blocks(n);
-    uint32_t* counts = nullptr;
+    int64_t* counts = nullptr;
     uint64_t* class_start = nullptr;
     int64_t* deg_new = nullptr;
     int64_t* rp_new = nullptr;
     int64_t* sums = nullptr;
-    KCHK2(dmalloc(h, &counts, (size_t)NUM_CLASSES * nb), "cudaMalloc counts");
+    KCHK2(dmalloc(h, &counts, (size_t)relabel_scratch(n)), "cudaMalloc counts");
     KCHK2(dmalloc(h, &class_start, NUM_CLASSES), "cudaMalloc");
     KCHK2(dmalloc(h, &g.perm, (size_t)n), "cudaMalloc perm");
     KCHK2(dmalloc(h, &g.inv, (size_t)n), "cudaMalloc inv");
@@ -740,7 +739,7 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     KCHK2(dmalloc(h, &rp_new, (size_t)n + 1), "cudaMalloc");
     KCHK2(dmalloc(h, &sums, (size_t)scan_blocks(n + 1)), "cudaMalloc");
     KCHK2(dmalloc(h, &g.col, (size_t)nnz), "cudaMalloc col");
-    KCHK2(relabel_by_degree_class(rp64, n, counts, nb, g.perm, g.inv, class_start, h->stream), "relabel");
+    KCHK2(relabel_by_degree_class(rp64, n, counts, g.perm, g.inv, class_start, h->stream), "relabel");
     KCHK2(relabel_offsets(rp64, g.perm, n, deg_new, rp_new, sums, h->stream), "relabel offsets");
     // small reads go through pinned memory: a pageable copy would queue
     // behind the column slices still in flight
@@ -766,38 +765,6 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     h->classes_exact = true;
     // rows of degree > 2048 / > 128 / > 16 come first: classes >= 13 / >= 9 / >= 6
     const int64_t row_warp = (int64_t)hv.cs[12], row_octet = (int64_t)hv.cs[8], row_thread = (int64_t)hv.cs[5];
-    // the low-degree rows reordered inside their classes by anchor (katz_opts.locality), once the
-    // whole column array is on the device; the new offsets follow the new order
-    const bool locality = h->opts.locality > 0 || (h->opts.locality == 0 && n >= ((int64_t)1 << 25));
-    if (locality && n - row_thread > 1) {
-        const int64_t m = n - row_thread, cnt = 256 * radix_tiles(m);
-        RadixBuffers rs;
-        auto drop_rs = [&]() {
-            for (int q = 0; q < 2; ++q) {
-                dfree(h, rs.hi[q]);
-                dfree(h, rs.lo[q]);
-                dfree(h, rs.val[q]);
-            }
-            dfree(h, rs.counts);
-            dfree(h, rs.offs);
-            dfree(h, rs.sums);
-        };
-        if ((e = dmalloc(h, &rs.hi[0], (size_t)m)) != cudaSuccess || (e = dmalloc(h, &rs.hi[1], (size_t)m)) != cudaSuccess ||
-            (e = dmalloc(h, &rs.lo[0], (size_t)m)) != cudaSuccess || (e = dmalloc(h, &rs.lo[1], (size_t)m)) != cudaSuccess ||
-            (e = dmalloc(h, &rs.val[0], (size_t)m)) != cudaSuccess || (e = dmalloc(h, &rs.val[1], (size_t)m)) != cudaSuccess ||
-            (e = dmalloc(h, &rs.counts, (size_t)cnt)) != cudaSuccess || (e = dmalloc(h, &rs.offs, (size_t)cnt)) != cudaSuccess ||
-            (e = dmalloc(h, &rs.sums, (size_t)scan_blocks(cnt))) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(h->stream, ev[slices - 1], 0)) != cudaSuccess ||
-            (e = locality_order(rp64, col0, n, row_thread, g.perm, g.inv, rs, h->stream)) != cudaSuccess ||
-            (e = relabel_offsets(rp64, g.perm, n, deg_new, rp_new, sums, h->stream)) != cudaSuccess) {
-            drop_rs();
-            drop_staging();
-            st = cuda_fail(h, e, "locality order");
-            katz_destroy(h);
-            return st;
-        }
-        drop_rs();
-    }
     // chunk table of the CHUNK rows, on the device (every CHUNK row holds more
     // than CHUNK_ARCS arcs, so the count stays below nnz / CHUNK_ARCS + row_warp)
     const int64_t chunks_cap = nnz / CHUNK_ARCS + row_warp + 1;
@@ -808,15 +775,52 @@ katz_status katz_create_csr(katz_h* out, int64_t n, int64_t nnz, const int64_t* 
     h->chunk_part_cap = chunks_cap;
     KCHK2(build_chunk_table(rp_new, row_warp, deg_new, sums, g.chunk_first, g.chunk_row, d_bad + 2, h->stream),
           "chunk table");
-    // the column array, slice by slice as it arrives (entries range-checked);
-    // the CHUNK rows once all of it is there
+    // the column array, slice by slice as it arrives (entries range-checked),
+    // renamed into degree-class order
     for (int i = 0; i < slices; ++i) {
         KCHK2(cudaStreamWaitEvent(h->stream, ev[i], 0), "event");
         KCHK2(remap_src_rows(rp64, col0, g.inv, rp_new, vcut[i], vcut[i + 1], n, row_warp, g.col, d_bad + 1,
                              h->stream), "relabel rows");
+        KCHK2(remap_hub_chunks(rp64, col0, g.perm, g.inv, rp_new, g.chunk_row, g.chunk_first, row_warp, chunks_cap,
+                               vcut[i], vcut[i + 1], n, g.col, d_bad + 1, h->stream), "relabel hub rows");
     }
-    KCHK2(remap_hub_chunks(rp64, col0, g.perm, g.inv, rp_new, g.chunk_row, g.chunk_first, row_warp, chunks_cap, n,
-                           g.col, d_bad + 1, h->stream), "relabel hub rows");
+    // then the low-degree rows reordered inside their classes by anchor
+    // (katz_opts.locality); the rows of degree > 16 keep their places, the
+    // staging column array holds the old tail
+    const bool locality = (h->opts.locality > 0 || (h->opts.locality == 0 && n >= ((int64_t)1 << 25))) &&
+                          n - row_thread > 1;
+    if (locality) {
+        const int64_t m = n - row_thread, cnt = 256 * radix_tiles(m);
+        RadixBuffers rs;
+        int64_t* rp_fin = nullptr;
+        e = dmalloc(h, &rp_fin, (size_t)n + 1);
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+            if ((e = dmalloc(h, &rs.hi[q], (size_t)m)) == cudaSuccess && (e = dmalloc(h, &rs.lo[q], (size_t)m)) == cudaSuccess)
+                e = dmalloc(h, &rs.val[q], (size_t)m);
+        if (e == cudaSuccess && (e = dmalloc(h, &rs.counts, (size_t)cnt)) == cudaSuccess &&
+            (e = dmalloc(h, &rs.offs, (size_t)cnt)) == cudaSuccess)
+            e = dmalloc(h, &rs.sums, (size_t)scan_blocks(cnt));
+        if (e == cudaSuccess)
+            e = locality_order(n, nnz, row_thread, rp_new, g.col, g.perm, g.inv, deg_new, rp_fin, col0, sums, rs,
+                               h->stream);
+        for (int q = 0; q < 2; ++q) {
+            dfree(h, rs.hi[q]);
+            dfree(h, rs.lo[q]);
+            dfree(h, rs.val[q]);
+        }
+        dfree(h, rs.counts);
+        dfree(h, rs.offs);
+        dfree(h, rs.sums);
+        dfree(h, rp_new);
+        rp_new = rp_fin;
+        if (e != cudaSuccess) {
+            dfree(h, rp_new);
+            drop_staging();
+            st = cuda_fail(h, e, "locality order");
+            katz_destroy(h);
+            return st;
+        }
+    }
     if (g.off64) {
         g.rowptr = rp_new;
         rp_new = nullptr;

@@ -233,8 +233,11 @@ struct RadixBuffers {
 };
 int64_t radix_tiles(int64_t n);
 cudaError_t radix_sort_passes(RadixBuffers& rs, int64_t n, int first, int last, int& cur, cudaStream_t st);
-cudaError_t locality_order(const int64_t* rowptr, const int32_t* col, int64_t n, int64_t start, int32_t* perm,
-                           int32_t* inv, RadixBuffers& rs, cudaStream_t st);
+// anchor order of the low-degree rows (internal ids >= start) of a graph
+// already renamed into degree-class order; see katz_relabel.cu
+cudaError_t locality_order(int64_t n, int64_t nnz, int64_t start, const int64_t* rowptr1, int32_t* col1,
+                           int32_t* perm, int32_t* inv, int64_t* deg, int64_t* rowptr_fin, int32_t* tail_copy,
+                           int64_t* sums, RadixBuffers& rs, cudaStream_t st);
 cudaError_t launch_crit_init(const IterBuffers& b, cudaStream_t st);
 cudaError_t launch_score_check(const IterBuffers& b, const IterParams& p, cudaStream_t st);
 cudaError_t launch_pair_check(const DeviceGraph& g, const IterBuffers& b, const IterParams& p, int32_t oa, int32_t ob,
@@ -265,8 +268,10 @@ SpmvLayout make_layout(int64_t n, int64_t row_warp, int64_t row_octet, int64_t r
 int relabel_blocks(int64_t n);
 int64_t scan_blocks(int64_t n);
 int degree_class_host(int64_t d);
-cudaError_t relabel_by_degree_class(const int64_t* rowptr64, int64_t n, uint32_t* counts_scratch, int nb,
-                                    int32_t* perm, int32_t* inv, uint64_t* class_start_dev, cudaStream_t st);
+// stable counting sort of the ids by degree class; scratch: relabel_scratch(n) int64
+int64_t relabel_scratch(int64_t n);
+cudaError_t relabel_by_degree_class(const int64_t* rowptr64, int64_t n, int64_t* scratch, int32_t* perm, int32_t* inv,
+                                    uint64_t* class_start_dev, cudaStream_t st);
 // in-degrees of a CSR's columns (cnt: n int64, zero on entry)
 cudaError_t launch_indegree(const int32_t* col, int64_t nnz, int64_t* cnt, cudaStream_t st);
 // the reverse graph of a validated CSR (int64 offsets): rowptr_rev[n+1],
@@ -279,14 +284,14 @@ cudaError_t exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64
 cudaError_t relabel_offsets(const int64_t* rowptr64, const int32_t* perm, int64_t n, int64_t* deg_new_scratch,
                             int64_t* rowptr_new, int64_t* sums_scratch, cudaStream_t st);
 // arcs of the original rows [v0, v1) that do not become CHUNK rows, renamed
-// into their new rows; then those of the CHUNK rows, chunk by chunk
+// into their new rows; then those of the CHUNK rows among them, chunk by chunk
 cudaError_t remap_src_rows(const int64_t* rowptr64, const int32_t* col, const int32_t* inv, const int64_t* rowptr_new,
                            int64_t v0, int64_t v1, int64_t n, int64_t row_warp, int32_t* col_new,
                            unsigned long long* bad, cudaStream_t st);
 cudaError_t remap_hub_chunks(const int64_t* rowptr64, const int32_t* col, const int32_t* perm, const int32_t* inv,
                              const int64_t* rowptr_new, const int32_t* chunk_row, const int64_t* chunk_first,
-                             int64_t row_warp, int64_t chunks_cap, int64_t n, int32_t* col_new,
-                             unsigned long long* bad, cudaStream_t st);
+                             int64_t row_warp, int64_t chunks_cap, int64_t v0, int64_t v1, int64_t n,
+                             int32_t* col_new, unsigned long long* bad, cudaStream_t st);
 // chunk table of the CHUNK rows from the new offsets: chunk_first (row_warp + 1
 // entries, exclusive scan of the chunk counts), chunk_row, and the largest count
 cudaError_t build_chunk_table(const int64_t* rowptr_new, int64_t row_warp, int64_t* cnt_scratch, int64_t* sums_scratch,

@@ -59,38 +59,69 @@ rs_hist_kernel(const uint64_t* __restrict__ hi, const uint32_t* __restrict__ lo,
 }
 
 // stable scatter: tile b's elements with digit d go, in their order, to
-// offs[d * blocks + b] onwards
+// offs[d * blocks + b] onwards.  The tile is first ordered by digit in shared
+// memory (its digit counts come from the histogram pass), then written out in
+// that order, so that consecutive threads write consecutive slots of one
+// digit's run instead of one slot each in up to 256 runs.
 __global__ void __launch_bounds__(RS_THREADS)
 rs_scatter_kernel(const uint64_t* __restrict__ hi, const uint32_t* __restrict__ lo, const int32_t* __restrict__ val,
-                  int64_t n, int pass, const int64_t* __restrict__ offs, int64_t blocks, uint64_t* hi2,
-                  uint32_t* lo2, int32_t* val2) {
-    __shared__ long long base[256];
+                  int64_t n, int pass, const int64_t* __restrict__ counts, const int64_t* __restrict__ offs,
+                  int64_t blocks, uint64_t* __restrict__ hi2, uint32_t* __restrict__ lo2, int32_t* __restrict__ val2) {
+    __shared__ uint64_t s_hi[RS_TILE];
+    __shared__ uint32_t s_lo[RS_TILE];
+    __shared__ int32_t s_val[RS_TILE];
+    __shared__ uint8_t s_d[RS_TILE];
+    __shared__ long long gbase[256];
+    __shared__ int lstart[256], run[256];
     __shared__ int wc[RS_WARPS][256];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    base[tid] = offs[(int64_t)tid * blocks + blockIdx.x];
     const int64_t tile = (int64_t)blockIdx.x * RS_TILE;
+    const int in_tile = (int)min((int64_t)RS_TILE, n - tile);
+    // exclusive scan of the tile's digit counts: each digit's first local slot
+    int c = (int)counts[(int64_t)tid * blocks + blockIdx.x];
+    int incl = c;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) wc[0][wid] = incl;
+    gbase[tid] = offs[(int64_t)tid * blocks + blockIdx.x];
+    __syncthreads();
+    int wsum = 0;
+    for (int w = 0; w < wid; ++w) wsum += wc[0][w];
+    lstart[tid] = wsum + incl - c;
+    run[tid] = wsum + incl - c;
+    __syncthreads();
     for (int q = 0; q < RS_ROUNDS; ++q) {
         for (int w = 0; w < RS_WARPS; ++w) wc[w][tid] = 0;
         __syncthreads();
-        const int64_t i = tile + q * RS_THREADS + tid;
-        const bool valid = i < n;
-        const int d = valid ? digit(hi, lo, i, pass) : 256;
+        const int li = q * RS_THREADS + tid;
+        const bool valid = li < in_tile;
+        const int d = valid ? digit(hi, lo, tile + li, pass) : 256;
         const unsigned peers = __match_any_sync(FULL, d);
         const int rank = __popc(peers & ((1u << lane) - 1u));
         if (valid && lane == __ffs(peers) - 1) wc[wid][d] = __popc(peers);
         __syncthreads();
         if (valid) {
-            long long pos = base[d] + rank;
+            int pos = run[d] + rank;
             for (int w = 0; w < wid; ++w) pos += wc[w][d];
-            hi2[pos] = hi[i];
-            lo2[pos] = lo[i];
-            val2[pos] = val[i];
+            s_hi[pos] = hi[tile + li];
+            s_lo[pos] = lo[tile + li];
+            s_val[pos] = val[tile + li];
+            s_d[pos] = (uint8_t)d;
         }
         __syncthreads();
-        long long add = 0;
+        int add = 0;
         for (int w = 0; w < RS_WARPS; ++w) add += wc[w][tid];
-        base[tid] += add;
+        run[tid] += add;
         __syncthreads();
+    }
+    for (int j = tid; j < in_tile; j += RS_THREADS) {
+        const int d = s_d[j];
+        const long long pos = gbase[d] + (j - lstart[d]);
+        hi2[pos] = s_hi[j];
+        lo2[pos] = s_lo[j];
+        val2[pos] = s_val[j];
     }
 }
 
@@ -205,8 +236,8 @@ cudaError_t launch_ranking_check(const DeviceGraph& g, const IterBuffers& b, con
         rs_hist_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(rs.hi[cur], rs.lo[cur], n, pass, rs.counts, tiles);
         cudaError_t e = exclusive_scan_i64(rs.counts, 256 * tiles, rs.offs, rs.sums, st);
         if (e != cudaSuccess) return e;
-        rs_scatter_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(rs.hi[cur], rs.lo[cur], rs.val[cur], n, pass, rs.offs,
-                                                                  tiles, rs.hi[1 - cur], rs.lo[1 - cur],
+        rs_scatter_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(rs.hi[cur], rs.lo[cur], rs.val[cur], n, pass,
+                                                                  rs.counts, rs.offs, tiles, rs.hi[1 - cur], rs.lo[1 - cur],
                                                                   rs.val[1 - cur]);
         cur = 1 - cur;
     }
@@ -223,8 +254,8 @@ cudaError_t radix_sort_passes(RadixBuffers& rs, int64_t n, int first, int last, 
         rs_hist_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(rs.hi[cur], rs.lo[cur], n, pass, rs.counts, tiles);
         cudaError_t e = exclusive_scan_i64(rs.counts, 256 * tiles, rs.offs, rs.sums, st);
         if (e != cudaSuccess) return e;
-        rs_scatter_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(rs.hi[cur], rs.lo[cur], rs.val[cur], n, pass, rs.offs,
-                                                                  tiles, rs.hi[1 - cur], rs.lo[1 - cur],
+        rs_scatter_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(rs.hi[cur], rs.lo[cur], rs.val[cur], n, pass,
+                                                                  rs.counts, rs.offs, tiles, rs.hi[1 - cur], rs.lo[1 - cur],
                                                                   rs.val[1 - cur]);
         cur = 1 - cur;
     }

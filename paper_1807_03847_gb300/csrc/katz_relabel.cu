@@ -27,9 +27,11 @@ __device__ __forceinline__ int degree_class(int64_t d) {
     return (d == 1) ? 1 : 65 - __clzll((unsigned long long)(d - 1)) + 0;  // ceil(log2 d) + 1
 }
 
-// counts[c * nb + b] = vertices of class c in block b
+// counts[(NUM_CLASSES - 1 - c) * nb + b] = vertices of class c in block b:
+// the classes from the highest down, so that one exclusive scan of the array
+// gives every (class, block) its first slot
 template <typename Off>
-__global__ void class_hist_kernel(const Off* __restrict__ rowptr, int64_t n, int nb, uint32_t* counts) {
+__global__ void class_hist_kernel(const Off* __restrict__ rowptr, int64_t n, int nb, int64_t* counts) {
     __shared__ uint32_t h[NUM_CLASSES];
     const int tid = threadIdx.x;
     if (tid < NUM_CLASSES) h[tid] = 0;
@@ -37,47 +39,21 @@ __global__ void class_hist_kernel(const Off* __restrict__ rowptr, int64_t n, int
     const int64_t v = (int64_t)blockIdx.x * RL_THREADS + tid;
     if (v < n) atomicAdd(&h[degree_class((int64_t)rowptr[v + 1] - (int64_t)rowptr[v])], 1u);
     __syncthreads();
-    if (tid < NUM_CLASSES) counts[(size_t)tid * nb + blockIdx.x] = h[tid];
+    if (tid < NUM_CLASSES) counts[(size_t)(NUM_CLASSES - 1 - tid) * nb + blockIdx.x] = h[tid];
 }
 
-// exclusive scan, in place, of counts laid out class-major but visited from
-// the highest class down: offset(c, b) = sum over classes > c + blocks < b of class c
-__global__ void class_scan_kernel(uint32_t* counts, int nb, uint64_t* class_start) {
-    __shared__ unsigned long long part[SCAN_THREADS];
-    const int tid = threadIdx.x;
-    const int64_t total = (int64_t)NUM_CLASSES * nb;
-    const int64_t chunk = (total + SCAN_THREADS - 1) / SCAN_THREADS;
-    // element e in visit order maps to class NUM_CLASSES-1 - e / nb, block e % nb
-    auto at = [&](int64_t e) -> uint32_t& {
-        const int64_t c = NUM_CLASSES - 1 - e / nb;
-        return counts[c * nb + e % nb];
-    };
-    unsigned long long s = 0;
-    for (int64_t e = tid * chunk; e < min(total, (int64_t)(tid + 1) * chunk); ++e) s += at(e);
-    part[tid] = s;
-    __syncthreads();
-    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
-        const unsigned long long a = tid >= off ? part[tid - off] : 0ull;
-        __syncthreads();
-        part[tid] += a;
-        __syncthreads();
-    }
-    unsigned long long run = tid ? part[tid - 1] : 0ull;
-    for (int64_t e = tid * chunk; e < min(total, (int64_t)(tid + 1) * chunk); ++e) {
-        const uint32_t x = at(e);
-        if (e % nb == 0) class_start[NUM_CLASSES - 1 - e / nb] = run;
-        at(e) = (uint32_t)run;
-        run += x;
-    }
+__global__ void class_start_kernel(const int64_t* __restrict__ offs, int nb, uint64_t* class_start) {
+    const int c = threadIdx.x;
+    if (c < NUM_CLASSES) class_start[c] = (uint64_t)offs[(size_t)(NUM_CLASSES - 1 - c) * nb];
 }
 
 // stable scatter: within a block, vertices of the same class keep id order
 template <typename Off>
-__global__ void class_scatter_kernel(const Off* __restrict__ rowptr, int64_t n, int nb, const uint32_t* counts,
+__global__ void class_scatter_kernel(const Off* __restrict__ rowptr, int64_t n, int nb, const int64_t* offs,
                                      int32_t* perm, int32_t* inv) {
     __shared__ uint32_t base[NUM_CLASSES];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid < NUM_CLASSES) base[tid] = counts[(size_t)tid * nb + blockIdx.x];
+    if (tid < NUM_CLASSES) base[tid] = (uint32_t)offs[(size_t)(NUM_CLASSES - 1 - tid) * nb + blockIdx.x];
     __syncthreads();
     const int64_t v = (int64_t)blockIdx.x * RL_THREADS + tid;
     const int cls = v < n ? degree_class((int64_t)rowptr[v + 1] - (int64_t)rowptr[v]) : -1;
@@ -171,42 +147,73 @@ __global__ void new_degree_kernel(const Off* __restrict__ rowptr, const int32_t*
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
+constexpr int REMAP_UNROLL = 4;  // arcs per lane in flight
+
 // Arcs of the original rows [v0, v1), renamed, into their new rows inv[v].
-// One warp per 32 consecutive rows: the lanes read the 32 rows' bounds and
-// targets at once, then the warp copies row after row.  Rows that become
-// CHUNK rows (inv[v] < row_warp) are left to remap_hub_chunks_kernel.  A
-// column entry outside [0, n) is counted in *bad and stored as 0 (the caller
-// rejects the graph).
+// One warp per 32 consecutive rows.  The lanes scan the rows' lengths, then
+// walk the group's arcs together, REMAP_UNROLL arcs per lane at a time: arc t
+// of the group belongs to the first lane whose inclusive prefix exceeds t (a
+// binary search over the lanes).  Rows that become CHUNK rows
+// (inv[v] < row_warp) count as empty here and are left to
+// remap_hub_chunks_kernel, so every other row holds at most 2048 arcs and a
+// group at most 2^16.  A column entry outside [0, n) is counted in *bad and
+// stored as 0 (the caller rejects the graph).
 template <typename Off>
 __global__ void remap_src_rows_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
                                       const int32_t* __restrict__ inv, const int64_t* __restrict__ rowptr_new,
-                                      int64_t v0, int64_t v1, int64_t n, int64_t row_warp, int32_t* col_new,
-                                      unsigned long long* bad) {
+                                      int64_t v0, int64_t v1, int64_t n, int64_t row_warp,
+                                      int32_t* __restrict__ col_new, unsigned long long* bad) {
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     const int lane = threadIdx.x & 31;
     const int64_t groups = (v1 - v0 + 31) / 32;
     unsigned long long nb = 0;
     for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; gi < groups; gi += warps) {
         const int64_t v = v0 + gi * 32 + lane;
-        int64_t a = 0, b = 0, o = 0;
+        int64_t a = 0, o = 0;
+        int len = 0;
         if (v < v1) {
             const int64_t u = inv[v];
             if (u >= row_warp) {
                 a = rowptr[v];
-                b = rowptr[v + 1];
+                len = (int)((int64_t)rowptr[v + 1] - a);
                 o = rowptr_new[u];
             }
         }
-        for (int q = 0; q < 32; ++q) {
-            const int64_t aq = __shfl_sync(FULL_MASK, a, q), bq = __shfl_sync(FULL_MASK, b, q);
-            const int64_t oq = __shfl_sync(FULL_MASK, o, q);
-            for (int64_t j = aq + lane; j < bq; j += 32) {
-                int32_t x = col[j];
-                if (x < 0 || (int64_t)x >= n) {
-                    ++nb;
-                    x = 0;
+        int pre = len;  // inclusive prefix over the lanes
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, pre, off);
+            if (lane >= off) pre += y;
+        }
+        const int total = __shfl_sync(FULL_MASK, pre, 31);
+        // arc t of this lane's row sits at src_base + t and goes to dst_base + t
+        const int64_t src_base = a - (pre - len), dst_base = o - (pre - len);
+        for (int t0 = 0; t0 < total; t0 += 32 * REMAP_UNROLL) {
+            int32_t x[REMAP_UNROLL];
+            int64_t dst[REMAP_UNROLL];
+#pragma unroll
+            for (int k = 0; k < REMAP_UNROLL; ++k) {
+                const int t = t0 + k * 32 + lane;
+                int q = 0;
+#pragma unroll
+                for (int s = 16; s; s >>= 1)
+                    if (__shfl_sync(FULL_MASK, pre, q + s - 1) <= t) q += s;
+                const int64_t sb = __shfl_sync(FULL_MASK, src_base, q), db = __shfl_sync(FULL_MASK, dst_base, q);
+                x[k] = 0;
+                dst[k] = -1;
+                if (t < total) {
+                    x[k] = col[sb + t];
+                    dst[k] = db + t;
                 }
-                col_new[oq + (j - aq)] = inv[x];
+            }
+#pragma unroll
+            for (int k = 0; k < REMAP_UNROLL; ++k) {
+                if (dst[k] < 0) continue;
+                int32_t xv = x[k];
+                if (xv < 0 || (int64_t)xv >= n) {
+                    ++nb;
+                    xv = 0;
+                }
+                col_new[dst[k]] = inv[xv];
             }
         }
     }
@@ -214,14 +221,16 @@ __global__ void remap_src_rows_kernel(const Off* __restrict__ rowptr, const int3
     if (lane == 0 && nb) atomicAdd(bad, nb);
 }
 
-// CHUNK rows (new ids below row_warp): one warp per chunk of CHUNK_ARCS arcs
-// (the chunk count is chunk_first[row_warp])
+// CHUNK rows (new ids below row_warp) of the original rows [v0, v1): one warp
+// per chunk of CHUNK_ARCS arcs (the chunk count is chunk_first[row_warp]),
+// REMAP_UNROLL arcs per lane in flight
 template <typename Off>
 __global__ void remap_hub_chunks_kernel(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
                                         const int32_t* __restrict__ perm, const int32_t* __restrict__ inv,
                                         const int64_t* __restrict__ rowptr_new, const int32_t* __restrict__ chunk_row,
-                                        const int64_t* __restrict__ chunk_first, int64_t row_warp, int64_t n,
-                                        int32_t* col_new, unsigned long long* bad) {
+                                        const int64_t* __restrict__ chunk_first, int64_t row_warp, int64_t v0,
+                                        int64_t v1, int64_t n, int32_t* __restrict__ col_new,
+                                        unsigned long long* bad) {
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     const int lane = threadIdx.x & 31;
     const int64_t chunks = chunk_first[row_warp];
@@ -229,17 +238,29 @@ __global__ void remap_hub_chunks_kernel(const Off* __restrict__ rowptr, const in
     for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; ch < chunks; ch += warps) {
         const int64_t u = chunk_row[ch];
         const int64_t v = perm[u];
+        if (v < v0 || v >= v1) continue;
         const int64_t a = rowptr[v], b = rowptr[v + 1];
         const int64_t j0 = a + (ch - chunk_first[u]) * (int64_t)CHUNK_ARCS;
         const int64_t j1 = min(j0 + (int64_t)CHUNK_ARCS, b);
         const int64_t o = rowptr_new[u] + (j0 - a);
-        for (int64_t j = j0 + lane; j < j1; j += 32) {
-            int32_t x = col[j];
-            if (x < 0 || (int64_t)x >= n) {
-                ++nb;
-                x = 0;
+        for (int64_t jb = j0; jb < j1; jb += 32 * REMAP_UNROLL) {
+            int32_t x[REMAP_UNROLL];
+#pragma unroll
+            for (int k = 0; k < REMAP_UNROLL; ++k) {
+                const int64_t j = jb + k * 32 + lane;
+                x[k] = j < j1 ? col[j] : 0;
             }
-            col_new[o + (j - j0)] = inv[x];
+#pragma unroll
+            for (int k = 0; k < REMAP_UNROLL; ++k) {
+                const int64_t j = jb + k * 32 + lane;
+                if (j >= j1) continue;
+                int32_t xv = x[k];
+                if (xv < 0 || (int64_t)xv >= n) {
+                    ++nb;
+                    xv = 0;
+                }
+                col_new[o + (j - j0)] = inv[xv];
+            }
         }
     }
     for (int off = 16; off; off >>= 1) nb += __shfl_xor_sync(FULL_MASK, nb, off);
@@ -304,55 +325,100 @@ int degree_class_host(int64_t d) {
     return k + 1;
 }
 
-cudaError_t relabel_by_degree_class(const int64_t* rowptr64, int64_t n, uint32_t* counts_scratch, int nb,
-                                    int32_t* perm, int32_t* inv, uint64_t* class_start_dev, cudaStream_t st) {
-    class_hist_kernel<int64_t><<<nb, RL_THREADS, 0, st>>>(rowptr64, n, nb, counts_scratch);
-    class_scan_kernel<<<1, SCAN_THREADS, 0, st>>>(counts_scratch, nb, class_start_dev);
-    class_scatter_kernel<int64_t><<<nb, RL_THREADS, 0, st>>>(rowptr64, n, nb, counts_scratch, perm, inv);
+int64_t relabel_scratch(int64_t n) {
+    const int64_t cells = (int64_t)NUM_CLASSES * relabel_blocks(n);
+    return 2 * cells + scan_blocks(cells);
+}
+
+cudaError_t relabel_by_degree_class(const int64_t* rowptr64, int64_t n, int64_t* scratch, int32_t* perm, int32_t* inv,
+                                    uint64_t* class_start_dev, cudaStream_t st) {
+    const int nb = relabel_blocks(n);
+    const int64_t cells = (int64_t)NUM_CLASSES * nb;
+    int64_t* counts = scratch;
+    int64_t* offs = scratch + cells;
+    class_hist_kernel<int64_t><<<nb, RL_THREADS, 0, st>>>(rowptr64, n, nb, counts);
+    cudaError_t e = exclusive_scan_i64(counts, cells, offs, scratch + 2 * cells, st);
+    if (e != cudaSuccess) return e;
+    class_start_kernel<<<1, 64, 0, st>>>(offs, nb, class_start_dev);
+    class_scatter_kernel<int64_t><<<nb, RL_THREADS, 0, st>>>(rowptr64, n, nb, offs, perm, inv);
     return cudaGetLastError();
 }
 
 namespace {
 
-// Locality order of the low-degree end (internal ids >= start): the key of
-// each vertex is its degree class (in the class order) and its anchor, the
-// smallest internal id among its neighbours (the neighbour whose row the SpMV
-// reaches first; n if none); val is its internal id so far.  Column ids
-// outside [0, n) are skipped here and refused by the remap that follows.
-__global__ void anchor_key_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                  const int32_t* __restrict__ perm, const int32_t* __restrict__ inv, int64_t n,
-                                  int64_t start, uint64_t* hi, uint32_t* lo, int32_t* val) {
+// Locality keys of the low-degree end (internal ids u >= start, rows of at
+// most 16 arcs) of the graph in degree-class order (rowptr1/col1, internal
+// ids), at index u - start.  The sort key is the row's degree class (in the
+// class order) and its anchor, the smallest internal id among its neighbours
+// (the neighbour whose row the SpMV reaches first; n if none): packed into
+// lo as class_rank << abits | anchor when that fits 32 bits, else the anchor
+// in lo and the class in the low byte of hi.  hi carries the row's degree
+// (bits 8-12) and original id (bits 13-43), val its class-order id u.
+__global__ void tail_keys_kernel(const int64_t* __restrict__ rowptr1, const int32_t* __restrict__ col1,
+                                 const int32_t* __restrict__ perm, int64_t n, int64_t start, int abits,
+                                 uint64_t* __restrict__ hi, uint32_t* __restrict__ lo, int32_t* __restrict__ val) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n - start; i += stride) {
-        const int64_t u = start + i;
-        const int32_t v = perm[u];
-        const int64_t a = rowptr[v], b = rowptr[v + 1];
+        const int64_t a = rowptr1[start + i], b = rowptr1[start + i + 1];
         uint32_t m = (uint32_t)n;
-        for (int64_t j = a; j < b; ++j) {
-            const int32_t c = col[j];
-            if (c >= 0 && (int64_t)c < n) m = min(m, (uint32_t)inv[c]);
-        }
-        hi[i] = (uint64_t)(NUM_CLASSES - 1 - degree_class(b - a));
-        lo[i] = m;
-        val[i] = (int32_t)u;
+        for (int64_t j = a; j < b; ++j) m = min(m, (uint32_t)col1[j]);
+        const int cls = degree_class(b - a);  // 0..5
+        hi[i] = (uint64_t)(NUM_CLASSES - 1 - cls) | (uint64_t)(b - a) << 8 | (uint64_t)(uint32_t)perm[start + i] << 13;
+        lo[i] = abits > 0 ? (uint32_t)(5 - cls) << abits | m : m;
+        val[i] = (int32_t)(start + i);
     }
 }
 
-// perm_new[start + i] = perm[sorted[i]], and inv of those vertices
-__global__ void locality_compose_kernel(const int32_t* __restrict__ sorted, int64_t n, int64_t start,
-                                        const int32_t* __restrict__ perm, int32_t* perm_tail) {
+// The row at sorted position i (class-order id u1 = sorted[i], degree and
+// original id v in hi_sorted[i]) becomes start + i: sigma[u1 - start] =
+// start + i, v goes to perm_tail[i] (copied into perm[start..] afterwards)
+// and inv, the degree to deg[start + i]; the head rows' degrees and
+// deg[n] = 0 complete deg
+__global__ void tail_order_kernel(const int32_t* __restrict__ sorted, const uint64_t* __restrict__ hi_sorted,
+                                  const int64_t* __restrict__ rowptr1, int64_t n, int64_t start,
+                                  int32_t* __restrict__ sigma, int32_t* __restrict__ perm_tail,
+                                  int32_t* __restrict__ inv, int64_t* __restrict__ deg) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n - start; i += stride)
-        perm_tail[i] = perm[sorted[i]];
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t u = t0; u < start; u += stride) deg[u] = rowptr1[u + 1] - rowptr1[u];  // head rows keep theirs
+    if (t0 == 0) deg[n] = 0;
+    for (int64_t i = t0; i < n - start; i += stride) {
+        const int32_t u1 = sorted[i];
+        const uint64_t h = hi_sorted[i];
+        const int32_t v = (int32_t)(h >> 13);
+        sigma[u1 - start] = (int32_t)(start + i);
+        perm_tail[i] = v;
+        inv[v] = (int32_t)(start + i);
+        deg[start + i] = (int64_t)((h >> 8) & 31u);
+    }
 }
 
-__global__ void locality_install_kernel(const int32_t* __restrict__ perm_tail, int64_t n, int64_t start, int32_t* perm,
-                                        int32_t* inv) {
+// every arc target u >= start renamed to sigma[u - start]: in place in the
+// head rows (arcs below rowptr1[start]), into tail_copy for the tail rows
+__global__ void tail_rename_kernel(const int64_t* __restrict__ rowptr1, int64_t nnz, int64_t start,
+                                   const int32_t* __restrict__ sigma, int32_t* __restrict__ col1,
+                                   int32_t* __restrict__ tail_copy) {
+    const int64_t head = rowptr1[start];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += stride) {
+        const int32_t x = col1[j];
+        const int32_t y = x >= start ? sigma[x - start] : x;
+        if (j >= head) tail_copy[j - head] = y;
+        else if (y != x) col1[j] = y;
+    }
+}
+
+// tail row start + i of the final order is class-order row sorted[i]
+__global__ void tail_rows_kernel(const int32_t* __restrict__ sorted, const int64_t* __restrict__ rowptr1,
+                                 const int64_t* __restrict__ rowptr_fin, int64_t n, int64_t start,
+                                 const int32_t* __restrict__ tail_copy, int32_t* __restrict__ col) {
+    const int64_t head = rowptr1[start];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n - start; i += stride) {
-        const int32_t v = perm_tail[i];
-        perm[start + i] = v;
-        inv[v] = (int32_t)(start + i);
+        const int32_t u1 = sorted[i];
+        const int64_t a = rowptr1[u1] - head, len = rowptr1[u1 + 1] - rowptr1[u1];
+        const int64_t o = rowptr_fin[start + i];
+        for (int64_t k = 0; k < len; ++k) col[o + k] = tail_copy[a + k];
     }
 }
 
@@ -362,19 +428,36 @@ __global__ void locality_install_kernel(const int32_t* __restrict__ perm_tail, i
 // already grouped by degree class) within their classes by anchor, ties kept
 // in their current order (a stable sort): the walk values that one hub row
 // gathers from low-degree rows then sit together, so a line fetched from DRAM
-// serves several of its gathers.  perm/inv are updated in place.  rs: radix
-// buffers for n - start entries.  rowptr/col: the input CSR (original ids).
-cudaError_t locality_order(const int64_t* rowptr, const int32_t* col, int64_t n, int64_t start, int32_t* perm,
-                           int32_t* inv, RadixBuffers& rs, cudaStream_t st) {
+// serves several of its gathers.  Works on the graph already renamed into
+// degree-class order (rowptr1, col1, perm, inv) and moves it to the new
+// order: perm/inv updated, col1 rewritten in place, the new offsets in
+// rowptr_fin (n + 1).  deg: n + 1 int64 of scratch; tail_copy: rowptr1[n] - rowptr1[start] entries; sums: scan
+// scratch for n + 1; rs: radix buffers for n - start entries.
+cudaError_t locality_order(int64_t n, int64_t nnz, int64_t start, const int64_t* rowptr1, int32_t* col1,
+                           int32_t* perm, int32_t* inv, int64_t* deg, int64_t* rowptr_fin, int32_t* tail_copy,
+                           int64_t* sums, RadixBuffers& rs, cudaStream_t st) {
     const int64_t m = n - start;
     if (m <= 1) return cudaSuccess;
-    anchor_key_kernel<<<grid_for(m, 256), 256, 0, st>>>(rowptr, col, perm, inv, n, start, rs.hi[0], rs.lo[0],
-                                                         rs.val[0]);
+    int abits = 1;  // bits of an anchor (<= n)
+    while (abits < 31 && ((int64_t)1 << abits) <= n) ++abits;
+    const bool packed = abits + 3 <= 32;  // class rank (0..5) above the anchor in lo
+    tail_keys_kernel<<<grid_for(m, 256), 256, 0, st>>>(rowptr1, col1, perm, n, start, packed ? abits : 0, rs.hi[0],
+                                                       rs.lo[0], rs.val[0]);
     int cur = 0;
-    cudaError_t e = radix_sort_passes(rs, m, 0, 4, cur, st);  // the anchor (4 digits), then the class
+    cudaError_t e = packed ? radix_sort_passes(rs, m, 0, (abits + 3 + 7) / 8 - 1, cur, st)
+                           : radix_sort_passes(rs, m, 0, 4, cur, st);  // the anchor (4 digits), then the class
     if (e != cudaSuccess) return e;
-    locality_compose_kernel<<<grid_for(m, 256), 256, 0, st>>>(rs.val[cur], n, start, perm, rs.val[1 - cur]);
-    locality_install_kernel<<<grid_for(m, 256), 256, 0, st>>>(rs.val[1 - cur], n, start, perm, inv);
+    const int32_t* sorted = rs.val[cur];
+    int32_t* sigma = (int32_t*)rs.lo[1 - cur];
+    int32_t* perm_tail = rs.val[1 - cur];
+    tail_order_kernel<<<grid_for(m, 256), 256, 0, st>>>(sorted, rs.hi[cur], rowptr1, n, start, sigma, perm_tail, inv,
+                                                        deg);
+    if ((e = cudaMemcpyAsync(perm + start, perm_tail, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToDevice, st)) !=
+            cudaSuccess ||
+        (e = exclusive_scan_i64(deg, n + 1, rowptr_fin, sums, st)) != cudaSuccess)
+        return e;
+    tail_rename_kernel<<<grid_for(nnz, 256, 152 * 32), 256, 0, st>>>(rowptr1, nnz, start, sigma, col1, tail_copy);
+    tail_rows_kernel<<<grid_for(m, 256), 256, 0, st>>>(sorted, rowptr1, rowptr_fin, n, start, tail_copy, col1);
     return cudaGetLastError();
 }
 
@@ -406,11 +489,11 @@ cudaError_t remap_src_rows(const int64_t* rowptr64, const int32_t* col, const in
 
 cudaError_t remap_hub_chunks(const int64_t* rowptr64, const int32_t* col, const int32_t* perm, const int32_t* inv,
                              const int64_t* rowptr_new, const int32_t* chunk_row, const int64_t* chunk_first,
-                             int64_t row_warp, int64_t chunks_cap, int64_t n, int32_t* col_new,
-                             unsigned long long* bad, cudaStream_t st) {
+                             int64_t row_warp, int64_t chunks_cap, int64_t v0, int64_t v1, int64_t n,
+                             int32_t* col_new, unsigned long long* bad, cudaStream_t st) {
     if (row_warp <= 0) return cudaSuccess;
     remap_hub_chunks_kernel<int64_t><<<grid_for(chunks_cap * 32, 256, 152 * 32), 256, 0, st>>>(
-        rowptr64, col, perm, inv, rowptr_new, chunk_row, chunk_first, row_warp, n, col_new, bad);
+        rowptr64, col, perm, inv, rowptr_new, chunk_row, chunk_first, row_warp, v0, v1, n, col_new, bad);
     return cudaGetLastError();
 }
 
