@@ -86,15 +86,23 @@ __global__ void na_reset(NoAllocScratch* S, long long k) {
 }
 
 // histogram of digit `pass` (bits 95-16*pass .. 80-16*pass) of the keys that
-// share the digits chosen so far
+// share the digits chosen so far; the lanes of a warp that hit the same bin
+// (bounds of one magnitude share their top digits) add once
 __global__ void na_hist(NoAllocScratch* S, const double* __restrict__ lower, long long n, int pass) {
     if (S->done) return;
     const int shift = 80 - 16 * pass;
     const u128 pre = ((u128)S->pre_hi << 32) | S->pre_lo;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-        const u128 key = key_of(lower[v], (int)v);
-        if (pass == 0 || (key >> (shift + 16)) == (pre >> (shift + 16)))
-            atomicAdd(&S->hist[(unsigned)(key >> shift) & 0xffffu], 1u);
+    const int lane = threadIdx.x & 31;
+    // base is the same for every thread of a block, so the loop is warp-uniform
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+        const long long v = base + threadIdx.x;
+        unsigned bin = 0x10000u;  // none
+        if (v < n) {
+            const u128 key = key_of(lower[v], (int)v);
+            if (pass == 0 || (key >> (shift + 16)) == (pre >> (shift + 16))) bin = (unsigned)(key >> shift) & 0xffffu;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (bin < 0x10000u && lane == __ffs(peers) - 1) atomicAdd(&S->hist[bin], (unsigned)__popc(peers));
     }
 }
 

@@ -202,6 +202,22 @@ def test_large_host_csr_is_copied_in_slices_and_matches_device_input():
     np.testing.assert_array_equal(a["u"], b["u"])
 
 
+def test_host_slices_hub_chunks_and_anchor_order_give_the_same_bits():
+    # a host CSR is renamed slice by slice as it arrives, hub rows (more than
+    # 2048 arcs, chunk by chunk) with the slice that holds them, and the anchor
+    # order then permutes the low-degree rows: host or device input, anchor
+    # order on or off, the results are the same bits
+    g = gg.chung_lu(1 << 19, 16.0, 2.1, seed=63)
+    assert g.nnz >= 1 << 22 and g.deg_max() > 2048
+    runs = [run_gpu(g, 0.0, 200, 1e-9, keep_history=False, on_device=dev, locality=loc)
+            for loc in (1, -1) for dev in (False, True)]
+    for b in runs[1:]:
+        assert b["info"].r == runs[0]["info"].r
+        np.testing.assert_array_equal(b["ranking"], runs[0]["ranking"])
+        np.testing.assert_array_equal(b["l"], runs[0]["l"])
+        np.testing.assert_array_equal(b["u"], runs[0]["u"])
+
+
 def test_large_host_csr_with_a_bad_column_entry_in_a_late_slice_is_rejected():
     g = gg.rmat(18, 16, seed=62)
     col = g.col.copy()
