@@ -290,18 +290,21 @@ __device__ __noinline__ XAcc xacc_add_slow(XAcc a, int e, uint32_t m0, uint32_t 
     return a;
 }
 
+// The fast path takes a normal term within XF binades below E; a zero term
+// (padding) adds nothing; the rest (rescale, truncation, subnormals, whose
+// exponent counts as 1 and whose mantissa has no implicit bit) goes through
+// xacc_add_slow, which gives the fast path's result wherever both apply.
 __device__ __forceinline__ void xacc_add(XAcc& a, double x) {
     const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-    const int eb = (int)(hi >> 20);
-    const int e = (hi | lo) ? max(eb, 1) : a.E;  // a zero term (padding) adds nothing on the fast path
-    const uint32_t m1 = (hi & 0xFFFFFu) | (eb ? 0x100000u : 0u);
-    const int d = a.E - e;
-    if ((unsigned)d > (unsigned)XF) {
-        a = xacc_add_slow(a, e, lo, m1);
-        return;
+    const uint32_t eb = hi >> 20;
+    const uint32_t d = (uint32_t)(a.E - (int)eb);
+    if (d <= (uint32_t)XF && eb != 0u) {
+        const uint32_t m1 = (hi & 0xFFFFFu) | 0x100000u;
+        const uint32_t sh = (uint32_t)XF - d;
+        add96(a, lo << sh, __funnelshift_l(lo, m1, sh), __funnelshift_l(m1, 0u, sh));
+    } else if ((hi | lo) != 0u) {
+        a = xacc_add_slow(a, eb ? (int)eb : 1, lo, (hi & 0xFFFFFu) | (eb ? 0x100000u : 0u));
     }
-    const uint32_t sh = (uint32_t)(XF - d);
-    add96(a, lo << sh, __funnelshift_l(lo, m1, sh), __funnelshift_l(m1, 0u, sh));
 }
 
 // a += b (any exponents)
