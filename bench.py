@@ -15,7 +15,10 @@ headline is the FP64 path (the paper's precision); the FP32-certified path is
 timed beside it on the same graph ("fp32cert", with the speedup and whether
 both certified the same ranking), and the FP32-certified bounds' per-node
 deviation from the FP64 oracle at the same r is reported against the
-rounding widening ("fp32cert_deviation_vs_oracle").
+rounding widening ("fp32cert_deviation_vs_oracle").  "cpu_baseline" times
+the CPU oracle on all host cores (complete rankings), with a single-threaded
+sample of its first iterations ("single_thread") and the host's nproc and CPU
+model ("host").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--precision fp64|fp32cert] [--no-compare]
@@ -37,6 +40,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -263,6 +267,17 @@ def cpu_baseline(g, wl, seconds):
     import oracle
 
     s = oracle.Session(g.rowptr, g.col, True)
+    # the same oracle on one thread, on a bounded sample (the first
+    # iterations of Algorithm 1), before the multi-threaded rankings so that
+    # the session ends on a complete ranking
+    threads = oracle.max_threads()
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    r1 = s.iterations(wl["alpha"], wl["k"], wl["eps"], SINGLE_THREAD_ITERS)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(threads)
+    single = {"value": r1 * g.nnz / dt1 / 1e9, "unit": "GTEPS", "threads": 1,
+              "sample": f"the first {r1} iterations of Algorithm 1 on the full {wl['graph']} graph; {dt1:.1f} s"}
     runs, arcs = 0, 0
     t0 = time.perf_counter()
     while True:
@@ -272,9 +287,23 @@ def cpu_baseline(g, wl, seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": arcs / dt / 1e9, "unit": "GTEPS", "cores": oracle.max_threads(), "kind": "oracle",
+    return {"value": arcs / dt / 1e9, "unit": "GTEPS", "cores": threads, "kind": "oracle",
             "sample": f"{runs} complete certified ranking(s) (r = {r}) of the full {wl['graph']} graph; "
-                      f"{dt:.1f} s"}, s
+                      f"{dt:.1f} s", "single_thread": single, "host": host_cpu()}, s
+
+
+def host_cpu():
+    """nproc and the CPU model of the host the oracle ran on."""
+    model = platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
 
 
 def run_serving(batches, workers=2, slots=8, precision="fp64"):
@@ -371,6 +400,8 @@ def serve_once(g, D, batches, rate, workers, slots, torch, precision="fp64"):
 # graphs above this many arcs are sampled by the reference arm: each step runs
 # the first --cpu-iters iterations of Algorithm 1 instead of a whole ranking
 REFERENCE_SAMPLE_ARCS = 1 << 30
+# iterations of the single-threaded oracle sample beside the cpu_baseline
+SINGLE_THREAD_ITERS = 2
 
 
 def run_reference(args):
@@ -418,7 +449,7 @@ def run_reference(args):
             "config": {"workload": f"{args.workload}-top{wl['k']}-fp64", "graph": wl["desc"], "n": g.n,
                        "nnz": g.nnz, "k": wl["k"], "eps": wl["eps"]},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_cpu()},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
