@@ -28,15 +28,15 @@ def _opts(**kw):
     return K.katz_default_opts(**base)
 
 
-@pytest.mark.parametrize("on_device", [True, False])
-def test_inbound_static_matches_oracle_on_the_reverse_graph(on_device):
+@pytest.mark.parametrize("on_device,locality", [(True, 0), (False, 0), (True, 1), (False, 1)])
+def test_inbound_static_matches_oracle_on_the_reverse_graph(on_device, locality):
     g = gg.orient(gg.rmat(14, 16, seed=71), seed=3)
     rev = gg.reverse(g)
     assert not np.array_equal(rev.col, g.col)
     k, eps = 200, 1e-9
     ref = oracle.katz_static(rev.rowptr, rev.col, 0.0, k, eps, undirected=False, r_max=256)
     conv = _dev if on_device else np.ascontiguousarray
-    h = K.Katz(conv(g.rowptr), conv(g.col), _opts())
+    h = K.Katz(conv(g.rowptr), conv(g.col), _opts(locality=locality))  # 1: anchor order of the reverse graph
     info = h.rank(0.0, k, eps)
     assert info.r == ref["r"] and info.converged == 1
     lo, up, _ = h.bounds()

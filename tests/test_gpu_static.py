@@ -232,6 +232,17 @@ def test_large_host_csr_with_a_bad_column_entry_in_a_late_slice_is_rejected():
     assert e.value.name == "KATZ_EINVAL"
 
 
+def test_directed_graph_with_anchor_order_matches_the_oracle():
+    # the anchor order on a directed graph (rows ordered by out-degree class,
+    # anchors among out-neighbours): oracle parity and the bits of the plain order
+    g = gg.orient(gg.chung_lu(1 << 15, 16.0, 2.1, seed=97), seed=98)
+    got, _ = check_parity(g, 0.0, 100, 1e-9, undirected=False, locality=1)
+    plain = run_gpu(g, 0.0, 100, 1e-9, undirected=False, locality=-1)
+    np.testing.assert_array_equal(got["ranking"], plain["ranking"])
+    np.testing.assert_array_equal(got["l"], plain["l"])
+    np.testing.assert_array_equal(got["u"], plain["u"])
+
+
 def test_l2_fetch_option_keeps_the_bits_and_restores_the_limit():
     """katz_opts.l2_fetch_bytes changes the context's maximum L2 fetch
     granularity only during the call: the ranking and bounds are the same
